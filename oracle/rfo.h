@@ -1,0 +1,97 @@
+/*
+ * rfo — the ORACLE: a plain, slow, FP64 CPU restatement of the discrete
+ * two-phase flow model, the BiCGSTAB + geometric-multigrid stage solver and the
+ * LIMEX step of "A highly scalable numerical framework for reservoir simulation
+ * on UG4 platform" (arXiv 2506.04763).
+ *
+ * This is TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.  It shares no code, header, table
+ * or helper with the CUDA library; the two meet only through the data formats
+ * below, which both sides implement on their own.
+ *
+ * Data formats (natural lexicographic order, x fastest):
+ *   vertex  v = i + nx*(j + ny*k)           cell c = i + (nx-1)*(j + (ny-1)*k)
+ *   state   u[2v+0] = p_w (Pa), u[2v+1] = S_n
+ *   residual F[2v+0] = water equation (kg/s), F[2v+1] = NAPL equation
+ *   stencil block b = (dx+1) + 3(dy+1) [+ 9(dz+1) in 3D]; nb = 9 (2D) or 27 (3D)
+ *   2x2 block entries e: 0=(w,p_w) 1=(w,S_n) 2=(n,p_w) 3=(n,S_n)
+ *   matrix  A[(v*nb + b)*4 + e]   (blocks reaching outside the grid are zero)
+ *   mass    mdiag[2v+0] = d m_w/d S_n, mdiag[2v+1] = d m_n/d S_n  (M is
+ *           vertex-diagonal and its p_w column is zero)
+ */
+#ifndef RFO_H
+#define RFO_H
+#include <stddef.h>
+
+typedef struct {
+  int dim;             /* 2 or 3 */
+  int n[3];            /* vertices per axis (n[2] = 1 in 2D) */
+  double h[3];         /* mesh spacing per axis (m) */
+  double g[3];         /* gravity vector (m/s^2) */
+  double rho_w, rho_n, mu_w, mu_n;
+  double S_wr, S_nr, lambda;       /* Brooks-Corey parameters (uniform) */
+  const double* K;     /* per cell permeability (m^2) */
+  const double* phi;   /* per cell porosity */
+  const double* pd;    /* per cell entry pressure (Pa) */
+  const unsigned char* dir;  /* per vertex: 1 = Dirichlet p_w (may be NULL) */
+  const double* pw_dir;      /* per vertex Dirichlet value (used where dir=1) */
+  const double* q_in;        /* per vertex [2] mass source kg/s (may be NULL) */
+} rfo_model;
+
+/* ---- constitutive laws (Brooks-Corey; interface condition) ---- */
+void rfo_brooks_corey(const rfo_model* m, double Se, double out[6]);
+/* out = {krw, dkrw/dSe, krn, dkrn/dSe, J, dJ/dSe} */
+void rfo_shat(const rfo_model* m, double Se, double pd_cell, double pdmin, double out[2]);
+/* out = {S_e hat, d S_e hat / d S_e} */
+
+/* ---- spatial discretisation ---- */
+void rfo_pdmin(const rfo_model* m, double* pdmin);   /* [nv] */
+void rfo_phiv(const rfo_model* m, double* phiv);     /* [nv] */
+void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, double* mdiag);
+/* J, mdiag may be NULL (residual only) */
+
+/* ---- algebra on the stencil format ---- */
+void rfo_make_A(int nv, int nb, const double* J, const double* mdiag, double shift, double* A);
+void rfo_spmv(int dim, const int n[3], const double* A, const double* x, double* y);
+void rfo_residual(int dim, const int n[3], const double* A, const double* b, const double* x, double* r);
+void rfo_jacobi(int dim, const int n[3], const double* A, const double* b, const double* xin,
+                double* xout, double omega);
+void rfo_gs_sweep(int dim, const int n[3], const double* A, const double* b, double* x, int forward);
+void rfo_restrict(int dim, const int nf[3], const unsigned char* dmf, const int nc[3],
+                  const unsigned char* dmc, const double* rf, double* bc);
+void rfo_prolong_add(int dim, const int nf[3], const unsigned char* dmf, const int nc[3],
+                     const unsigned char* dmc, const double* xc, double* xf);
+void rfo_galerkin(int dim, const int nf[3], const unsigned char* dmf, const double* Af,
+                  const int nc[3], const unsigned char* dmc, double* Ac);
+int  rfo_lu_factor(int N, double* LU, int* piv);
+void rfo_lu_solve(int N, const double* LU, const int* piv, double* x);
+
+/* ---- geometric multigrid ---- */
+typedef struct rfo_gmg rfo_gmg;
+enum { RFO_JACOBI = 0, RFO_GS8 = 1 };
+rfo_gmg* rfo_gmg_create(int dim, const int n[3], const double* A0, const unsigned char* dmask,
+                        int nlevels, int smoother, int nu1, int nu2, double omega);
+void rfo_gmg_free(rfo_gmg* g);
+int  rfo_gmg_nlevels(const rfo_gmg* g);
+void rfo_gmg_level_dims(const rfo_gmg* g, int level, int n[3]);
+void rfo_gmg_level_matrix(const rfo_gmg* g, int level, double* A);
+void rfo_gmg_vcycle(rfo_gmg* g, const double* b, double* x);
+
+/* ---- BiCGSTAB, right-preconditioned by one V-cycle (g may be NULL) ---- */
+int rfo_bicgstab(int dim, const int n[3], const double* A, rfo_gmg* g, const double* b, double* x,
+                 double rtol, int maxit, int* iters, double* relres);
+
+/* ---- LIMEX ---- */
+void rfo_extrapolate(int kappa, const int* nseq, int len, const double* T1, double* Tkk, double* Tkk1);
+double rfo_h1_seminorm2(int dim, const int n[3], const double* h, const double* q, int stride);
+double rfo_lumped_l2norm2(int dim, const int n[3], const double* h, const double* q, int stride);
+typedef struct {
+  int kappa; double tol, rho, fac_min, fac_max;
+  int nlevels, smoother, nu1, nu2; double omega;
+  double rtol; int maxit;
+} rfo_limex_opts;
+typedef struct { double eps, H_new; int accepted, solves, iterations; } rfo_limex_info;
+int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_limex_opts* o,
+                   double* u_out, rfo_limex_info* info);
+
+#endif

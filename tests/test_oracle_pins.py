@@ -1,0 +1,464 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test fixes one part of the oracle by something other than the oracle's
+own formula: a value printed in the paper, a closed form, an invariant, a
+library routine on a dense matrix, or brute force.  CPU only.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2506_04763_gb300 import inputs as I
+from tests import _helpers as H
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split()
+            out[k] = v
+    return out
+
+
+def _poisson_problem(dim, nv, K=1e-10):
+    """Constant K, uniform p_d, S_n = 0, no gravity: the p-block of J is the
+    VCFVM Laplacian with coefficient K rho_w / mu_w."""
+    p = I.random_problem(dim, nv, 3, gravity=False)
+    p["K"][:] = K
+    p["pd"][:] = 755.0
+    p["u0"][0::2] = I.P_TOP
+    p["u0"][1::2] = 0.0
+    return p
+
+
+# ---------------------------------------------------------------- P9 / grid
+def test_dof_counts_match_paper():
+    """Sec. 5 scaling tables: DoF = 2 x (elements+1 per axis) vertices."""
+    with open(os.path.join(GOLDEN, "dof_counts.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for mesh, dof in rows:
+        el = [int(t) for t in mesh.split("x")]
+        nv = int(np.prod([e + 1 for e in el]))
+        assert 2 * nv == int(dof)
+
+
+# ---------------------------------------------------------------- laws
+def test_brooks_corey_special_values(oracle):
+    m = oracle.Model(I.config1())
+    kr = oracle.brooks_corey(m, 1.0)
+    assert kr[0] == 1.0 and kr[2] == 0.0 and kr[4] == 1.0     # krw(1)=1, krn(1)=0, J(1)=1
+    kr = oracle.brooks_corey(m, 0.0)
+    assert kr[0] == 0.0 and kr[2] == 1.0                        # krw(0)=0, krn(0)=1
+    # clamps outside [0,1] for k_r, linear continuation of J
+    for s in (-0.3, 1.4):
+        kr = oracle.brooks_corey(m, s)
+        assert kr[1] == 0.0 and kr[3] == 0.0
+    assert oracle.brooks_corey(m, 1.4)[4] == pytest.approx(1.0 - 0.5 * 0.4)
+
+
+def test_brooks_corey_lambda2_path_equals_general_pow_path(oracle):
+    """The sqrt/integer-power special case for lambda=2 agrees with the general
+    pow() path evaluated at lambda = 2 + 1e-12."""
+    p = I.config1()
+    m2 = oracle.Model(p)
+    p2 = dict(p)
+    p2["lam"] = 2.0 + 1e-12
+    mg = oracle.Model(p2)
+    for s in np.linspace(0.005, 1.2, 41):
+        a = oracle.brooks_corey(m2, s)
+        b = oracle.brooks_corey(mg, s)
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12)
+
+
+def test_brooks_corey_derivatives_by_finite_differences(oracle):
+    m = oracle.Model(I.config1())
+    for s in np.linspace(0.02, 0.98, 25):
+        d = 1e-6
+        f0 = oracle.brooks_corey(m, s)
+        fp = oracle.brooks_corey(m, s + d)
+        fm = oracle.brooks_corey(m, s - d)
+        for val, der in ((0, 1), (2, 3), (4, 5)):
+            fd = (fp[val] - fm[val]) / (2 * d)
+            assert fd == pytest.approx(f0[der], rel=1e-6, abs=1e-9)
+    # J is C^1 at the continuation points 0.01 and 1
+    for s in (0.01, 1.0):
+        lo = oracle.brooks_corey(m, s - 1e-9)
+        hi = oracle.brooks_corey(m, s + 1e-9)
+        assert abs(lo[4] - hi[4]) <= 1.01 * 2e-9 * abs(hi[5])   # no jump in J
+        assert lo[5] == pytest.approx(hi[5], rel=1e-5)           # no jump in J'
+
+
+def test_case4_threshold_saturation(oracle):
+    """Paper, Case 4: S_w* = 0.7778 at the layer-2/layer-3 interface.  The
+    oracle's S hat (Eq. hSw) must switch from the capped branch (S_e hat = 1,
+    NAPL blocked) to the open branch exactly at that wetting saturation."""
+    g = _read_golden("case4_threshold.txt")
+    p = I.config1()
+    p["S_wr"], p["S_nr"], p["lam"] = float(g["S_wr"]), float(g["S_nr"]), float(g["lambda"])
+    m = oracle.Model(p)
+    pd2 = float(g["pd_coef"]) * float(g["K2"]) ** float(g["pd_exp"])
+    pd3 = float(g["pd_coef"]) * float(g["K3"]) ** float(g["pd_exp"])
+    den = 1.0 - p["S_wr"] - p["S_nr"]
+
+    def capped(Sw):
+        return oracle.shat(m, (Sw - p["S_wr"]) / den, pd3, pd2)[0] >= 1.0
+
+    lo, hi = 0.3, 0.9 - 1e-9   # open at lo, capped at hi
+    assert not capped(lo) and capped(hi)
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if capped(mid):
+            hi = mid
+        else:
+            lo = mid
+    assert round(hi, int(g["digits"])) == float(g["S_w_star"])
+    # continuity of S hat at the cap
+    s_star = (hi - p["S_wr"]) / den
+    assert oracle.shat(m, s_star - 1e-12, pd3, pd2)[0] == pytest.approx(1.0, abs=1e-9)
+
+
+def test_shat_branches(oracle):
+    m = oracle.Model(I.config1())
+    assert list(oracle.shat(m, 0.4, 755.0, 755.0)) == [0.4, 1.0]      # case 1
+    r2 = (1163.0 / 755.0) ** 2
+    out = oracle.shat(m, 0.3, 1163.0, 755.0)                           # case 3
+    assert out[0] == pytest.approx(r2 * 0.3) and out[1] == pytest.approx(r2)
+    assert list(oracle.shat(m, 0.9, 1163.0, 755.0)) == [1.0, 0.0]      # case 2
+    # sand/lens threshold of the synthetic workloads: S_e* = (755/1163)^2
+    se_star = (755.0 / 1163.0) ** 2
+    assert oracle.shat(m, se_star * (1 - 1e-9), 1163.0, 755.0)[0] < 1.0
+    assert oracle.shat(m, se_star * (1 + 1e-9), 1163.0, 755.0)[0] == 1.0
+
+
+# ---------------------------------------------------------------- P1 stencil
+@pytest.mark.parametrize("dim,nv,expect", [
+    (2, (9, 9), {(0, 0, 0): -3.0, (1, 0, 0): 0.5, (0, 1, 0): 0.5, (1, 1, 0): 0.25}),
+    (3, (9, 9, 9), {(0, 0, 0): -27 / 8, (1, 0, 0): 3 / 16, (1, 1, 0): 5 / 32, (1, 1, 1): 3 / 64}),
+])
+def test_p1_laplacian_stencil_closed_form(oracle, dim, nv, expect):
+    """Constant K, S_n = 0, g = 0: the (w, p_w) entries of J are the VCFVM
+    Laplacian stencil of bilinear/trilinear elements with midpoint SCVF
+    quadrature: 2D centre -3, face 1/2, corner 1/4; 3D (times h) centre
+    -27/8, face 3/16, edge 5/32, corner 3/64 (per unit K rho_w/mu_w)."""
+    K = 1e-10
+    p = _poisson_problem(dim, nv, K)
+    p["dir"][:] = 0
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    scale = K * p["rho_w"] / p["mu_w"] * (p["h"][0] if dim == 3 else 1.0)
+    offs = H.offsets(dim)
+    c = tuple(t // 2 for t in m.n)
+    v = c[0] + m.n[0] * (c[1] + m.n[1] * c[2])
+    for b, off in enumerate(offs):
+        key = tuple(sorted(np.abs(off), reverse=True))
+        key = (key[0], key[1], key[2] if dim == 3 else 0) if dim == 3 else (key[0], key[1], 0)
+        assert J[v, b, 0] / scale == pytest.approx(expect[key], rel=1e-12, abs=1e-14)
+        assert J[v, b, 2] == 0.0          # k_rn(S_e = 1) = 0
+    # symmetric, zero row and column sums
+    D = H.stencil_to_dense(dim, m.n, J)[0::2, 0::2]
+    np.testing.assert_allclose(D, D.T, atol=1e-12 * np.abs(D).max())
+    assert np.abs(D.sum(axis=1)).max() <= 1e-13 * np.abs(D).max()
+    assert np.abs(F).max() == 0.0
+
+
+# ---------------------------------------------------------------- P3 exact J
+@pytest.mark.parametrize("dim,nv,seed", [(2, (7, 6), 11), (3, (5, 4, 5), 12)])
+def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed):
+    """J = F_u exactly (Sec. 4): central differences of the oracle's own F,
+    entry by entry; columns where one-sided differences disagree (a kink or an
+    upwind switch inside the step) are skipped."""
+    p = I.random_problem(dim, nv, seed)
+    m = oracle.Model(p)
+    u = p["u0"].copy()
+    F0, J, md = oracle.assemble(m, u)
+    Jd = H.stencil_to_dense(dim, m.n, J)
+    checked = skipped = 0
+    for col in range(2 * m.nv):
+        d = (1e-7 * 1e5) if col % 2 == 0 else 1e-7
+        up, um = u.copy(), u.copy()
+        up[col] += d
+        um[col] -= d
+        Fp = oracle.assemble(m, up, jacobian=False)[0]
+        Fm = oracle.assemble(m, um, jacobian=False)[0]
+        fwd, bwd = (Fp - F0) / d, (F0 - Fm) / d
+        cen = (Fp - Fm) / (2 * d)
+        scale = np.abs(Jd[:, col]).max() + 1e-300
+        if np.abs(fwd - bwd).max() > 1e-3 * scale:
+            skipped += 1
+            continue
+        checked += 1
+        assert np.abs(cen - Jd[:, col]).max() <= 1e-6 * scale
+    assert checked > 0.9 * (checked + skipped)
+
+
+# ---------------------------------------------------------------- P4 conservation
+@pytest.mark.parametrize("dim,nv", [(2, (9, 7)), (3, (5, 6, 5))])
+def test_p4_discrete_conservation(oracle, dim, nv):
+    """Without Dirichlet rows: sum_i F_alpha,i = sum_i q_alpha,i (every face
+    flux leaves one control volume and enters its neighbour), and every column
+    of J sums to zero."""
+    p = I.random_problem(dim, nv, 5, stress=True, dirichlet=False)
+    rng = np.random.default_rng(9)
+    p["q_in"] = rng.normal(0, 1e-6, 2 * int(np.prod(p["n"])))
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    p0 = dict(p)
+    p0["q_in"] = None
+    Fnoq = oracle.assemble(oracle.Model(p0), p["u0"], jacobian=False)[0]
+    flux_scale = np.abs(Fnoq).sum()
+    for a in (0, 1):
+        assert abs(F[a::2].sum() - p["q_in"][a::2].sum()) <= 1e-13 * flux_scale
+    D = H.stencil_to_dense(dim, m.n, J)
+    assert np.abs(D.sum(axis=0)).max() <= 1e-13 * np.abs(D).max()
+
+
+# ---------------------------------------------------------------- P5 equilibrium
+@pytest.mark.parametrize("dim,nv", [(2, (17, 17)), (3, (9, 9, 9))])
+def test_p5_hydrostatic_equilibrium(oracle, dim, nv):
+    """Exact hydrostatic p_w with S_n = 0 in heterogeneous K and p_d: F = 0 up
+    to rounding, and a LIMEX step leaves the state unchanged."""
+    p = I.random_problem(dim, nv, 21)
+    n, h = p["n"], p["h"]
+    nvx = int(np.prod(n))
+    v = np.arange(nvx)
+    vert = ((v // n[0]) % n[1]) * h[1] if dim == 2 else (v // (n[0] * n[1])) * h[2]
+    u = np.zeros(2 * nvx)
+    u[0::2] = I.P_TOP + p["rho_w"] * I.GRAV * (1.0 - vert)
+    u[1::2] = 0.0
+    p["u0"] = u
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, u)
+    flux = p["K"].max() * p["rho_w"] ** 2 * I.GRAV / p["mu_w"] * h[0] ** (dim - 1)
+    assert np.abs(F).max() <= 1e-11 * flux
+    u1, info = oracle.limex_step(m, u, 10.0, kappa=3, nlevels=3, rtol=1e-12)
+    assert info["status"] == 0
+    np.testing.assert_allclose(u1[0::2], u[0::2], rtol=1e-12)
+    assert np.abs(u1[1::2]).max() <= 1e-12
+
+
+def test_p5_no_gravity_uniform_saturation_is_stationary(oracle):
+    p = I.random_problem(2, (9, 9), 4, gravity=False)
+    p["pd"][:] = 755.0
+    p["u0"][0::2] = I.P_TOP
+    p["u0"][1::2] = 0.3
+    m = oracle.Model(p)
+    F = oracle.assemble(m, p["u0"], jacobian=False)[0]
+    assert np.abs(F).max() <= 1e-20
+
+
+# ---------------------------------------------------------------- algebra
+def test_spmv_and_make_A_match_dense(oracle):
+    p = I.random_problem(3, (5, 4, 6), 8)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.37)
+    Md = np.zeros((2 * m.nv, 2 * m.nv))
+    for v in range(m.nv):
+        Md[2 * v, 2 * v + 1] = md[v, 0]
+        Md[2 * v + 1, 2 * v + 1] = md[v, 1]
+    Ad = 0.37 * Md - H.stencil_to_dense(3, m.n, J)
+    np.testing.assert_allclose(H.stencil_to_dense(3, m.n, A), Ad, rtol=0, atol=1e-15 * np.abs(Ad).max())
+    x = np.random.default_rng(1).standard_normal(2 * m.nv)
+    np.testing.assert_allclose(oracle.spmv(3, m.n, A, x), Ad @ x, rtol=1e-12, atol=1e-14 * np.abs(Ad @ x).max())
+
+
+def test_dense_lu_matches_numpy(oracle):
+    rng = np.random.default_rng(2)
+    for N in (1, 5, 50):
+        M = rng.standard_normal((N, N)) + np.diag(rng.uniform(0, 0.1, N))
+        b = rng.standard_normal(N)
+        np.testing.assert_allclose(oracle.lu_solve_dense(M, b), np.linalg.solve(M, b), rtol=1e-10)
+
+
+def test_transfer_operators(oracle):
+    """Prolongation = textbook trilinear interpolation (dense reference), it
+    reproduces linear functions, and restriction is its exact transpose."""
+    dim, nf = 3, (9, 5, 7)
+    nc = H.coarse_dims(dim, nf)
+    rng = np.random.default_rng(3)
+    dmf = (rng.uniform(size=int(np.prod(nf))) < 0.2).astype(np.uint8)
+    dmc = np.zeros(int(np.prod(nc)), np.uint8)
+    for vc in range(len(dmc)):
+        I_, J_, K_ = vc % nc[0], (vc // nc[0]) % nc[1], vc // (nc[0] * nc[1])
+        dmc[vc] = dmf[2 * I_ + nf[0] * (2 * J_ + nf[1] * 2 * K_)]
+    P = H.dense_prolongation(dim, nf, nc, dmf, dmc)
+    xc = rng.standard_normal(P.shape[1])
+    xf = rng.standard_normal(P.shape[0])
+    np.testing.assert_allclose(oracle.prolong_add(dim, nf, dmf, nc, dmc, xc, xf), xf + P @ xc, rtol=1e-14, atol=1e-14)
+    rf = rng.standard_normal(P.shape[0])
+    np.testing.assert_allclose(oracle.restrict(dim, nf, dmf, nc, dmc, rf), P.T @ rf, rtol=1e-14, atol=1e-14)
+    # linear reproduction (no mask)
+    z = np.zeros(int(np.prod(nf)), np.uint8)
+    zc = np.zeros(int(np.prod(nc)), np.uint8)
+    cv = np.arange(int(np.prod(nc)))
+    fc = np.arange(int(np.prod(nf)))
+    lin_c = np.zeros(2 * len(cv))
+    lin_c[1::2] = 2 * (cv % nc[0]) + 3 * 2 * ((cv // nc[0]) % nc[1]) - 2 * (cv // (nc[0] * nc[1]))
+    lin_f = 1 * (fc % nf[0]) + 3 * ((fc // nf[0]) % nf[1]) - 1 * (fc // (nf[0] * nf[1]))
+    out = oracle.prolong_add(dim, nf, z, nc, zc, lin_c, np.zeros(2 * len(fc)))
+    np.testing.assert_allclose(out[1::2], lin_f, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim,nf", [(2, (9, 7)), (3, (5, 7, 5))])
+def test_galerkin_equals_dense_PtAP(oracle, dim, nf):
+    p = I.random_problem(dim, nf if dim == 3 else nf, 6)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.1)
+    nc = H.coarse_dims(dim, m.n)
+    dmf = p["dir"]
+    dmc = np.array([dmf[2 * (v % nc[0]) + m.n[0] * (2 * ((v // nc[0]) % nc[1]) + m.n[1] * 2 * (v // (nc[0] * nc[1])))]
+                    for v in range(int(np.prod(nc)))], np.uint8)
+    P = H.dense_prolongation(dim, m.n, nc, dmf, dmc)
+    Ac_dense = P.T @ H.stencil_to_dense(dim, m.n, A) @ P
+    for vc in np.nonzero(dmc)[0]:
+        Ac_dense[2 * vc, 2 * vc] = 1.0
+    Ac = oracle.galerkin(dim, m.n, dmf, A, nc, dmc)
+    np.testing.assert_allclose(H.stencil_to_dense(dim, nc, Ac), Ac_dense, rtol=0, atol=1e-13 * np.abs(Ac_dense).max())
+    # Galerkin of the 3^d stencil stays within the 3^d stencil
+    assert np.allclose(H.dense_to_stencil(dim, nc, Ac_dense), Ac, atol=1e-13 * np.abs(Ac_dense).max())
+
+
+def test_smoothers_match_dense_formulas(oracle):
+    """Jacobi: x + w D^-1 (b - A x).  Forward multicolour GS: one sweep equals
+    solving (D + L) x_new = b - U x_old with L/U the couplings to earlier/later
+    colours in colour order (numpy dense solve)."""
+    dim = 3
+    p = I.random_problem(dim, (5, 5, 4), 7)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.1)
+    Ad = H.stencil_to_dense(dim, m.n, A)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(2 * m.nv)
+    x = rng.standard_normal(2 * m.nv)
+    Dinv = np.zeros_like(Ad)
+    for v in range(m.nv):
+        Dinv[2 * v:2 * v + 2, 2 * v:2 * v + 2] = np.linalg.inv(Ad[2 * v:2 * v + 2, 2 * v:2 * v + 2])
+    ref = x + 0.8 * Dinv @ (b - Ad @ x)
+    np.testing.assert_allclose(oracle.jacobi(dim, m.n, A, b, x, 0.8), ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+    col = np.repeat(H.colour(dim, m.n), 2)
+    for forward in (True, False):
+        order = col if forward else (7 - col)
+        lower = order[:, None] > order[None, :]
+        same_v = np.kron(np.eye(m.nv), np.ones((2, 2))).astype(bool)
+        DL = np.where(lower | same_v, Ad, 0.0)
+        U = np.where(~(lower | same_v), Ad, 0.0)
+        ref = np.linalg.solve(DL, b - U @ x)
+        got = oracle.gs_sweep(dim, m.n, A, b, x, forward=forward)
+        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------- P6 / P7 solver
+@pytest.mark.parametrize("dim,nv,smoother", [(2, (9, 9), 0), (3, (5, 5, 5), 1), (3, (9, 9, 9), 0)])
+def test_p6_bicgstab_gmg_matches_dense_solve(oracle, dim, nv, smoother):
+    p = I.random_problem(dim, nv, 13)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.1)
+    g = oracle.GMG(dim, m.n, A, p["dir"], 3, smoother=smoother)
+    x, info = oracle.bicgstab(dim, m.n, A, g, F, rtol=1e-14, maxit=100)
+    Ad = H.stencil_to_dense(dim, m.n, A)
+    xr = np.linalg.solve(Ad, F)
+    assert info["status"] == 0
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
+
+
+@pytest.mark.parametrize("dim,nv,levels", [(2, (33, 33), 4), (3, (17, 17, 17), 4)])
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_p7_gmg_convergence_factor_poisson(oracle, dim, nv, levels, smoother):
+    """V(2,2) on the constant-coefficient VCFVM Laplacian: asymptotic factor
+    <= 0.15 (local Fourier analysis gives ~0.05-0.1 for these smoothers)."""
+    p = _poisson_problem(dim, nv)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.1)
+    g = oracle.GMG(dim, m.n, A, p["dir"], levels, smoother=smoother)
+    assert g.nlevels == levels
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(2 * m.nv)
+    x[0::2][p["dir"].astype(bool)] = 0.0
+    rs = []
+    for _ in range(20):
+        r = -oracle.spmv(dim, m.n, A, x)
+        rs.append(np.linalg.norm(r))
+        x = x + g.vcycle(r)
+    factor = (rs[-1] / rs[-6]) ** (1 / 5)
+    assert factor <= 0.15
+
+
+# ---------------------------------------------------------------- P8 LIMEX
+def test_p8_extrapolation_order_on_linear_ode(oracle):
+    """y' = lam y: the linearly implicit Euler column with n steps gives
+    (1 - lam H/n)^-n exactly; extrapolating kappa columns of the harmonic
+    sequence has local error O(H^(kappa+1)) against exp(lam H)."""
+    lam = -1.3
+    for kappa in (1, 2, 3, 4):
+        errs = []
+        Hs = np.array([0.02, 0.01, 0.005])
+        for Hh in Hs:
+            T1 = np.array([[(1 - lam * Hh / j) ** (-j)] for j in range(1, kappa + 1)])
+            Tkk, _ = oracle.extrapolate(T1, list(range(1, kappa + 1)))
+            errs.append(abs(Tkk[0] - np.exp(lam * Hh)))
+        slope = np.polyfit(np.log(Hs), np.log(errs), 1)[0]
+        assert abs(slope - (kappa + 1)) < 0.1
+
+
+def test_limex_columns_match_dense_linearly_implicit_euler(oracle):
+    """kappa = 2 LIMEX step of the oracle = dense reconstruction: columns of
+    linearly implicit Euler with the frozen J(u0), M(u0) (numpy solves), then
+    T22 = T21 + (T21 - T11)/(2/1 - 1)."""
+    p = I.random_problem(2, (9, 9), 17)
+    m = oracle.Model(p)
+    u0 = p["u0"]
+    Hh = 5.0
+    F0, J, md = oracle.assemble(m, u0)
+    Jd = H.stencil_to_dense(2, m.n, J)
+    Md = np.zeros_like(Jd)
+    for v in range(m.nv):
+        Md[2 * v, 2 * v + 1] = md[v, 0]
+        Md[2 * v + 1, 2 * v + 1] = md[v, 1]
+    T11 = u0 + np.linalg.solve(Md / Hh - Jd, F0)
+    u = u0 + np.linalg.solve(Md / (Hh / 2) - Jd, F0)
+    F1 = oracle.assemble(m, u, jacobian=False)[0]
+    T21 = u + np.linalg.solve(Md / (Hh / 2) - Jd, F1)
+    T22 = T21 + (T21 - T11) / (2.0 / 1.0 - 1.0)
+    u_out, info = oracle.limex_step(m, u0, Hh, kappa=2, tol=1e9, nlevels=3, rtol=1e-14, maxit=300)
+    assert info["accepted"] == 1 and info["solves"] == 3
+    np.testing.assert_allclose(u_out[0::2], T22[0::2], rtol=1e-11)
+    np.testing.assert_allclose(u_out[1::2], T22[1::2], atol=1e-11)
+
+
+def test_error_norm_quadratures(oracle):
+    """H1 seminorm of a linear function = |a|^2 |Omega|; of x*y on the unit
+    square = 2/3 (bilinear, exact); lumped L2 of 1 = |Omega|."""
+    n = (9, 5, 1)
+    h = (1 / 8, 1 / 4, 1.0)
+    v = np.arange(45)
+    x, y = (v % 9) * h[0], (v // 9) * h[1]
+    assert oracle.h1_seminorm2(2, n, h, 2 * x - 3 * y) == pytest.approx(13.0, rel=1e-13)
+    assert oracle.h1_seminorm2(2, n, h, x * y) == pytest.approx(2 / 3, rel=1e-13)
+    assert oracle.lumped_l2norm2(2, n, h, np.ones(45)) == pytest.approx(1.0, rel=1e-14)
+    n3 = (5, 3, 9)
+    h3 = (0.25, 0.5, 0.125)
+    v3 = np.arange(int(np.prod(n3)))
+    z = (v3 // 15) * h3[2]
+    assert oracle.h1_seminorm2(3, n3, h3, 4 * z) == pytest.approx(16.0, rel=1e-13)
+
+
+def test_pdmin_and_storage_invariants(oracle):
+    p = I.random_problem(3, (6, 5, 4), 2)
+    m = oracle.Model(p)
+    pdm = oracle.pdmin(m)
+    assert set(np.unique(pdm)) <= set(np.unique(p["pd"]))
+    assert pdm.min() == p["pd"].min()
+    phiv = oracle.phiv(m)
+    vol = np.prod(p["h"])
+    assert phiv.sum() == pytest.approx((p["phi"] * vol).sum(), rel=1e-13)
