@@ -1,0 +1,180 @@
+/*
+ * rf.h — C ABI of the GB300 (sm_103a) LIMEX stage solver for incompressible,
+ * immiscible two-phase (water / DNAPL) flow in heterogeneous porous media.
+ *
+ * The method is that of "A highly scalable numerical framework for reservoir
+ * simulation on UG4 platform" (arXiv 2506.04763):
+ *   - vertex-centred finite volumes (Sec. 3.1, Eqs. dsW, dpN) with fully
+ *     upwinded relative permeabilities (Sec. 3.2, Eqs. up_krw, up_krn),
+ *     gravity, capillary pressure, and the p_dmin interface condition between
+ *     materials of different entry pressure (Sec. 3.3, Eqs. pdmin, hSw,
+ *     krn_ip, krw_ip);
+ *   - the linearly implicit Euler / LIMEX stage (M - tau J) du = tau F with the
+ *     exact Jacobian J = F_u and extrapolation (Sec. 4);
+ *   - BiCGSTAB preconditioned by geometric multigrid (Sec. 5, setup paragraph).
+ * Primary unknowns per vertex are (p_w, S_n), interleaved.
+ *
+ * Conventions shared by every entry point
+ *   Grid: structured box of n[0] x n[1] (x n[2]) vertices, spacing h.  Vertex
+ *     v = i + n0*(j + n1*k) (x fastest); cell c = i + (n0-1)*(j + (n1-1)*k).
+ *     Multigrid coarsening needs n[a]-1 divisible by 2 per level.
+ *   Vectors: double, length 2*nv, u[2v] = p_w (Pa), u[2v+1] = S_n; residual
+ *     F[2v] water mass balance, F[2v+1] NAPL mass balance (kg/s).
+ *   Pointers: every array argument may be HOST or DEVICE memory (the library
+ *     asks the CUDA driver which); host buffers are staged through device
+ *     memory inside the call, device buffers are used in place.  All inputs
+ *     stay owned by the caller and are only borrowed for the call.
+ *   Streams: every call is ordered on the given cudaStream_t (NULL = legacy
+ *     default stream).  Calls that return numbers on the host (info structs,
+ *     host outputs) synchronise that stream before returning.
+ *   Errors: argument errors return RF_EINVAL synchronously; CUDA failures
+ *     RF_ECUDA; device-detected conditions (non-convergence, breakdown,
+ *     non-finite values) are returned once the stream has been synchronised.
+ *     rf_last_error() gives a one-line message for the calling thread.
+ *   Memory: all device memory of a grid comes from the rf_allocator given to
+ *     rf_grid_create (cudaMalloc/cudaFree when it is NULL) and is released by
+ *     rf_grid_destroy.  There is no CPU fallback: every step runs on the GPU.
+ */
+#ifndef RF_H
+#define RF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RF_OK = 0,
+  RF_EINVAL = 1,      /* bad argument (checked before any GPU work)          */
+  RF_ENOMEM = 2,      /* the allocator returned NULL                          */
+  RF_ECUDA = 3,       /* a CUDA runtime call failed                           */
+  RF_ENOTCONV = 4,    /* linear solve hit max_it before reaching rtol         */
+  RF_EBREAKDOWN = 5,  /* BiCGSTAB breakdown that a restart did not cure       */
+  RF_ENONFINITE = 6,  /* NaN/Inf met in the state, residual or iteration      */
+  RF_ETIMEOUT = 7     /* a bounded device wait gave up                        */
+} rf_status;
+
+typedef struct rf_grid rf_grid;
+
+/* Device allocator: alloc(bytes, stream, ctx) -> device pointer or NULL;
+ * free(ptr, bytes, stream, ctx).  NULL allocator = cudaMalloc / cudaFree. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* ctx;
+} rf_allocator;
+
+/* dim = 2 or 3; n = vertices per axis (n[2] = 1 in 2D); h = spacing (m);
+ * g = gravity vector (m/s^2), e.g. (0, -9.81, 0) in 2D. */
+typedef struct { int dim; int64_t n[3]; double h[3]; double g[3]; } rf_grid_desc;
+
+/* Densities (kg/m^3) and viscosities (Pa s) of water (w) and DNAPL (n). */
+typedef struct { double rho_w, rho_n, mu_w, mu_n; } rf_fluids;
+
+/* Brooks-Corey residual saturations and pore-size index (uniform), and per
+ * cell permeability K (m^2), porosity phi and entry pressure p_d (Pa), each
+ * of length (n0-1)(n1-1)(n2-1) (2D: (n0-1)(n1-1)).  Copied at creation. */
+typedef struct { double S_wr, S_nr, lambda; const double *K, *phi, *pd; } rf_materials;
+
+/* Boundary data, per vertex (copied at creation): dir_pw[v] = 1 makes the
+ * water-balance row of v the algebraic equation 0 = pw_dir[v] - p_w (Dirichlet
+ * p_w); q_in[2v+a] is a mass source of phase a (kg/s; Neumann inflow).  Any
+ * pointer may be NULL (no Dirichlet vertices / no sources). */
+typedef struct { const uint8_t* dir_pw; const double* pw_dir; const double* q_in; } rf_bc;
+
+enum { RF_SMOOTH_JACOBI = 0, RF_SMOOTH_GS8 = 1 };
+enum { RF_PREC_FP64 = 0, RF_PREC_FP32 = 1, RF_PREC_FP16 = 2 };
+
+/* Multigrid options.  nlevels: vertex-nested levels (coarsened while possible,
+ * at most this many); smoother: damped point-block Jacobi or multicolour
+ * (4 colours 2D / 8 colours 3D) block Gauss-Seidel; nu1/nu2 pre/post sweeps;
+ * omega: Jacobi damping; precision: storage and arithmetic of the
+ * preconditioner (FP64; FP32; FP16 storage with per-block-row FP32 scales and
+ * FP32 arithmetic).  The coarsest level is solved exactly in FP64. */
+typedef struct { int nlevels, smoother, nu1, nu2; double omega; int precision; } rf_gmg_opts;
+
+/* Stop when the TRUE FP64 residual |b - A x|_2 <= rtol |b|_2. */
+typedef struct { double rtol; int max_it; } rf_solve_opts;
+typedef struct { int iterations; double relres; int status; int restarts; } rf_solve_info;
+
+/* LIMEX step options: kappa columns (n_j = 1..kappa, one shared Jacobian),
+ * error tolerance tol, safety factor rho, step factor bounds. */
+typedef struct {
+  int kappa; double tol, rho, fac_min, fac_max;
+  rf_gmg_opts gmg; rf_solve_opts solve;
+} rf_limex_opts;
+typedef struct { double eps, H_new; int accepted, solves, iterations, status; } rf_limex_info;
+
+/* Create a grid: validates the description, copies materials and boundary
+ * data to the device and precomputes p_dmin,i = min of p_d over the elements
+ * around vertex i (Eq. pdmin) and the lumped pore volume (Phi V)_i. */
+rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* fluids, const rf_materials* mat,
+                         const rf_bc* bc, const rf_allocator* alloc, void* stream, rf_grid** out);
+void rf_grid_destroy(rf_grid* g);
+
+/* Number of vertices of the grid (0 if g is NULL). */
+int64_t rf_grid_nv(const rf_grid* g);
+
+/* Assemble at state u [2nv]: F(u) into F_out (may be NULL) and, when
+ * want_jacobian, the exact Jacobian J = F_u (27 or 9 2x2 blocks per vertex,
+ * FP64) and the lumped mass matrix M (vertex-diagonal) kept inside the grid.
+ * Sec. 3 (Eqs. dsW, dpN, up_krw, up_krn, hSw, krn_ip, krw_ip), Sec. 4 (J=F_u). */
+rf_status rf_assemble(rf_grid* g, const double* u, int want_jacobian, double* F_out, void* stream);
+
+/* Build the multigrid hierarchy for the stage matrices A_j = shift[j] M - J,
+ * j < nshift <= 4 (shift = 1/h_j), from the last assembled J, M: Galerkin
+ * coarse operators P^T A P with trilinear P (FP64), the preconditioner copies
+ * in the chosen precision, block-diagonal inverses and the coarsest inverse. */
+rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, const rf_gmg_opts* opts, void* stream);
+
+/* Solve A_shift x = b by BiCGSTAB right-preconditioned with one V-cycle per
+ * application, x0 = 0.  b, x: [2nv].  info (host, may be NULL) receives the
+ * iteration count, the true relative residual and the status. */
+rf_status rf_solve(rf_grid* g, int shift, const double* b, double* x, const rf_solve_opts* opts,
+                   rf_solve_info* info, void* stream);
+
+/* One LIMEX step of size H from state u (in/out [2nv]): assembly of J, M at
+ * u, multigrid setup for the kappa shifts n_j/H, the columns of linearly
+ * implicit Euler steps (each an rf_solve), Aitken-Neville extrapolation, the
+ * scaled error estimate and the step-size proposal (q = 2).  u is replaced by
+ * the extrapolated state only when the step is accepted (eps <= tol). */
+rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* opts, rf_limex_info* info,
+                        void* stream);
+
+/* ---- test and inspection hooks (host buffers, natural vertex order) ---- */
+
+/* Copy out J as [nv][nb][4] (entries (w,p_w),(w,S_n),(n,p_w),(n,S_n)) and the
+ * mass diagonal as [nv][2] (dm_w/dS_n, dm_n/dS_n); either may be NULL. */
+rf_status rf_export_jacobian(rf_grid* g, double* J_host, double* mdiag_host, void* stream);
+
+/* Copy out the multigrid operator of `level` for shift index `shift` as
+ * [nv_l][nb][4] in FP64 (the Galerkin product as computed; level 0 is
+ * shift*M - J); dims_out[3] receives the level's vertex counts. */
+rf_status rf_export_level(rf_grid* g, int level, int shift, double* A_host, int64_t dims_out[3], void* stream);
+
+enum {
+  RF_OP_SPMV = 0,        /* out = A_shift in0 on the fine grid, FP64            */
+  RF_OP_VCYCLE = 1,      /* out = V-cycle(in0) (fine grid, preconditioner)      */
+  RF_OP_SMOOTH = 2,      /* out = one smoother sweep at `level`: b = in0, x = in1
+                            (Jacobi; forward colour sweep for GS)               */
+  RF_OP_RESIDUAL = 3,    /* out = in0 - A_level in1 at `level`                  */
+  RF_OP_RESTRICT = 4,    /* out (level+1) = P^T in0 (level)                     */
+  RF_OP_PROLONG = 5,     /* out (level) = in1 (level) + P in0 (level+1)         */
+  RF_OP_COARSE = 6       /* out = A_coarsest^-1 in0                             */
+};
+/* Apply one preconditioner building block with the precision of the current
+ * hierarchy (inputs are rounded to it); vectors are [2 nv_level] doubles. */
+rf_status rf_apply(rf_grid* g, int op, int level, int shift, const double* in0, const double* in1,
+                   double* out, void* stream);
+
+/* Kernels launched by this library in this process so far. */
+int64_t rf_launch_count(void);
+const char* rf_status_string(rf_status s);
+const char* rf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

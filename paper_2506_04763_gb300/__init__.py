@@ -1,0 +1,317 @@
+"""GB300 (sm_103a) LIMEX stage solver for two-phase porous-media flow.
+
+Thin ctypes binding of the C ABI in ``include/rf.h`` (``librf.so``, built
+in-tree by ``paper_2506_04763_gb300.build``).  The functions ``rf_*`` keep the
+ABI's names and only marshal arguments; every step of the path runs in the
+library's CUDA kernels.  PyTorch supplies device memory (as the library's
+allocator and for user tensors) and streams.  There is no CPU fallback: if the
+library or a GPU is missing, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librf.so")
+
+RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ENOTCONV, RF_EBREAKDOWN, RF_ENONFINITE, RF_ETIMEOUT = range(8)
+RF_SMOOTH_JACOBI, RF_SMOOTH_GS8 = 0, 1
+RF_PREC_FP64, RF_PREC_FP32, RF_PREC_FP16 = 0, 1, 2
+RF_OP_SPMV, RF_OP_VCYCLE, RF_OP_SMOOTH, RF_OP_RESIDUAL, RF_OP_RESTRICT, RF_OP_PROLONG, RF_OP_COARSE = range(7)
+
+
+class RFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("rf status %d (%s): %s" % (status, _status_name(status), msg))
+        self.status = status
+
+
+def _status_name(s):
+    return ["ok", "invalid argument", "out of memory", "CUDA error", "not converged", "breakdown",
+            "non-finite", "timeout"][s] if 0 <= s < 8 else "unknown"
+
+
+# ------------------------------------------------------------------ structs
+class rf_grid_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("h", ctypes.c_double * 3),
+                ("g", ctypes.c_double * 3)]
+
+
+class rf_fluids(ctypes.Structure):
+    _fields_ = [("rho_w", ctypes.c_double), ("rho_n", ctypes.c_double), ("mu_w", ctypes.c_double),
+                ("mu_n", ctypes.c_double)]
+
+
+class rf_materials(ctypes.Structure):
+    _fields_ = [("S_wr", ctypes.c_double), ("S_nr", ctypes.c_double), ("lam", ctypes.c_double),
+                ("K", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("pd", ctypes.c_void_p)]
+
+
+class rf_bc(ctypes.Structure):
+    _fields_ = [("dir_pw", ctypes.c_void_p), ("pw_dir", ctypes.c_void_p), ("q_in", ctypes.c_void_p)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class rf_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class rf_gmg_opts(ctypes.Structure):
+    _fields_ = [("nlevels", ctypes.c_int), ("smoother", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int)]
+
+
+class rf_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int)]
+
+
+class rf_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("relres", ctypes.c_double), ("status", ctypes.c_int),
+                ("restarts", ctypes.c_int)]
+
+
+class rf_limex_opts(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_int), ("tol", ctypes.c_double), ("rho", ctypes.c_double),
+                ("fac_min", ctypes.c_double), ("fac_max", ctypes.c_double), ("gmg", rf_gmg_opts),
+                ("solve", rf_solve_opts)]
+
+
+class rf_limex_info(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("H_new", ctypes.c_double), ("accepted", ctypes.c_int),
+                ("solves", ctypes.c_int), ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
+
+
+# exported symbols of include/rf.h and their signatures
+_P, _I, _D, _I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+SIGNATURES = {
+    "rf_grid_create": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "rf_grid_destroy": (None, [_P]),
+    "rf_grid_nv": (_I64, [_P]),
+    "rf_assemble": (_I, [_P, _P, _I, _P, _P]),
+    "rf_gmg_setup": (_I, [_P, _P, _I, _P, _P]),
+    "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
+    "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
+    "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
+    "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
+    "rf_apply": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "rf_launch_count": (_I64, []),
+    "rf_status_string": (ctypes.c_char_p, [_I]),
+    "rf_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Load librf.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("librf.so is not built: run `python -m paper_2506_04763_gb300.build` "
+                               "(needs nvcc); this package has no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != RF_OK:
+        raise RFError(status, lib().rf_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------------------ ABI wrappers (same names)
+def rf_grid_create(desc, fluids, mat, bc, alloc, stream):
+    h = ctypes.c_void_p()
+    _check(lib().rf_grid_create(ctypes.byref(desc), ctypes.byref(fluids), ctypes.byref(mat),
+                                ctypes.byref(bc) if bc is not None else None,
+                                ctypes.byref(alloc) if alloc is not None else None, stream, ctypes.byref(h)))
+    return h.value
+
+
+def rf_grid_destroy(grid):
+    lib().rf_grid_destroy(grid)
+
+
+def rf_assemble(grid, u_ptr, want_jacobian, F_ptr, stream):
+    _check(lib().rf_assemble(grid, u_ptr, int(want_jacobian), F_ptr, stream))
+
+
+def rf_gmg_setup(grid, shifts, opts, stream):
+    arr = (ctypes.c_double * len(shifts))(*[float(s) for s in shifts])
+    _check(lib().rf_gmg_setup(grid, arr, len(shifts), ctypes.byref(opts), stream))
+
+
+def rf_solve(grid, shift, b_ptr, x_ptr, opts, stream):
+    info = rf_solve_info()
+    st = lib().rf_solve(grid, int(shift), b_ptr, x_ptr, ctypes.byref(opts), ctypes.byref(info), stream)
+    if st not in (RF_OK, RF_ENOTCONV):
+        _check(st)
+    return st, info
+
+
+def rf_limex_step(grid, u_ptr, H, opts, stream):
+    info = rf_limex_info()
+    st = lib().rf_limex_step(grid, u_ptr, float(H), ctypes.byref(opts), ctypes.byref(info), stream)
+    if st not in (RF_OK, RF_ENOTCONV):
+        _check(st)
+    return st, info
+
+
+def rf_export_jacobian(grid, J_host, md_host, stream):
+    _check(lib().rf_export_jacobian(grid, J_host, md_host, stream))
+
+
+def rf_export_level(grid, level, shift, A_host, dims_host, stream):
+    _check(lib().rf_export_level(grid, int(level), int(shift), A_host, dims_host, stream))
+
+
+def rf_apply(grid, op, level, shift, in0, in1, out, stream):
+    _check(lib().rf_apply(grid, int(op), int(level), int(shift), in0, in1, out, stream))
+
+
+def rf_launch_count():
+    return int(lib().rf_launch_count())
+
+
+def rf_status_string(s):
+    return lib().rf_status_string(int(s)).decode()
+
+
+def rf_last_error():
+    return lib().rf_last_error().decode(errors="replace")
+
+
+# ------------------------------------------------------------------ convenience layer
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if not a.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return a.data_ptr()
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _torch_allocator():
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = rf_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    return a
+
+
+SMOOTHERS = {"jacobi": RF_SMOOTH_JACOBI, "gs8": RF_SMOOTH_GS8, "gs": RF_SMOOTH_GS8}
+PRECISIONS = {"fp64": RF_PREC_FP64, "fp32": RF_PREC_FP32, "fp16": RF_PREC_FP16}
+
+
+def gmg_opts(nlevels, smoother="jacobi", nu1=2, nu2=2, omega=0.8, precision="fp32"):
+    return rf_gmg_opts(int(nlevels), SMOOTHERS.get(smoother, smoother), int(nu1), int(nu2), float(omega),
+                       PRECISIONS.get(precision, precision))
+
+
+class Grid:
+    """A problem on the GPU.  ``prob`` is a dict as made by
+    ``paper_2506_04763_gb300.inputs`` (grid, fluids, Brooks-Corey parameters,
+    per-cell K/phi/p_d, Dirichlet mask and values, optional sources)."""
+
+    def __init__(self, prob, allocator="torch", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA GPU is required (no CPU fallback)")
+        self.prob = prob
+        self.dim = int(prob["dim"])
+        self.n = tuple(int(t) for t in prob["n"])
+        self.nv = self.n[0] * self.n[1] * self.n[2]
+        self.nb = 27 if self.dim == 3 else 9
+        self.stream = _stream_handle(stream)
+        desc = rf_grid_desc(self.dim, (ctypes.c_int64 * 3)(*self.n), (ctypes.c_double * 3)(*prob["h"]),
+                            (ctypes.c_double * 3)(*prob["g"]))
+        fl = rf_fluids(prob["rho_w"], prob["rho_n"], prob["mu_w"], prob["mu_n"])
+        keep = {k: np.ascontiguousarray(prob[k], np.float64) for k in ("K", "phi", "pd", "pw_dir")}
+        keep["dir"] = np.ascontiguousarray(prob["dir"], np.uint8)
+        keep["q_in"] = None if prob.get("q_in") is None else np.ascontiguousarray(prob["q_in"], np.float64)
+        mat = rf_materials(prob["S_wr"], prob["S_nr"], prob["lam"], _ptr(keep["K"]), _ptr(keep["phi"]),
+                           _ptr(keep["pd"]))
+        bc = rf_bc(_ptr(keep["dir"]), _ptr(keep["pw_dir"]), _ptr(keep["q_in"]))
+        self._alloc = _torch_allocator() if allocator == "torch" else None
+        self.handle = rf_grid_create(desc, fl, mat, bc, self._alloc, self.stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rf_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- wrappers over the ABI (tensors on the GPU, or numpy arrays on the host)
+    def assemble(self, u, jacobian=True, F=None):
+        rf_assemble(self.handle, _ptr(u), jacobian, _ptr(F), self.stream)
+        return F
+
+    def gmg_setup(self, shifts, opts):
+        rf_gmg_setup(self.handle, list(shifts), opts, self.stream)
+
+    def solve(self, shift, b, x, rtol=1e-10, max_it=200):
+        st, info = rf_solve(self.handle, shift, _ptr(b), _ptr(x), rf_solve_opts(float(rtol), int(max_it)), self.stream)
+        return dict(status=st, iterations=info.iterations, relres=info.relres, restarts=info.restarts)
+
+    def limex_step(self, u, H, kappa=4, tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4.0, gmg=None, rtol=1e-10,
+                   max_it=200):
+        gmg = gmg if gmg is not None else gmg_opts(4)
+        o = rf_limex_opts(int(kappa), float(tol), float(rho), float(fac_min), float(fac_max), gmg,
+                          rf_solve_opts(float(rtol), int(max_it)))
+        st, info = rf_limex_step(self.handle, _ptr(u), H, o, self.stream)
+        return dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted, solves=info.solves,
+                    iterations=info.iterations)
+
+    def export_jacobian(self):
+        J = np.zeros((self.nv, self.nb, 4))
+        md = np.zeros((self.nv, 2))
+        rf_export_jacobian(self.handle, _ptr(J), _ptr(md), self.stream)
+        return J, md
+
+    def export_level(self, level, shift):
+        dims = (ctypes.c_int64 * 3)()
+        # size of the level first: at most nv
+        buf = np.zeros(self.nv * self.nb * 4)
+        rf_export_level(self.handle, level, shift, _ptr(buf), ctypes.addressof(dims), self.stream)
+        n = tuple(int(t) for t in dims)
+        nvl = n[0] * n[1] * n[2]
+        return buf[:nvl * self.nb * 4].reshape(nvl, self.nb, 4).copy(), n
+
+    def apply(self, op, level, shift, in0, in1=None, out_len=None):
+        in0 = np.ascontiguousarray(in0, np.float64)
+        in1 = None if in1 is None else np.ascontiguousarray(in1, np.float64)
+        out = np.zeros(out_len if out_len is not None else 2 * self.nv)
+        rf_apply(self.handle, op, level, shift, _ptr(in0), _ptr(in1), _ptr(out), self.stream)
+        return out

@@ -1,0 +1,395 @@
+// assemble.cu — grid set-up (K0) and vertex-centred finite-volume assembly
+// (K1: F, exact Jacobian J = F_u and lumped M; K1r: F only).
+//
+// Compiled with -fmad=false: every product and sum of the discrete fluxes is
+// rounded separately, in the order written, so that the upwind decisions
+// (sign of T_w, T_n), the interface-condition cap and the k_r clamps are taken
+// on exactly the values that the order of operations below defines.
+//
+// Method (arXiv 2506.04763):
+//   Sec. 3.1, Eqs. (dsW),(dpN): dual-mesh control volumes b_i; storage lumped
+//     at the vertex; one sub-control-volume face (SCVF) per element edge,
+//     flux evaluated at the face midpoint x_M with face size A_f.
+//   Sec. 3.2, Eqs. (up_krw),(up_krn): k_r taken from the upstream vertex by
+//     the sign of v_alpha . n (v_alpha excludes the capillary-diffusion
+//     part); T >= 0 picks the edge's lower vertex a.
+//   Sec. 3.3, Eqs. (pdmin),(hSw),(krn_ip),(krw_ip): p_dmin per vertex and the
+//     per-sub-control-volume saturation S hat, used in k_rn only.
+//   Sec. 2, Eqs. (sW),(pN),(vW),(vN): the water flux splits into k_rw v_w and
+//     the capillary-diffusion term, which is not upwinded.
+// With p_w as primary pressure, p_n = p_w + p_c at vertices (p_c,i =
+// p_dmin,i J(S_e,i)); per face of element e along axis k (edge a->b):
+//   T_w = -K_e A_f (G(p_n) - rho_w g_k), T_n = -K_e A_f (G(p_n) - rho_n g_k),
+//   T_c = -K_e A_f G(p_c),  G = d/dx_k of the element's Q1 interpolant at x_M,
+//   F_w = rho_w (lam_w(S_up) T_w - lam_w(S(x_M)) T_c),
+//   F_n = rho_n lam_n(S hat_up) T_n.
+//
+// K1 runs one thread per vertex: it visits the 2^d elements around its vertex
+// and, in each, the d faces that touch it, and accumulates its own block row
+// (27 or 9 2x2 blocks) in shared memory; no atomics, no second pass.  The row
+// is written once with 1 KB-per-warp coalesced stores.
+#include "rf_common.cuh"
+#include "rf_kernels.h"
+
+namespace rf {
+
+struct Phys {
+  double rho_w, rho_n, mu_w, mu_n, S_wr, S_nr, lam, den;
+  double h[3], g[3];
+};
+
+// ---- constitutive laws (Brooks-Corey; J continued linearly outside [0.01, 1])
+__device__ __forceinline__ void leverett_pow(double lam, double S, double& J, double& dJ) {
+  if (lam == 2.0) {
+    double r = sqrt(S);
+    J = 1.0 / r;
+    dJ = -0.5 / (S * r);
+  } else {
+    J = pow(S, -1.0 / lam);
+    dJ = (-1.0 / lam) * pow(S, -1.0 / lam - 1.0);
+  }
+}
+
+__device__ __forceinline__ void leverett(double lam, double Se, double& J, double& dJ) {
+  if (Se < 0.01) {
+    double j0, d0;
+    leverett_pow(lam, 0.01, j0, d0);
+    J = j0 + d0 * (Se - 0.01);
+    dJ = d0;
+  } else if (Se > 1.0) {
+    J = 1.0 + (-1.0 / lam) * (Se - 1.0);
+    dJ = -1.0 / lam;
+  } else {
+    leverett_pow(lam, Se, J, dJ);
+  }
+}
+
+// k_rw, dk_rw/dS_e (k_r use S_e clamped to [0,1], derivative 0 outside)
+__device__ __forceinline__ void krw_of(double lam, double Se, double& k, double& dk) {
+  double Sc = fmin(fmax(Se, 0.0), 1.0);
+  bool inside = Se > 0.0 && Se < 1.0;
+  if (lam == 2.0) {
+    double s2 = Sc * Sc;
+    k = s2 * s2;
+    dk = inside ? 4.0 * s2 * Sc : 0.0;
+  } else {
+    double ew = (2.0 + 3.0 * lam) / lam;
+    k = pow(Sc, ew);
+    dk = inside ? ew * pow(Sc, ew - 1.0) : 0.0;
+  }
+}
+
+__device__ __forceinline__ void krn_of(double lam, double Se, double& k, double& dk) {
+  double Sc = fmin(fmax(Se, 0.0), 1.0);
+  bool inside = Se > 0.0 && Se < 1.0;
+  double om = 1.0 - Sc;
+  if (lam == 2.0) {
+    double s2 = Sc * Sc;
+    k = om * om * (1.0 - s2);
+    dk = inside ? (-2.0 * om * (1.0 - s2) - 2.0 * Sc * om * om) : 0.0;
+  } else {
+    double en = (2.0 + lam) / lam, sa = pow(Sc, en);
+    k = om * om * (1.0 - sa);
+    dk = inside ? (-2.0 * om * (1.0 - sa) - en * om * om * pow(Sc, en - 1.0)) : 0.0;
+  }
+}
+
+// Eq. (hSw): S_e hat of vertex i inside an element of entry pressure pdc.
+__device__ __forceinline__ void shat_of(double lam, double Se, double pdc, double pdmin, double& s, double& ds) {
+  if (pdc == pdmin) { s = Se; ds = 1.0; return; }
+  double r = pdc / pdmin;
+  double rl = (lam == 2.0) ? r * r : pow(r, lam);
+  double t = rl * Se;
+  if (t >= 1.0) { s = 1.0; ds = 0.0; }
+  else { s = t; ds = rl; }
+}
+
+// ---------------------------------------------------------------- K0
+// p_dmin (Eq. pdmin) and lumped pore volume per vertex, parity-split order.
+__global__ void k_vertex_setup(Dims d, const double* __restrict__ pd, const double* __restrict__ phi,
+                               double vol, double* __restrict__ pdmin, double* __restrict__ phiv) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= d.nv) return;
+  int i, j, k;
+  pcoords(d, p, i, j, k);
+  const int cx = d.nx - 1, cy = d.ny - 1, cz = d.dim == 3 ? d.nz - 1 : 1;
+  const double frac = d.dim == 3 ? 0.125 : 0.25;
+  double best = INFINITY, s = 0.0;
+  for (int c = 0; c < (1 << d.dim); ++c) {
+    int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = d.dim == 3 ? k - ((c >> 2) & 1) : 0;
+    if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+    int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+    best = fmin(best, pd[cell]);
+    s += phi[cell] * vol * frac;
+  }
+  pdmin[p] = best;
+  phiv[p] = s;
+}
+
+// natural <-> parity-split permutation of interleaved pairs / bytes
+__global__ void k_perm_to_p(Dims d, const double2* __restrict__ nat, double2* __restrict__ out) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= d.nv) return;
+  int i = (int)(v % d.nx);
+  int64_t line = v / d.nx;
+  out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat[v];
+}
+
+__global__ void k_perm_from_p(Dims d, const double2* __restrict__ pl, double2* __restrict__ nat) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= d.nv) return;
+  int i = (int)(v % d.nx);
+  int64_t line = v / d.nx;
+  nat[v] = pl[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))];
+}
+
+__global__ void k_perm_bytes_to_p(Dims d, const uint8_t* __restrict__ nat, uint8_t* __restrict__ out) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= d.nv) return;
+  int i = (int)(v % d.nx);
+  int64_t line = v / d.nx;
+  out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat ? nat[v] : 0;
+}
+
+__global__ void k_perm_scalar_to_p(Dims d, const double* __restrict__ nat, double* __restrict__ out) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= d.nv) return;
+  int i = (int)(v % d.nx);
+  int64_t line = v / d.nx;
+  out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat ? nat[v] : 0.0;
+}
+
+// ---------------------------------------------------------------- K1a
+// Per-vertex quantities of the state (parity-split order): S_e, p_n = p_w +
+// p_c, p_c, dp_c/dS_n, k_rw, dk_rw/dS_n.
+__global__ void k_vertex_state(Dims d, Phys ph, const double2* __restrict__ u, const double* __restrict__ pdmin,
+                               double* __restrict__ Se, double* __restrict__ pn, double* __restrict__ pc,
+                               double* __restrict__ dpc, double* __restrict__ krw, double* __restrict__ dkrw) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= d.nv) return;
+  double2 uv = u[p];
+  double se = (1.0 - uv.y - ph.S_wr) / ph.den;
+  double J, dJ, k, dk;
+  leverett(ph.lam, se, J, dJ);
+  krw_of(ph.lam, se, k, dk);
+  double pdm = pdmin[p];
+  double c = pdm * J;
+  Se[p] = se;
+  pc[p] = c;
+  dpc[p] = -(pdm * dJ) / ph.den;
+  pn[p] = uv.x + c;
+  krw[p] = k;
+  dkrw[p] = -dk / ph.den;
+}
+
+// ---------------------------------------------------------------- K1 / K1r
+struct AsmIn {
+  const double2* u;
+  const double *Se, *pn, *pc, *dpc, *krw, *dkrw, *pdmin, *phiv;
+  const double *K, *pd;           // per cell (natural cell order)
+  const uint8_t* dir;             // parity-split
+  const double* pw_dir;           // parity-split
+  const double2* q_in;            // parity-split (may be null)
+};
+
+template <int DIM, bool WANT_J>
+__global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, double2* __restrict__ F,
+                                                  double* __restrict__ J, double2* __restrict__ mdiag) {
+  extern __shared__ double acc[];  // [nb*4][blockDim]
+  constexpr int NC = 1 << DIM, NE = 1 << (DIM - 1), NB = DIM == 3 ? 27 : 9;
+  const int tid = threadIdx.x, BS = blockDim.x;
+  int64_t p = blockIdx.x * (int64_t)BS + tid;
+  const bool live = p < d.nv;
+  if (WANT_J) {
+#pragma unroll 4
+    for (int t = 0; t < NB * 4; ++t) acc[t * BS + tid] = 0.0;
+  }
+  if (!live) return;
+  int i, j, k;
+  pcoords(d, p, i, j, k);
+  const int cx = d.nx - 1, cy = d.ny - 1, cz = DIM == 3 ? d.nz - 1 : 1;
+  double F0 = 0.0, F1 = 0.0;
+  if (in.q_in) { double2 q = in.q_in[p]; F0 = q.x; F1 = q.y; }
+  const double neg_inv_den = -1.0 / ph.den;
+
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    // element whose corner c (bits: x,y,z offsets) is this vertex
+    const int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = DIM == 3 ? k - ((c >> 2) & 1) : 0;
+    if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+    const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+    const double Kc = in.K[cell], pdc = in.pd[cell];
+    int64_t vq[NC];
+    double se[NC], pnq[NC], pcq[NC], dpcq[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      vq[q] = pidx(d, ci + (q & 1), cj + ((q >> 1) & 1), DIM == 3 ? ck + ((q >> 2) & 1) : 0);
+      se[q] = in.Se[vq[q]];
+      pnq[q] = in.pn[vq[q]];
+      pcq[q] = in.pc[vq[q]];
+      dpcq[q] = in.dpc[vq[q]];
+    }
+#pragma unroll
+    for (int kk = 0; kk < DIM; ++kk) {
+      // the face of this element along axis kk through this vertex's edge
+      int oth[2], no = 0;
+#pragma unroll
+      for (int m = 0; m < DIM; ++m)
+        if (m != kk) oth[no++] = m;
+      double Af = 1.0;
+#pragma unroll
+      for (int t = 0; t < DIM - 1; ++t) Af = Af * (ph.h[oth[t]] * 0.5);
+      const double KA = Kc * Af;
+      int o[2] = {0, 0};
+#pragma unroll
+      for (int t = 0; t < DIM - 1; ++t) o[t] = (c >> oth[t]) & 1;
+      const int a = c & ~(1 << kk), b = c | (1 << kk);
+      const double sgn = ((c >> kk) & 1) ? 1.0 : -1.0;  // this vertex is b: +flux, a: -flux
+      double gpn = 0.0, gpc = 0.0;
+#pragma unroll
+      for (int e2 = 0; e2 < NE; ++e2) {
+        int o2[2] = {e2 & 1, (e2 >> 1) & 1};
+        double w = 1.0;
+        int a2 = 0;
+#pragma unroll
+        for (int t = 0; t < DIM - 1; ++t) {
+          w = w * (o2[t] == o[t] ? 0.75 : 0.25);
+          a2 |= o2[t] << oth[t];
+        }
+        const int b2 = a2 | (1 << kk);
+        gpn = gpn + w * (pnq[b2] - pnq[a2]);
+        gpc = gpc + w * (pcq[b2] - pcq[a2]);
+      }
+      gpn = gpn / ph.h[kk];
+      gpc = gpc / ph.h[kk];
+      double wM[NC], SeM = 0.0;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        double w = 0.5;
+#pragma unroll
+        for (int t = 0; t < DIM - 1; ++t) w = w * ((((q >> oth[t]) & 1) == o[t]) ? 0.75 : 0.25);
+        wM[q] = w;
+        SeM = SeM + w * se[q];
+      }
+      const double Tw = -KA * (gpn - ph.rho_w * ph.g[kk]);
+      const double Tn = -KA * (gpn - ph.rho_n * ph.g[kk]);
+      const double Tc = -KA * gpc;
+      const bool wa = Tw >= 0.0, na = Tn >= 0.0;
+      const int64_t vw = wa ? vq[a] : vq[b];
+      const int64_t vn = na ? vq[a] : vq[b];
+      const double lw_up = in.krw[vw] / ph.mu_w;
+      double kM, dkM;
+      krw_of(ph.lam, SeM, kM, dkM);
+      const double lwM = kM / ph.mu_w;
+      double sh, dsh, kn, dkn;
+      shat_of(ph.lam, in.Se[vn], pdc, in.pdmin[vn], sh, dsh);
+      krn_of(ph.lam, sh, kn, dkn);
+      const double ln_up = kn / ph.mu_n;
+      const double Fw = ph.rho_w * (lw_up * Tw - lwM * Tc);
+      const double Fn = ph.rho_n * (ln_up * Tn);
+      F0 += sgn * Fw;
+      F1 += sgn * Fn;
+      if (WANT_J) {
+        const double dlw_up = in.dkrw[vw] / ph.mu_w;
+        const double dlwM_dSeM = dkM / ph.mu_w;
+        const double dln_up = dkn * dsh * neg_inv_den / ph.mu_n;
+        const int qw = wa ? a : b, qn = na ? a : b;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          double w = 1.0;
+#pragma unroll
+          for (int t = 0; t < DIM - 1; ++t) w = w * ((((q >> oth[t]) & 1) == o[t]) ? 0.75 : 0.25);
+          const double gq = (((q >> kk) & 1) ? w : -w) / ph.h[kk];
+          const double dT = -KA * gq;
+          const double dlwM = wM[q] * dlwM_dSeM * neg_inv_den;
+          const double d0 = ph.rho_w * lw_up * dT;
+          const double d1 = ph.rho_w * ((q == qw ? dlw_up * Tw : 0.0) + lw_up * dT * dpcq[q] - dlwM * Tc -
+                                        lwM * dT * dpcq[q]);
+          const double d2 = ph.rho_n * ln_up * dT;
+          const double d3 = ph.rho_n * ((q == qn ? dln_up * Tn : 0.0) + ln_up * dT * dpcq[q]);
+          const int dx = (q & 1) - (c & 1), dy = ((q >> 1) & 1) - ((c >> 1) & 1),
+                    dz = DIM == 3 ? ((q >> 2) & 1) - ((c >> 2) & 1) : 0;
+          const int bi = blk_of(DIM, dx, dy, dz);
+          double* r = acc + (bi * 4) * BS + tid;
+          r[0] += sgn * d0;
+          r[BS] += sgn * d1;
+          r[2 * BS] += sgn * d2;
+          r[3 * BS] += sgn * d3;
+        }
+      }
+    }
+  }
+  const bool dirv = in.dir[p] != 0;
+  if (dirv) F0 = in.pw_dir[p] - in.u[p].x;
+  F[p] = make_double2(F0, F1);
+  if (WANT_J) {
+    const double pv = in.phiv[p];
+    mdiag[p] = make_double2(dirv ? 0.0 : -ph.rho_w * pv, ph.rho_n * pv);
+    const int centre = DIM == 3 ? 13 : 4;
+#pragma unroll 3
+    for (int bi = 0; bi < NB; ++bi) {
+      double e0 = acc[(bi * 4 + 0) * BS + tid], e1 = acc[(bi * 4 + 1) * BS + tid];
+      double e2 = acc[(bi * 4 + 2) * BS + tid], e3 = acc[(bi * 4 + 3) * BS + tid];
+      if (dirv) { e0 = (bi == centre) ? -1.0 : 0.0; e1 = 0.0; }
+      double2* dst = reinterpret_cast<double2*>(J + ((int64_t)bi * d.nv + p) * 4);
+      dst[0] = make_double2(e0, e1);
+      dst[1] = make_double2(e2, e3);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_vertex_setup(const Dims& d, const double* pd, const double* phi, double vol, double* pdmin,
+                         double* phiv, void* s) {
+  RF_LAUNCH(k_vertex_setup, (int)((d.nv + 255) / 256), 256, 0, s, d, pd, phi, vol, pdmin, phiv);
+}
+
+void launch_perm_to_p(const Dims& d, const double* nat, double* out, void* s) {
+  RF_LAUNCH(k_perm_to_p, (int)((d.nv + 255) / 256), 256, 0, s, d, (const double2*)nat, (double2*)out);
+}
+void launch_perm_from_p(const Dims& d, const double* pl, double* nat, void* s) {
+  RF_LAUNCH(k_perm_from_p, (int)((d.nv + 255) / 256), 256, 0, s, d, (const double2*)pl, (double2*)nat);
+}
+void launch_perm_bytes_to_p(const Dims& d, const uint8_t* nat, uint8_t* out, void* s) {
+  RF_LAUNCH(k_perm_bytes_to_p, (int)((d.nv + 255) / 256), 256, 0, s, d, nat, out);
+}
+void launch_perm_scalar_to_p(const Dims& d, const double* nat, double* out, void* s) {
+  RF_LAUNCH(k_perm_scalar_to_p, (int)((d.nv + 255) / 256), 256, 0, s, d, nat, out);
+}
+
+cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays& a, bool want_j, void* s) {
+  Phys ph;
+  ph.rho_w = pp.rho_w; ph.rho_n = pp.rho_n; ph.mu_w = pp.mu_w; ph.mu_n = pp.mu_n;
+  ph.S_wr = pp.S_wr; ph.S_nr = pp.S_nr; ph.lam = pp.lambda;
+  ph.den = 1.0 - pp.S_wr - pp.S_nr;
+  for (int t = 0; t < 3; ++t) { ph.h[t] = pp.h[t]; ph.g[t] = pp.g[t]; }
+  const int nblk = (int)((d.nv + 255) / 256);
+  RF_LAUNCH(k_vertex_state, nblk, 256, 0, s, d, ph, (const double2*)a.u, a.pdmin, a.Se, a.pn, a.pc, a.dpc,
+            a.krw, a.dkrw);
+  AsmIn in;
+  in.u = (const double2*)a.u; in.Se = a.Se; in.pn = a.pn; in.pc = a.pc; in.dpc = a.dpc; in.krw = a.krw;
+  in.dkrw = a.dkrw; in.pdmin = a.pdmin; in.phiv = a.phiv; in.K = a.K; in.pd = a.pd; in.dir = a.dir;
+  in.pw_dir = a.pw_dir; in.q_in = (const double2*)a.q_in;
+  const int BS = 128;
+  const int grid = (int)((d.nv + BS - 1) / BS);
+  const int nb = d.dim == 3 ? 27 : 9;
+  size_t smem = want_j ? (size_t)nb * 4 * BS * sizeof(double) : 0;
+  if (d.dim == 3) {
+    if (want_j) {
+      cudaFuncSetAttribute(k_assemble<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      RF_LAUNCH((k_assemble<3, true>), grid, BS, smem, s, d, ph, in, (double2*)a.F, a.J, (double2*)a.mdiag);
+    } else {
+      RF_LAUNCH((k_assemble<3, false>), grid, BS, 0, s, d, ph, in, (double2*)a.F, a.J, (double2*)a.mdiag);
+    }
+  } else {
+    if (want_j) {
+      cudaFuncSetAttribute(k_assemble<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      RF_LAUNCH((k_assemble<2, true>), grid, BS, smem, s, d, ph, in, (double2*)a.F, a.J, (double2*)a.mdiag);
+    } else {
+      RF_LAUNCH((k_assemble<2, false>), grid, BS, 0, s, d, ph, in, (double2*)a.F, a.J, (double2*)a.mdiag);
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rf

@@ -1,0 +1,858 @@
+// driver.cu — host side of the C ABI (include/rf.h): grid lifetime, memory,
+// the multigrid set-up, the V-cycle schedule, the BiCGSTAB iteration and the
+// LIMEX step.  Every arithmetic step on grid data runs in the kernels of
+// assemble.cu, levelops.cu and krylov.cu; this file only sequences launches
+// and moves scalars (convergence flags, the error estimate) to the host.
+#include <atomic>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rf.h"
+#include "rf_common.cuh"
+#include "rf_kernels.h"
+
+namespace rf {
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+int grid_for(int64_t n, int block, int max_blocks_per_sm) {
+  int64_t b = (n + block - 1) / block;
+  int64_t cap = (int64_t)num_sms() * max_blocks_per_sm;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace rf
+
+using namespace rf;
+
+static thread_local std::string t_err;
+
+static rf_status fail(rf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+#define CU(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) return fail(RF_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Level {
+  Dims d;
+  Nbr nb;
+  int64_t pad = 0;
+  uint8_t* dmask = nullptr;
+  double* Jc = nullptr;  // FP64 Galerkin J (levels >= 1)
+  double* Mc = nullptr;  // FP64 Galerkin M, S_n column (levels >= 1)
+  void* A[RF_MAXSHIFT] = {};
+  float* scale[RF_MAXSHIFT] = {};
+  void* Dinv[RF_MAXSHIFT] = {};
+  void *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+};
+
+struct Alloc {
+  void* p;
+  size_t bytes;
+};
+
+struct rf_grid {
+  rf_allocator alloc{};
+  bool user_alloc = false;
+  std::vector<Alloc> bufs;   // lifetime of the grid
+  std::vector<Alloc> gbufs;  // lifetime of the multigrid hierarchy
+  Dims d;
+  Nbr nb;
+  PhysParams pp;
+  double h[3], g[3];
+  int64_t ncell = 0;
+  double *Kcell = nullptr, *phi = nullptr, *pd = nullptr;
+  uint8_t* dir = nullptr;
+  double *pw_dir = nullptr, *q_in = nullptr;
+  double *pdmin = nullptr, *phiv = nullptr;
+  double *J = nullptr, *mdiag = nullptr;
+  bool have_J = false;
+  double *Se, *pn, *pc, *dpc, *krw, *dkrw;
+  double *u_p = nullptr, *F_p = nullptr, *nat_a = nullptr, *nat_b = nullptr;
+  // multigrid
+  bool gmg_ready = false;
+  rf_gmg_opts gopt{};
+  int kind = STORE_F64;
+  int nshift = 0;
+  double shifts[RF_MAXSHIFT] = {};
+  int nl = 0;
+  Level L[RF_MAXL];
+  double* Ainv[RF_MAXSHIFT] = {};
+  // Krylov
+  KrylovVecs K{};
+  double2* b_p = nullptr;
+  double* hscal = nullptr;  // pinned host copy of the scalars
+  // LIMEX
+  double* T = nullptr;
+  int T_kappa = 0;
+  double* du = nullptr;
+  double* norms = nullptr;
+};
+
+// ------------------------------------------------------------------ memory
+static void* dalloc(rf_grid* g, size_t bytes, void* stream, bool hierarchy) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  void* p = nullptr;
+  if (g->user_alloc) {
+    p = g->alloc.alloc(bytes, stream, g->alloc.ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) (hierarchy ? g->gbufs : g->bufs).push_back({p, bytes});
+  return p;
+}
+
+static void dfree_all(rf_grid* g, std::vector<Alloc>& v, void* stream) {
+  for (auto& a : v) {
+    if (g->user_alloc) g->alloc.free(a.p, a.bytes, stream, g->alloc.ctx);
+    else cudaFree(a.p);
+  }
+  v.clear();
+}
+
+// padded vector of nv pairs of `elem` bytes; returns the interior pointer
+static void* dvec(rf_grid* g, const Dims& d, size_t elem, void* stream, bool hierarchy, int64_t* pad_out = nullptr) {
+  const int64_t pad = vec_pad(d);
+  const size_t bytes = (size_t)(d.nv + 2 * pad) * 2 * elem;
+  char* base = (char*)dalloc(g, bytes, stream, hierarchy);
+  if (!base) return nullptr;
+  if (cudaMemsetAsync(base, 0, bytes, (cudaStream_t)stream) != cudaSuccess) return nullptr;
+  if (pad_out) *pad_out = pad;
+  return base + (size_t)pad * 2 * elem;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// copy `bytes` from a host or device source into device memory `dst`
+static cudaError_t to_device(void* dst, const void* src, size_t bytes, void* stream) {
+  return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         (cudaStream_t)stream);
+}
+
+// natural-order pairs (host or device) -> parity-split device pairs
+static rf_status pairs_in(rf_grid* g, const Dims& d, const double* src, double* dst_p, void* s) {
+  if (is_device_ptr(src)) {
+    launch_perm_to_p(d, src, dst_p, s);
+  } else {
+    CU(cudaMemcpyAsync(g->nat_a, src, sizeof(double) * 2 * d.nv, cudaMemcpyHostToDevice, (cudaStream_t)s));
+    launch_perm_to_p(d, g->nat_a, dst_p, s);
+  }
+  CU(cudaGetLastError());
+  return RF_OK;
+}
+
+// parity-split device pairs -> natural-order pairs (host or device); syncs for host
+static rf_status pairs_out(rf_grid* g, const Dims& d, const double* src_p, double* dst, void* s) {
+  if (is_device_ptr(dst)) {
+    launch_perm_from_p(d, src_p, dst, s);
+    CU(cudaGetLastError());
+  } else {
+    launch_perm_from_p(d, src_p, g->nat_b, s);
+    CU(cudaMemcpyAsync(dst, g->nat_b, sizeof(double) * 2 * d.nv, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaStreamSynchronize((cudaStream_t)s));
+  }
+  return RF_OK;
+}
+
+// ------------------------------------------------------------------ ABI: grid
+extern "C" int64_t rf_launch_count(void) { return g_launches.load(); }
+extern "C" const char* rf_last_error(void) { return t_err.c_str(); }
+extern "C" int64_t rf_grid_nv(const rf_grid* g) { return g ? g->d.nv : 0; }
+
+extern "C" const char* rf_status_string(rf_status s) {
+  switch (s) {
+    case RF_OK: return "ok";
+    case RF_EINVAL: return "invalid argument";
+    case RF_ENOMEM: return "out of device memory";
+    case RF_ECUDA: return "CUDA error";
+    case RF_ENOTCONV: return "linear solver did not converge";
+    case RF_EBREAKDOWN: return "BiCGSTAB breakdown";
+    case RF_ENONFINITE: return "non-finite value";
+    case RF_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+extern "C" void rf_grid_destroy(rf_grid* g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  dfree_all(g, g->gbufs, nullptr);
+  dfree_all(g, g->bufs, nullptr);
+  if (g->hscal) cudaFreeHost(g->hscal);
+  delete g;
+}
+
+#define NEED(ptr)                                                  \
+  do {                                                             \
+    if (!(ptr)) { rf_grid_destroy(g); return fail(RF_ENOMEM, "device allocation failed (%s)", #ptr); } \
+  } while (0)
+
+extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* fl, const rf_materials* mat,
+                                    const rf_bc* bc, const rf_allocator* alloc, void* stream, rf_grid** out) {
+  if (!out) return fail(RF_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!desc || !fl || !mat) return fail(RF_EINVAL, "desc, fluids and materials are required");
+  if (desc->dim != 2 && desc->dim != 3) return fail(RF_EINVAL, "dim must be 2 or 3");
+  for (int a = 0; a < 3; ++a) {
+    const bool active = a < desc->dim;
+    if (active && (desc->n[a] < 2 || desc->n[a] > (1 << 20))) return fail(RF_EINVAL, "n[%d] out of range", a);
+    if (!active && desc->n[a] != 1) return fail(RF_EINVAL, "n[2] must be 1 in 2D");
+    if (active && !(desc->h[a] > 0.0)) return fail(RF_EINVAL, "h[%d] must be positive", a);
+  }
+  const int64_t nv = desc->n[0] * desc->n[1] * desc->n[2];
+  if (nv > ((int64_t)1 << 31)) return fail(RF_EINVAL, "grid too large (%lld vertices)", (long long)nv);
+  if (!(fl->rho_w > 0 && fl->rho_n > 0 && fl->mu_w > 0 && fl->mu_n > 0)) return fail(RF_EINVAL, "fluid properties must be positive");
+  if (!(mat->S_wr >= 0 && mat->S_nr >= 0 && mat->S_wr + mat->S_nr < 1.0 && mat->lambda > 0))
+    return fail(RF_EINVAL, "Brooks-Corey parameters out of range");
+  if (!mat->K || !mat->phi || !mat->pd) return fail(RF_EINVAL, "material arrays are required");
+  if (alloc && (!alloc->alloc || !alloc->free)) return fail(RF_EINVAL, "allocator needs alloc and free");
+
+  rf_grid* g = new rf_grid();
+  if (alloc) { g->alloc = *alloc; g->user_alloc = true; }
+  int n[3] = {(int)desc->n[0], (int)desc->n[1], (int)desc->n[2]};
+  g->d = make_dims(desc->dim, n);
+  g->nb = make_nbr(g->d);
+  for (int a = 0; a < 3; ++a) { g->h[a] = desc->h[a]; g->g[a] = desc->g[a]; g->pp.h[a] = desc->h[a]; g->pp.g[a] = desc->g[a]; }
+  g->pp.rho_w = fl->rho_w; g->pp.rho_n = fl->rho_n; g->pp.mu_w = fl->mu_w; g->pp.mu_n = fl->mu_n;
+  g->pp.S_wr = mat->S_wr; g->pp.S_nr = mat->S_nr; g->pp.lambda = mat->lambda;
+  g->ncell = (int64_t)(n[0] - 1) * (n[1] - 1) * (desc->dim == 3 ? n[2] - 1 : 1);
+  const Dims& d = g->d;
+  const size_t cb = sizeof(double) * g->ncell;
+
+  NEED(g->Kcell = (double*)dalloc(g, cb, stream, false));
+  NEED(g->phi = (double*)dalloc(g, cb, stream, false));
+  NEED(g->pd = (double*)dalloc(g, cb, stream, false));
+  CU(to_device(g->Kcell, mat->K, cb, stream));
+  CU(to_device(g->phi, mat->phi, cb, stream));
+  CU(to_device(g->pd, mat->pd, cb, stream));
+
+  NEED(g->nat_a = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  NEED(g->nat_b = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  NEED(g->dir = (uint8_t*)dalloc(g, nv, stream, false));
+  NEED(g->pw_dir = (double*)dalloc(g, sizeof(double) * nv, stream, false));
+  const uint8_t* dir_src = nullptr;
+  const double* pwd_src = nullptr;
+  if (bc && bc->dir_pw) {
+    CU(to_device(g->nat_a, bc->dir_pw, nv, stream));
+    dir_src = (const uint8_t*)g->nat_a;
+  }
+  launch_perm_bytes_to_p(d, dir_src, g->dir, stream);
+  if (bc && bc->pw_dir) {
+    CU(to_device(g->nat_b, bc->pw_dir, sizeof(double) * nv, stream));
+    pwd_src = g->nat_b;
+  }
+  launch_perm_scalar_to_p(d, pwd_src, g->pw_dir, stream);
+  CU(cudaStreamSynchronize((cudaStream_t)stream));
+  if (bc && bc->q_in) {
+    NEED(g->q_in = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+    rf_status st = pairs_in(g, d, bc->q_in, g->q_in, stream);
+    if (st != RF_OK) { rf_grid_destroy(g); return st; }
+  }
+  NEED(g->pdmin = (double*)dalloc(g, sizeof(double) * nv, stream, false));
+  NEED(g->phiv = (double*)dalloc(g, sizeof(double) * nv, stream, false));
+  const double vol = g->h[0] * g->h[1] * (d.dim == 3 ? g->h[2] : 1.0);
+  launch_vertex_setup(d, g->pd, g->phi, vol, g->pdmin, g->phiv, stream);
+
+  NEED(g->J = (double*)dalloc(g, sizeof(double) * 4 * d.nb * nv, stream, false));
+  NEED(g->mdiag = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  double** scratch[6] = {&g->Se, &g->pn, &g->pc, &g->dpc, &g->krw, &g->dkrw};
+  for (auto p : scratch) NEED(*p = (double*)dalloc(g, sizeof(double) * nv, stream, false));
+  NEED(g->u_p = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  NEED(g->F_p = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  // Krylov FP64 vectors (x padded: the outer operator reads it for the true residual)
+  NEED(g->K.x = (double2*)dvec(g, d, sizeof(double), stream, false));
+  double2** kv[6] = {&g->K.r, &g->K.rh, &g->K.p, &g->K.v, &g->K.s, &g->K.t};
+  for (auto p : kv) NEED(*p = (double2*)dalloc(g, sizeof(double2) * nv, stream, false));
+  NEED(g->b_p = (double2*)dalloc(g, sizeof(double2) * nv, stream, false));
+  NEED(g->du = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
+  NEED(g->K.partial = (double*)dalloc(g, sizeof(double) * 16 * 2048, stream, false));
+  NEED(g->K.scal = (double*)dalloc(g, sizeof(double) * 32, stream, false));
+  NEED(g->norms = (double*)dalloc(g, sizeof(double) * 8, stream, false));
+  if (cudaMallocHost((void**)&g->hscal, sizeof(double) * 32) != cudaSuccess) {
+    cudaGetLastError();
+    g->hscal = nullptr;
+    rf_grid_destroy(g);
+    return fail(RF_ENOMEM, "pinned host allocation failed");
+  }
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) { rf_grid_destroy(g); return fail(RF_ECUDA, "grid set-up: %s", cudaGetErrorString(e)); }
+  *out = g;
+  return RF_OK;
+}
+
+// ------------------------------------------------------------------ assembly
+static rf_status assemble_p(rf_grid* g, bool want_j, void* s) {
+  AsmArrays a;
+  a.u = g->u_p; a.Se = g->Se; a.pn = g->pn; a.pc = g->pc; a.dpc = g->dpc; a.krw = g->krw; a.dkrw = g->dkrw;
+  a.pdmin = g->pdmin; a.phiv = g->phiv; a.K = g->Kcell; a.pd = g->pd; a.dir = g->dir; a.pw_dir = g->pw_dir;
+  a.q_in = g->q_in; a.F = g->F_p; a.J = want_j ? g->J : nullptr; a.mdiag = want_j ? g->mdiag : nullptr;
+  cudaError_t e = launch_assemble(g->d, g->pp, a, want_j, s);
+  if (e != cudaSuccess) return fail(RF_ECUDA, "assembly launch: %s", cudaGetErrorString(e));
+  if (want_j) { g->have_J = true; g->gmg_ready = false; }
+  return RF_OK;
+}
+
+extern "C" rf_status rf_assemble(rf_grid* g, const double* u, int want_jacobian, double* F_out, void* s) {
+  if (!g || !u) return fail(RF_EINVAL, "grid and u are required");
+  rf_status st = pairs_in(g, g->d, u, g->u_p, s);
+  if (st) return st;
+  if ((st = assemble_p(g, want_jacobian != 0, s))) return st;
+  if (F_out) return pairs_out(g, g->d, g->F_p, F_out, s);
+  return RF_OK;
+}
+
+// ------------------------------------------------------------------ multigrid set-up
+static size_t t_size(int kind) { return kind == STORE_F64 ? sizeof(double) : sizeof(float); }
+static size_t s_size(int kind) { return kind == STORE_F64 ? 8 : (kind == STORE_F32 ? 4 : 2); }
+
+static LevelOp level_op(rf_grid* g, int l, int sh) {
+  LevelOp op;
+  const Level& Lv = g->L[l];
+  op.d = Lv.d;
+  op.nb = Lv.nb;
+  op.kind = g->kind;
+  op.fine = (l == 0);
+  op.A = (l == 0) ? Lv.A[0] : Lv.A[sh];
+  op.scale = (l == 0) ? Lv.scale[0] : Lv.scale[sh];
+  op.mdiag = g->mdiag;
+  op.shift = g->shifts[sh];
+  op.Dinv = Lv.Dinv[sh];
+  op.dmask = Lv.dmask;
+  return op;
+}
+
+#define GNEED(ptr)                                                                     \
+  do {                                                                                 \
+    if (!(ptr)) { dfree_all(g, g->gbufs, s); return fail(RF_ENOMEM, "device allocation failed (%s)", #ptr); } \
+  } while (0)
+
+extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, const rf_gmg_opts* o, void* s) {
+  if (!g || !shifts || !o) return fail(RF_EINVAL, "grid, shifts and options are required");
+  if (!g->have_J) return fail(RF_EINVAL, "rf_assemble with want_jacobian must precede rf_gmg_setup");
+  if (nshift < 1 || nshift > RF_MAXSHIFT) return fail(RF_EINVAL, "nshift must be 1..4");
+  if (o->nlevels < 1 || o->nlevels > RF_MAXL) return fail(RF_EINVAL, "nlevels must be 1..%d", RF_MAXL);
+  if (o->smoother != RF_SMOOTH_JACOBI && o->smoother != RF_SMOOTH_GS8) return fail(RF_EINVAL, "unknown smoother");
+  if (o->nu1 < 1 || o->nu2 < 0 || o->nu1 > 16 || o->nu2 > 16) return fail(RF_EINVAL, "need 1 <= nu1 <= 16, 0 <= nu2 <= 16");
+  if (o->precision < RF_PREC_FP64 || o->precision > RF_PREC_FP16) return fail(RF_EINVAL, "unknown precision");
+  for (int j = 0; j < nshift; ++j)
+    if (!(shifts[j] >= 0.0) || !std::isfinite(shifts[j])) return fail(RF_EINVAL, "shifts must be finite and >= 0");
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  dfree_all(g, g->gbufs, s);
+  for (int l = 0; l < RF_MAXL; ++l) g->L[l] = Level();
+  for (int j = 0; j < RF_MAXSHIFT; ++j) g->Ainv[j] = nullptr;
+  g->gmg_ready = false;
+  g->gopt = *o;
+  g->kind = o->precision == RF_PREC_FP64 ? STORE_F64 : (o->precision == RF_PREC_FP32 ? STORE_F32 : STORE_F16);
+  g->nshift = nshift;
+  for (int j = 0; j < nshift; ++j) g->shifts[j] = shifts[j];
+
+  // level dimensions (vertex-nested: coarse vertex I at fine 2I)
+  int n[3] = {g->d.nx, g->d.ny, g->d.nz};
+  g->nl = 1;
+  g->L[0].d = g->d;
+  while (g->nl < o->nlevels) {
+    bool ok = true;
+    int nn[3];
+    for (int a = 0; a < 3; ++a) {
+      if (a >= g->d.dim) { nn[a] = 1; continue; }
+      if ((n[a] - 1) % 2 != 0 || n[a] < 3) ok = false;
+      nn[a] = (n[a] - 1) / 2 + 1;
+    }
+    if (!ok) break;
+    for (int a = 0; a < 3; ++a) n[a] = nn[a];
+    g->L[g->nl].d = make_dims(g->d.dim, n);
+    ++g->nl;
+  }
+  const int kind = g->kind;
+  for (int l = 0; l < g->nl; ++l) {
+    Level& Lv = g->L[l];
+    Lv.nb = make_nbr(Lv.d);
+    const Dims& d = Lv.d;
+    if (l == 0) {
+      Lv.dmask = g->dir;
+    } else {
+      GNEED(Lv.dmask = (uint8_t*)dalloc(g, d.nv, s, true));
+      launch_coarse_mask(g->L[l - 1].d, g->L[l - 1].dmask, d, Lv.dmask, s);
+      GNEED(Lv.Jc = (double*)dalloc(g, sizeof(double) * 4 * d.nb * d.nv, s, true));
+      GNEED(Lv.Mc = (double*)dalloc(g, sizeof(double) * 2 * d.nb * d.nv, s, true));
+      const Level& F = g->L[l - 1];
+      if (l == 1)
+        launch_galerkin(F.d, F.nb, F.dmask, g->J, nullptr, g->mdiag, d, Lv.dmask, Lv.Jc, Lv.Mc, s);
+      else
+        launch_galerkin(F.d, F.nb, F.dmask, F.Jc, F.Mc, nullptr, d, Lv.dmask, Lv.Jc, Lv.Mc, s);
+    }
+    const size_t te = t_size(kind), se = s_size(kind);
+    if (l < g->nl - 1 || g->nl == 1) {
+      // smoothed levels: storage + inverse diagonal blocks per shift
+      if (l == 0) {
+        if (kind == STORE_F64) {
+          Lv.A[0] = g->J;
+        } else {
+          GNEED(Lv.A[0] = dalloc(g, se * 4 * d.nb * d.nv, s, true));
+          if (kind == STORE_F16) GNEED(Lv.scale[0] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
+          launch_pack_level(d, true, g->J, nullptr, g->mdiag, 0.0, kind, Lv.A[0], Lv.scale[0], nullptr, s);
+        }
+        for (int j = 0; j < nshift; ++j) {
+          GNEED(Lv.Dinv[j] = dalloc(g, te * 4 * d.nv, s, true));
+          launch_pack_level(d, true, g->J, nullptr, g->mdiag, shifts[j], kind, nullptr, nullptr, Lv.Dinv[j], s);
+        }
+      } else {
+        for (int j = 0; j < nshift; ++j) {
+          GNEED(Lv.A[j] = dalloc(g, se * 4 * d.nb * d.nv, s, true));
+          if (kind == STORE_F16) GNEED(Lv.scale[j] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
+          GNEED(Lv.Dinv[j] = dalloc(g, te * 4 * d.nv, s, true));
+          launch_pack_level(d, false, Lv.Jc, Lv.Mc, nullptr, shifts[j], kind, Lv.A[j], Lv.scale[j], Lv.Dinv[j], s);
+        }
+      }
+    }
+    GNEED(Lv.x = dvec(g, d, te, s, true, &Lv.pad));
+    GNEED(Lv.b = dvec(g, d, te, s, true));
+    GNEED(Lv.r = dvec(g, d, te, s, true));
+    GNEED(Lv.t = dvec(g, d, te, s, true));
+  }
+  // coarsest level: dense FP64 operator per shift, LU with partial pivoting, explicit inverse
+  {
+    const Level& C = g->L[g->nl - 1];
+    const int N = (int)(2 * C.d.nv);
+    if (N > 4096) { dfree_all(g, g->gbufs, s); return fail(RF_EINVAL, "coarsest level too large (%d unknowns): use more levels", N); }
+    double* D;
+    double* work;
+    int* piv;
+    int* status;
+    GNEED(D = (double*)dalloc(g, sizeof(double) * N * N, s, true));
+    GNEED(work = (double*)dalloc(g, sizeof(double) * N * N, s, true));
+    GNEED(piv = (int*)dalloc(g, sizeof(int) * N, s, true));
+    GNEED(status = (int*)dalloc(g, sizeof(int), s, true));
+    for (int j = 0; j < nshift; ++j) {
+      GNEED(g->Ainv[j] = (double*)dalloc(g, sizeof(double) * N * N, s, true));
+      CU(cudaMemsetAsync(D, 0, sizeof(double) * N * N, (cudaStream_t)s));
+      CU(cudaMemsetAsync(status, 0, sizeof(int), (cudaStream_t)s));
+      if (g->nl == 1) launch_dense_coarsest(C.d, C.nb, g->J, nullptr, g->mdiag, true, shifts[j], D, s);
+      else launch_dense_coarsest(C.d, C.nb, C.Jc, C.Mc, nullptr, false, shifts[j], D, s);
+      CU(launch_dense_inverse(N, D, g->Ainv[j], piv, work, status, s));
+      int hst = 0;
+      CU(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)s));
+      CU(cudaStreamSynchronize((cudaStream_t)s));
+      if (hst) { dfree_all(g, g->gbufs, s); return fail(RF_ENONFINITE, "coarsest operator is singular (shift %d)", j); }
+    }
+  }
+  // Krylov preconditioned vectors in the preconditioner type
+  {
+    const size_t te = t_size(kind);
+    GNEED(g->K.y = dvec(g, g->d, te, s, true));
+    GNEED(g->K.z = dvec(g, g->d, te, s, true));
+    GNEED(g->K.p_lo = dvec(g, g->d, te, s, true));
+    GNEED(g->K.s_lo = dvec(g, g->d, te, s, true));
+  }
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  CU(cudaGetLastError());
+  g->gmg_ready = true;
+  return RF_OK;
+}
+
+// ------------------------------------------------------------------ V-cycle
+static void smooth_pre(rf_grid* g, int l, int sh, const void* b, void* x_final, void** cur, void* s) {
+  LevelOp op = level_op(g, l, sh);
+  Level& Lv = g->L[l];
+  const rf_gmg_opts& o = g->gopt;
+  const size_t te = t_size(g->kind);
+  if (o.smoother == RF_SMOOTH_JACOBI) {
+    const int W = o.nu1 + o.nu2;
+    void* first = (W % 2 == 1) ? x_final : Lv.t;
+    void* c = first;
+    launch_jacobi(op, b, nullptr, first, o.omega, true, s);
+    for (int k = 1; k < o.nu1; ++k) {
+      void* dst = (c == x_final) ? Lv.t : x_final;
+      launch_jacobi(op, b, c, dst, o.omega, false, s);
+      c = dst;
+    }
+    *cur = c;
+  } else {
+    cudaMemsetAsync(x_final, 0, (size_t)Lv.d.nv * 2 * te, (cudaStream_t)s);
+    for (int k = 0; k < o.nu1; ++k) launch_gs_sweep(op, b, x_final, true, k == 0, s);
+    *cur = x_final;
+  }
+}
+
+static void smooth_post(rf_grid* g, int l, int sh, const void* b, void* x_final, void* cur, void* s) {
+  LevelOp op = level_op(g, l, sh);
+  Level& Lv = g->L[l];
+  const rf_gmg_opts& o = g->gopt;
+  if (o.smoother == RF_SMOOTH_JACOBI) {
+    void* c = cur;
+    for (int k = 0; k < o.nu2; ++k) {
+      void* dst = (c == x_final) ? Lv.t : x_final;
+      launch_jacobi(op, b, c, dst, o.omega, false, s);
+      c = dst;
+    }
+  } else {
+    for (int k = 0; k < o.nu2; ++k) launch_gs_sweep(op, b, x_final, false, false, s);
+  }
+}
+
+static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void* s) {
+  if (l == g->nl - 1) {
+    launch_coarse_solve(level_op(g, l, sh), g->Ainv[sh], b, x, s);
+    return;
+  }
+  Level& Lv = g->L[l];
+  Level& Lc = g->L[l + 1];
+  void* cur = nullptr;
+  smooth_pre(g, l, sh, b, x, &cur, s);
+  LevelOp op = level_op(g, l, sh), opc = level_op(g, l + 1, sh);
+  launch_residual(op, b, cur, Lv.r, s);
+  launch_restrict(op, opc, Lv.r, Lc.b, s);
+  vcycle_level(g, l + 1, sh, Lc.b, Lc.x, s);
+  launch_prolong(op, opc, Lc.x, cur, s);
+  smooth_post(g, l, sh, b, x, cur, s);
+}
+
+// ------------------------------------------------------------------ BiCGSTAB
+enum { H_RHO = 0, H_RR = 5, H_BB = 6, H_CONV = 10, H_BAD = 11, H_TRUE = 12, H_BREAK = 13 };
+
+static rf_status read_scal(rf_grid* g, void* s) {
+  CU(cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return RF_OK;
+}
+
+// Solve A_sh x = b with b, x parity-split device pairs (x is g->K.x on return).
+static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info, void* s) {
+  const Dims& d = g->d;
+  const bool lo32 = g->kind != STORE_F64;
+  KrylovVecs& K = g->K;
+  const double shift = g->shifts[sh];
+  launch_bicg_init(d.nv, b, K, s);
+  rf_status st = read_scal(g, s);
+  if (st) return st;
+  const double bb = g->hscal[H_BB];
+  int it = 0, restarts = 0;
+  double relres = 0.0;
+  rf_status result = RF_ENOTCONV;
+  if (!std::isfinite(bb)) return fail(RF_ENONFINITE, "right-hand side is not finite");
+  if (bb == 0.0) {
+    result = RF_OK;
+  } else {
+    const double bn = std::sqrt(bb);
+    for (it = 1; it <= max_it; ++it) {
+      launch_bicg_p(d.nv, K, lo32, it == 1, s);
+      vcycle_level(g, 0, sh, K.p_lo, K.y, s);
+      launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+      launch_bicg_s(d.nv, K, lo32, s);
+      vcycle_level(g, 0, sh, K.s_lo, K.z, s);
+      launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+      launch_bicg_xr(d.nv, K, lo32, rtol, s);
+      if ((st = read_scal(g, s))) return st;
+      if (g->hscal[H_BAD] != 0.0) { result = RF_ENONFINITE; break; }
+      if (g->hscal[H_CONV] != 0.0 || g->hscal[H_BREAK] != 0.0) {
+        launch_true_residual(d, g->nb, g->J, g->mdiag, shift, b, K, s);
+        if ((st = read_scal(g, s))) return st;
+        relres = std::sqrt(g->hscal[H_TRUE]) / bn;
+        if (!std::isfinite(relres)) { result = RF_ENONFINITE; break; }
+        if (relres <= rtol) { result = RF_OK; break; }
+        if (++restarts > 20) { result = RF_EBREAKDOWN; break; }
+        launch_restart(d.nv, K, s);
+      }
+    }
+    if (it > max_it) it = max_it;
+    if (result != RF_OK && result != RF_ENONFINITE) {
+      launch_true_residual(d, g->nb, g->J, g->mdiag, shift, b, K, s);
+      if ((st = read_scal(g, s))) return st;
+      relres = std::sqrt(g->hscal[H_TRUE]) / bn;
+    }
+  }
+  if (info) { info->iterations = it; info->relres = relres; info->status = result; info->restarts = restarts; }
+  if (result == RF_ENOTCONV) return fail(result, "no convergence in %d iterations (relres %.3e)", max_it, relres);
+  if (result == RF_ENONFINITE) return fail(result, "non-finite value in the BiCGSTAB iteration");
+  if (result == RF_EBREAKDOWN) return fail(result, "BiCGSTAB breakdown after %d restarts", restarts);
+  return RF_OK;
+}
+
+extern "C" rf_status rf_solve(rf_grid* g, int sh, const double* b, double* x, const rf_solve_opts* o,
+                              rf_solve_info* info, void* s) {
+  if (!g || !b || !x || !o) return fail(RF_EINVAL, "grid, b, x and options are required");
+  if (!g->gmg_ready) return fail(RF_EINVAL, "rf_gmg_setup must precede rf_solve");
+  if (sh < 0 || sh >= g->nshift) return fail(RF_EINVAL, "shift index %d out of range", sh);
+  if (!(o->rtol > 0.0) || o->max_it < 1) return fail(RF_EINVAL, "need rtol > 0 and max_it >= 1");
+  rf_status st = pairs_in(g, g->d, b, (double*)g->b_p, s);
+  if (st) return st;
+  rf_status r = solve_p(g, sh, g->b_p, o->rtol, o->max_it, info, s);
+  if (r != RF_OK && r != RF_ENOTCONV) return r;
+  st = pairs_out(g, g->d, (const double*)g->K.x, x, s);
+  if (st) return st;
+  if (r == RF_ENOTCONV) return fail(r, "no convergence in %d iterations", o->max_it);
+  return RF_OK;
+}
+
+// ------------------------------------------------------------------ LIMEX
+extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* o, rf_limex_info* info,
+                                   void* s) {
+  if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
+  if (!(H > 0.0) || !std::isfinite(H)) return fail(RF_EINVAL, "H must be positive");
+  if (o->kappa < 1 || o->kappa > RF_MAXSHIFT) return fail(RF_EINVAL, "kappa must be 1..4");
+  if (!(o->tol > 0) || !(o->rho > 0) || !(o->fac_min > 0) || !(o->fac_max >= o->fac_min))
+    return fail(RF_EINVAL, "bad step-control parameters");
+  const Dims& d = g->d;
+  const int kap = o->kappa;
+  const size_t vb = sizeof(double) * 2 * d.nv;
+  if (!g->T || g->T_kappa < kap) {
+    g->T = (double*)dalloc(g, vb * kap, s, false);
+    if (!g->T) return fail(RF_ENOMEM, "LIMEX table allocation failed");
+    g->T_kappa = kap;
+  }
+  rf_status st = pairs_in(g, d, u, g->u_p, s);
+  if (st) return st;
+  // u0 is kept in column 0's slot until column 0 is computed: copy to nat_a as backup
+  double* u0 = g->nat_a;
+  CU(cudaMemcpyAsync(u0, g->u_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  if ((st = assemble_p(g, true, s))) return st;   // J, M, F(u0) in F_p
+  double* F0 = g->nat_b;
+  CU(cudaMemcpyAsync(F0, g->F_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  double shifts[RF_MAXSHIFT];
+  for (int j = 0; j < kap; ++j) shifts[j] = (double)(j + 1) / H;
+  if ((st = rf_gmg_setup(g, shifts, kap, &o->gmg, s))) return st;
+  int solves = 0, iters = 0;
+  rf_status worst = RF_OK;
+  for (int j = 0; j < kap; ++j) {
+    double* U = g->T + (size_t)j * 2 * d.nv;
+    CU(cudaMemcpyAsync(U, u0, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    for (int k = 0; k <= j; ++k) {
+      const double* F;
+      if (k == 0) {
+        F = F0;
+      } else {
+        CU(cudaMemcpyAsync(g->u_p, U, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+        if ((st = assemble_p(g, false, s))) return st;
+        F = g->F_p;
+      }
+      rf_solve_info si{};
+      rf_status r = solve_p(g, j, (const double2*)F, o->solve.rtol, o->solve.max_it, &si, s);
+      ++solves;
+      iters += si.iterations;
+      if (r != RF_OK) {
+        if (r != RF_ENOTCONV) return r;
+        worst = r;
+      }
+      launch_axpy_pairs(d.nv, (double2*)U, g->K.x, s);
+    }
+  }
+  launch_extrapolate(2 * d.nv, kap, g->T, s);
+  const double* Tkk = g->T;
+  const double* Tkk1 = g->T + 2 * d.nv;
+  launch_error_norms(d, g->h, Tkk, kap > 1 ? Tkk1 : Tkk, g->norms, g->K.partial, s);
+  double nrm[4];
+  CU(cudaMemcpyAsync(nrm, g->norms, sizeof nrm, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  double vol = 1.0;
+  for (int a = 0; a < d.dim; ++a) vol *= (double)((a == 0 ? d.nx : a == 1 ? d.ny : d.nz) - 1) * g->h[a];
+  const double alpha = 1.0 / (nrm[0] + 1e-30);
+  const double beta = 1.0 / (nrm[2] + 1e-4 * vol);
+  const double eps = std::sqrt((alpha * nrm[1] + beta * nrm[3]) / 2.0);
+  double fac = (eps > 0.0) ? std::pow(o->rho * o->tol / eps, 1.0 / 3.0) : o->fac_max;
+  if (fac > o->fac_max) fac = o->fac_max;
+  if (fac < o->fac_min) fac = o->fac_min;
+  const int acc = (eps <= o->tol) && worst == RF_OK;
+  if (acc) {
+    if ((st = pairs_out(g, d, Tkk, u, s))) return st;
+  }
+  if (info) {
+    info->eps = eps; info->H_new = H * fac; info->accepted = acc; info->solves = solves;
+    info->iterations = iters; info->status = worst;
+  }
+  if (!std::isfinite(eps)) return fail(RF_ENONFINITE, "error estimate is not finite");
+  return worst;
+}
+
+// ------------------------------------------------------------------ test hooks
+extern "C" rf_status rf_export_jacobian(rf_grid* g, double* J_host, double* md_host, void* s) {
+  if (!g) return fail(RF_EINVAL, "grid is required");
+  if (!g->have_J) return fail(RF_EINVAL, "no Jacobian assembled yet");
+  const Dims& d = g->d;
+  if (J_host) {
+    double* tmp = (double*)dalloc(g, sizeof(double) * 4 * d.nb * d.nv, s, true);
+    if (!tmp) return fail(RF_ENOMEM, "export buffer");
+    launch_export_level(d, true, g->J, nullptr, nullptr, 0.0, tmp, s);
+    CU(cudaMemcpyAsync(J_host, tmp, sizeof(double) * 4 * d.nb * d.nv, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaStreamSynchronize((cudaStream_t)s));
+    // keep the hierarchy list consistent: release just this buffer
+    Alloc a = g->gbufs.back();
+    g->gbufs.pop_back();
+    if (g->user_alloc) g->alloc.free(a.p, a.bytes, s, g->alloc.ctx); else cudaFree(a.p);
+  }
+  if (md_host) return pairs_out(g, d, g->mdiag, md_host, s);
+  return RF_OK;
+}
+
+static void* tmp_alloc(rf_grid* g, size_t bytes, void* s) {
+  void* p = dalloc(g, bytes, s, true);
+  return p;
+}
+static void tmp_release(rf_grid* g, int count, void* s) {
+  cudaStreamSynchronize((cudaStream_t)s);
+  for (int i = 0; i < count && !g->gbufs.empty(); ++i) {
+    Alloc a = g->gbufs.back();
+    g->gbufs.pop_back();
+    if (g->user_alloc) g->alloc.free(a.p, a.bytes, s, g->alloc.ctx); else cudaFree(a.p);
+  }
+}
+
+extern "C" rf_status rf_export_level(rf_grid* g, int level, int sh, double* A_host, int64_t dims_out[3], void* s) {
+  if (!g || !A_host) return fail(RF_EINVAL, "grid and output are required");
+  if (!g->gmg_ready) return fail(RF_EINVAL, "no multigrid hierarchy");
+  if (level < 0 || level >= g->nl || sh < 0 || sh >= g->nshift) return fail(RF_EINVAL, "level/shift out of range");
+  const Level& Lv = g->L[level];
+  const Dims& d = Lv.d;
+  if (dims_out) { dims_out[0] = d.nx; dims_out[1] = d.ny; dims_out[2] = d.nz; }
+  const size_t bytes = sizeof(double) * 4 * d.nb * d.nv;
+  double* tmp = (double*)tmp_alloc(g, bytes, s);
+  if (!tmp) return fail(RF_ENOMEM, "export buffer");
+  if (level == 0) launch_export_level(d, true, g->J, nullptr, g->mdiag, g->shifts[sh], tmp, s);
+  else launch_export_level(d, false, Lv.Jc, Lv.Mc, nullptr, g->shifts[sh], tmp, s);
+  cudaError_t e = cudaMemcpyAsync(A_host, tmp, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)s);
+  tmp_release(g, 1, s);
+  if (e != cudaSuccess) return fail(RF_ECUDA, "export copy: %s", cudaGetErrorString(e));
+  return RF_OK;
+}
+
+// host natural doubles -> level vector in the preconditioner type (parity split, padded)
+static rf_status level_in(rf_grid* g, const Dims& d, const double* host, void* dst, double* tmp_nat, double* tmp_p,
+                          void* s) {
+  CU(cudaMemcpyAsync(tmp_nat, host, sizeof(double) * 2 * d.nv, cudaMemcpyHostToDevice, (cudaStream_t)s));
+  if (g->kind == STORE_F64) {
+    launch_perm_to_p(d, tmp_nat, (double*)dst, s);
+  } else {
+    launch_perm_to_p(d, tmp_nat, tmp_p, s);
+    launch_cast_f64_to_f32(tmp_p, (float*)dst, 2 * d.nv, s);
+  }
+  return RF_OK;
+}
+
+static rf_status level_out(rf_grid* g, const Dims& d, const void* src, double* host, double* tmp_nat, double* tmp_p,
+                           void* s) {
+  const double* pp = (const double*)src;
+  if (g->kind != STORE_F64) {
+    launch_cast_f32_to_f64((const float*)src, tmp_p, 2 * d.nv, s);
+    pp = tmp_p;
+  }
+  launch_perm_from_p(d, pp, tmp_nat, s);
+  CU(cudaMemcpyAsync(host, tmp_nat, sizeof(double) * 2 * d.nv, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return RF_OK;
+}
+
+extern "C" rf_status rf_apply(rf_grid* g, int op, int level, int sh, const double* in0, const double* in1,
+                              double* out, void* s) {
+  if (!g || !in0 || !out) return fail(RF_EINVAL, "grid, in0 and out are required");
+  if (op == RF_OP_SPMV) {
+    if (!g->have_J) return fail(RF_EINVAL, "no Jacobian assembled");
+    if (!g->gmg_ready && sh != 0) return fail(RF_EINVAL, "shift index without hierarchy");
+  } else if (!g->gmg_ready) {
+    return fail(RF_EINVAL, "no multigrid hierarchy");
+  }
+  if (sh < 0 || (g->gmg_ready && sh >= g->nshift)) return fail(RF_EINVAL, "shift out of range");
+  if (level < 0 || level >= (g->gmg_ready ? g->nl : 1)) return fail(RF_EINVAL, "level out of range");
+  const bool two = (op == RF_OP_SMOOTH || op == RF_OP_RESIDUAL || op == RF_OP_PROLONG);
+  if (two && !in1) return fail(RF_EINVAL, "this operation needs in1");
+  if ((op == RF_OP_RESTRICT || op == RF_OP_PROLONG) && level >= g->nl - 1) return fail(RF_EINVAL, "no coarser level");
+  if (op == RF_OP_COARSE && level != g->nl - 1) return fail(RF_EINVAL, "RF_OP_COARSE works on the coarsest level");
+  const Dims& d = g->L[level].d;
+  const Dims& dc = (level + 1 < g->nl) ? g->L[level + 1].d : d;
+  const Dims& dl = (op == RF_OP_PROLONG) ? dc : d;   // dims of in0
+  const int64_t nmax = g->d.nv;
+  double* tnat = (double*)tmp_alloc(g, sizeof(double) * 2 * nmax, s);
+  double* tp = (double*)tmp_alloc(g, sizeof(double) * 2 * nmax, s);
+  const size_t te = t_size(g->kind);
+  void* v0 = dvec(g, g->d, te, s, true);
+  void* v1 = dvec(g, g->d, te, s, true);
+  void* v2 = dvec(g, g->d, te, s, true);
+  if (!tnat || !tp || !v0 || !v1 || !v2) { tmp_release(g, 5, s); return fail(RF_ENOMEM, "rf_apply buffers"); }
+  rf_status st = RF_OK;
+  if (op == RF_OP_SPMV) {
+    const double shift = g->gmg_ready ? g->shifts[sh] : 0.0;
+    double* xp = (double*)dvec(g, g->d, sizeof(double), s, true);
+    if (!xp) { tmp_release(g, 5, s); return fail(RF_ENOMEM, "rf_apply buffers"); }
+    CU(cudaMemcpyAsync(tnat, in0, sizeof(double) * 2 * d.nv, cudaMemcpyHostToDevice, (cudaStream_t)s));
+    launch_perm_to_p(d, tnat, xp, s);
+    launch_spmv64(d, g->nb, g->J, g->mdiag, shift, xp, false, (double2*)tp, s);
+    launch_perm_from_p(d, tp, tnat, s);
+    CU(cudaMemcpyAsync(out, tnat, sizeof(double) * 2 * d.nv, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaStreamSynchronize((cudaStream_t)s));
+    tmp_release(g, 6, s);
+    return RF_OK;
+  }
+  if ((st = level_in(g, dl, in0, v0, tnat, tp, s))) { tmp_release(g, 5, s); return st; }
+  if (two && (st = level_in(g, d, in1, v1, tnat, tp, s))) { tmp_release(g, 5, s); return st; }
+  LevelOp L = level_op(g, level, sh);
+  const Dims* dout = &d;
+  switch (op) {
+    case RF_OP_VCYCLE:
+      vcycle_level(g, 0, sh, v0, v2, s);
+      break;
+    case RF_OP_SMOOTH:
+      if (g->gopt.smoother == RF_SMOOTH_JACOBI) {
+        launch_jacobi(L, v0, v1, v2, g->gopt.omega, false, s);
+      } else {
+        CU(cudaMemcpyAsync(v2, v1, (size_t)d.nv * 2 * te, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+        launch_gs_sweep(L, v0, v2, true, false, s);
+      }
+      break;
+    case RF_OP_RESIDUAL:
+      launch_residual(L, v0, v1, v2, s);
+      break;
+    case RF_OP_RESTRICT:
+      launch_restrict(L, level_op(g, level + 1, sh), v0, v2, s);
+      dout = &dc;
+      break;
+    case RF_OP_PROLONG:
+      CU(cudaMemcpyAsync(v2, v1, (size_t)d.nv * 2 * te, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+      launch_prolong(L, level_op(g, level + 1, sh), v0, v2, s);
+      break;
+    case RF_OP_COARSE:
+      launch_coarse_solve(L, g->Ainv[sh], v0, v2, s);
+      break;
+    default:
+      tmp_release(g, 5, s);
+      return fail(RF_EINVAL, "unknown operation %d", op);
+  }
+  CU(cudaGetLastError());
+  st = level_out(g, *dout, v2, out, tnat, tp, s);
+  tmp_release(g, 5, s);
+  return st;
+}

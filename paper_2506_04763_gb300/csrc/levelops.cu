@@ -1,0 +1,691 @@
+// levelops.cu — geometric multigrid building blocks on the vertex-nested
+// hierarchy (the preconditioner of the BiCGSTAB stage solve; the paper's
+// Sec. 5 setup paragraph names BiCGSTAB + GMG without further detail):
+//   - residual r = b - A x, damped point-block Jacobi, multicolour block
+//     Gauss-Seidel (2^d colours by coordinate parity), all with the 2x2 block
+//     stencil read as coalesced 16/32-byte loads in parity-split order;
+//   - full-weighting restriction P^T and trilinear prolongation P (per
+//     component; Dirichlet p_w unknowns excluded from the correction space);
+//   - Galerkin coarse operators J_c = P^T J P, M_c = P^T M P in FP64;
+//   - packing of A = shift*M - J into FP64 / FP32 / FP16-with-row-scales
+//     storage and the 2x2 diagonal-block inverses;
+//   - the coarsest level's dense LU (partial pivoting) and explicit inverse.
+// All of these are HBM-bandwidth kernels except the set-up ones.
+#include "rf_common.cuh"
+#include "rf_kernels.h"
+
+namespace rf {
+
+// ----------------------------------------------------------------- loads
+template <int KIND> struct Ty;
+template <> struct Ty<STORE_F64> { typedef double T; typedef double S; };
+template <> struct Ty<STORE_F32> { typedef float T; typedef float S; };
+template <> struct Ty<STORE_F16> { typedef float T; typedef __half S; };
+
+// Streaming read of matrix data: read-only path, do not keep in L1.
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double2 ld_stream_d2(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+  return v;
+}
+
+template <int KIND>
+__device__ __forceinline__ void load_block(const void* A, int64_t nv, int b, int64_t p, const float4& sc,
+                                           typename Ty<KIND>::T (&a)[4]) {
+  const int64_t o = (int64_t)b * nv + p;
+  if (KIND == STORE_F64) {
+    const double2* q = reinterpret_cast<const double2*>(A) + o * 2;
+    double2 u = ld_stream_d2(q), w = ld_stream_d2(q + 1);
+    a[0] = u.x; a[1] = u.y; a[2] = w.x; a[3] = w.y;
+  } else if (KIND == STORE_F32) {
+    float4 u = ld_stream_f4(reinterpret_cast<const float4*>(A) + o);
+    a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+  } else {
+    uint2 u = ld_stream_u2(reinterpret_cast<const uint2*>(A) + o);
+    __half2 h01 = *reinterpret_cast<__half2*>(&u.x), h23 = *reinterpret_cast<__half2*>(&u.y);
+    float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+    a[0] = f01.x * sc.x; a[1] = f01.y * sc.y; a[2] = f23.x * sc.z; a[3] = f23.y * sc.w;
+  }
+}
+
+// sum over the stencil of blocks * x (centre optionally skipped)
+template <int KIND, int NB>
+__device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par,
+                                            const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                            bool skip_centre, typename Ty<KIND>::T& s0,
+                                            typename Ty<KIND>::T& s1) {
+  typedef typename Ty<KIND>::T T;
+  constexpr int C = NB == 27 ? 13 : 4;
+  float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (KIND == STORE_F16) sc = reinterpret_cast<const float4*>(L.scale)[p];
+  T a0 = 0, a1 = 0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (skip_centre && b == C) continue;
+    T a[4];
+    load_block<KIND>(L.A, L.d.nv, b, p, sc, a);
+    const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
+    const typename V2<T>::t xv = x[p + off];
+    a0 += a[0] * xv.x + a[1] * xv.y;
+    a1 += a[2] * xv.x + a[3] * xv.y;
+  }
+  s0 = a0; s1 = a1;
+}
+
+// (A x)_p, with A = shift*M - J on the fine level (blocks hold J)
+template <int KIND, bool FINE, int NB>
+__device__ __forceinline__ void apply_row(const LevelOp& L, int64_t p, int par,
+                                          const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                          typename Ty<KIND>::T& s0, typename Ty<KIND>::T& s1) {
+  typedef typename Ty<KIND>::T T;
+  stencil_sum<KIND, NB>(L, p, par, x, false, s0, s1);
+  if (FINE) {
+    const double2 m = reinterpret_cast<const double2*>(L.mdiag)[p];
+    const T xs = x[p].y, sh = (T)L.shift;
+    s0 = (T)(sh * (T)m.x) * xs - s0;
+    s1 = (T)(sh * (T)m.y) * xs - s1;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void dinv_apply(const T* Dinv, int64_t p, T r0, T r1, T& y0, T& y1) {
+  const T* D = Dinv + p * 4;
+  y0 = D[0] * r0 + D[1] * r1;
+  y1 = D[2] * r0 + D[3] * r1;
+}
+
+// ----------------------------------------------------------------- residual
+template <int KIND, bool FINE, int NB>
+__global__ void __launch_bounds__(256) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                  const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                                  typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
+  typedef typename Ty<KIND>::T T;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  const int par = (int)(p % L.d.nx) >= L.d.E;
+  T s0, s1;
+  apply_row<KIND, FINE, NB>(L, p, par, x, s0, s1);
+  const typename V2<T>::t bv = b[p];
+  typename V2<T>::t o;
+  o.x = bv.x - s0;
+  o.y = bv.y - s1;
+  r[p] = o;
+}
+
+// ----------------------------------------------------------------- Jacobi
+template <int KIND, bool FINE, int NB>
+__global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
+                                                typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
+                                                int zero_x) {
+  typedef typename Ty<KIND>::T T;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  const typename V2<T>::t bv = b[p];
+  T r0 = bv.x, r1 = bv.y, x0 = 0, x1 = 0;
+  if (!zero_x) {
+    const int par = (int)(p % L.d.nx) >= L.d.E;
+    T s0, s1;
+    apply_row<KIND, FINE, NB>(L, p, par, xin, s0, s1);
+    r0 -= s0;
+    r1 -= s1;
+    x0 = xin[p].x;
+    x1 = xin[p].y;
+  }
+  T y0, y1;
+  dinv_apply<T>(reinterpret_cast<const T*>(L.Dinv), p, r0, r1, y0, y1);
+  typename V2<T>::t o;
+  o.x = x0 + (T)omega * y0;
+  o.y = x1 + (T)omega * y1;
+  xout[p] = o;
+}
+
+// ----------------------------------------------------------------- multicolour GS
+// One colour (px,py,pz) of the sweep: x_p <- D_p^-1 (b_p - sum_{q != p} A_pq x_q).
+template <int KIND, bool FINE, int NB>
+__global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
+                                                   int pz, int cnt_x, int lines_y, int64_t count) {
+  typedef typename Ty<KIND>::T T;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int64_t line = t / cnt_x;
+  const int pos = (int)(t - line * cnt_x);
+  const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
+  const int j = 2 * jj + py, k = 2 * kk + pz;
+  const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
+  T s0, s1;
+  stencil_sum<KIND, NB>(L, p, px, x, true, s0, s1);
+  const typename V2<T>::t bv = b[p];
+  // off-diagonal part of A: fine level A_pq = -J_pq (q != p), coarse A_pq
+  const T r0 = FINE ? bv.x + s0 : bv.x - s0;
+  const T r1 = FINE ? bv.y + s1 : bv.y - s1;
+  T y0, y1;
+  dinv_apply<T>(reinterpret_cast<const T*>(L.Dinv), p, r0, r1, y0, y1);
+  typename V2<T>::t o;
+  o.x = y0;
+  o.y = y1;
+  x[p] = o;
+}
+
+// ----------------------------------------------------------------- transfers
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                  const uint8_t* __restrict__ dmc,
+                                                  const typename V2<T>::t* __restrict__ rf,
+                                                  typename V2<T>::t* __restrict__ bc) {
+  int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pc >= dc.nv) return;
+  int I, J, K;
+  pcoords(dc, pc, I, J, K);
+  const bool mc = dmc[pc] != 0;
+  T s0 = 0, s1 = 0;
+  const int zlo = df.dim == 3 ? -1 : 0, zhi = df.dim == 3 ? 1 : 0;
+  for (int dz = zlo; dz <= zhi; ++dz) {
+    const int fk = df.dim == 3 ? 2 * K + dz : 0;
+    if (fk < 0 || fk >= df.nz) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int fj = 2 * J + dy;
+      if (fj < 0 || fj >= df.ny) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int fi = 2 * I + dx;
+        if (fi < 0 || fi >= df.nx) continue;
+        const T w = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+        const int64_t pf = pidx(df, fi, fj, fk);
+        const typename V2<T>::t r = rf[pf];
+        if (!(mc || dmf[pf])) s0 += w * r.x;
+        s1 += w * r.y;
+      }
+    }
+  }
+  typename V2<T>::t o;
+  o.x = s0;
+  o.y = s1;
+  bc[pc] = o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                 const uint8_t* __restrict__ dmc,
+                                                 const typename V2<T>::t* __restrict__ xc,
+                                                 typename V2<T>::t* __restrict__ xf) {
+  int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pf >= df.nv) return;
+  int fi, fj, fk;
+  pcoords(df, pf, fi, fj, fk);
+  const bool mf = dmf[pf] != 0;
+  T s0 = 0, s1 = 0;
+  for (int K = fk >> 1; K <= ((fk + 1) >> 1); ++K) {
+    if (K >= dc.nz) continue;
+    const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
+    for (int J = fj >> 1; J <= ((fj + 1) >> 1); ++J) {
+      if (J >= dc.ny) continue;
+      const T wy = (fj & 1) ? (T)0.5 : (T)1;
+      for (int I = fi >> 1; I <= ((fi + 1) >> 1); ++I) {
+        if (I >= dc.nx) continue;
+        const T w = ((fi & 1) ? (T)0.5 : (T)1) * wy * wz;
+        const int64_t pc = pidx(dc, I, J, K);
+        const typename V2<T>::t c = xc[pc];
+        if (!(mf || dmc[pc])) s0 += w * c.x;
+        s1 += w * c.y;
+      }
+    }
+  }
+  typename V2<T>::t o = xf[pf];
+  o.x += s0;
+  o.y += s1;
+  xf[pf] = o;
+}
+
+// ----------------------------------------------------------------- coarsest solve
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
+                                                      const T* __restrict__ b, T* __restrict__ x) {
+  extern __shared__ double sb[];
+  for (int t = threadIdx.x; t < N; t += blockDim.x) sb[t] = (double)b[t];
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= N) return;
+  const double* row = Ainv + (int64_t)r * N;
+  double s = 0.0;
+  for (int c = 0; c < N; ++c) s += row[c] * sb[c];
+  x[r] = (T)s;
+}
+
+// ----------------------------------------------------------------- Galerkin (FP64)
+// Thread per (coarse vertex, coarse block): (P^T A P)(I, I+D) summed over fine
+// rows i near 2I and fine columns j near 2(I+D), j - i within the stencil.
+// J is summed in all four entries, M in its S_n column only.
+__global__ void __launch_bounds__(128) k_galerkin(Dims df, Nbr nf, const uint8_t* __restrict__ dmf,
+                                                  const double* __restrict__ Jf, const double* __restrict__ Mf,
+                                                  const double2* __restrict__ mdf, Dims dc,
+                                                  const uint8_t* __restrict__ dmc, double* __restrict__ Jc,
+                                                  double* __restrict__ Mc) {
+  const int nb = dc.nb;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= dc.nv * nb) return;
+  const int bc = (int)(t % nb);
+  const int64_t pc = t / nb;
+  int I, J, K;
+  pcoords(dc, pc, I, J, K);
+  const int DX = bc % 3 - 1, DY = (bc / 3) % 3 - 1, DZ = dc.dim == 3 ? bc / 9 - 1 : 0;
+  const int I2 = I + DX, J2 = J + DY, K2 = K + DZ;
+  double j0 = 0, j1 = 0, j2 = 0, j3 = 0, m0 = 0, m1 = 0;
+  const int centre_f = df.dim == 3 ? 13 : 4;
+  if (I2 >= 0 && I2 < dc.nx && J2 >= 0 && J2 < dc.ny && K2 >= 0 && K2 < dc.nz) {
+    const int64_t pc2 = pidx(dc, I2, J2, K2);
+    const bool mI = dmc[pc] != 0, mJ = dmc[pc2] != 0;
+    const int zr = df.dim == 3 ? 1 : 0;
+    for (int az = -zr; az <= zr; ++az)
+      for (int ay = -1; ay <= 1; ++ay)
+        for (int ax = -1; ax <= 1; ++ax) {
+          const int fi = 2 * I + ax, fj = 2 * J + ay, fk = df.dim == 3 ? 2 * K + az : 0;
+          if (fi < 0 || fi >= df.nx || fj < 0 || fj >= df.ny || fk < 0 || fk >= df.nz) continue;
+          const int64_t pi = pidx(df, fi, fj, fk);
+          const double wi = (ax ? 0.5 : 1.0) * (ay ? 0.5 : 1.0) * (az ? 0.5 : 1.0);
+          const double pa0 = (mI || dmf[pi]) ? 0.0 : wi, pa1 = wi;
+          for (int cz = -zr; cz <= zr; ++cz) {
+            const int ez = df.dim == 3 ? 2 * DZ + cz - az : 0;
+            if (ez < -1 || ez > 1) continue;
+            for (int cy = -1; cy <= 1; ++cy) {
+              const int ey = 2 * DY + cy - ay;
+              if (ey < -1 || ey > 1) continue;
+              for (int cx = -1; cx <= 1; ++cx) {
+                const int ex = 2 * DX + cx - ax;
+                if (ex < -1 || ex > 1) continue;
+                const int gi = 2 * I2 + cx, gj = 2 * J2 + cy, gk = df.dim == 3 ? 2 * K2 + cz : 0;
+                if (gi < 0 || gi >= df.nx || gj < 0 || gj >= df.ny || gk < 0 || gk >= df.nz) continue;
+                const int64_t pj = pidx(df, gi, gj, gk);
+                const double wj = (cx ? 0.5 : 1.0) * (cy ? 0.5 : 1.0) * (cz ? 0.5 : 1.0);
+                const double pb0 = (mJ || dmf[pj]) ? 0.0 : wj, pb1 = wj;
+                const int bf = blk_of(df.dim, ex, ey, ez);
+                const double* a = Jf + ((int64_t)bf * df.nv + pi) * 4;
+                j0 += pa0 * a[0] * pb0;
+                j1 += pa0 * a[1] * pb1;
+                j2 += pa1 * a[2] * pb0;
+                j3 += pa1 * a[3] * pb1;
+                if (mdf) {
+                  if (bf == centre_f) {
+                    const double2 md = mdf[pi];
+                    m0 += pa0 * md.x * pb1;
+                    m1 += pa1 * md.y * pb1;
+                  }
+                } else {
+                  const double* mm = Mf + ((int64_t)bf * df.nv + pi) * 2;
+                  m0 += pa0 * mm[0] * pb1;
+                  m1 += pa1 * mm[1] * pb1;
+                }
+              }
+            }
+          }
+        }
+    if (mI && bc == (dc.dim == 3 ? 13 : 4)) j0 = -1.0;  // Dirichlet row: A = +identity
+  }
+  double* o = Jc + ((int64_t)bc * dc.nv + pc) * 4;
+  o[0] = j0; o[1] = j1; o[2] = j2; o[3] = j3;
+  double* om = Mc + ((int64_t)bc * dc.nv + pc) * 2;
+  om[0] = m0; om[1] = m1;
+}
+
+__global__ void k_coarse_mask(Dims df, const uint8_t* __restrict__ dmf, Dims dc, uint8_t* __restrict__ dmc) {
+  int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pc >= dc.nv) return;
+  int I, J, K;
+  pcoords(dc, pc, I, J, K);
+  dmc[pc] = dmf[pidx(df, 2 * I, 2 * J, df.dim == 3 ? 2 * K : 0)];
+}
+
+// ----------------------------------------------------------------- packing
+// Per vertex: entries of A (coarse: shift*Mc - Jc; fine: J itself) into the
+// storage kind, FP16 with one FP32 scale per entry position over the block
+// row, and the inverse of the 2x2 diagonal block of A = shift*M - J.
+template <int KIND>
+__global__ void k_pack(Dims d, bool fine, const double* __restrict__ J, const double* __restrict__ M,
+                       const double2* __restrict__ md, double shift, void* __restrict__ Aout,
+                       float* __restrict__ scale, typename Ty<KIND>::T* __restrict__ Dinv) {
+  typedef typename Ty<KIND>::T T;
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= d.nv) return;
+  const int nb = d.nb, C = d.dim == 3 ? 13 : 4;
+  if (Aout) {
+    double mx[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b) {
+      const double* a = J + ((int64_t)b * d.nv + p) * 4;
+      double e[4] = {a[0], a[1], a[2], a[3]};
+      if (!fine) {
+        const double* m = M + ((int64_t)b * d.nv + p) * 2;
+        e[0] = -e[0]; e[1] = shift * m[0] - e[1]; e[2] = -e[2]; e[3] = shift * m[1] - e[3];
+      }
+      if (KIND == STORE_F16) {
+        for (int q = 0; q < 4; ++q) mx[q] = fmax(mx[q], fabs(e[q]));
+      } else {
+        typename Ty<KIND>::S* o = reinterpret_cast<typename Ty<KIND>::S*>(Aout) + ((int64_t)b * d.nv + p) * 4;
+        for (int q = 0; q < 4; ++q) o[q] = (typename Ty<KIND>::S)e[q];
+      }
+    }
+    if (KIND == STORE_F16) {
+      float sc[4];
+      for (int q = 0; q < 4; ++q) sc[q] = mx[q] > 0.0 ? (float)mx[q] : 1.0f;
+      reinterpret_cast<float4*>(scale)[p] = make_float4(sc[0], sc[1], sc[2], sc[3]);
+      for (int b = 0; b < nb; ++b) {
+        const double* a = J + ((int64_t)b * d.nv + p) * 4;
+        double e[4] = {a[0], a[1], a[2], a[3]};
+        if (!fine) {
+          const double* m = M + ((int64_t)b * d.nv + p) * 2;
+          e[0] = -e[0]; e[1] = shift * m[0] - e[1]; e[2] = -e[2]; e[3] = shift * m[1] - e[3];
+        }
+        __half* o = reinterpret_cast<__half*>(Aout) + ((int64_t)b * d.nv + p) * 4;
+        for (int q = 0; q < 4; ++q) o[q] = __double2half((double)(float)(e[q] / (double)sc[q]));
+      }
+    }
+  }
+  if (Dinv) {
+    // diagonal block of A in FP64
+    const double* a = J + ((int64_t)C * d.nv + p) * 4;
+    double A00, A01, A10, A11;
+    if (fine) {
+      const double2 m = md[p];
+      A00 = -a[0]; A01 = shift * m.x - a[1]; A10 = -a[2]; A11 = shift * m.y - a[3];
+    } else {
+      const double* m = M + ((int64_t)C * d.nv + p) * 2;
+      A00 = -a[0]; A01 = shift * m[0] - a[1]; A10 = -a[2]; A11 = shift * m[1] - a[3];
+    }
+    const double det = A00 * A11 - A01 * A10;
+    T* o = Dinv + p * 4;
+    o[0] = (T)(A11 / det); o[1] = (T)(-A01 / det); o[2] = (T)(-A10 / det); o[3] = (T)(A00 / det);
+  }
+}
+
+// dense coarsest matrix, rows/cols in parity-split unknown order 2p+alpha
+__global__ void k_dense(Dims d, Nbr nb, const double* __restrict__ J, const double* __restrict__ M,
+                        const double2* __restrict__ md, bool fine, double shift, double* __restrict__ D) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= d.nv * d.nb) return;
+  const int b = (int)(t % d.nb);
+  const int64_t p = t / d.nb;
+  int i, j, k;
+  pcoords(d, p, i, j, k);
+  const int dx = b % 3 - 1, dy = (b / 3) % 3 - 1, dz = d.dim == 3 ? b / 9 - 1 : 0;
+  const int ii = i + dx, jj = j + dy, kk = k + dz;
+  if (ii < 0 || ii >= d.nx || jj < 0 || jj >= d.ny || kk < 0 || kk >= d.nz) return;
+  const int64_t q = pidx(d, ii, jj, kk);
+  const int64_t N = 2 * d.nv;
+  const double* a = J + ((int64_t)b * d.nv + p) * 4;
+  double e0 = -a[0], e1 = -a[1], e2 = -a[2], e3 = -a[3];
+  const int C = d.dim == 3 ? 13 : 4;
+  if (fine) {
+    if (b == C) { e1 += shift * md[p].x; e3 += shift * md[p].y; }
+  } else {
+    const double* m = M + ((int64_t)b * d.nv + p) * 2;
+    e1 += shift * m[0];
+    e3 += shift * m[1];
+  }
+  D[(2 * p) * N + 2 * q] = e0;
+  D[(2 * p) * N + 2 * q + 1] = e1;
+  D[(2 * p + 1) * N + 2 * q] = e2;
+  D[(2 * p + 1) * N + 2 * q + 1] = e3;
+}
+
+// LU with partial pivoting in one CTA (first maximal pivot on ties).
+__global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int* __restrict__ piv,
+                                             int* __restrict__ status) {
+  __shared__ double sval[32];
+  __shared__ int sidx[32];
+  __shared__ int sp;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = 0; c < N; ++c) {
+    double best = -1.0;
+    int bi = N;
+    for (int r = c + tid; r < N; r += nt) {
+      double v = fabs(D[(int64_t)r * N + c]);
+      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { sval[tid >> 5] = best; sidx[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = sval[0];
+      int bidx = sidx[0];
+      for (int w = 1; w < (nt + 31) / 32; ++w)
+        if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
+      if (!(bv > 0.0)) { status[0] = 1; bidx = c; }
+      sp = bidx;
+      piv[c] = bidx;
+    }
+    __syncthreads();
+    const int pr = sp;
+    if (pr != c)
+      for (int t = tid; t < N; t += nt) {
+        double tmp = D[(int64_t)c * N + t];
+        D[(int64_t)c * N + t] = D[(int64_t)pr * N + t];
+        D[(int64_t)pr * N + t] = tmp;
+      }
+    __syncthreads();
+    const double dc = D[(int64_t)c * N + c];
+    for (int r = c + 1 + tid; r < N; r += nt) D[(int64_t)r * N + c] = (dc != 0.0) ? D[(int64_t)r * N + c] / dc : 0.0;
+    __syncthreads();
+    const int rem = N - c - 1;
+    for (int64_t e = tid; e < (int64_t)rem * rem; e += nt) {
+      const int r = c + 1 + (int)(e / rem), t = c + 1 + (int)(e % rem);
+      D[(int64_t)r * N + t] -= D[(int64_t)r * N + c] * D[(int64_t)c * N + t];
+    }
+    __syncthreads();
+  }
+}
+
+// column `col` of the inverse from the LU factors: solve L U x = P e_col
+__global__ void k_lu_inverse_cols(int N, const double* __restrict__ LU, const int* __restrict__ piv,
+                                  double* __restrict__ work, double* __restrict__ Ainv) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= N) return;
+  double* x = work + (int64_t)col * N;
+  for (int r = 0; r < N; ++r) x[r] = (r == col) ? 1.0 : 0.0;
+  for (int c = 0; c < N; ++c) {
+    const int p = piv[c];
+    if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
+  }
+  for (int r = 0; r < N; ++r) {
+    double s = x[r];
+    for (int c = 0; c < r; ++c) s -= LU[(int64_t)r * N + c] * x[c];
+    x[r] = s;
+  }
+  for (int r = N - 1; r >= 0; --r) {
+    double s = x[r];
+    for (int c = r + 1; c < N; ++c) s -= LU[(int64_t)r * N + c] * x[c];
+    x[r] = s / LU[(int64_t)r * N + r];
+  }
+  for (int r = 0; r < N; ++r) Ainv[(int64_t)r * N + col] = x[r];
+}
+
+// natural-order FP64 export of a level operator
+__global__ void k_export(Dims d, bool fine, const double* __restrict__ J, const double* __restrict__ M,
+                         const double2* __restrict__ md, double shift, double* __restrict__ out) {
+  int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (v >= d.nv) return;
+  const int i = (int)(v % d.nx);
+  const int64_t line = v / d.nx;
+  const int64_t p = line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1));
+  const int C = d.dim == 3 ? 13 : 4;
+  for (int b = 0; b < d.nb; ++b) {
+    const double* a = J + ((int64_t)b * d.nv + p) * 4;
+    double e[4] = {-a[0], -a[1], -a[2], -a[3]};
+    if (fine) {
+      if (b == C && md) { e[1] += shift * md[p].x; e[3] += shift * md[p].y; }
+      if (!md) { e[0] = a[0]; e[1] = a[1]; e[2] = a[2]; e[3] = a[3]; }
+    } else {
+      const double* m = M + ((int64_t)b * d.nv + p) * 2;
+      e[1] += shift * m[0];
+      e[3] += shift * m[1];
+    }
+    double* o = out + (v * d.nb + b) * 4;
+    o[0] = e[0]; o[1] = e[1]; o[2] = e[2]; o[3] = e[3];
+  }
+}
+
+__global__ void k_cast_f64_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (float)in[t];
+}
+__global__ void k_cast_f32_f64(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (double)in[t];
+}
+
+// ----------------------------------------------------------------- launchers
+template <int KIND, bool FINE>
+static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, void* s) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  const int g = (int)((L.d.nv + 255) / 256);
+  if (L.d.nb == 27)
+    RF_LAUNCH((k_residual<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+  else
+    RF_LAUNCH((k_residual<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+}
+
+template <int KIND, bool FINE>
+static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x,
+                     void* s) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  const int g = (int)((L.d.nv + 255) / 256);
+  if (L.d.nb == 27)
+    RF_LAUNCH((k_jacobi<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+  else
+    RF_LAUNCH((k_jacobi<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+}
+
+template <int KIND, bool FINE>
+static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, void* s) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  const int ncol = 1 << L.d.dim;
+  for (int cc = 0; cc < ncol; ++cc) {
+    const int col = forward ? cc : ncol - 1 - cc;
+    const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
+    const int cnt_x = px ? L.d.nx / 2 : (L.d.nx + 1) / 2;
+    const int lines_y = (L.d.ny - py + 1) / 2;
+    const int lines_z = L.d.dim == 3 ? (L.d.nz - pz + 1) / 2 : 1;
+    const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
+    if (count == 0) continue;
+    const int g = (int)((count + 255) / 256);
+    if (L.d.nb == 27)
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count);
+    else
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count);
+  }
+}
+
+void launch_residual(const LevelOp& L, const void* b, const void* x, void* r, void* s) {
+  switch (L.kind) {
+    case STORE_F64: L.fine ? residual_t<STORE_F64, true>(L, b, x, r, s) : residual_t<STORE_F64, false>(L, b, x, r, s); break;
+    case STORE_F32: L.fine ? residual_t<STORE_F32, true>(L, b, x, r, s) : residual_t<STORE_F32, false>(L, b, x, r, s); break;
+    default: L.fine ? residual_t<STORE_F16, true>(L, b, x, r, s) : residual_t<STORE_F16, false>(L, b, x, r, s); break;
+  }
+}
+
+void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x, void* s) {
+  switch (L.kind) {
+    case STORE_F64: L.fine ? jacobi_t<STORE_F64, true>(L, b, xin, xout, omega, zero_x, s) : jacobi_t<STORE_F64, false>(L, b, xin, xout, omega, zero_x, s); break;
+    case STORE_F32: L.fine ? jacobi_t<STORE_F32, true>(L, b, xin, xout, omega, zero_x, s) : jacobi_t<STORE_F32, false>(L, b, xin, xout, omega, zero_x, s); break;
+    default: L.fine ? jacobi_t<STORE_F16, true>(L, b, xin, xout, omega, zero_x, s) : jacobi_t<STORE_F16, false>(L, b, xin, xout, omega, zero_x, s); break;
+  }
+}
+
+void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool /*zero_start*/, void* s) {
+  switch (L.kind) {
+    case STORE_F64: L.fine ? gs_t<STORE_F64, true>(L, b, x, forward, s) : gs_t<STORE_F64, false>(L, b, x, forward, s); break;
+    case STORE_F32: L.fine ? gs_t<STORE_F32, true>(L, b, x, forward, s) : gs_t<STORE_F32, false>(L, b, x, forward, s); break;
+    default: L.fine ? gs_t<STORE_F16, true>(L, b, x, forward, s) : gs_t<STORE_F16, false>(L, b, x, forward, s); break;
+  }
+}
+
+void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s) {
+  const int g = (int)((C.d.nv + 255) / 256);
+  if (F.kind == STORE_F64)
+    RF_LAUNCH(k_restrict<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
+  else
+    RF_LAUNCH(k_restrict<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
+}
+
+void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s) {
+  const int g = (int)((F.d.nv + 255) / 256);
+  if (F.kind == STORE_F64)
+    RF_LAUNCH(k_prolong<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
+  else
+    RF_LAUNCH(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
+}
+
+void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s) {
+  const int N = (int)(2 * C.d.nv);
+  const int g = (N + 255) / 256;
+  const size_t smem = sizeof(double) * N;
+  if (C.kind == STORE_F64)
+    RF_LAUNCH(k_coarse_solve<double>, g, 256, smem, s, N, Ainv, (const double*)b, (double*)x);
+  else
+    RF_LAUNCH(k_coarse_solve<float>, g, 256, smem, s, N, Ainv, (const float*)b, (float*)x);
+}
+
+void launch_galerkin(const Dims& df, const Nbr& nf, const uint8_t* dmf, const double* Jf, const double* Mf,
+                     const double* mdiag_f, const Dims& dc, const uint8_t* dmc, double* Jc, double* Mc, void* s) {
+  const int64_t n = dc.nv * dc.nb;
+  RF_LAUNCH(k_galerkin, (int)((n + 127) / 128), 128, 0, s, df, nf, dmf, Jf, Mf, (const double2*)mdiag_f, dc, dmc,
+            Jc, Mc);
+}
+
+void launch_coarse_mask(const Dims& df, const uint8_t* dmf, const Dims& dc, uint8_t* dmc, void* s) {
+  RF_LAUNCH(k_coarse_mask, (int)((dc.nv + 255) / 256), 256, 0, s, df, dmf, dc, dmc);
+}
+
+void launch_pack_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
+                       double shift, int kind, void* A_out, float* scale_out, void* Dinv_out, void* s) {
+  const int g = (int)((d.nv + 127) / 128);
+  if (kind == STORE_F64)
+    RF_LAUNCH(k_pack<STORE_F64>, g, 128, 0, s, d, fine, J, M, (const double2*)mdiag, shift, A_out, scale_out,
+              (double*)Dinv_out);
+  else if (kind == STORE_F32)
+    RF_LAUNCH(k_pack<STORE_F32>, g, 128, 0, s, d, fine, J, M, (const double2*)mdiag, shift, A_out, scale_out,
+              (float*)Dinv_out);
+  else
+    RF_LAUNCH(k_pack<STORE_F16>, g, 128, 0, s, d, fine, J, M, (const double2*)mdiag, shift, A_out, scale_out,
+              (float*)Dinv_out);
+}
+
+void launch_dense_coarsest(const Dims& d, const Nbr& nb, const double* Jc, const double* Mc,
+                           const double* mdiag, bool fine, double shift, double* D, void* s) {
+  const int64_t n = d.nv * d.nb;
+  RF_LAUNCH(k_dense, (int)((n + 127) / 128), 128, 0, s, d, nb, Jc, Mc, (const double2*)mdiag, fine, shift, D);
+}
+
+cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status, void* s) {
+  RF_LAUNCH(k_lu, 1, 1024, 0, s, N, D, piv, status);
+  RF_LAUNCH(k_lu_inverse_cols, (N + 31) / 32, 32, 0, s, N, D, piv, work, Ainv);
+  return cudaGetLastError();
+}
+
+void launch_export_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
+                         double shift, double* A_nat, void* s) {
+  RF_LAUNCH(k_export, (int)((d.nv + 127) / 128), 128, 0, s, d, fine, J, M, (const double2*)mdiag, shift, A_nat);
+}
+
+void launch_cast_f64_to_f32(const double* in, float* out, int64_t n, void* s) {
+  RF_LAUNCH(k_cast_f64_f32, grid_for(n, 256), 256, 0, s, in, out, n);
+}
+void launch_cast_f32_to_f64(const float* in, double* out, int64_t n, void* s) {
+  RF_LAUNCH(k_cast_f32_f64, grid_for(n, 256), 256, 0, s, in, out, n);
+}
+
+}  // namespace rf

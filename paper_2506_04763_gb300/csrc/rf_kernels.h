@@ -1,0 +1,111 @@
+// rf_kernels.h — launchers exported by the kernel translation units to the
+// host driver (driver.cu).  Plain C++ types only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "rf_common.cuh"
+
+namespace rf {
+
+struct PhysParams {
+  double rho_w, rho_n, mu_w, mu_n, S_wr, S_nr, lambda;
+  double h[3], g[3];
+};
+
+struct AsmArrays {
+  const double* u;                 // [2nv] parity-split
+  double *Se, *pn, *pc, *dpc, *krw, *dkrw;  // [nv] scratch
+  const double *pdmin, *phiv;      // [nv]
+  const double *K, *pd;            // per cell
+  const uint8_t* dir;              // [nv]
+  const double* pw_dir;            // [nv]
+  const double* q_in;              // [2nv] or null
+  double* F;                       // [2nv]
+  double* J;                       // [nb][nv][4] or null
+  double* mdiag;                   // [2nv] or null
+};
+
+// assemble.cu
+void launch_vertex_setup(const Dims& d, const double* pd, const double* phi, double vol, double* pdmin,
+                         double* phiv, void* s);
+void launch_perm_to_p(const Dims& d, const double* nat, double* out, void* s);
+void launch_perm_from_p(const Dims& d, const double* pl, double* nat, void* s);
+void launch_perm_bytes_to_p(const Dims& d, const uint8_t* nat, uint8_t* out, void* s);
+void launch_perm_scalar_to_p(const Dims& d, const double* nat, double* out, void* s);
+cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays& a, bool want_j, void* s);
+
+// ---- multigrid level operators (levelops.cu) ----
+enum StoreKind { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2 };
+
+// One level's operator as seen by the smoothing / residual kernels.
+struct LevelOp {
+  Dims d;
+  Nbr nb;
+  int kind;              // StoreKind of the blocks (and T = double for F64, float otherwise)
+  bool fine;             // true: blocks hold J and A = shift*M - J with M = mdiag;
+                         // false: blocks hold A itself
+  const void* A;         // [nb][nv] blocks of 4
+  const float* scale;    // F16: [nv][4] per-entry-position row scales
+  const double* mdiag;   // fine: [2nv] (dm_w/dS_n, dm_n/dS_n)
+  double shift;          // fine: 1/h_j
+  const void* Dinv;      // [nv][4] inverse diagonal blocks (T)
+  const uint8_t* dmask;  // [nv]
+};
+
+// Vectors are T2 pointers to the first interior element of padded buffers.
+void launch_residual(const LevelOp& L, const void* b, const void* x, void* r, void* s);
+void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x,
+                   void* s);
+void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s);
+void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s);
+void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s);
+void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s);
+
+// set-up kernels (levelops.cu)
+void launch_galerkin(const Dims& df, const Nbr& nf, const uint8_t* dmf, const double* Jf, const double* Mf,
+                     const double* mdiag_f, const Dims& dc, const uint8_t* dmc, double* Jc, double* Mc,
+                     void* s);
+void launch_coarse_mask(const Dims& df, const uint8_t* dmf, const Dims& dc, uint8_t* dmc, void* s);
+// pack A = shift*M - J (coarse: from Jc/Mc; fine: keep J, only Dinv) into storage `kind`; write Dinv
+void launch_pack_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
+                       double shift, int kind, void* A_out, float* scale_out, void* Dinv_out, void* s);
+void launch_dense_coarsest(const Dims& d, const Nbr& nb, const double* Jc, const double* Mc,
+                           const double* mdiag, bool fine, double shift, double* D, void* s);
+cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status,
+                                 void* s);
+void launch_export_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
+                         double shift, double* A_nat, void* s);
+void launch_cast_f64_to_f32(const double* in, float* out, int64_t n, void* s);
+void launch_cast_f32_to_f64(const float* in, double* out, int64_t n, void* s);
+
+// ---- Krylov (krylov.cu) ----
+struct KrylovVecs {
+  double2 *x, *r, *rh, *p, *v, *s, *t;   // FP64, parity-split (x and p padded not required)
+  void *y, *z;                            // preconditioned vectors (T2, padded)
+  void *p_lo, *s_lo;                      // preconditioner inputs (T2)
+  double* partial;                        // reduction partials [8][max_blocks]
+  double* scal;                           // device scalars (see krylov.cu)
+};
+int krylov_blocks(int64_t nv);
+// outer operator: y = (shift*M - J) x with J FP64, x FP64 or FP32 (x_is_f32)
+void launch_spmv64(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
+                   const void* x, bool x_is_f32, double2* y, void* s);
+void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, void* s);
+void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool first, void* s);
+void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
+                   KrylovVecs& K, bool y_is_f32, void* s);
+void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s);
+void launch_bicg_t(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
+                   KrylovVecs& K, bool z_is_f32, void* s);
+void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, double rtol, void* s);
+void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
+                          const double2* b, KrylovVecs& K, void* s);
+void launch_restart(int64_t nv, KrylovVecs& K, void* s);
+void launch_axpy_pairs(int64_t nv, double2* u, const double2* du, void* s);
+
+// ---- LIMEX (krylov.cu) ----
+void launch_extrapolate(int64_t n2, int kappa, double* T, void* s);
+void launch_error_norms(const Dims& d, const double* h, const double* Tkk, const double* Tkk1, double* out4,
+                        double* partial, void* s);
+
+}  // namespace rf

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, element
+by element, on seeded inputs that span several thread blocks and ragged tails.
+
+Tolerances:
+  FP64 kernels: 1e-12 relative to the row's largest entry (Jacobian, Galerkin
+    operators) or to the largest magnitude of the compared vector; the two
+    sides sum in different orders, so bitwise equality is not expected.
+  FP32 preconditioner kernels: inputs are rounded to FP32 identically on both
+    sides; the bound is 64 u32 (|A||x| + |b|) per component, u32 = 2^-24, i.e.
+    a few rounding errors of every term of the 27-block row sum.
+  Solves: both sides converge to a true relative residual <= 1e-12; the
+    solutions then agree to cond(A) * 1e-12, checked as 1e-8 relative in p_w
+    increments and 1e-9 absolute in S_n increments.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2506_04763_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+rf = pytest.importorskip("paper_2506_04763_gb300")
+
+CASES = {
+    "2d-config1": lambda: I.config1(),
+    "2d-17x13-stress": lambda: I.random_problem(2, (17, 13), 3, stress=True),
+    "3d-9x7x5-stress": lambda: I.random_problem(3, (9, 7, 5), 4, stress=True),
+    "3d-17cube": lambda: I.random_problem(3, (17, 17, 17), 5),
+    "3d-33x17x9-nodir": lambda: I.random_problem(3, (33, 17, 9), 6, dirichlet=False),
+    "2d-even-10x8": lambda: I.random_problem(2, (10, 8), 8),
+}
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as G
+    G.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _grid(prob):
+    return rf.Grid(prob)
+
+
+def _assembled(prob):
+    g = _grid(prob)
+    u = torch.tensor(prob["u0"], device="cuda")
+    F = torch.empty_like(u)
+    g.assemble(u, True, F)
+    torch.cuda.synchronize()
+    return g, F.cpu().numpy()
+
+
+def _levels(prob):
+    n = prob["n"][0]
+    L = 1
+    m = [t for t in prob["n"][:prob["dim"]]]
+    while all((t - 1) % 2 == 0 and t >= 3 for t in m) and L < 4:
+        m = [(t - 1) // 2 + 1 for t in m]
+        L += 1
+    return L
+
+
+# ------------------------------------------------------------------ assembly
+@pytest.mark.parametrize("case", list(CASES))
+def test_assembly_matches_oracle(case):
+    prob = CASES[case]()
+    g, F = _assembled(prob)
+    J, md = g.export_jacobian()
+    m = O.Model(prob)
+    F_o, J_o, md_o = O.assemble(m, prob["u0"])
+    for a in range(2):
+        rows = np.abs(J_o[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2)) + 1e-300
+        err = np.abs(J[:, :, 2 * a:2 * a + 2] - J_o[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2))
+        assert np.all(err <= 1e-12 * rows), (case, a, (err / rows).max())
+        sc = np.abs(F_o[a::2]).max()
+        assert np.abs(F[a::2] - F_o[a::2]).max() <= 1e-12 * sc
+    np.testing.assert_allclose(md, md_o, rtol=1e-14, atol=0)
+    g.close()
+
+
+def test_assembly_host_and_device_pointers_agree():
+    prob = CASES["3d-9x7x5-stress"]()
+    g = _grid(prob)
+    F_host = np.zeros(2 * g.nv)
+    g.assemble(np.ascontiguousarray(prob["u0"]), True, F_host)
+    u = torch.tensor(prob["u0"], device="cuda")
+    F = torch.empty_like(u)
+    g.assemble(u, True, F)
+    torch.cuda.synchronize()
+    assert np.array_equal(F.cpu().numpy(), F_host)
+    g.close()
+
+
+# ------------------------------------------------------------------ outer operator
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress"])
+def test_fp64_spmv_matches_oracle(case):
+    prob = CASES[case]()
+    g, F = _assembled(prob)
+    shift = 0.1
+    g.gmg_setup([shift], rf.gmg_opts(_levels(prob), precision="fp64"))
+    m = O.Model(prob)
+    _, J_o, md_o = O.assemble(m, prob["u0"])
+    A = O.make_A(J_o, md_o, shift)
+    x = np.random.default_rng(1).standard_normal(2 * g.nv) * np.tile([1e3, 0.1], g.nv)
+    y = g.apply(rf.RF_OP_SPMV, 0, 0, x)
+    y_o = O.spmv(m.dim, m.n, A, x)
+    for a in range(2):
+        scale = np.abs(A[:, :, 2 * a:2 * a + 2]).max() * np.abs(x).max()
+        assert np.abs(y[a::2] - y_o[a::2]).max() <= 1e-13 * scale
+    g.close()
+
+
+# ------------------------------------------------------------------ multigrid pieces
+def _setup_both(prob, precision, smoother, levels=None):
+    g, F = _assembled(prob)
+    shift = 1.0 / prob["H"]
+    L = levels or _levels(prob)
+    g.gmg_setup([shift, 2 * shift], rf.gmg_opts(L, smoother, precision=precision))
+    m = O.Model(prob)
+    _, J_o, md_o = O.assemble(m, prob["u0"])
+    A = O.make_A(J_o, md_o, 2 * shift)
+    gm = O.GMG(m.dim, m.n, A, prob["dir"], L, smoother=O.JACOBI if smoother == "jacobi" else O.GS8)
+    return g, F, m, A, gm
+
+
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-33x17x9-nodir"])
+def test_galerkin_levels_match_oracle(case):
+    prob = CASES[case]()
+    g, F, m, A, gm = _setup_both(prob, "fp64", "jacobi")
+    assert gm.nlevels == _levels(prob)
+    for level in range(gm.nlevels):
+        Ag, dims = g.export_level(level, 1)
+        Ao = gm.level_matrix(level)
+        assert dims == gm.level_dims(level)
+        for a in range(2):
+            rows = np.abs(Ao[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2)) + 1e-300
+            err = np.abs(Ag[:, :, 2 * a:2 * a + 2] - Ao[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2))
+            assert np.all(err <= 1e-12 * rows), (level, a, (err / rows).max())
+    g.close()
+
+
+def _rel_bound(Ao, x, b, dim, n, prec):
+    """per-component bound: c u (|A||x| + |b|)."""
+    if prec == "fp64":
+        c, u = 64.0, 2.0 ** -53
+    else:
+        c, u = 64.0, U32
+    absx = np.abs(x)
+    ax = O.spmv(dim, n, np.abs(Ao), absx)
+    return c * u * (ax + np.abs(b)) + 1e-300
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "2d-17x13-stress"])
+def test_level_kernels_match_oracle(case, smoother, precision):
+    prob = CASES[case]()
+    g, F, m, A, gm = _setup_both(prob, precision, smoother)
+    rng = np.random.default_rng(5)
+    rnd = np.float32 if precision == "fp32" else np.float64
+    for level in range(gm.nlevels - 1):
+        n = gm.level_dims(level)
+        nv = int(np.prod(n))
+        Ao = gm.level_matrix(level)
+        if precision == "fp32":
+            Ao32 = Ao.astype(np.float32).astype(np.float64)
+        else:
+            Ao32 = Ao
+        b = rng.standard_normal(2 * nv).astype(rnd).astype(np.float64)
+        x = rng.standard_normal(2 * nv).astype(rnd).astype(np.float64)
+        # residual
+        r = g.apply(rf.RF_OP_RESIDUAL, level, 1, b, x)[:2 * nv]
+        r_o = O.residual(m.dim, n, Ao32, b, x)
+        assert np.all(np.abs(r - r_o) <= _rel_bound(Ao32, x, b, m.dim, n, precision)), level
+        # one smoothing sweep
+        sm = g.apply(rf.RF_OP_SMOOTH, level, 1, b, x)[:2 * nv]
+        if smoother == "jacobi":
+            sm_o = O.jacobi(m.dim, n, Ao32, b, x, 0.8)
+        else:
+            sm_o = O.gs_sweep(m.dim, n, Ao32, b, x, True)
+        tol = 1e-9 if precision == "fp64" else 2e-4
+        assert np.abs(sm - sm_o).max() <= tol * np.abs(sm_o).max(), (level, np.abs(sm - sm_o).max() / np.abs(sm_o).max())
+        # transfers
+        nc = gm.level_dims(level + 1)
+        nvc = int(np.prod(nc))
+        dmf = np.zeros(nv, np.uint8)
+        dmc = np.zeros(nvc, np.uint8)
+        if level == 0:
+            dmf = prob["dir"]
+        else:
+            dmf = _mask_chain(prob, m, gm, level)
+        dmc = _mask_chain(prob, m, gm, level + 1)
+        rc = g.apply(rf.RF_OP_RESTRICT, level, 1, b)[:2 * nvc]
+        rc_o = O.restrict(m.dim, n, dmf, nc, dmc, b)
+        assert np.abs(rc - rc_o).max() <= (1e-14 if precision == "fp64" else 1e-6) * np.abs(rc_o).max()
+        xc = rng.standard_normal(2 * nvc).astype(rnd).astype(np.float64)
+        pr = g.apply(rf.RF_OP_PROLONG, level, 1, xc, x)[:2 * nv]
+        pr_o = O.prolong_add(m.dim, n, dmf, nc, dmc, xc, x)
+        assert np.abs(pr - pr_o).max() <= (1e-14 if precision == "fp64" else 1e-6) * np.abs(pr_o).max()
+    g.close()
+
+
+def _mask_chain(prob, m, gm, level):
+    dm = np.asarray(prob["dir"], np.uint8)
+    n = m.n
+    for l in range(1, level + 1):
+        nc = gm.level_dims(l)
+        v = np.arange(int(np.prod(nc)))
+        I_, J_, K_ = v % nc[0], (v // nc[0]) % nc[1], v // (nc[0] * nc[1])
+        dm = dm[2 * I_ + n[0] * (2 * J_ + n[1] * (2 * K_ if m.dim == 3 else 0))]
+        n = nc
+    return dm
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube"])
+def test_vcycle_and_coarse_solve_match_oracle(case, smoother):
+    prob = CASES[case]()
+    g, F, m, A, gm = _setup_both(prob, "fp64", smoother)
+    b = np.random.default_rng(2).standard_normal(2 * g.nv)
+    x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
+    x_o = gm.vcycle(b)
+    assert np.abs(x - x_o).max() <= 1e-9 * np.abs(x_o).max()
+    L = gm.nlevels - 1
+    nc = gm.level_dims(L)
+    bc = np.random.default_rng(3).standard_normal(2 * int(np.prod(nc)))
+    xc = g.apply(rf.RF_OP_COARSE, L, 1, bc)[:len(bc)]
+    Ac = __import__("tests._helpers", fromlist=["x"]).stencil_to_dense(m.dim, nc, gm.level_matrix(L))
+    xc_o = np.linalg.solve(Ac, bc)
+    assert np.abs(xc - xc_o).max() <= 1e-10 * np.abs(xc_o).max()
+    g.close()
+
+
+# ------------------------------------------------------------------ solves
+@pytest.mark.parametrize("precision,smoother", [("fp64", "jacobi"), ("fp32", "jacobi"), ("fp32", "gs8"),
+                                                ("fp16", "gs8"), ("fp64", "gs8")])
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress", "2d-even-10x8"])
+def test_solve_matches_oracle(case, precision, smoother):
+    prob = CASES[case]()
+    g, F = _assembled(prob)
+    shift = 1.0 / prob["H"]
+    L = _levels(prob)
+    g.gmg_setup([shift], rf.gmg_opts(L, smoother, precision=precision))
+    b = torch.tensor(F, device="cuda")
+    x = torch.empty_like(b)
+    info = g.solve(0, b, x, rtol=1e-12, max_it=300)
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["relres"] <= 1e-12, info
+    m = O.Model(prob)
+    _, J_o, md_o = O.assemble(m, prob["u0"])
+    A = O.make_A(J_o, md_o, shift)
+    gm = O.GMG(m.dim, m.n, A, prob["dir"], L)
+    x_o, inf_o = O.bicgstab(m.dim, m.n, A, gm, F, rtol=1e-13, maxit=400)
+    assert inf_o["status"] == 0
+    xs = x.cpu().numpy()
+    # the oracle's own residual of the GPU solution
+    r = F - O.spmv(m.dim, m.n, A, xs)
+    assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(F)
+    p_scale = np.abs(prob["u0"][0::2]).max()
+    assert np.abs(xs[0::2] - x_o[0::2]).max() <= 1e-8 * p_scale
+    assert np.abs(xs[1::2] - x_o[1::2]).max() <= 1e-9
+    g.close()
+
+
+def test_solve_host_buffers_and_zero_rhs():
+    prob = CASES["2d-config1"]()
+    g, F = _assembled(prob)
+    g.gmg_setup([0.1], rf.gmg_opts(4, precision="fp32"))
+    x_host = np.zeros(2 * g.nv)
+    info = g.solve(0, np.ascontiguousarray(F), x_host, rtol=1e-10)
+    assert info["status"] == 0
+    b = torch.tensor(F, device="cuda")
+    x = torch.empty_like(b)
+    g.solve(0, b, x, rtol=1e-10)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), x_host)
+    z = np.zeros(2 * g.nv)
+    x0 = np.ones(2 * g.nv)
+    info = g.solve(0, z, x0)
+    assert info["status"] == 0 and np.all(x0 == 0.0)
+    g.close()
+
+
+def test_invalid_arguments_are_rejected():
+    prob = CASES["2d-config1"]()
+    g = _grid(prob)
+    with pytest.raises(rf.RFError) as e:
+        g.solve(0, np.zeros(2 * g.nv), np.zeros(2 * g.nv))
+    assert e.value.status == rf.RF_EINVAL
+    with pytest.raises(rf.RFError):
+        g.gmg_setup([0.1], rf.gmg_opts(4))       # no Jacobian yet
+    u = torch.tensor(prob["u0"], device="cuda")
+    g.assemble(u, True, None)
+    with pytest.raises(rf.RFError):
+        g.gmg_setup([0.1], rf.gmg_opts(0))
+    with pytest.raises(rf.RFError):
+        g.gmg_setup([0.1] * 5, rf.gmg_opts(2))
+    g.gmg_setup([0.1], rf.gmg_opts(2))
+    with pytest.raises(rf.RFError):
+        g.solve(3, np.zeros(2 * g.nv), np.zeros(2 * g.nv))
+    g.close()
+
+
+def test_nonfinite_state_is_reported():
+    prob = CASES["2d-config1"]()
+    g, F = _assembled(prob)
+    g.gmg_setup([0.1], rf.gmg_opts(4))
+    b = F.copy()
+    b[10] = np.nan
+    with pytest.raises(rf.RFError) as e:
+        g.solve(0, b, np.zeros_like(b))
+    assert e.value.status == rf.RF_ENONFINITE
+    g.close()
+
+
+# ------------------------------------------------------------------ LIMEX
+@pytest.mark.parametrize("kappa", [1, 2, 4])
+def test_limex_step_matches_oracle(kappa):
+    prob = I.random_problem(2, (17, 17), 31)
+    H = 5.0
+    g = _grid(prob)
+    u = torch.tensor(prob["u0"], device="cuda")
+    info = g.limex_step(u, H, kappa=kappa, tol=1e9, gmg=rf.gmg_opts(3, precision="fp64"), rtol=1e-13, max_it=300)
+    torch.cuda.synchronize()
+    m = O.Model(prob)
+    u_o, inf_o = O.limex_step(m, prob["u0"], H, kappa=kappa, tol=1e9, nlevels=3, rtol=1e-13, maxit=400)
+    assert info["accepted"] == 1 and inf_o["accepted"] == 1
+    assert info["solves"] == inf_o["solves"] == kappa * (kappa + 1) // 2
+    us = u.cpu().numpy()
+    assert np.abs(us[0::2] - u_o[0::2]).max() <= 1e-9 * np.abs(u_o[0::2]).max()
+    assert np.abs(us[1::2] - u_o[1::2]).max() <= 1e-9
+    if kappa > 1:
+        assert info["eps"] == pytest.approx(inf_o["eps"], rel=1e-5)
+        assert info["H_new"] == pytest.approx(inf_o["H_new"], rel=1e-5)
+    g.close()
+
+
+def test_limex_rejects_and_keeps_state():
+    prob = I.random_problem(2, (17, 17), 32)
+    g = _grid(prob)
+    u = torch.tensor(prob["u0"], device="cuda")
+    u0 = u.clone()
+    info = g.limex_step(u, 50.0, kappa=3, tol=1e-12, gmg=rf.gmg_opts(3, precision="fp32"))
+    torch.cuda.synchronize()
+    assert info["accepted"] == 0 and info["H_new"] < 50.0
+    assert torch.equal(u, u0)
+    g.close()
