@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: BiCGSTAB-GMG stage solve to true relative residual 1e-10.
+
+Workload (one step = one solve from x0 = 0): the 257^3-vertex box with a
+lognormal permeability field (seed 2) and six low-K lenses, stage matrix
+A = M/h - J at h = 10 s assembled at the initial state, right-hand side F(u0);
+FP64 BiCGSTAB preconditioned by one FP32 V(2,2)-cycle (7 levels, 8-colour
+block Gauss-Seidel).  The metric is DoF/s = 2 * vertices / solve time, with the
+multigrid set-up excluded (reported separately, as are the assembly and the
+all-FP64 and FP16-storage variants of the same solve).
+
+Inputs stay resident in HBM; the FP64 Jacobian alone (14.7 GB) is far larger
+than L2, so nothing is flushed between steps.  `--impl reference` times the
+CPU oracle (single thread, FP64) on a bounded sample of the same recipe.
+Under torchrun (N > 1) every rank solves its own replica (the path is one
+coupled problem, so ranks do not shard it); value = total DoF/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BiCGSTAB-GMG DoF/s to rel.res 1e-10, FP32-GMG vs FP64, % of HBM peak"
+RTOL = 1e-10
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nvert", type=int, default=257)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
+    ap.add_argument("--smoother", default="gs8", choices=["gs8", "jacobi"])
+    ap.add_argument("--variants", default="fp64,fp16", help="extra solve variants to time (comma list)")
+    ap.add_argument("--sample-nvert", type=int, default=65, help="oracle sample size (vertices per axis)")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm=d.get("hbm_gbs", 6800.0), src="measured")
+    return dict(hbm=6800.0, src="fallback")
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.p = None
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [t.strip() for t in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if c[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_sample(nvert, smoother):
+    """The CPU oracle (as it stands, one thread) on the same recipe at a bounded
+    size: returns (DoF/s of the solve, seconds, DoF, iterations)."""
+    import oracle as O
+    from paper_2506_04763_gb300 import inputs as I
+    prob = I.config3(nvert)
+    m = O.Model(prob)
+    F, J, md = O.assemble(m, prob["u0"])
+    A = O.make_A(J, md, 1.0 / prob["H"])
+    gm = O.GMG(3, m.n, A, prob["dir"], I.levels_for(nvert), smoother=O.GS8 if smoother == "gs8" else O.JACOBI)
+    t0 = time.perf_counter()
+    x, info = O.bicgstab(3, m.n, A, gm, F, rtol=RTOL, maxit=200)
+    dt = time.perf_counter() - t0
+    dof = 2 * m.nv
+    return dof / dt, dt, dof, info["iterations"]
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    vals = []
+    for k in range(a.warmup + a.steps):
+        v, dt, dof, it = oracle_sample(a.sample_nvert, a.smoother)
+        if k >= a.warmup:
+            vals.append((v, dt, it))
+    value = statistics.median([v for v, _, _ in vals])
+    ms = statistics.median([dt for _, dt, _ in vals]) * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "config3 recipe (lognormal K seed 2 + 6 lenses), %d^3 vertices, FP64 "
+                                   "BiCGSTAB + FP64 GMG (8-colour GS V(2,2)), rel.res 1e-10" % a.sample_nvert,
+                       "dofs": 2 * a.sample_nvert ** 3},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": "oracle solve of the same recipe at %d^3 vertices (set-up excluded)"
+                                       % a.sample_nvert},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    a = args_()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__ as G
+    import paper_2506_04763_gb300 as rf
+    from paper_2506_04763_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    if rank == 0:
+        G.build()
+    if world > 1:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    prob = I.config3(a.nvert)
+    L = I.levels_for(a.nvert)
+    g = rf.Grid(prob)
+    dof = 2 * g.nv
+    u = torch.tensor(prob["u0"], device=dev)
+    F = torch.empty_like(u)
+    shift = 1.0 / prob["H"]
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # assembly (K0..K1): J, M, F(u0)
+    g.assemble(u, True, F)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    g.assemble(u, True, F)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    asm_ms = e0.elapsed_time(e1)
+
+    def setup(precision):
+        torch.cuda.synchronize()
+        s0, s1 = ev(), ev()
+        s0.record(stream)
+        g.gmg_setup([shift], rf.gmg_opts(L, a.smoother, precision=precision))
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1)
+
+    x = torch.empty_like(F)
+
+    def timed(nsteps, profile=False):
+        infos = []
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            g.profile(1)
+        l0 = rf.rf_launch_count()
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        for _ in range(nsteps):
+            infos.append(g.solve(0, F, x, rtol=RTOL, max_it=500))
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        launches = rf.rf_launch_count() - l0
+        prof = None
+        if profile:
+            g.profile(0)
+            prof = g.profile_read()
+        ms = t0.elapsed_time(t1) / nsteps
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, launches, prof
+
+    # ---- headline: FP32 (or chosen) GMG
+    setup_ms = setup(a.precision)
+    for _ in range(a.warmup):
+        g.solve(0, F, x, rtol=RTOL, max_it=500)
+    clk = Clocks(local) if rank == 0 else None
+    ms, infos, launches, prof = timed(a.steps, profile=True)
+    clocks = clk.stop() if clk else None
+    bad = [i for i in infos if i["status"] != 0 or i["relres"] > RTOL]
+    if bad:
+        raise SystemExit("solve did not reach rel.res %g: %s" % (RTOL, bad[0]))
+    value = world * dof / (ms / 1e3)
+    iters = infos[-1]["iterations"]
+
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    b_h = torch.empty(F.numel(), dtype=torch.float64, pin_memory=True)
+    b_h.copy_(F)
+    x_h = torch.empty_like(b_h).pin_memory()
+    bn, xn = b_h.numpy(), x_h.numpy()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    w0 = time.perf_counter()
+    for _ in range(a.steps):
+        g.solve(0, bn, xn, rtol=RTOL, max_it=500)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - w0) * 1e3 / a.steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel class, from the live event timings
+    pk = peaks()
+    cands = {k: v for k, v in prof.items() if k in ("spmv64", "smooth_fine", "resid_fine") and v["ms"] > 0}
+    dom = max(cands, key=lambda k: cands[k]["ms"])
+    dv = prof[dom]
+    achieved = dv["bytes"] / (dv["ms"] / 1e3) / 1e9
+    shares = {k: round(v["ms"] / sum(p["ms"] for p in prof.values()), 4) for k, v in prof.items()}
+    per_class = {k: {"ms_per_step": round(v["ms"] / a.steps, 3), "launches": v["launches"],
+                     "GB_per_s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
+                     "frac_hbm": round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / pk["hbm"], 3) if v["ms"] > 0 else None}
+                 for k, v in prof.items()}
+
+    # ---- variants of the same solve: all-FP64 GPU path, FP16 storage
+    variants = {}
+    for var in [v for v in a.variants.split(",") if v and v != a.precision]:
+        try:
+            vs = setup(var)
+            g.solve(0, F, x, rtol=RTOL, max_it=500)
+            vms, vinf, _, vprof = timed(max(1, min(3, a.steps)), profile=True)
+        except rf.RFError as e:
+            variants[var + "_gmg"] = {"error": str(e)}
+            continue
+        variants[var + "_gmg"] = {"value": world * dof / (vms / 1e3), "unit": "DoF/s", "ms_per_solve": round(vms, 2),
+                                  "iterations": vinf[-1]["iterations"], "relres": vinf[-1]["relres"],
+                                  "setup_ms": round(vs, 1), "speedup_of_headline": round(vms / ms, 3),
+                                  "per_class_ms_per_solve": {k: round(v["ms"] / len(vinf), 3)
+                                                             for k, v in vprof.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        v, dt, sdof, sit = oracle_sample(a.sample_nvert, a.smoother)
+        cpu = {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+               "sample": "oracle FP64 BiCGSTAB-GMG solve (set-up excluded) of the same recipe at %d^3 "
+                         "vertices (%d DoF, %d iterations, %.1f s)" % (a.sample_nvert, sdof, sit, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/%s" % a.precision.replace("fp", "f"), "data": "synthetic",
+            "config": {"workload": "config3: %d^3-vertex box, lognormal K (seed 2) + 6 lenses, A = M/h - J "
+                                   "(h = 10 s) at u0, b = F(u0); FP64 BiCGSTAB + %s GMG (%d levels, %s, "
+                                   "V(2,2)), x0 = 0, true rel.res <= 1e-10" % (a.nvert, a.precision.upper(), L,
+                                                                            "8-colour block GS" if a.smoother == "gs8" else "block Jacobi w=0.8"),
+                       "dofs": dof, "vertices": [a.nvert] * 3, "levels": L,
+                       "l2": "no flush: inputs larger than L2 (FP64 Jacobian %.1f GB)" % (dof / 2 * 864 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "iterations": iters, "relres": infos[-1]["relres"],
+            "setup_ms": round(setup_ms, 1), "assembly_ms": round(asm_ms, 1),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm"],
+                         "unit": "GB/s", "frac": round(achieved / pk["hbm"], 4), "traffic": None,
+                         "peak_source": pk["src"], "note": "of %s HBM copy bandwidth" % pk["src"]},
+            "per_class": per_class, "time_shares": shares,
+            "variants": variants,
+            "e2e": {"value": world * dof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": 16 * g.nv,
+                    "d2h_bytes_per_step": 16 * g.nv},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,24 @@ enum {
 rf_status rf_apply(rf_grid* g, int op, int level, int shift, const double* in0, const double* in1,
                    double* out, void* stream);
 
+/* Per-kernel-class timing (inspection hook).  While enabled, the library
+ * brackets each launch group of a class with CUDA events on the launching
+ * stream and accounts the group's ALGORITHMIC bytes (every matrix entry and
+ * every vector element counted once per launch).  rf_profile(g, 1) clears and
+ * starts, rf_profile(g, 0) stops; rf_profile_read synchronises the device and
+ * returns, for class cls, the summed event time (ms), launches and bytes. */
+enum {
+  RF_PROF_SPMV64 = 0,     /* outer FP64 operator applications (fused with dots)  */
+  RF_PROF_SMOOTH_FINE,    /* smoother sweeps on the finest level                 */
+  RF_PROF_RESID_FINE,     /* residual on the finest level                        */
+  RF_PROF_TRANSFER,       /* restrictions and prolongations, all levels          */
+  RF_PROF_COARSE_LEVELS,  /* smoothing/residual on levels >= 1, coarsest solve   */
+  RF_PROF_VECTOR,         /* BiCGSTAB vector updates and reduction finalisation  */
+  RF_PROF_NCLASS
+};
+rf_status rf_profile(rf_grid* g, int enable);
+rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, double* bytes);
+
 /* Kernels launched by this library in this process so far. */
 int64_t rf_launch_count(void);
 const char* rf_status_string(rf_status s);

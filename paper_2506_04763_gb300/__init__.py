@@ -19,6 +19,7 @@ RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ENOTCONV, RF_EBREAKDOWN, RF_ENONFINITE
 RF_SMOOTH_JACOBI, RF_SMOOTH_GS8 = 0, 1
 RF_PREC_FP64, RF_PREC_FP32, RF_PREC_FP16 = 0, 1, 2
 RF_OP_SPMV, RF_OP_VCYCLE, RF_OP_SMOOTH, RF_OP_RESIDUAL, RF_OP_RESTRICT, RF_OP_PROLONG, RF_OP_COARSE = range(7)
+PROF_CLASSES = ["spmv64", "smooth_fine", "resid_fine", "transfer", "coarse_levels", "vector"]
 
 
 class RFError(RuntimeError):
@@ -98,6 +99,8 @@ SIGNATURES = {
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
     "rf_apply": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "rf_profile": (_I, [_P, _I]),
+    "rf_profile_read": (_I, [_P, _I, _P, _P, _P]),
     "rf_launch_count": (_I64, []),
     "rf_status_string": (ctypes.c_char_p, [_I]),
     "rf_last_error": (ctypes.c_char_p, []),
@@ -175,6 +178,18 @@ def rf_export_level(grid, level, shift, A_host, dims_host, stream):
 
 def rf_apply(grid, op, level, shift, in0, in1, out, stream):
     _check(lib().rf_apply(grid, int(op), int(level), int(shift), in0, in1, out, stream))
+
+
+def rf_profile(grid, enable):
+    _check(lib().rf_profile(grid, int(enable)))
+
+
+def rf_profile_read(grid, cls):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    by = ctypes.c_double()
+    _check(lib().rf_profile_read(grid, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
+    return ms.value, n.value, by.value
 
 
 def rf_launch_count():
@@ -293,6 +308,13 @@ class Grid:
         st, info = rf_limex_step(self.handle, _ptr(u), H, o, self.stream)
         return dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted, solves=info.solves,
                     iterations=info.iterations)
+
+    def profile(self, enable):
+        rf_profile(self.handle, enable)
+
+    def profile_read(self):
+        return {name: dict(zip(("ms", "launches", "bytes"), rf_profile_read(self.handle, c)))
+                for c, name in enumerate(PROF_CLASSES)}
 
     def export_jacobian(self):
         J = np.zeros((self.nv, self.nb, 4))

@@ -113,7 +113,48 @@ struct rf_grid {
   int T_kappa = 0;
   double* du = nullptr;
   double* norms = nullptr;
+  // profiling (rf_profile)
+  struct ProfRec { cudaEvent_t a, b; int cls; double bytes; int launches; };
+  bool prof_on = false;
+  std::vector<ProfRec> prec;
+  std::vector<cudaEvent_t> evpool;
+  size_t evnext = 0;
 };
+
+// ------------------------------------------------------------------ profiling
+static cudaEvent_t prof_event(rf_grid* g) {
+  if (g->evnext < g->evpool.size()) return g->evpool[g->evnext++];
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  g->evpool.push_back(e);
+  g->evnext++;
+  return e;
+}
+
+// Brackets one launch group of class `cls` with events when profiling is on.
+struct ProfScope {
+  rf_grid* g;
+  void* s;
+  int cls, launches;
+  double bytes;
+  cudaEvent_t a{};
+  bool on;
+  ProfScope(rf_grid* g_, void* s_, int cls_, double bytes_, int launches_)
+      : g(g_), s(s_), cls(cls_), launches(launches_), bytes(bytes_), on(g_->prof_on) {
+    if (on) { a = prof_event(g); cudaEventRecord(a, (cudaStream_t)s); }
+  }
+  ~ProfScope() {
+    if (!on) return;
+    cudaEvent_t b = prof_event(g);
+    cudaEventRecord(b, (cudaStream_t)s);
+    g->prec.push_back({a, b, cls, bytes, launches});
+  }
+};
+
+// algorithmic bytes of the level kernels (each matrix entry / vector element once)
+static double blk_bytes(int kind) { return kind == STORE_F64 ? 32.0 : (kind == STORE_F32 ? 16.0 : 8.0); }
+static double tb(int kind) { return kind == STORE_F64 ? 8.0 : 4.0; }
+static double row_extra(int kind) { return kind == STORE_F16 ? 16.0 : 0.0; }  // FP16 row scales
 
 // ------------------------------------------------------------------ memory
 static void* dalloc(rf_grid* g, size_t bytes, void* stream, bool hierarchy) {
@@ -209,9 +250,39 @@ extern "C" const char* rf_status_string(rf_status s) {
   return "unknown status";
 }
 
+extern "C" rf_status rf_profile(rf_grid* g, int enable) {
+  if (!g) return fail(RF_EINVAL, "grid is required");
+  if (enable) {
+    g->prec.clear();
+    g->evnext = 0;
+  }
+  g->prof_on = enable != 0;
+  return RF_OK;
+}
+
+extern "C" rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, double* bytes) {
+  if (!g || cls < 0 || cls >= RF_PROF_NCLASS) return fail(RF_EINVAL, "bad grid or class");
+  CU(cudaDeviceSynchronize());
+  double t = 0.0, by = 0.0;
+  int64_t n = 0;
+  for (auto& r : g->prec) {
+    if (r.cls != cls) continue;
+    float e = 0.f;
+    CU(cudaEventElapsedTime(&e, r.a, r.b));
+    t += e;
+    by += r.bytes;
+    n += r.launches;
+  }
+  if (ms) *ms = t;
+  if (launches) *launches = n;
+  if (bytes) *bytes = by;
+  return RF_OK;
+}
+
 extern "C" void rf_grid_destroy(rf_grid* g) {
   if (!g) return;
   cudaDeviceSynchronize();
+  for (auto e : g->evpool) cudaEventDestroy(e);
   dfree_all(g, g->gbufs, nullptr);
   dfree_all(g, g->bufs, nullptr);
   if (g->hscal) cudaFreeHost(g->hscal);
@@ -488,25 +559,46 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
 }
 
 // ------------------------------------------------------------------ V-cycle
+// bytes of one smoothing sweep on a level of nv vertices
+static double sweep_bytes(rf_grid* g, int l, bool zero_x) {
+  const Dims& d = g->L[l].d;
+  const int k = g->kind;
+  const double T = tb(k), nv = (double)d.nv;
+  if (g->gopt.smoother == RF_SMOOTH_JACOBI) {
+    if (zero_x) return nv * (4 * T + 4 * T);  // Dinv, b, x out
+    return nv * (d.nb * blk_bytes(k) + row_extra(k) + (l == 0 ? 16.0 : 0.0) + 4 * T + 6 * T);
+  }
+  return nv * ((d.nb - 1) * blk_bytes(k) + row_extra(k) + 4 * T + 6 * T);  // GS: off-diagonal blocks
+}
+
 static void smooth_pre(rf_grid* g, int l, int sh, const void* b, void* x_final, void** cur, void* s) {
   LevelOp op = level_op(g, l, sh);
   Level& Lv = g->L[l];
   const rf_gmg_opts& o = g->gopt;
   const size_t te = t_size(g->kind);
+  const int cls = l == 0 ? RF_PROF_SMOOTH_FINE : RF_PROF_COARSE_LEVELS;
+  const int ncol = 1 << Lv.d.dim;
   if (o.smoother == RF_SMOOTH_JACOBI) {
     const int W = o.nu1 + o.nu2;
     void* first = (W % 2 == 1) ? x_final : Lv.t;
     void* c = first;
-    launch_jacobi(op, b, nullptr, first, o.omega, true, s);
+    {
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, true), 1);
+      launch_jacobi(op, b, nullptr, first, o.omega, true, s);
+    }
     for (int k = 1; k < o.nu1; ++k) {
       void* dst = (c == x_final) ? Lv.t : x_final;
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, false), 1);
       launch_jacobi(op, b, c, dst, o.omega, false, s);
       c = dst;
     }
     *cur = c;
   } else {
     cudaMemsetAsync(x_final, 0, (size_t)Lv.d.nv * 2 * te, (cudaStream_t)s);
-    for (int k = 0; k < o.nu1; ++k) launch_gs_sweep(op, b, x_final, true, k == 0, s);
+    for (int k = 0; k < o.nu1; ++k) {
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, false), ncol);
+      launch_gs_sweep(op, b, x_final, true, k == 0, s);
+    }
     *cur = x_final;
   }
 }
@@ -515,32 +607,53 @@ static void smooth_post(rf_grid* g, int l, int sh, const void* b, void* x_final,
   LevelOp op = level_op(g, l, sh);
   Level& Lv = g->L[l];
   const rf_gmg_opts& o = g->gopt;
+  const int cls = l == 0 ? RF_PROF_SMOOTH_FINE : RF_PROF_COARSE_LEVELS;
+  const int ncol = 1 << Lv.d.dim;
   if (o.smoother == RF_SMOOTH_JACOBI) {
     void* c = cur;
     for (int k = 0; k < o.nu2; ++k) {
       void* dst = (c == x_final) ? Lv.t : x_final;
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, false), 1);
       launch_jacobi(op, b, c, dst, o.omega, false, s);
       c = dst;
     }
   } else {
-    for (int k = 0; k < o.nu2; ++k) launch_gs_sweep(op, b, x_final, false, false, s);
+    for (int k = 0; k < o.nu2; ++k) {
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, false), ncol);
+      launch_gs_sweep(op, b, x_final, false, false, s);
+    }
   }
 }
 
 static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void* s) {
+  const int k = g->kind;
+  const double T = tb(k);
   if (l == g->nl - 1) {
+    const double N = 2.0 * g->L[l].d.nv;
+    ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, N * N * 8.0 + 2 * N * T, 1);
     launch_coarse_solve(level_op(g, l, sh), g->Ainv[sh], b, x, s);
     return;
   }
   Level& Lv = g->L[l];
   Level& Lc = g->L[l + 1];
+  const double nvf = (double)Lv.d.nv, nvc = (double)Lc.d.nv;
   void* cur = nullptr;
   smooth_pre(g, l, sh, b, x, &cur, s);
   LevelOp op = level_op(g, l, sh), opc = level_op(g, l + 1, sh);
-  launch_residual(op, b, cur, Lv.r, s);
-  launch_restrict(op, opc, Lv.r, Lc.b, s);
+  {
+    ProfScope ps(g, s, l == 0 ? RF_PROF_RESID_FINE : RF_PROF_COARSE_LEVELS,
+                 nvf * (Lv.d.nb * blk_bytes(k) + row_extra(k) + (l == 0 ? 16.0 : 0.0) + 6 * T), 1);
+    launch_residual(op, b, cur, Lv.r, s);
+  }
+  {
+    ProfScope ps(g, s, RF_PROF_TRANSFER, nvf * (2 * T + 1) + nvc * (2 * T + 1), 1);
+    launch_restrict(op, opc, Lv.r, Lc.b, s);
+  }
   vcycle_level(g, l + 1, sh, Lc.b, Lc.x, s);
-  launch_prolong(op, opc, Lc.x, cur, s);
+  {
+    ProfScope ps(g, s, RF_PROF_TRANSFER, nvf * (4 * T + 1) + nvc * (2 * T + 1), 1);
+    launch_prolong(op, opc, Lc.x, cur, s);
+  }
   smooth_post(g, l, sh, b, x, cur, s);
 }
 
@@ -571,14 +684,31 @@ static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int 
     result = RF_OK;
   } else {
     const double bn = std::sqrt(bb);
+    const double T = tb(g->kind), nv = (double)d.nv;
+    const double spmv_bytes = nv * (d.nb * 32.0 + 16.0 + 2 * T + 16.0 + 16.0);
     for (it = 1; it <= max_it; ++it) {
-      launch_bicg_p(d.nv, K, lo32, it == 1, s);
+      {
+        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 4 + 2 * T), 1);
+        launch_bicg_p(d.nv, K, lo32, it == 1, s);
+      }
       vcycle_level(g, 0, sh, K.p_lo, K.y, s);
-      launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
-      launch_bicg_s(d.nv, K, lo32, s);
+      {
+        ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
+        launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+      }
+      {
+        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 3 + 2 * T), 1);
+        launch_bicg_s(d.nv, K, lo32, s);
+      }
       vcycle_level(g, 0, sh, K.s_lo, K.z, s);
-      launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
-      launch_bicg_xr(d.nv, K, lo32, rtol, s);
+      {
+        ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
+        launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+      }
+      {
+        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (4 * T + 16.0 * 6), 1);
+        launch_bicg_xr(d.nv, K, lo32, rtol, s);
+      }
       if ((st = read_scal(g, s))) return st;
       if (g->hscal[H_BAD] != 0.0) { result = RF_ENONFINITE; break; }
       if (g->hscal[H_CONV] != 0.0 || g->hscal[H_BREAK] != 0.0) {

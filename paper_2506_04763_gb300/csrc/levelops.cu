@@ -376,8 +376,10 @@ __global__ void k_pack(Dims d, bool fine, const double* __restrict__ J, const do
       }
     }
     if (KIND == STORE_F16) {
+      // A position whose largest magnitude is below the smallest normal float
+      // holds only entries that FP32 arithmetic flushes anyway: scale 1, entries 0.
       float sc[4];
-      for (int q = 0; q < 4; ++q) sc[q] = mx[q] > 0.0 ? (float)mx[q] : 1.0f;
+      for (int q = 0; q < 4; ++q) sc[q] = mx[q] >= 1.17549435e-38 ? (float)mx[q] : 1.0f;
       reinterpret_cast<float4*>(scale)[p] = make_float4(sc[0], sc[1], sc[2], sc[3]);
       for (int b = 0; b < nb; ++b) {
         const double* a = J + ((int64_t)b * d.nv + p) * 4;
@@ -387,7 +389,7 @@ __global__ void k_pack(Dims d, bool fine, const double* __restrict__ J, const do
           e[0] = -e[0]; e[1] = shift * m[0] - e[1]; e[2] = -e[2]; e[3] = shift * m[1] - e[3];
         }
         __half* o = reinterpret_cast<__half*>(Aout) + ((int64_t)b * d.nv + p) * 4;
-        for (int q = 0; q < 4; ++q) o[q] = __double2half((double)(float)(e[q] / (double)sc[q]));
+        for (int q = 0; q < 4; ++q) o[q] = __double2half(e[q] / (double)sc[q]);
       }
     }
   }
