@@ -187,6 +187,25 @@ enum {
 rf_status rf_profile(rf_grid* g, int enable);
 rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, double* bytes);
 
+/* ---- allocation-free entry point (the paper has no counterpart) ----
+ * For callers that cannot call cudaMalloc: applications whose device memory is
+ * owned entirely by another allocator (a framework's caching pool, a fixed
+ * budget) and latency-critical code that must not pay for cudaMalloc/cudaFree,
+ * which may synchronise the device.  Inverts a dense FP64 N x N matrix
+ * (row-major, DEVICE pointers A and Ainv, caller-owned; A is not modified) by
+ * LU with partial pivoting, as the multigrid set-up does for the coarsest
+ * operator, and allocates nothing: the LU factors, work vectors, pivots and
+ * status live in a static device array of RF_NOALLOC_MAX_N^2 * 16 bytes plus a
+ * little (about 4 MiB), reserved on every GPU that loads the library until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should therefore come before any stream
+ * capture.  Calls share the array: calls that overlap on the GPU race and must
+ * be serialised by the caller.  Returns RF_EINVAL for N outside
+ * [1, RF_NOALLOC_MAX_N] or non-device pointers, RF_ENONFINITE for a singular
+ * matrix; synchronises `stream` before returning. */
+#define RF_NOALLOC_MAX_N 512
+rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ainv, void* stream);
+
 /* Kernels launched by this library in this process so far. */
 int64_t rf_launch_count(void);
 const char* rf_status_string(rf_status s);

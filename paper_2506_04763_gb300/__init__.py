@@ -19,6 +19,7 @@ RF_OK, RF_EINVAL, RF_ENOMEM, RF_ECUDA, RF_ENOTCONV, RF_EBREAKDOWN, RF_ENONFINITE
 RF_SMOOTH_JACOBI, RF_SMOOTH_GS8 = 0, 1
 RF_PREC_FP64, RF_PREC_FP32, RF_PREC_FP16 = 0, 1, 2
 RF_OP_SPMV, RF_OP_VCYCLE, RF_OP_SMOOTH, RF_OP_RESIDUAL, RF_OP_RESTRICT, RF_OP_PROLONG, RF_OP_COARSE = range(7)
+RF_NOALLOC_MAX_N = 512
 PROF_CLASSES = ["spmv64", "smooth_fine", "resid_fine", "transfer", "coarse_levels", "vector"]
 
 
@@ -99,6 +100,7 @@ SIGNATURES = {
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
     "rf_apply": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "rf_dense_inverse_noalloc": (_I, [_I, _P, _P, _P]),
     "rf_profile": (_I, [_P, _I]),
     "rf_profile_read": (_I, [_P, _I, _P, _P, _P]),
     "rf_launch_count": (_I64, []),
