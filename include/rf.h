@@ -149,6 +149,12 @@ rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* op
  * mass diagonal as [nv][2] (dm_w/dS_n, dm_n/dS_n); either may be NULL. */
 rf_status rf_export_jacobian(rf_grid* g, double* J_host, double* mdiag_host, void* stream);
 
+/* Copy out the Jacobian block rows [count][nb][4] and mass diagonals
+ * [count][2] of the listed vertices (natural indices, host array) — for
+ * sampled checks on grids too large to export whole. */
+rf_status rf_export_rows(rf_grid* g, const int64_t* vertices, int count, double* J_rows_host,
+                         double* mdiag_host, void* stream);
+
 /* Copy out the multigrid operator of `level` for shift index `shift` as
  * [nv_l][nb][4] in FP64 (the Galerkin product as computed; level 0 is
  * shift*M - J); dims_out[3] receives the level's vertex counts. */

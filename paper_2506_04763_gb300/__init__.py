@@ -99,6 +99,7 @@ SIGNATURES = {
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
+    "rf_export_rows": (_I, [_P, _P, _I, _P, _P, _P]),
     "rf_apply": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
     "rf_dense_inverse_noalloc": (_I, [_I, _P, _P, _P]),
     "rf_profile": (_I, [_P, _I]),
@@ -322,6 +323,13 @@ class Grid:
         J = np.zeros((self.nv, self.nb, 4))
         md = np.zeros((self.nv, 2))
         rf_export_jacobian(self.handle, _ptr(J), _ptr(md), self.stream)
+        return J, md
+
+    def export_rows(self, vertices):
+        v = np.ascontiguousarray(vertices, dtype=np.int64)
+        J = np.zeros((len(v), self.nb, 4))
+        md = np.zeros((len(v), 2))
+        _check(lib().rf_export_rows(self.handle, _ptr(v), len(v), _ptr(J), _ptr(md), self.stream))
         return J, md
 
     def export_level(self, level, shift):

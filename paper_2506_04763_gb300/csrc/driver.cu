@@ -119,10 +119,30 @@ struct rf_grid {
   std::vector<ProfRec> prec;
   std::vector<cudaEvent_t> evpool;
   size_t evnext = 0;
+  double acc_ms[RF_PROF_NCLASS] = {}, acc_bytes[RF_PROF_NCLASS] = {};
+  int64_t acc_launches[RF_PROF_NCLASS] = {};
+  // one BiCGSTAB iteration captured as a CUDA graph, per shift and profiling flag
+  struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;                 // kernel launches per replay
+    std::vector<ProfRec> recs;           // event pairs recorded by the graph
+    std::vector<cudaEvent_t> events;     // owned by the graph
+  };
+  IterGraph ig[RF_MAXSHIFT][2];
+  bool capturing = false;
+  IterGraph* cap = nullptr;
+  cudaStream_t cs = nullptr;             // internal stream for the iteration
+  cudaEvent_t join_in = nullptr, join_out = nullptr;
 };
 
 // ------------------------------------------------------------------ profiling
 static cudaEvent_t prof_event(rf_grid* g) {
+  if (g->capturing) {                    // events baked into a graph belong to it
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g->cap->events.push_back(e);
+    return e;
+  }
   if (g->evnext < g->evpool.size()) return g->evpool[g->evnext++];
   cudaEvent_t e;
   cudaEventCreate(&e);
@@ -131,7 +151,13 @@ static cudaEvent_t prof_event(rf_grid* g) {
   return e;
 }
 
-// Brackets one launch group of class `cls` with events when profiling is on.
+static void prof_record(rf_grid* g, cudaEvent_t e, void* s) {
+  if (g->capturing) cudaEventRecordWithFlags(e, (cudaStream_t)s, cudaEventRecordExternal);
+  else cudaEventRecord(e, (cudaStream_t)s);
+}
+
+// Brackets one launch group of class `cls` with events when profiling is on
+// (inside a graph capture the events become event-record nodes of the graph).
 struct ProfScope {
   rf_grid* g;
   void* s;
@@ -141,15 +167,24 @@ struct ProfScope {
   bool on;
   ProfScope(rf_grid* g_, void* s_, int cls_, double bytes_, int launches_)
       : g(g_), s(s_), cls(cls_), launches(launches_), bytes(bytes_), on(g_->prof_on) {
-    if (on) { a = prof_event(g); cudaEventRecord(a, (cudaStream_t)s); }
+    if (on) { a = prof_event(g); prof_record(g, a, s); }
   }
   ~ProfScope() {
     if (!on) return;
     cudaEvent_t b = prof_event(g);
-    cudaEventRecord(b, (cudaStream_t)s);
-    g->prec.push_back({a, b, cls, bytes, launches});
+    prof_record(g, b, s);
+    (g->capturing ? g->cap->recs : g->prec).push_back({a, b, cls, bytes, launches});
   }
 };
+
+static void destroy_graphs(rf_grid* g) {
+  for (auto& row : g->ig)
+    for (auto& G : row) {
+      if (G.exec) cudaGraphExecDestroy(G.exec);
+      for (auto e : G.events) cudaEventDestroy(e);
+      G = rf_grid::IterGraph();
+    }
+}
 
 // algorithmic bytes of the level kernels (each matrix entry / vector element once)
 static double blk_bytes(int kind) { return kind == STORE_F64 ? 32.0 : (kind == STORE_F32 ? 16.0 : 8.0); }
@@ -255,6 +290,7 @@ extern "C" rf_status rf_profile(rf_grid* g, int enable) {
   if (enable) {
     g->prec.clear();
     g->evnext = 0;
+    for (int c = 0; c < RF_PROF_NCLASS; ++c) { g->acc_ms[c] = 0.0; g->acc_bytes[c] = 0.0; g->acc_launches[c] = 0; }
   }
   g->prof_on = enable != 0;
   return RF_OK;
@@ -263,8 +299,8 @@ extern "C" rf_status rf_profile(rf_grid* g, int enable) {
 extern "C" rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, double* bytes) {
   if (!g || cls < 0 || cls >= RF_PROF_NCLASS) return fail(RF_EINVAL, "bad grid or class");
   CU(cudaDeviceSynchronize());
-  double t = 0.0, by = 0.0;
-  int64_t n = 0;
+  double t = g->acc_ms[cls], by = g->acc_bytes[cls];
+  int64_t n = g->acc_launches[cls];
   for (auto& r : g->prec) {
     if (r.cls != cls) continue;
     float e = 0.f;
@@ -282,7 +318,11 @@ extern "C" rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* l
 extern "C" void rf_grid_destroy(rf_grid* g) {
   if (!g) return;
   cudaDeviceSynchronize();
+  destroy_graphs(g);
   for (auto e : g->evpool) cudaEventDestroy(e);
+  if (g->join_in) cudaEventDestroy(g->join_in);
+  if (g->join_out) cudaEventDestroy(g->join_out);
+  if (g->cs) cudaStreamDestroy(g->cs);
   dfree_all(g, g->gbufs, nullptr);
   dfree_all(g, g->bufs, nullptr);
   if (g->hscal) cudaFreeHost(g->hscal);
@@ -381,6 +421,13 @@ extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* f
     rf_grid_destroy(g);
     return fail(RF_ENOMEM, "pinned host allocation failed");
   }
+  if (cudaStreamCreateWithFlags(&g->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->join_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->join_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    rf_grid_destroy(g);
+    return fail(RF_ECUDA, "internal stream creation failed");
+  }
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) { rf_grid_destroy(g); return fail(RF_ECUDA, "grid set-up: %s", cudaGetErrorString(e)); }
@@ -429,6 +476,53 @@ static LevelOp level_op(rf_grid* g, int l, int sh) {
   return op;
 }
 
+static void dfree_ptr(rf_grid* g, void* p, void* s) {
+  for (size_t i = 0; i < g->gbufs.size(); ++i)
+    if (g->gbufs[i].p == p) {
+      if (g->user_alloc) g->alloc.free(p, g->gbufs[i].bytes, s, g->alloc.ctx);
+      else cudaFree(p);
+      g->gbufs.erase(g->gbufs.begin() + i);
+      return;
+    }
+}
+
+// Galerkin operators of level C from level F, one axis at a time (x, y[, z]);
+// intermediate operators live only for the duration of the call.
+static rf_status galerkin_level(rf_grid* g, const Level& F, Level& C, bool from_fine, void* s) {
+  const int dim = F.d.dim;
+  const double* Jin = from_fine ? g->J : F.Jc;
+  const double* Min = from_fine ? nullptr : F.Mc;
+  const double* md = from_fine ? g->mdiag : nullptr;
+  int n[3] = {F.d.nx, F.d.ny, F.d.nz};
+  Dims cur = F.d;
+  std::vector<void*> temps;
+  rf_status st = RF_OK;
+  for (int axis = 0; axis < dim; ++axis) {
+    n[axis] = (n[axis] - 1) / 2 + 1;
+    const Dims nxt = make_dims(dim, n);
+    const bool last = axis == dim - 1;
+    double* Jo = C.Jc;
+    double* Mo = C.Mc;
+    if (!last) {
+      Jo = (double*)dalloc(g, sizeof(double) * 4 * nxt.nb * nxt.nv, s, true);
+      Mo = (double*)dalloc(g, sizeof(double) * 2 * nxt.nb * nxt.nv, s, true);
+      if (Jo) temps.push_back(Jo);
+      if (Mo) temps.push_back(Mo);
+      if (!Jo || !Mo) { st = fail(RF_ENOMEM, "Galerkin temporaries"); break; }
+    }
+    launch_galerkin_axis(axis, cur, axis == 0 ? F.dmask : nullptr, Jin, Min, md, nxt, last ? C.dmask : nullptr, Jo,
+                         Mo, s);
+    Jin = Jo;
+    Min = Mo;
+    md = nullptr;
+    cur = nxt;
+  }
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)s);
+  for (void* p : temps) dfree_ptr(g, p, s);
+  if (st == RF_OK && e != cudaSuccess) st = fail(RF_ECUDA, "Galerkin: %s", cudaGetErrorString(e));
+  return st;
+}
+
 #define GNEED(ptr)                                                                     \
   do {                                                                                 \
     if (!(ptr)) { dfree_all(g, g->gbufs, s); return fail(RF_ENOMEM, "device allocation failed (%s)", #ptr); } \
@@ -445,6 +539,8 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
   for (int j = 0; j < nshift; ++j)
     if (!(shifts[j] >= 0.0) || !std::isfinite(shifts[j])) return fail(RF_EINVAL, "shifts must be finite and >= 0");
   CU(cudaStreamSynchronize((cudaStream_t)s));
+  CU(cudaStreamSynchronize(g->cs));
+  destroy_graphs(g);
   dfree_all(g, g->gbufs, s);
   for (int l = 0; l < RF_MAXL; ++l) g->L[l] = Level();
   for (int j = 0; j < RF_MAXSHIFT; ++j) g->Ainv[j] = nullptr;
@@ -483,11 +579,8 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       launch_coarse_mask(g->L[l - 1].d, g->L[l - 1].dmask, d, Lv.dmask, s);
       GNEED(Lv.Jc = (double*)dalloc(g, sizeof(double) * 4 * d.nb * d.nv, s, true));
       GNEED(Lv.Mc = (double*)dalloc(g, sizeof(double) * 2 * d.nb * d.nv, s, true));
-      const Level& F = g->L[l - 1];
-      if (l == 1)
-        launch_galerkin(F.d, F.nb, F.dmask, g->J, nullptr, g->mdiag, d, Lv.dmask, Lv.Jc, Lv.Mc, s);
-      else
-        launch_galerkin(F.d, F.nb, F.dmask, F.Jc, F.Mc, nullptr, d, Lv.dmask, Lv.Jc, Lv.Mc, s);
+      rf_status gst = galerkin_level(g, g->L[l - 1], Lv, l == 1, s);
+      if (gst) { dfree_all(g, g->gbufs, s); return gst; }
     }
     const size_t te = t_size(kind), se = s_size(kind);
     if (l < g->nl - 1 || g->nl == 1) {
@@ -551,6 +644,13 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     GNEED(g->K.z = dvec(g, g->d, te, s, true));
     GNEED(g->K.p_lo = dvec(g, g->d, te, s, true));
     GNEED(g->K.s_lo = dvec(g, g->d, te, s, true));
+    if (kind == STORE_F64) {
+      g->K.y64 = (double2*)g->K.y;
+      g->K.z64 = (double2*)g->K.z;
+    } else {
+      GNEED(g->K.y64 = (double2*)dvec(g, g->d, sizeof(double), s, true));
+      GNEED(g->K.z64 = (double2*)dvec(g, g->d, sizeof(double), s, true));
+    }
   }
   CU(cudaStreamSynchronize((cudaStream_t)s));
   CU(cudaGetLastError());
@@ -568,7 +668,10 @@ static double sweep_bytes(rf_grid* g, int l, bool zero_x) {
     if (zero_x) return nv * (4 * T + 4 * T);  // Dinv, b, x out
     return nv * (d.nb * blk_bytes(k) + row_extra(k) + (l == 0 ? 16.0 : 0.0) + 4 * T + 6 * T);
   }
-  return nv * ((d.nb - 1) * blk_bytes(k) + row_extra(k) + 4 * T + 6 * T);  // GS: off-diagonal blocks
+  // GS: off-diagonal blocks; the first sweep from zero reads only the blocks
+  // that reach already-visited colours, half of them over the 2^d colours
+  if (zero_x) return nv * ((d.nb - 1) * 0.5 * blk_bytes(k) + row_extra(k) + 4 * T + 2 * T + 2 * T + 2 * T * 0.5);
+  return nv * ((d.nb - 1) * blk_bytes(k) + row_extra(k) + 4 * T + 6 * T);
 }
 
 static void smooth_pre(rf_grid* g, int l, int sh, const void* b, void* x_final, void** cur, void* s) {
@@ -594,9 +697,11 @@ static void smooth_pre(rf_grid* g, int l, int sh, const void* b, void* x_final, 
     }
     *cur = c;
   } else {
-    cudaMemsetAsync(x_final, 0, (size_t)Lv.d.nv * 2 * te, (cudaStream_t)s);
+    // the first forward sweep skips every not-yet-visited neighbour, so x
+    // needs no clearing
+    (void)te;
     for (int k = 0; k < o.nu1; ++k) {
-      ProfScope ps(g, s, cls, sweep_bytes(g, l, false), ncol);
+      ProfScope ps(g, s, cls, sweep_bytes(g, l, k == 0), ncol);
       launch_gs_sweep(op, b, x_final, true, k == 0, s);
     }
     *cur = x_final;
@@ -666,13 +771,119 @@ static rf_status read_scal(rf_grid* g, void* s) {
   return RF_OK;
 }
 
-// Solve A_sh x = b with b, x parity-split device pairs (x is g->K.x on return).
-static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info, void* s) {
+// One BiCGSTAB iteration, both V-cycles included, launched on stream s.
+static void iteration_body(rf_grid* g, int sh, void* s) {
   const Dims& d = g->d;
   const bool lo32 = g->kind != STORE_F64;
   KrylovVecs& K = g->K;
   const double shift = g->shifts[sh];
-  launch_bicg_init(d.nv, b, K, s);
+  const double T = tb(g->kind), nv = (double)d.nv;
+  const double spmv_bytes = nv * (d.nb * 32.0 + 16.0 + 16.0 + 16.0 + 16.0);
+  {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 4 + 2 * T), 1);
+    launch_bicg_p(d.nv, K, lo32, false, s);
+  }
+  vcycle_level(g, 0, sh, K.p_lo, K.y, s);
+  if (lo32) {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (2 * T + 16.0), 1);
+    launch_cast_f32_to_f64((const float*)K.y, (double*)K.y64, 2 * d.nv, s);
+  }
+  {
+    ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
+    launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+  }
+  {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 3 + 2 * T), 1);
+    launch_bicg_s(d.nv, K, lo32, s);
+  }
+  vcycle_level(g, 0, sh, K.s_lo, K.z, s);
+  if (lo32) {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (2 * T + 16.0), 1);
+    launch_cast_f32_to_f64((const float*)K.z, (double*)K.z64, 2 * d.nv, s);
+  }
+  {
+    ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
+    launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+  }
+  {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (4 * T + 16.0 * 6), 1);
+    launch_bicg_xr(d.nv, K, lo32, s);
+  }
+}
+
+// Run one iteration and bring its scalars to the host.  The iteration is
+// captured once per (shift, profiling) as a CUDA graph and replayed: the ~300
+// launches of the V-cycles, most of them on small coarse levels, then cost
+// GPU-side dispatch only.  RF_NO_GRAPHS=1 in the environment runs it eagerly.
+static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
+  static const bool eager = getenv("RF_NO_GRAPHS") && getenv("RF_NO_GRAPHS")[0] == '1';
+  if (eager) {
+    iteration_body(g, sh, cs);
+    return read_scal(g, cs);
+  }
+  const bool prof = g->prof_on;
+  rf_grid::IterGraph& G = g->ig[sh][prof ? 1 : 0];
+  if (!G.exec) {
+    const int64_t c0 = g_launches.load();
+    CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    g->capturing = true;
+    g->cap = &G;
+    iteration_body(g, sh, cs);
+    cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, cs);
+    g->capturing = false;
+    g->cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    G.kernels = g_launches.load() - c0;   // counted again at every replay
+    g_launches.fetch_sub(G.kernels);
+    if (e != cudaSuccess) return fail(RF_ECUDA, "iteration capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      G.exec = nullptr;
+      return fail(RF_ECUDA, "iteration graph: %s", cudaGetErrorString(e));
+    }
+  }
+  CU(cudaGraphLaunch(G.exec, cs));
+  g_launches.fetch_add(G.kernels);
+  CU(cudaStreamSynchronize(cs));
+  if (prof)
+    for (auto& r : G.recs) {
+      float e = 0.f;
+      CU(cudaEventElapsedTime(&e, r.a, r.b));
+      g->acc_ms[r.cls] += e;
+      g->acc_bytes[r.cls] += r.bytes;
+      g->acc_launches[r.cls] += r.launches;
+    }
+  return RF_OK;
+}
+
+static rf_status solve_cs(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info,
+                          cudaStream_t s);
+
+// Solve A_sh x = b with b, x parity-split device pairs (x is g->K.x on return).
+// The iteration runs on the grid's internal stream, ordered after and before
+// the caller's stream.
+static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info, void* s) {
+  CU(cudaEventRecord(g->join_in, (cudaStream_t)s));
+  CU(cudaStreamWaitEvent(g->cs, g->join_in, 0));
+  rf_status r = solve_cs(g, sh, b, rtol, max_it, info, g->cs);
+  cudaEventRecord(g->join_out, g->cs);
+  cudaStreamWaitEvent((cudaStream_t)s, g->join_out, 0);
+  return r;
+}
+
+static rf_status solve_cs(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info,
+                          cudaStream_t s) {
+  const Dims& d = g->d;
+  KrylovVecs& K = g->K;
+  const double shift = g->shifts[sh];
+  const double nvd = (double)d.nv;
+  const double true_res_bytes = nvd * (d.nb * 32.0 + 16.0 + 16.0 + 16.0 + 16.0);
+  {
+    ProfScope ps(g, s, RF_PROF_VECTOR, nvd * 16.0 * 6, 1);
+    launch_bicg_init(d.nv, b, K, rtol, s);
+  }
   rf_status st = read_scal(g, s);
   if (st) return st;
   const double bb = g->hscal[H_BB];
@@ -684,35 +895,14 @@ static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int 
     result = RF_OK;
   } else {
     const double bn = std::sqrt(bb);
-    const double T = tb(g->kind), nv = (double)d.nv;
-    const double spmv_bytes = nv * (d.nb * 32.0 + 16.0 + 2 * T + 16.0 + 16.0);
     for (it = 1; it <= max_it; ++it) {
-      {
-        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 4 + 2 * T), 1);
-        launch_bicg_p(d.nv, K, lo32, it == 1, s);
-      }
-      vcycle_level(g, 0, sh, K.p_lo, K.y, s);
-      {
-        ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
-        launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
-      }
-      {
-        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 3 + 2 * T), 1);
-        launch_bicg_s(d.nv, K, lo32, s);
-      }
-      vcycle_level(g, 0, sh, K.s_lo, K.z, s);
-      {
-        ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
-        launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
-      }
-      {
-        ProfScope ps(g, s, RF_PROF_VECTOR, nv * (4 * T + 16.0 * 6), 1);
-        launch_bicg_xr(d.nv, K, lo32, rtol, s);
-      }
-      if ((st = read_scal(g, s))) return st;
+      if ((st = run_iteration(g, sh, s))) return st;
       if (g->hscal[H_BAD] != 0.0) { result = RF_ENONFINITE; break; }
       if (g->hscal[H_CONV] != 0.0 || g->hscal[H_BREAK] != 0.0) {
-        launch_true_residual(d, g->nb, g->J, g->mdiag, shift, b, K, s);
+        {
+          ProfScope ps(g, s, RF_PROF_SPMV64, true_res_bytes, 1);
+          launch_true_residual(d, g->nb, g->J, g->mdiag, shift, b, K, s);
+        }
         if ((st = read_scal(g, s))) return st;
         relres = std::sqrt(g->hscal[H_TRUE]) / bn;
         if (!std::isfinite(relres)) { result = RF_ENONFINITE; break; }
@@ -847,6 +1037,31 @@ extern "C" rf_status rf_export_jacobian(rf_grid* g, double* J_host, double* md_h
     if (g->user_alloc) g->alloc.free(a.p, a.bytes, s, g->alloc.ctx); else cudaFree(a.p);
   }
   if (md_host) return pairs_out(g, d, g->mdiag, md_host, s);
+  return RF_OK;
+}
+
+static void tmp_release(rf_grid* g, int count, void* s);
+static void* tmp_alloc(rf_grid* g, size_t bytes, void* s);
+
+extern "C" rf_status rf_export_rows(rf_grid* g, const int64_t* verts, int count, double* J_host, double* md_host,
+                                    void* s) {
+  if (!g || !verts || count < 1 || !J_host || !md_host) return fail(RF_EINVAL, "grid, vertices and outputs are required");
+  if (!g->have_J) return fail(RF_EINVAL, "no Jacobian assembled yet");
+  for (int r = 0; r < count; ++r)
+    if (verts[r] < 0 || verts[r] >= g->d.nv) return fail(RF_EINVAL, "vertex %lld out of range", (long long)verts[r]);
+  const Dims& d = g->d;
+  int64_t* dv = (int64_t*)tmp_alloc(g, sizeof(int64_t) * count, s);
+  double* dj = (double*)tmp_alloc(g, sizeof(double) * 4 * d.nb * count, s);
+  double* dm = (double*)tmp_alloc(g, sizeof(double) * 2 * count, s);
+  if (!dv || !dj || !dm) { tmp_release(g, 3, s); return fail(RF_ENOMEM, "export buffers"); }
+  cudaError_t e = cudaMemcpyAsync(dv, verts, sizeof(int64_t) * count, cudaMemcpyHostToDevice, (cudaStream_t)s);
+  if (e == cudaSuccess) {
+    launch_gather_rows(d, g->J, g->mdiag, dv, count, dj, dm, s);
+    e = cudaMemcpyAsync(J_host, dj, sizeof(double) * 4 * d.nb * count, cudaMemcpyDeviceToHost, (cudaStream_t)s);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(md_host, dm, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, (cudaStream_t)s);
+  tmp_release(g, 3, s);
+  if (e != cudaSuccess) return fail(RF_ECUDA, "export rows: %s", cudaGetErrorString(e));
   return RF_OK;
 }
 

@@ -23,7 +23,7 @@ namespace rf {
 // scalar slots (double)
 enum {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_RR, S_BB, S_RHV, S_TS, S_TT,
-  S_CONV, S_BAD, S_TRUE_RR, S_BREAK, S_NSLOTS
+  S_CONV, S_BAD, S_TRUE_RR, S_BREAK, S_RTOL, S_NSLOTS
 };
 static constexpr int MAXB = 2048;   // max blocks of a reducing kernel
 static constexpr int BS = 256;
@@ -253,6 +253,7 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
       scal[S_BB] = bb; scal[S_RR] = bb; scal[S_RHO] = bb; scal[S_RHO_OLD] = 1.0;
       scal[S_ALPHA] = 1.0; scal[S_OMEGA] = 1.0; scal[S_BETA] = 0.0;
       scal[S_CONV] = (bb == 0.0) ? 1.0 : 0.0; scal[S_BAD] = isfinite(bb) ? 0.0 : 1.0; scal[S_BREAK] = 0.0;
+      scal[S_RTOL] = rtol;
     }
   } else if (stage == 1) {
     const double rhv = sum_partials(partial, S_RHV, nblk);
@@ -280,7 +281,7 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
       scal[S_BETA] = (rhr / rho) * (scal[S_ALPHA] / scal[S_OMEGA]);
       scal[S_RHO_OLD] = rho;
       scal[S_RHO] = rhr;
-      scal[S_CONV] = (sqrt(rr) <= rtol * sqrt(scal[S_BB])) ? 1.0 : 0.0;
+      scal[S_CONV] = (sqrt(rr) <= scal[S_RTOL] * sqrt(scal[S_BB])) ? 1.0 : 0.0;
       if (!isfinite(rr)) scal[S_BAD] = 1.0;
       if (!(rhr != 0.0) || !isfinite(scal[S_BETA])) scal[S_BREAK] = 1.0;
     }
@@ -315,10 +316,10 @@ void launch_spmv64(const Dims& d, const Nbr& nb, const double* J, const double* 
   }
 }
 
-void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, void* s) {
+void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, double rtol, void* s) {
   const int g = krylov_blocks(nv);
   RF_LAUNCH(k_bicg_init, g, BS, 0, s, nv, b, K.x, K.r, K.rh, K.p, K.v, K.partial);
-  fin(0, g, K, 0.0, s);
+  fin(0, g, K, rtol, s);
 }
 
 void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool /*first*/, void* s) {
@@ -327,17 +328,15 @@ void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool /*first*/, vo
   else RF_LAUNCH(k_bicg_p<double2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.p, (double2*)K.p_lo);
 }
 
+// The operand is the FP64 copy y64 of the preconditioned vector: converting
+// FP32 neighbours inside the row loop would cost one FP64-pipe instruction per
+// use, as much as the FMA itself on this GPU.
 void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
-                   KrylovVecs& K, bool y_is_f32, void* s) {
+                   KrylovVecs& K, bool /*y_is_f32*/, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) {
-    if (y_is_f32) RF_LAUNCH((k_bicg_v<float2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
-    else RF_LAUNCH((k_bicg_v<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y, K.rh, K.v, K.partial);
-  } else {
-    if (y_is_f32) RF_LAUNCH((k_bicg_v<float2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
-    else RF_LAUNCH((k_bicg_v<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y, K.rh, K.v, K.partial);
-  }
+  if (d.nb == 27) RF_LAUNCH((k_bicg_v<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
+  else RF_LAUNCH((k_bicg_v<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
   fin(1, g, K, 0.0, s);
 }
 
@@ -348,26 +347,21 @@ void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s) {
 }
 
 void launch_bicg_t(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
-                   KrylovVecs& K, bool z_is_f32, void* s) {
+                   KrylovVecs& K, bool /*z_is_f32*/, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) {
-    if (z_is_f32) RF_LAUNCH((k_bicg_t<float2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
-    else RF_LAUNCH((k_bicg_t<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z, K.s, K.t, K.partial);
-  } else {
-    if (z_is_f32) RF_LAUNCH((k_bicg_t<float2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
-    else RF_LAUNCH((k_bicg_t<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z, K.s, K.t, K.partial);
-  }
+  if (d.nb == 27) RF_LAUNCH((k_bicg_t<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
+  else RF_LAUNCH((k_bicg_t<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
   fin(2, g, K, 0.0, s);
 }
 
-void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, double rtol, void* s) {
+void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, void* s) {
   const int g = krylov_blocks(nv);
   if (yz_is_f32)
     RF_LAUNCH(k_bicg_xr<float2>, g, BS, 0, s, nv, K.scal, (const float2*)K.y, (const float2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
   else
     RF_LAUNCH(k_bicg_xr<double2>, g, BS, 0, s, nv, K.scal, (const double2*)K.y, (const double2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
-  fin(3, g, K, rtol, s);
+  fin(3, g, K, 0.0, s);
 }
 
 void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,

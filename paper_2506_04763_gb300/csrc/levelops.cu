@@ -63,7 +63,7 @@ __device__ __forceinline__ void load_block(const void* A, int64_t nv, int b, int
 template <int KIND, int NB>
 __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par,
                                             const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
-                                            bool skip_centre, typename Ty<KIND>::T& s0,
+                                            bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
                                             typename Ty<KIND>::T& s1) {
   typedef typename Ty<KIND>::T T;
   constexpr int C = NB == 27 ? 13 : 4;
@@ -73,6 +73,7 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (skip_centre && b == C) continue;
+    if ((skipmask >> b) & 1u) continue;   // neighbour known to be zero
     T a[4];
     load_block<KIND>(L.A, L.d.nv, b, p, sc, a);
     const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
@@ -89,7 +90,7 @@ __device__ __forceinline__ void apply_row(const LevelOp& L, int64_t p, int par,
                                           const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                           typename Ty<KIND>::T& s0, typename Ty<KIND>::T& s1) {
   typedef typename Ty<KIND>::T T;
-  stencil_sum<KIND, NB>(L, p, par, x, false, s0, s1);
+  stencil_sum<KIND, NB>(L, p, par, x, false, 0u, s0, s1);
   if (FINE) {
     const double2 m = reinterpret_cast<const double2*>(L.mdiag)[p];
     const T xs = x[p].y, sh = (T)L.shift;
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typ
 template <int KIND, bool FINE, int NB>
 __global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                    typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
-                                                   int pz, int cnt_x, int lines_y, int64_t count) {
+                                                   int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
   typedef typename Ty<KIND>::T T;
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
   T s0, s1;
-  stencil_sum<KIND, NB>(L, p, px, x, true, s0, s1);
+  stencil_sum<KIND, NB>(L, p, px, x, true, skipmask, s0, s1);
   const typename V2<T>::t bv = b[p];
   // off-diagonal part of A: fine level A_pq = -J_pq (q != p), coarse A_pq
   const T r0 = FINE ? bv.x + s0 : bv.x - s0;
@@ -264,79 +265,95 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __res
   x[r] = (T)s;
 }
 
-// ----------------------------------------------------------------- Galerkin (FP64)
-// Thread per (coarse vertex, coarse block): (P^T A P)(I, I+D) summed over fine
-// rows i near 2I and fine columns j near 2(I+D), j - i within the stencil.
-// J is summed in all four entries, M in its S_n column only.
-__global__ void __launch_bounds__(128) k_galerkin(Dims df, Nbr nf, const uint8_t* __restrict__ dmf,
-                                                  const double* __restrict__ Jf, const double* __restrict__ Mf,
-                                                  const double2* __restrict__ mdf, Dims dc,
-                                                  const uint8_t* __restrict__ dmc, double* __restrict__ Jc,
-                                                  double* __restrict__ Mc) {
-  const int nb = dc.nb;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= dc.nv * nb) return;
-  const int bc = (int)(t % nb);
-  const int64_t pc = t / nb;
-  int I, J, K;
-  pcoords(dc, pc, I, J, K);
-  const int DX = bc % 3 - 1, DY = (bc / 3) % 3 - 1, DZ = dc.dim == 3 ? bc / 9 - 1 : 0;
-  const int I2 = I + DX, J2 = J + DY, K2 = K + DZ;
+// Galerkin product one axis at a time.  Trilinear P is the tensor product
+// P_z P_y P_x of 1D linear interpolations and the Dirichlet masks are diagonal,
+// so P_m^T A P_m = D_c P^T (D_f A D_f) P D_c is computed as three 1D
+// coarsenings (x, then y, then z): the output grid halves one axis, every
+// block offset along that axis becomes a coarse offset, the other offsets stay.
+// Output entry (I, D) along the axis = sum over fine rows 2I+a (weight w_a) and
+// fine columns 2(I+D)+c (weight w_c), |2D+c-a| <= 1, w_0 = 1, w_+-1 = 1/2.
+// The fine masks D_f are applied while reading the first stage, the coarse
+// masks D_c (and the identity of coarse Dirichlet rows) when writing the last.
+__global__ void __launch_bounds__(256) k_galerkin_axis(int axis, Dims din, const uint8_t* __restrict__ dmf,
+                                                       const double* __restrict__ Jin, const double* __restrict__ Min,
+                                                       const double2* __restrict__ mdiag, Dims dout,
+                                                       const uint8_t* __restrict__ dmc, double* __restrict__ Jout,
+                                                       double* __restrict__ Mout) {
+  const int nb = dout.nb;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= dout.nv * nb) return;
+  const int bo = (int)(t / dout.nv);
+  const int64_t po = t - (int64_t)bo * dout.nv;
+  int oc[3];
+  pcoords(dout, po, oc[0], oc[1], oc[2]);
+  int off[3] = {bo % 3 - 1, (bo / 3) % 3 - 1, dout.dim == 3 ? bo / 9 - 1 : 0};
+  const int nin[3] = {din.nx, din.ny, din.nz}, nout[3] = {dout.nx, dout.ny, dout.nz};
+  const int D = off[axis];
   double j0 = 0, j1 = 0, j2 = 0, j3 = 0, m0 = 0, m1 = 0;
-  const int centre_f = df.dim == 3 ? 13 : 4;
-  if (I2 >= 0 && I2 < dc.nx && J2 >= 0 && J2 < dc.ny && K2 >= 0 && K2 < dc.nz) {
-    const int64_t pc2 = pidx(dc, I2, J2, K2);
-    const bool mI = dmc[pc] != 0, mJ = dmc[pc2] != 0;
-    const int zr = df.dim == 3 ? 1 : 0;
-    for (int az = -zr; az <= zr; ++az)
-      for (int ay = -1; ay <= 1; ++ay)
-        for (int ax = -1; ax <= 1; ++ax) {
-          const int fi = 2 * I + ax, fj = 2 * J + ay, fk = df.dim == 3 ? 2 * K + az : 0;
-          if (fi < 0 || fi >= df.nx || fj < 0 || fj >= df.ny || fk < 0 || fk >= df.nz) continue;
-          const int64_t pi = pidx(df, fi, fj, fk);
-          const double wi = (ax ? 0.5 : 1.0) * (ay ? 0.5 : 1.0) * (az ? 0.5 : 1.0);
-          const double pa0 = (mI || dmf[pi]) ? 0.0 : wi, pa1 = wi;
-          for (int cz = -zr; cz <= zr; ++cz) {
-            const int ez = df.dim == 3 ? 2 * DZ + cz - az : 0;
-            if (ez < -1 || ez > 1) continue;
-            for (int cy = -1; cy <= 1; ++cy) {
-              const int ey = 2 * DY + cy - ay;
-              if (ey < -1 || ey > 1) continue;
-              for (int cx = -1; cx <= 1; ++cx) {
-                const int ex = 2 * DX + cx - ax;
-                if (ex < -1 || ex > 1) continue;
-                const int gi = 2 * I2 + cx, gj = 2 * J2 + cy, gk = df.dim == 3 ? 2 * K2 + cz : 0;
-                if (gi < 0 || gi >= df.nx || gj < 0 || gj >= df.ny || gk < 0 || gk >= df.nz) continue;
-                const int64_t pj = pidx(df, gi, gj, gk);
-                const double wj = (cx ? 0.5 : 1.0) * (cy ? 0.5 : 1.0) * (cz ? 0.5 : 1.0);
-                const double pb0 = (mJ || dmf[pj]) ? 0.0 : wj, pb1 = wj;
-                const int bf = blk_of(df.dim, ex, ey, ez);
-                const double* a = Jf + ((int64_t)bf * df.nv + pi) * 4;
-                j0 += pa0 * a[0] * pb0;
-                j1 += pa0 * a[1] * pb1;
-                j2 += pa1 * a[2] * pb0;
-                j3 += pa1 * a[3] * pb1;
-                if (mdf) {
-                  if (bf == centre_f) {
-                    const double2 md = mdf[pi];
-                    m0 += pa0 * md.x * pb1;
-                    m1 += pa1 * md.y * pb1;
-                  }
-                } else {
-                  const double* mm = Mf + ((int64_t)bf * df.nv + pi) * 2;
-                  m0 += pa0 * mm[0] * pb1;
-                  m1 += pa1 * mm[1] * pb1;
-                }
-              }
-            }
-          }
+  const int Ic = oc[axis];
+  // the column vertex must exist on the output grid
+  bool col_ok = Ic + D >= 0 && Ic + D < nout[axis];
+  for (int q = 0; q < 3; ++q)
+    if (q != axis && (oc[q] + off[q] < 0 || oc[q] + off[q] >= nout[q])) col_ok = false;
+  if (col_ok) {
+    for (int a = -1; a <= 1; ++a) {
+      const int f = 2 * Ic + a;
+      if (f < 0 || f >= nin[axis]) continue;
+      int rc[3] = {oc[0], oc[1], oc[2]};
+      rc[axis] = f;
+      const int64_t pi = pidx(din, rc[0], rc[1], rc[2]);
+      const double wa = a ? 0.5 : 1.0;
+      const bool mrow = dmf && dmf[pi];
+      for (int c = -1; c <= 1; ++c) {
+        const int e = 2 * D + c - a;
+        if (e < -1 || e > 1) continue;
+        const int gcol = 2 * (Ic + D) + c;
+        if (gcol < 0 || gcol >= nin[axis]) continue;
+        const double w = wa * (c ? 0.5 : 1.0);
+        int eo[3] = {off[0], off[1], off[2]};
+        eo[axis] = e;
+        const int bi = blk_of(din.dim, eo[0], eo[1], eo[2]);
+        bool mcol = false;
+        if (dmf) {
+          int cc[3] = {rc[0] + eo[0], rc[1] + eo[1], rc[2] + eo[2]};
+          mcol = dmf[pidx(din, cc[0], cc[1], cc[2])] != 0;
         }
-    if (mI && bc == (dc.dim == 3 ? 13 : 4)) j0 = -1.0;  // Dirichlet row: A = +identity
+        const double* A = Jin + ((int64_t)bi * din.nv + pi) * 4;
+        const double a0 = mrow || mcol ? 0.0 : A[0], a1 = mrow ? 0.0 : A[1], a2 = mcol ? 0.0 : A[2], a3 = A[3];
+        j0 += w * a0; j1 += w * a1; j2 += w * a2; j3 += w * a3;
+        double s0, s1;
+        if (Min) {
+          const double* M = Min + ((int64_t)bi * din.nv + pi) * 2;
+          s0 = M[0]; s1 = M[1];
+        } else {
+          const bool centre = eo[0] == 0 && eo[1] == 0 && eo[2] == 0;
+          const double2 md = centre ? mdiag[pi] : make_double2(0.0, 0.0);
+          s0 = md.x; s1 = md.y;
+        }
+        m0 += w * (mrow ? 0.0 : s0);
+        m1 += w * s1;
+      }
+    }
+    if (dmc) {
+      const bool crow = dmc[po] != 0;
+      const bool ccol = dmc[pidx(dout, oc[0] + off[0], oc[1] + off[1], oc[2] + off[2])] != 0;
+      if (crow) { j0 = 0.0; j1 = 0.0; m0 = 0.0; }
+      if (ccol) { j0 = 0.0; j2 = 0.0; }
+      if (crow && bo == (dout.dim == 3 ? 13 : 4)) j0 = -1.0;   // Dirichlet row: A = +identity
+    }
   }
-  double* o = Jc + ((int64_t)bc * dc.nv + pc) * 4;
+  double* o = Jout + ((int64_t)bo * dout.nv + po) * 4;
   o[0] = j0; o[1] = j1; o[2] = j2; o[3] = j3;
-  double* om = Mc + ((int64_t)bc * dc.nv + pc) * 2;
+  double* om = Mout + ((int64_t)bo * dout.nv + po) * 2;
   om[0] = m0; om[1] = m1;
+}
+
+void launch_galerkin_axis(int axis, const Dims& din, const uint8_t* dmf, const double* Jin, const double* Min,
+                          const double* mdiag, const Dims& dout, const uint8_t* dmc, double* Jout, double* Mout,
+                          void* s) {
+  const int64_t n = dout.nv * dout.nb;
+  RF_LAUNCH(k_galerkin_axis, (int)((n + 255) / 256), 256, 0, s, axis, din, dmf, Jin, Min, (const double2*)mdiag,
+            dout, dmc, Jout, Mout);
 }
 
 __global__ void k_coarse_mask(Dims df, const uint8_t* __restrict__ dmf, Dims dc, uint8_t* __restrict__ dmc) {
@@ -540,6 +557,30 @@ __global__ void k_export(Dims d, bool fine, const double* __restrict__ J, const 
   }
 }
 
+// gather the block rows and mass diagonals of listed natural vertices
+__global__ void k_gather_rows(Dims d, const double* __restrict__ J, const double2* __restrict__ md,
+                              const int64_t* __restrict__ verts, int count, double* __restrict__ Jout,
+                              double2* __restrict__ mout) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count * d.nb) return;
+  const int r = t / d.nb, b = t % d.nb;
+  const int64_t v = verts[r];
+  const int i = (int)(v % d.nx);
+  const int64_t line = v / d.nx;
+  const int64_t p = line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1));
+  const double* a = J + ((int64_t)b * d.nv + p) * 4;
+  double* o = Jout + ((int64_t)r * d.nb + b) * 4;
+  o[0] = a[0]; o[1] = a[1]; o[2] = a[2]; o[3] = a[3];
+  if (b == 0) mout[r] = md[p];
+}
+
+void launch_gather_rows(const Dims& d, const double* J, const double* mdiag, const int64_t* verts, int count,
+                        double* Jout, double* mout, void* s) {
+  const int n = count * d.nb;
+  RF_LAUNCH(k_gather_rows, (n + 127) / 128, 128, 0, s, d, J, (const double2*)mdiag, verts, count, Jout,
+            (double2*)mout);
+}
+
 __global__ void k_cast_f64_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     out[t] = (float)in[t];
@@ -571,12 +612,26 @@ static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xou
     RF_LAUNCH((k_jacobi<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
 }
 
+// First forward sweep from x = 0: the neighbours of colour c that have a
+// higher colour are still zero, so their blocks are neither read nor applied.
+static uint32_t zero_start_mask(int dim, int col) {
+  uint32_t m = 0;
+  const int nb = dim == 3 ? 27 : 9;
+  for (int b = 0; b < nb; ++b) {
+    const int dx = b % 3 - 1, dy = (b / 3) % 3 - 1, dz = dim == 3 ? b / 9 - 1 : 0;
+    const int nc = ((col & 1) ^ (dx & 1)) | ((((col >> 1) & 1) ^ (dy & 1)) << 1) | ((((col >> 2) & 1) ^ (dz & 1)) << 2);
+    if (nc > col) m |= 1u << b;
+  }
+  return m;
+}
+
 template <int KIND, bool FINE>
-static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, void* s) {
+static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
   const int ncol = 1 << L.d.dim;
   for (int cc = 0; cc < ncol; ++cc) {
     const int col = forward ? cc : ncol - 1 - cc;
+    const uint32_t skip = (zero_start && forward) ? zero_start_mask(L.d.dim, col) : 0u;
     const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
     const int cnt_x = px ? L.d.nx / 2 : (L.d.nx + 1) / 2;
     const int lines_y = (L.d.ny - py + 1) / 2;
@@ -585,9 +640,9 @@ static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, void* s
     if (count == 0) continue;
     const int g = (int)((count + 255) / 256);
     if (L.d.nb == 27)
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count);
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
     else
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count);
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
   }
 }
 
@@ -607,11 +662,11 @@ void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout,
   }
 }
 
-void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool /*zero_start*/, void* s) {
+void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s) {
   switch (L.kind) {
-    case STORE_F64: L.fine ? gs_t<STORE_F64, true>(L, b, x, forward, s) : gs_t<STORE_F64, false>(L, b, x, forward, s); break;
-    case STORE_F32: L.fine ? gs_t<STORE_F32, true>(L, b, x, forward, s) : gs_t<STORE_F32, false>(L, b, x, forward, s); break;
-    default: L.fine ? gs_t<STORE_F16, true>(L, b, x, forward, s) : gs_t<STORE_F16, false>(L, b, x, forward, s); break;
+    case STORE_F64: L.fine ? gs_t<STORE_F64, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F64, false>(L, b, x, forward, zero_start, s); break;
+    case STORE_F32: L.fine ? gs_t<STORE_F32, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F32, false>(L, b, x, forward, zero_start, s); break;
+    default: L.fine ? gs_t<STORE_F16, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F16, false>(L, b, x, forward, zero_start, s); break;
   }
 }
 
@@ -641,12 +696,6 @@ void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, vo
     RF_LAUNCH(k_coarse_solve<float>, g, 256, smem, s, N, Ainv, (const float*)b, (float*)x);
 }
 
-void launch_galerkin(const Dims& df, const Nbr& nf, const uint8_t* dmf, const double* Jf, const double* Mf,
-                     const double* mdiag_f, const Dims& dc, const uint8_t* dmc, double* Jc, double* Mc, void* s) {
-  const int64_t n = dc.nv * dc.nb;
-  RF_LAUNCH(k_galerkin, (int)((n + 127) / 128), 128, 0, s, df, nf, dmf, Jf, Mf, (const double2*)mdiag_f, dc, dmc,
-            Jc, Mc);
-}
 
 void launch_coarse_mask(const Dims& df, const uint8_t* dmf, const Dims& dc, uint8_t* dmc, void* s) {
   RF_LAUNCH(k_coarse_mask, (int)((dc.nv + 255) / 256), 256, 0, s, df, dmf, dc, dmc);

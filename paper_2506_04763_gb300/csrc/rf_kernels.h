@@ -56,15 +56,17 @@ struct LevelOp {
 void launch_residual(const LevelOp& L, const void* b, const void* x, void* r, void* s);
 void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x,
                    void* s);
+// zero_start: x holds no data yet (first forward sweep of a V-cycle); blocks that
+// reach colours not yet visited in this sweep are skipped and x need not be cleared
 void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s);
 void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s);
 void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s);
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s);
 
 // set-up kernels (levelops.cu)
-void launch_galerkin(const Dims& df, const Nbr& nf, const uint8_t* dmf, const double* Jf, const double* Mf,
-                     const double* mdiag_f, const Dims& dc, const uint8_t* dmc, double* Jc, double* Mc,
-                     void* s);
+void launch_galerkin_axis(int axis, const Dims& din, const uint8_t* dmf, const double* Jin, const double* Min,
+                          const double* mdiag, const Dims& dout, const uint8_t* dmc, double* Jout, double* Mout,
+                          void* s);
 void launch_coarse_mask(const Dims& df, const uint8_t* dmf, const Dims& dc, uint8_t* dmc, void* s);
 // pack A = shift*M - J (coarse: from Jc/Mc; fine: keep J, only Dinv) into storage `kind`; write Dinv
 void launch_pack_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
@@ -75,6 +77,8 @@ cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, doubl
                                  void* s);
 void launch_export_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
                          double shift, double* A_nat, void* s);
+void launch_gather_rows(const Dims& d, const double* J, const double* mdiag, const int64_t* verts, int count,
+                        double* Jout, double* mout, void* s);
 void launch_cast_f64_to_f32(const double* in, float* out, int64_t n, void* s);
 void launch_cast_f32_to_f64(const float* in, double* out, int64_t n, void* s);
 
@@ -82,6 +86,7 @@ void launch_cast_f32_to_f64(const float* in, double* out, int64_t n, void* s);
 struct KrylovVecs {
   double2 *x, *r, *rh, *p, *v, *s, *t;   // FP64, parity-split (x and p padded not required)
   void *y, *z;                            // preconditioned vectors (T2, padded)
+  double2 *y64, *z64;                     // FP64 copies read by the outer operator (padded)
   void *p_lo, *s_lo;                      // preconditioner inputs (T2)
   double* partial;                        // reduction partials [8][max_blocks]
   double* scal;                           // device scalars (see krylov.cu)
@@ -90,14 +95,14 @@ int krylov_blocks(int64_t nv);
 // outer operator: y = (shift*M - J) x with J FP64, x FP64 or FP32 (x_is_f32)
 void launch_spmv64(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    const void* x, bool x_is_f32, double2* y, void* s);
-void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, void* s);
+void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, double rtol, void* s);
 void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool first, void* s);
 void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    KrylovVecs& K, bool y_is_f32, void* s);
 void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s);
 void launch_bicg_t(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    KrylovVecs& K, bool z_is_f32, void* s);
-void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, double rtol, void* s);
+void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, void* s);
 void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                           const double2* b, KrylovVecs& K, void* s);
 void launch_restart(int64_t nv, KrylovVecs& K, void* s);
