@@ -30,6 +30,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "BiCGSTAB-GMG DoF/s to rel.res 1e-10, FP32-GMG vs FP64, % of HBM peak"
 RTOL = 1e-10
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per colour vertex of
+# a full fine-level FP32 GS colour launch, from one ncu capture of this
+# workload's recipe at 129^3 (traffic grows with the vertices processed); the
+# algorithmic count is 456 B.
+GS_TRAFFIC_PER_COLOUR_VERTEX = 560.0
+GS_ALGO_PER_COLOUR_VERTEX = 456.0
 
 
 def args_():
@@ -274,6 +280,13 @@ def main():
     dom = max(cands, key=lambda k: cands[k]["ms"])
     dv = prof[dom]
     achieved = dv["bytes"] / (dv["ms"] / 1e3) / 1e9
+    traffic = None
+    if dom == "smooth_fine" and a.smoother == "gs8" and a.precision == "fp32":
+        colour_vertices = g.nv / 8.0
+        traffic = {"bytes_per_launch": GS_TRAFFIC_PER_COLOUR_VERTEX * colour_vertices,
+                   "algorithmic_bytes_per_launch": GS_ALGO_PER_COLOUR_VERTEX * colour_vertices,
+                   "launch": "one full-sweep colour (nv/8 vertices)",
+                   "source": "ncu capture at 129^3 scaled by vertices"}
     shares = {k: round(v["ms"] / sum(p["ms"] for p in prof.values()), 4) for k, v in prof.items()}
     per_class = {k: {"ms_per_step": round(v["ms"] / a.steps, 3), "launches": v["launches"],
                      "GB_per_s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
@@ -348,7 +361,7 @@ def main():
             "iterations": iters, "relres": infos[-1]["relres"],
             "setup_ms": round(setup_ms, 1), "assembly_ms": round(asm_ms, 1),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm"],
-                         "unit": "GB/s", "frac": round(achieved / pk["hbm"], 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(achieved / pk["hbm"], 4), "traffic": traffic,
                          "peak_source": pk["src"], "note": "of %s HBM copy bandwidth" % pk["src"]},
             "per_class": per_class, "time_shares": shares,
             "variants": variants,

@@ -104,6 +104,9 @@ struct rf_grid {
   int nl = 0;
   Level L[RF_MAXL];
   double* Ainv[RF_MAXSHIFT] = {};
+  int tail_first = -1;      // first level run by the one-cluster V-cycle tail (-1: none)
+  int tail_cs = 0;          // its cluster size
+  TailParams tail[RF_MAXSHIFT];
   // Krylov
   KrylovVecs K{};
   double2* b_p = nullptr;
@@ -652,6 +655,45 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       GNEED(g->K.z64 = (double2*)dvec(g, g->d, sizeof(double), s, true));
     }
   }
+  // Optionally the small levels (<= RF_TAIL_NV vertices) run as one cluster
+  // kernel.  Off by default: measured on GB300 it saves < 1% of a 257^3 solve
+  // (each of its ~100 barrier-separated phases is latency-bound) and costs ~40%
+  // of an FP64 LIMEX step at 65^3, where the tail's first level is too large
+  // for 16 SMs.
+  g->tail_first = -1;
+  {
+    const char* env = getenv("RF_TAIL_NV");
+    const long long thr = env ? atoll(env) : 0;
+    if (thr > 0)
+      for (int l = 1; l < g->nl - 1; ++l)
+        if (g->L[l].d.nv <= thr) { g->tail_first = l; break; }
+    if (g->tail_first > 0) {
+      g->tail_cs = tail_cluster_size(kind, g->d.nb);
+      cudaGetLastError();
+      if (g->tail_cs == 0) g->tail_first = -1;
+    }
+    if (g->tail_first > 0)
+      for (int j = 0; j < nshift; ++j) {
+        TailParams& P = g->tail[j];
+        P = TailParams();
+        P.first = g->tail_first;
+        P.coarsest = g->nl - 1;
+        P.smoother = o->smoother;
+        P.nu1 = o->nu1;
+        P.nu2 = o->nu2;
+        P.omega = o->omega;
+        fill_tail_masks(P, g->d.dim);
+        P.Ainv = g->Ainv[j];
+        P.N = (int)(2 * g->L[g->nl - 1].d.nv);
+        for (int l = g->tail_first; l < g->nl; ++l) {
+          P.L[l].op = level_op(g, l, j);
+          P.L[l].x = g->L[l].x;
+          P.L[l].b = g->L[l].b;
+          P.L[l].r = g->L[l].r;
+          P.L[l].t = g->L[l].t;
+        }
+      }
+  }
   CU(cudaStreamSynchronize((cudaStream_t)s));
   CU(cudaGetLastError());
   g->gmg_ready = true;
@@ -733,6 +775,18 @@ static void smooth_post(rf_grid* g, int l, int sh, const void* b, void* x_final,
 static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void* s) {
   const int k = g->kind;
   const double T = tb(k);
+  if (l == g->tail_first) {
+    // the whole remaining V-cycle in one cluster launch (x, b are level l's own vectors)
+    double by = 4.0 * g->L[g->nl - 1].d.nv * g->L[g->nl - 1].d.nv * 8.0;
+    for (int q = l; q < g->nl - 1; ++q) {
+      const double nvq = (double)g->L[q].d.nv, nvc = (double)g->L[q + 1].d.nv;
+      by += sweep_bytes(g, q, true) + (g->gopt.nu1 - 1 + g->gopt.nu2) * sweep_bytes(g, q, false);
+      by += nvq * (g->L[q].d.nb * blk_bytes(k) + row_extra(k) + 6 * T) + nvq * (6 * T + 2) + nvc * (4 * T + 2);
+    }
+    ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, by, 1);
+    launch_vcycle_tail(g->tail[sh], k, g->d.nb, g->tail_cs, s);
+    return;
+  }
   if (l == g->nl - 1) {
     const double N = 2.0 * g->L[l].d.nv;
     ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, N * N * 8.0 + 2 * N * T, 1);

@@ -11,8 +11,12 @@
 //     storage and the 2x2 diagonal-block inverses;
 //   - the coarsest level's dense LU (partial pivoting) and explicit inverse.
 // All of these are HBM-bandwidth kernels except the set-up ones.
+#include <cooperative_groups.h>
+
 #include "rf_common.cuh"
 #include "rf_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace rf {
 
@@ -108,12 +112,10 @@ __device__ __forceinline__ void dinv_apply(const T* Dinv, int64_t p, T r0, T r1,
 
 // ----------------------------------------------------------------- residual
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
-                                                  const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
-                                                  typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
+__device__ __forceinline__ void residual_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                               const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                               typename V2<typename Ty<KIND>::T>::t* __restrict__ r, int64_t p) {
   typedef typename Ty<KIND>::T T;
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p >= L.d.nv) return;
   const int par = (int)(p % L.d.nx) >= L.d.E;
   T s0, s1;
   apply_row<KIND, FINE, NB>(L, p, par, x, s0, s1);
@@ -124,15 +126,22 @@ __global__ void __launch_bounds__(256) k_residual(LevelOp L, const typename V2<t
   r[p] = o;
 }
 
-// ----------------------------------------------------------------- Jacobi
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
-                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
-                                                typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
-                                                int zero_x) {
-  typedef typename Ty<KIND>::T T;
+__global__ void __launch_bounds__(256) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                  const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                                  typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= L.d.nv) return;
+  residual_point<KIND, FINE, NB>(L, b, x, r, p);
+}
+
+// ----------------------------------------------------------------- Jacobi
+template <int KIND, bool FINE, int NB>
+__device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                             const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
+                                             typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
+                                             int zero_x, int64_t p) {
+  typedef typename Ty<KIND>::T T;
   const typename V2<T>::t bv = b[p];
   T r0 = bv.x, r1 = bv.y, x0 = 0, x1 = 0;
   if (!zero_x) {
@@ -152,15 +161,24 @@ __global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typ
   xout[p] = o;
 }
 
+template <int KIND, bool FINE, int NB>
+__global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
+                                                typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
+                                                int zero_x) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  jacobi_point<KIND, FINE, NB>(L, b, xin, xout, omega, zero_x, p);
+}
+
 // ----------------------------------------------------------------- multicolour GS
 // One colour (px,py,pz) of the sweep: x_p <- D_p^-1 (b_p - sum_{q != p} A_pq x_q).
+// Work item t of the colour: t enumerates the colour's x-runs line by line.
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
-                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
-                                                   int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+__device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                         typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py, int pz,
+                                         int cnt_x, int lines_y, int64_t t, uint32_t skipmask) {
   typedef typename Ty<KIND>::T T;
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (t >= count) return;
   const int64_t line = t / cnt_x;
   const int pos = (int)(t - line * cnt_x);
   const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
@@ -180,14 +198,20 @@ __global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<
   x[p] = o;
 }
 
+template <int KIND, bool FINE, int NB>
+__global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
+                                                   int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  gs_point<KIND, FINE, NB>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
+}
+
 // ----------------------------------------------------------------- transfers
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
-                                                  const uint8_t* __restrict__ dmc,
-                                                  const typename V2<T>::t* __restrict__ rf,
-                                                  typename V2<T>::t* __restrict__ bc) {
-  int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pc >= dc.nv) return;
+__device__ __forceinline__ void restrict_point(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
+                                               const uint8_t* __restrict__ dmc, const typename V2<T>::t* __restrict__ rf,
+                                               typename V2<T>::t* __restrict__ bc, int64_t pc) {
   int I, J, K;
   pcoords(dc, pc, I, J, K);
   const bool mc = dmc[pc] != 0;
@@ -218,12 +242,19 @@ __global__ void __launch_bounds__(256) k_restrict(Dims df, Dims dc, const uint8_
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
-                                                 const uint8_t* __restrict__ dmc,
-                                                 const typename V2<T>::t* __restrict__ xc,
-                                                 typename V2<T>::t* __restrict__ xf) {
-  int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pf >= df.nv) return;
+__global__ void __launch_bounds__(256) k_restrict(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                  const uint8_t* __restrict__ dmc,
+                                                  const typename V2<T>::t* __restrict__ rf,
+                                                  typename V2<T>::t* __restrict__ bc) {
+  int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pc >= dc.nv) return;
+  restrict_point<T>(df, dc, dmf, dmc, rf, bc, pc);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_point(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
+                                              const uint8_t* __restrict__ dmc, const typename V2<T>::t* __restrict__ xc,
+                                              typename V2<T>::t* __restrict__ xf, int64_t pf) {
   int fi, fj, fk;
   pcoords(df, pf, fi, fj, fk);
   const bool mf = dmf[pf] != 0;
@@ -250,6 +281,16 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
   xf[pf] = o;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                 const uint8_t* __restrict__ dmc,
+                                                 const typename V2<T>::t* __restrict__ xc,
+                                                 typename V2<T>::t* __restrict__ xf) {
+  int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pf >= df.nv) return;
+  prolong_point<T>(df, dc, dmf, dmc, xc, xf, pf);
+}
+
 // ----------------------------------------------------------------- coarsest solve
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
@@ -263,6 +304,160 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __res
   double s = 0.0;
   for (int c = 0; c < N; ++c) s += row[c] * sb[c];
   x[r] = (T)s;
+}
+
+// ----------------------------------------------------------------- V-cycle tail
+// Levels below a few 10^4 vertices cannot fill the GPU: launched one kernel per
+// GS colour, each costs a launch gap.  Here ONE thread-block cluster runs the
+// whole V-cycle from level `first` down to the coarsest and back up, phases
+// separated by hardware cluster barriers (every thread of the cluster reaches
+// every barrier: all loop bounds below are uniform across the cluster).
+template <int KIND, int NB>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailParams P) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  cg::cluster_group cl = cg::this_cluster();
+  const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
+  const int64_t gt = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+  const int ncol = 1 << P.L[P.first].op.d.dim;
+  V* curs[RF_MAXL];
+  auto gs_sweep = [&](const LevelOp& op, const V* b, V* x, bool forward, bool zero_start) {
+    for (int cc = 0; cc < ncol; ++cc) {
+      const int col = forward ? cc : ncol - 1 - cc;
+      const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
+      const int cnt_x = px ? op.d.nx / 2 : (op.d.nx + 1) / 2;
+      const int lines_y = (op.d.ny - py + 1) / 2;
+      const int lines_z = op.d.dim == 3 ? (op.d.nz - pz + 1) / 2 : 1;
+      const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
+      const uint32_t skip = (zero_start && forward) ? P.zmask[col] : 0u;
+      for (int64_t t = gt; t < count; t += nthr) gs_point<KIND, false, NB>(op, b, x, px, py, pz, cnt_x, lines_y, t, skip);
+      cl.sync();
+    }
+  };
+  auto jacobi_sweep = [&](const LevelOp& op, const V* b, const V* xin, V* xout, bool zero_x) {
+    for (int64_t p = gt; p < op.d.nv; p += nthr) jacobi_point<KIND, false, NB>(op, b, xin, xout, P.omega, zero_x, p);
+    cl.sync();
+  };
+  for (int l = P.first; l < P.coarsest; ++l) {
+    const TailLevel& Lv = P.L[l];
+    const TailLevel& Lc = P.L[l + 1];
+    const V* b = (const V*)Lv.b;
+    V* x = (V*)Lv.x;
+    V* tmp = (V*)Lv.t;
+    V* cur = x;
+    if (P.smoother == 1) {
+      for (int sw = 0; sw < P.nu1; ++sw) gs_sweep(Lv.op, b, x, true, sw == 0);
+    } else {
+      V* first = ((P.nu1 + P.nu2) & 1) ? x : tmp;
+      jacobi_sweep(Lv.op, b, nullptr, first, true);
+      cur = first;
+      for (int sw = 1; sw < P.nu1; ++sw) {
+        V* dst = (cur == x) ? tmp : x;
+        jacobi_sweep(Lv.op, b, cur, dst, false);
+        cur = dst;
+      }
+    }
+    curs[l] = cur;
+    for (int64_t p = gt; p < Lv.op.d.nv; p += nthr) residual_point<KIND, false, NB>(Lv.op, b, cur, (V*)Lv.r, p);
+    cl.sync();
+    for (int64_t p = gt; p < Lc.op.d.nv; p += nthr)
+      restrict_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lv.r, (V*)Lc.b, p);
+    cl.sync();
+  }
+  {
+    const T* bc = (const T*)P.L[P.coarsest].b;
+    T* xc = (T*)P.L[P.coarsest].x;
+    for (int64_t r = gt; r < P.N; r += nthr) {
+      const double* row = P.Ainv + r * P.N;
+      double s = 0.0;
+      for (int c = 0; c < P.N; ++c) s += row[c] * (double)bc[c];
+      xc[r] = (T)s;
+    }
+    cl.sync();
+  }
+  for (int l = P.coarsest - 1; l >= P.first; --l) {
+    const TailLevel& Lv = P.L[l];
+    const TailLevel& Lc = P.L[l + 1];
+    const V* b = (const V*)Lv.b;
+    V* x = (V*)Lv.x;
+    V* tmp = (V*)Lv.t;
+    V* cur = curs[l];
+    for (int64_t p = gt; p < Lv.op.d.nv; p += nthr)
+      prolong_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lc.x, cur, p);
+    cl.sync();
+    if (P.smoother == 1) {
+      for (int sw = 0; sw < P.nu2; ++sw) gs_sweep(Lv.op, b, x, false, false);
+    } else {
+      for (int sw = 0; sw < P.nu2; ++sw) {
+        V* dst = (cur == x) ? tmp : x;
+        jacobi_sweep(Lv.op, b, cur, dst, false);
+        cur = dst;
+      }
+    }
+  }
+}
+
+static uint32_t zero_start_mask(int dim, int col);
+
+template <int KIND, int NB>
+static cudaLaunchConfig_t tail_config(int csize, void* s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize, 1, 1);
+  cfg.blockDim = dim3(TAIL_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = (cudaStream_t)s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+template <int KIND, int NB>
+static cudaError_t tail_launch(const TailParams& P, int csize, void* s) {
+  cudaError_t e = cudaFuncSetAttribute(k_vcycle_tail<KIND, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = tail_config<KIND, NB>(csize, s, attr);
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, k_vcycle_tail<KIND, NB>, P);
+}
+
+template <int KIND, int NB>
+static int tail_size_t() {
+  cudaFuncSetAttribute(k_vcycle_tail<KIND, NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const int sizes[2] = {16, 8};
+  for (int q = 0; q < 2; ++q) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = tail_config<KIND, NB>(sizes[q], nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail<KIND, NB>, &cfg) == cudaSuccess && n >= 1) return sizes[q];
+    cudaGetLastError();
+  }
+  return 0;
+}
+
+// largest cluster size (16, else 8) the device can co-schedule for the tail; 0: none
+int tail_cluster_size(int kind, int nb) {
+  if (nb == 27) return kind == STORE_F64 ? tail_size_t<STORE_F64, 27>() : kind == STORE_F32 ? tail_size_t<STORE_F32, 27>() : tail_size_t<STORE_F16, 27>();
+  return kind == STORE_F64 ? tail_size_t<STORE_F64, 9>() : kind == STORE_F32 ? tail_size_t<STORE_F32, 9>() : tail_size_t<STORE_F16, 9>();
+}
+
+void fill_tail_masks(TailParams& P, int dim) {
+  for (int c = 0; c < 8; ++c) P.zmask[c] = c < (1 << dim) ? zero_start_mask(dim, c) : 0u;
+}
+
+cudaError_t launch_vcycle_tail(const TailParams& P, int kind, int nb, int csize, void* s) {
+  if (nb == 27) {
+    if (kind == STORE_F64) return tail_launch<STORE_F64, 27>(P, csize, s);
+    if (kind == STORE_F32) return tail_launch<STORE_F32, 27>(P, csize, s);
+    return tail_launch<STORE_F16, 27>(P, csize, s);
+  }
+  if (kind == STORE_F64) return tail_launch<STORE_F64, 9>(P, csize, s);
+  if (kind == STORE_F32) return tail_launch<STORE_F32, 9>(P, csize, s);
+  return tail_launch<STORE_F16, 9>(P, csize, s);
 }
 
 // Galerkin product one axis at a time.  Trilinear P is the tensor product

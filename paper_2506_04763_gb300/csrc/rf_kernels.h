@@ -63,6 +63,25 @@ void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* b
 void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s);
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s);
 
+// The V-cycle below a size threshold, run by one thread-block cluster.
+#define TAIL_THREADS 512
+struct TailLevel {
+  LevelOp op;                 // coarse-level operator (blocks hold A)
+  void *x, *b, *r, *t;        // level vectors (T2, padded)
+};
+struct TailParams {
+  int first, coarsest;        // levels first .. coarsest (coarsest solved exactly)
+  int smoother, nu1, nu2;
+  double omega;
+  uint32_t zmask[8];          // first-sweep skip masks per colour
+  const double* Ainv;         // coarsest inverse, N x N
+  int N;
+  TailLevel L[RF_MAXL];
+};
+int tail_cluster_size(int kind, int nb);
+void fill_tail_masks(TailParams& P, int dim);
+cudaError_t launch_vcycle_tail(const TailParams& P, int kind, int nb, int csize, void* s);
+
 // set-up kernels (levelops.cu)
 void launch_galerkin_axis(int axis, const Dims& din, const uint8_t* dmf, const double* Jin, const double* Min,
                           const double* mdiag, const Dims& dout, const uint8_t* dmc, double* Jout, double* Mout,

@@ -239,6 +239,22 @@ def test_vcycle_and_coarse_solve_match_oracle(case, smoother):
     g.close()
 
 
+@pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vcycle_cluster_tail_matches_oracle(smoother, precision, monkeypatch):
+    """The optional one-cluster execution of the small levels (RF_TAIL_NV)
+    computes the same V-cycle."""
+    monkeypatch.setenv("RF_TAIL_NV", "100000")
+    prob = CASES["3d-17cube"]()
+    g, F, m, A, gm = _setup_both(prob, precision, smoother)
+    b = np.random.default_rng(2).standard_normal(2 * g.nv)
+    x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
+    x_o = gm.vcycle(b)
+    tol = 1e-9 if precision == "fp64" else 1e-4
+    assert np.abs(x - x_o).max() <= tol * np.abs(x_o).max()
+    g.close()
+
+
 # ------------------------------------------------------------------ solves
 @pytest.mark.parametrize("precision,smoother", [("fp64", "jacobi"), ("fp32", "jacobi"), ("fp32", "gs8"),
                                                 ("fp16", "gs8"), ("fp64", "gs8")])
