@@ -47,8 +47,12 @@ def args_():
     ap.add_argument("--nvert", type=int, default=257)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "jacobi"])
-    ap.add_argument("--variants", default="fp64,fp16", help="extra solve variants to time (comma list)")
+    ap.add_argument("--outer", default="fp64", choices=["fp64", "df32"],
+                    help="arithmetic of the operator applications inside the iteration")
+    ap.add_argument("--variants", default="fp64,fp16,fp32+df32",
+                    help="extra solve variants to time: precision[+outer], comma separated")
     ap.add_argument("--sample-nvert", type=int, default=65, help="oracle sample size (vertices per axis)")
+    ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-realisation ensemble (1/0)")
     return ap.parse_args()
 
 
@@ -210,7 +214,8 @@ def main():
 
     x = torch.empty_like(F)
 
-    def timed(nsteps, profile=False):
+    def timed(nsteps, profile=False, outer=None):
+        outer = outer or a.outer
         infos = []
         if world > 1:
             dist.barrier()
@@ -219,14 +224,14 @@ def main():
             # the profiled iteration graph (with event nodes) is captured on its
             # first use: do that outside the timed region
             g.profile(1)
-            g.solve(0, F, x, rtol=RTOL, max_it=500)
+            g.solve(0, F, x, rtol=RTOL, max_it=500, outer=outer)
             torch.cuda.synchronize()
             g.profile(1)
         l0 = rf.rf_launch_count()
         t0, t1 = ev(), ev()
         t0.record(stream)
         for _ in range(nsteps):
-            infos.append(g.solve(0, F, x, rtol=RTOL, max_it=500))
+            infos.append(g.solve(0, F, x, rtol=RTOL, max_it=500, outer=outer))
         t1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -246,7 +251,7 @@ def main():
     # ---- headline: FP32 (or chosen) GMG
     setup_ms = setup(a.precision)
     for _ in range(a.warmup):
-        g.solve(0, F, x, rtol=RTOL, max_it=500)
+        g.solve(0, F, x, rtol=RTOL, max_it=500, outer=a.outer)
     clk = Clocks(local) if rank == 0 else None
     ms, infos, launches, prof = timed(a.steps, profile=True)
     clocks = clk.stop() if clk else None
@@ -266,7 +271,7 @@ def main():
         dist.barrier()
     w0 = time.perf_counter()
     for _ in range(a.steps):
-        g.solve(0, bn, xn, rtol=RTOL, max_it=500)
+        g.solve(0, bn, xn, rtol=RTOL, max_it=500, outer=a.outer)
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - w0) * 1e3 / a.steps
     if world > 1:
@@ -295,17 +300,22 @@ def main():
 
     # ---- variants of the same solve: all-FP64 GPU path, FP16 storage
     variants = {}
-    for var in [v for v in a.variants.split(",") if v and v != a.precision]:
-        try:
-            vs = setup(var)
-            g.solve(0, F, x, rtol=RTOL, max_it=500)
-            vms, vinf, _, vprof = timed(max(1, min(3, a.steps)), profile=True)
-        except rf.RFError as e:
-            variants[var + "_gmg"] = {"error": str(e)}
+    for var in [v for v in a.variants.split(",") if v and v != "%s+%s" % (a.precision, a.outer)]:
+        vprec, _, vout = var.partition("+")
+        vout = vout or "fp64"
+        if vprec == a.precision and vout == a.outer:
             continue
-        variants[var + "_gmg"] = {"value": world * dof / (vms / 1e3), "unit": "DoF/s", "ms_per_solve": round(vms, 2),
+        name = vprec + "_gmg" + ("" if vout == "fp64" else "_" + vout + "_outer")
+        try:
+            vs = setup(vprec)
+            g.solve(0, F, x, rtol=RTOL, max_it=500, outer=vout)
+            vms, vinf, _, vprof = timed(max(1, min(3, a.steps)), profile=True, outer=vout)
+        except rf.RFError as e:
+            variants[name] = {"error": str(e)}
+            continue
+        variants[name] = {"value": world * dof / (vms / 1e3), "unit": "DoF/s", "ms_per_solve": round(vms, 2),
                                   "iterations": vinf[-1]["iterations"], "relres": vinf[-1]["relres"],
-                                  "setup_ms": round(vs, 1), "speedup_of_headline": round(vms / ms, 3),
+                                  "setup_ms": round(vs, 1), "time_vs_headline": round(vms / ms, 3),
                                   "per_class_ms_per_solve": {k: round(v["ms"] / len(vinf), 3)
                                                              for k, v in vprof.items()}}
 
@@ -339,6 +349,48 @@ def main():
     except rf.RFError as e:
         limex = {"error": str(e)}
 
+    # ---- ensemble (config4): 64 realisations on uneven grids, one LIMEX step each
+    ensemble = None
+    if a.ensemble:
+        try:
+            members = I.ensemble_members()
+            eprobs = [I.ensemble_member(sd, nv) for sd, nv in members]
+            egrids = [rf.Grid(p) for p in eprobs]
+            eu0 = [torch.tensor(p["u0"], device=dev) for p in eprobs]
+            egm = [rf.gmg_opts(p["nlevels"], "jacobi", precision="fp32") for p in eprobs]
+            edof = sum(2 * gg.nv for gg in egrids)
+
+            def batched():
+                us = [t.clone() for t in eu0]
+                torch.cuda.synchronize()
+                w0 = time.perf_counter()
+                st, infos = rf.limex_step_batched(egrids, us, 10.0, kappa=4, tol=1e-3, gmg=egm)
+                torch.cuda.synchronize()
+                return time.perf_counter() - w0, infos
+
+            batched()                                   # warm-up (captures graphs)
+            tb_s, einfo = batched()
+            us = [t.clone() for t in eu0]
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for gg, uu, oo in zip(egrids, us, egm):
+                gg.limex_step(uu, 10.0, kappa=4, tol=1e-3, gmg=oo)
+            torch.cuda.synchronize()
+            ts_s = time.perf_counter() - w0
+            ensemble = {"workload": "config4: 64 lognormal realisations (seeds 100..163) on 33^3/49^3/65^3/97^3 "
+                                    "(16 each), one LIMEX step each (kappa = 4, 10 solves), FP32 GMG (block "
+                                    "Jacobi) / FP64 outer, rel.res 1e-10",
+                        "dofs_total": edof, "stage_solves": sum(i["solves"] for i in einfo),
+                        "iterations_total": sum(i["iterations"] for i in einfo),
+                        "batched_s": round(tb_s, 3), "dofs_per_s_batched": edof / tb_s,
+                        "sequential_s": round(ts_s, 3), "dofs_per_s_sequential": edof / ts_s,
+                        "batching_speedup": round(ts_s / tb_s, 2),
+                        "accepted": sum(i["accepted"] for i in einfo)}
+            for gg in egrids:
+                gg.close()
+        except rf.RFError as e:
+            ensemble = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1:
         v, dt, sdof, sit = oracle_sample(a.sample_nvert, a.smoother)
@@ -352,8 +404,8 @@ def main():
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64/%s" % a.precision.replace("fp", "f"), "data": "synthetic",
             "config": {"workload": "config3: %d^3-vertex box, lognormal K (seed 2) + 6 lenses, A = M/h - J "
-                                   "(h = 10 s) at u0, b = F(u0); FP64 BiCGSTAB + %s GMG (%d levels, %s, "
-                                   "V(2,2)), x0 = 0, true rel.res <= 1e-10" % (a.nvert, a.precision.upper(), L,
+                                   "(h = 10 s) at u0, b = F(u0); FP64 BiCGSTAB (%s operator) + %s GMG (%d levels, %s, "
+                                   "V(2,2)), x0 = 0, true rel.res <= 1e-10" % (a.nvert, a.outer.upper(), a.precision.upper(), L,
                                                                             "8-colour block GS" if a.smoother == "gs8" else "block Jacobi w=0.8"),
                        "dofs": dof, "vertices": [a.nvert] * 3, "levels": L,
                        "l2": "no flush: inputs larger than L2 (FP64 Jacobian %.1f GB)" % (dof / 2 * 864 / 1e9),
@@ -366,6 +418,7 @@ def main():
             "per_class": per_class, "time_shares": shares,
             "variants": variants,
             "limex_step": limex,
+            "ensemble": ensemble,
             "e2e": {"value": world * dof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": 16 * g.nv,
                     "d2h_bytes_per_step": 16 * g.nv},
             "gpu_launches": launches,

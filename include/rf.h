@@ -95,8 +95,14 @@ enum { RF_PREC_FP64 = 0, RF_PREC_FP32 = 1, RF_PREC_FP16 = 2 };
  * FP32 arithmetic).  The coarsest level is solved exactly in FP64. */
 typedef struct { int nlevels, smoother, nu1, nu2; double omega; int precision; } rf_gmg_opts;
 
-/* Stop when the TRUE FP64 residual |b - A x|_2 <= rtol |b|_2. */
-typedef struct { double rtol; int max_it; } rf_solve_opts;
+/* Stop when the TRUE FP64 residual |b - A x|_2 <= rtol |b|_2.  outer selects
+ * the arithmetic of the two operator applications inside each iteration:
+ * RF_OUTER_FP64 (FP64 J), or RF_OUTER_DF32 (J split once into FP32 hi + lo,
+ * |J - hi - lo| <= 2^-48 |J|, exact FP32 products via FMA, compensated FP32
+ * sums; only with an FP32/FP16 preconditioner, whose outputs are exact FP32).
+ * The convergence decision always uses the FP64 true residual. */
+enum { RF_OUTER_FP64 = 0, RF_OUTER_DF32 = 1 };
+typedef struct { double rtol; int max_it; int outer; } rf_solve_opts;
 typedef struct { int iterations; double relres; int status; int restarts; } rf_solve_info;
 
 /* LIMEX step options: kappa columns (n_j = 1..kappa, one shared Jacobian),
@@ -142,6 +148,18 @@ rf_status rf_solve(rf_grid* g, int shift, const double* b, double* x, const rf_s
  * the extrapolated state only when the step is accepted (eps <= tol). */
 rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* opts, rf_limex_info* info,
                         void* stream);
+
+/* One LIMEX step for each of nprob independent problems (an ensemble of
+ * realisations on grids of any sizes), run concurrently: every grid works on
+ * its own stream with its own captured iteration graphs, and up to
+ * max_concurrent host workers (<= 0: min(nprob, 16)) keep the GPU fed while
+ * each waits for its convergence checks.  grids[i], u[i] (in/out), H[i] and
+ * opts[i] (an array of nprob options, e.g. with per-grid level counts) as in
+ * rf_limex_step; infos[i] receives each problem's result (status included).
+ * Ordered after `stream`; `stream` waits for all problems.  Returns the first
+ * non-OK status in problem order (all problems are attempted). */
+rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
+                                const rf_limex_opts* opts, rf_limex_info* infos, int max_concurrent, void* stream);
 
 /* ---- test and inspection hooks (host buffers, natural vertex order) ---- */
 

@@ -67,8 +67,12 @@ class rf_gmg_opts(ctypes.Structure):
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int)]
 
 
+RF_OUTER_FP64, RF_OUTER_DF32 = 0, 1
+OUTERS = {"fp64": RF_OUTER_FP64, "df32": RF_OUTER_DF32}
+
+
 class rf_solve_opts(ctypes.Structure):
-    _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int)]
+    _fields_ = [("rtol", ctypes.c_double), ("max_it", ctypes.c_int), ("outer", ctypes.c_int)]
 
 
 class rf_solve_info(ctypes.Structure):
@@ -97,6 +101,7 @@ SIGNATURES = {
     "rf_gmg_setup": (_I, [_P, _P, _I, _P, _P]),
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
+    "rf_limex_step_batched": (_I, [_P, _P, _P, _I, _P, _P, _I, _P]),
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
     "rf_export_rows": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -169,6 +174,34 @@ def rf_limex_step(grid, u_ptr, H, opts, stream):
     if st not in (RF_OK, RF_ENOTCONV):
         _check(st)
     return st, info
+
+
+def rf_limex_step_batched(grids, u_ptrs, H, opts, max_concurrent, stream):
+    n = len(grids)
+    ga = (ctypes.c_void_p * n)(*grids)
+    ua = (ctypes.c_void_p * n)(*u_ptrs)
+    ha = (ctypes.c_double * n)(*[float(h) for h in H])
+    oa = (rf_limex_opts * n)(*opts)
+    infos = (rf_limex_info * n)()
+    st = lib().rf_limex_step_batched(ga, ua, ha, n, oa, infos, int(max_concurrent), stream)
+    if st not in (RF_OK, RF_ENOTCONV):
+        _check(st)
+    return st, list(infos)
+
+
+def limex_step_batched(grids, us, H, kappa=4, tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4.0, gmg=None, rtol=1e-10,
+                       max_it=200, outer="fp64", max_concurrent=0, stream=None):
+    """LIMEX steps of an ensemble of Grid objects, run concurrently by the
+    library.  gmg: one rf_gmg_opts or a list (one per grid)."""
+    n = len(grids)
+    gm = gmg if isinstance(gmg, (list, tuple)) else [gmg if gmg is not None else gmg_opts(4)] * n
+    Hs = H if isinstance(H, (list, tuple)) else [H] * n
+    opts = [rf_limex_opts(int(kappa), float(tol), float(rho), float(fac_min), float(fac_max), gm[i],
+                          rf_solve_opts(float(rtol), int(max_it), OUTERS.get(outer, outer))) for i in range(n)]
+    st, infos = rf_limex_step_batched([g.handle for g in grids], [_ptr(u) for u in us], Hs, opts, max_concurrent,
+                                      _stream_handle(stream))
+    return st, [dict(status=i.status, eps=i.eps, H_new=i.H_new, accepted=i.accepted, solves=i.solves,
+                     iterations=i.iterations) for i in infos]
 
 
 def rf_export_jacobian(grid, J_host, md_host, stream):
@@ -299,15 +332,16 @@ class Grid:
     def gmg_setup(self, shifts, opts):
         rf_gmg_setup(self.handle, list(shifts), opts, self.stream)
 
-    def solve(self, shift, b, x, rtol=1e-10, max_it=200):
-        st, info = rf_solve(self.handle, shift, _ptr(b), _ptr(x), rf_solve_opts(float(rtol), int(max_it)), self.stream)
+    def solve(self, shift, b, x, rtol=1e-10, max_it=200, outer="fp64"):
+        o = rf_solve_opts(float(rtol), int(max_it), OUTERS.get(outer, outer))
+        st, info = rf_solve(self.handle, shift, _ptr(b), _ptr(x), o, self.stream)
         return dict(status=st, iterations=info.iterations, relres=info.relres, restarts=info.restarts)
 
     def limex_step(self, u, H, kappa=4, tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4.0, gmg=None, rtol=1e-10,
-                   max_it=200):
+                   max_it=200, outer="fp64"):
         gmg = gmg if gmg is not None else gmg_opts(4)
         o = rf_limex_opts(int(kappa), float(tol), float(rho), float(fac_min), float(fac_max), gmg,
-                          rf_solve_opts(float(rtol), int(max_it)))
+                          rf_solve_opts(float(rtol), int(max_it), OUTERS.get(outer, outer)))
         st, info = rf_limex_step(self.handle, _ptr(u), H, o, self.stream)
         return dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted, solves=info.solves,
                     iterations=info.iterations)

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rf.h"
@@ -131,7 +132,10 @@ struct rf_grid {
     std::vector<ProfRec> recs;           // event pairs recorded by the graph
     std::vector<cudaEvent_t> events;     // owned by the graph
   };
-  IterGraph ig[RF_MAXSHIFT][2];
+  IterGraph ig[RF_MAXSHIFT][2][2];       // [shift][profiling][outer operator]
+  int outer_df = 0;                      // the current solve's RF_OUTER_* mode
+  float* Jdf = nullptr;                  // J as FP32 hi/lo pairs (RF_OUTER_DF32)
+  bool jdf_valid = false;
   bool capturing = false;
   IterGraph* cap = nullptr;
   cudaStream_t cs = nullptr;             // internal stream for the iteration
@@ -182,11 +186,12 @@ struct ProfScope {
 
 static void destroy_graphs(rf_grid* g) {
   for (auto& row : g->ig)
-    for (auto& G : row) {
-      if (G.exec) cudaGraphExecDestroy(G.exec);
-      for (auto e : G.events) cudaEventDestroy(e);
-      G = rf_grid::IterGraph();
-    }
+    for (auto& pair : row)
+      for (auto& G : pair) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        for (auto e : G.events) cudaEventDestroy(e);
+        G = rf_grid::IterGraph();
+      }
 }
 
 // algorithmic bytes of the level kernels (each matrix entry / vector element once)
@@ -446,7 +451,7 @@ static rf_status assemble_p(rf_grid* g, bool want_j, void* s) {
   a.q_in = g->q_in; a.F = g->F_p; a.J = want_j ? g->J : nullptr; a.mdiag = want_j ? g->mdiag : nullptr;
   cudaError_t e = launch_assemble(g->d, g->pp, a, want_j, s);
   if (e != cudaSuccess) return fail(RF_ECUDA, "assembly launch: %s", cudaGetErrorString(e));
-  if (want_j) { g->have_J = true; g->gmg_ready = false; }
+  if (want_j) { g->have_J = true; g->gmg_ready = false; g->jdf_valid = false; }
   return RF_OK;
 }
 
@@ -837,27 +842,31 @@ static void iteration_body(rf_grid* g, int sh, void* s) {
     ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 4 + 2 * T), 1);
     launch_bicg_p(d.nv, K, lo32, false, s);
   }
+  const bool df = lo32 && g->outer_df;   // double-FP32 operator on the FP32 operands
+  const double spmv_df_bytes = nv * (d.nb * 32.0 + 16.0 + 8.0 + 16.0 + 16.0);
   vcycle_level(g, 0, sh, K.p_lo, K.y, s);
-  if (lo32) {
+  if (lo32 && !df) {
     ProfScope ps(g, s, RF_PROF_VECTOR, nv * (2 * T + 16.0), 1);
     launch_cast_f32_to_f64((const float*)K.y, (double*)K.y64, 2 * d.nv, s);
   }
   {
-    ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
-    launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+    ProfScope ps(g, s, RF_PROF_SPMV64, df ? spmv_df_bytes : spmv_bytes, 1);
+    if (df) launch_bicg_v_df(d, g->nb, g->Jdf, g->mdiag, shift, K, s);
+    else launch_bicg_v(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
   }
   {
     ProfScope ps(g, s, RF_PROF_VECTOR, nv * (16.0 * 3 + 2 * T), 1);
     launch_bicg_s(d.nv, K, lo32, s);
   }
   vcycle_level(g, 0, sh, K.s_lo, K.z, s);
-  if (lo32) {
+  if (lo32 && !df) {
     ProfScope ps(g, s, RF_PROF_VECTOR, nv * (2 * T + 16.0), 1);
     launch_cast_f32_to_f64((const float*)K.z, (double*)K.z64, 2 * d.nv, s);
   }
   {
-    ProfScope ps(g, s, RF_PROF_SPMV64, spmv_bytes, 1);
-    launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
+    ProfScope ps(g, s, RF_PROF_SPMV64, df ? spmv_df_bytes : spmv_bytes, 1);
+    if (df) launch_bicg_t_df(d, g->nb, g->Jdf, g->mdiag, shift, K, s);
+    else launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
   }
   {
     ProfScope ps(g, s, RF_PROF_VECTOR, nv * (4 * T + 16.0 * 6), 1);
@@ -876,7 +885,7 @@ static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
     return read_scal(g, cs);
   }
   const bool prof = g->prof_on;
-  rf_grid::IterGraph& G = g->ig[sh][prof ? 1 : 0];
+  rf_grid::IterGraph& G = g->ig[sh][prof ? 1 : 0][g->outer_df];
   if (!G.exec) {
     const int64_t c0 = g_launches.load();
     CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -918,7 +927,17 @@ static rf_status solve_cs(rf_grid* g, int sh, const double2* b, double rtol, int
 // Solve A_sh x = b with b, x parity-split device pairs (x is g->K.x on return).
 // The iteration runs on the grid's internal stream, ordered after and before
 // the caller's stream.
-static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int max_it, rf_solve_info* info, void* s) {
+static rf_status solve_p(rf_grid* g, int sh, const double2* b, double rtol, int max_it, int outer,
+                         rf_solve_info* info, void* s) {
+  g->outer_df = (outer == RF_OUTER_DF32 && g->kind != STORE_F64) ? 1 : 0;
+  if (g->outer_df && !g->jdf_valid) {
+    if (!g->Jdf) {
+      g->Jdf = (float*)dalloc(g, sizeof(double) * 4 * g->d.nb * g->d.nv, s, false);
+      if (!g->Jdf) return fail(RF_ENOMEM, "double-FP32 operator copy");
+    }
+    launch_split_df(g->d, g->J, g->Jdf, s);
+    g->jdf_valid = true;
+  }
   CU(cudaEventRecord(g->join_in, (cudaStream_t)s));
   CU(cudaStreamWaitEvent(g->cs, g->join_in, 0));
   rf_status r = solve_cs(g, sh, b, rtol, max_it, info, g->cs);
@@ -985,9 +1004,10 @@ extern "C" rf_status rf_solve(rf_grid* g, int sh, const double* b, double* x, co
   if (!g->gmg_ready) return fail(RF_EINVAL, "rf_gmg_setup must precede rf_solve");
   if (sh < 0 || sh >= g->nshift) return fail(RF_EINVAL, "shift index %d out of range", sh);
   if (!(o->rtol > 0.0) || o->max_it < 1) return fail(RF_EINVAL, "need rtol > 0 and max_it >= 1");
+  if (o->outer != RF_OUTER_FP64 && o->outer != RF_OUTER_DF32) return fail(RF_EINVAL, "unknown outer operator mode");
   rf_status st = pairs_in(g, g->d, b, (double*)g->b_p, s);
   if (st) return st;
-  rf_status r = solve_p(g, sh, g->b_p, o->rtol, o->max_it, info, s);
+  rf_status r = solve_p(g, sh, g->b_p, o->rtol, o->max_it, o->outer, info, s);
   if (r != RF_OK && r != RF_ENOTCONV) return r;
   st = pairs_out(g, g->d, (const double*)g->K.x, x, s);
   if (st) return st;
@@ -1037,7 +1057,7 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
         F = g->F_p;
       }
       rf_solve_info si{};
-      rf_status r = solve_p(g, j, (const double2*)F, o->solve.rtol, o->solve.max_it, &si, s);
+      rf_status r = solve_p(g, j, (const double2*)F, o->solve.rtol, o->solve.max_it, o->solve.outer, &si, s);
       ++solves;
       iters += si.iterations;
       if (r != RF_OK) {
@@ -1072,6 +1092,52 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
   }
   if (!std::isfinite(eps)) return fail(RF_ENONFINITE, "error estimate is not finite");
   return worst;
+}
+
+// ------------------------------------------------------------------ ensembles
+extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
+                                           const rf_limex_opts* o, rf_limex_info* infos, int max_concurrent,
+                                           void* stream) {
+  if (!grids || !u || !H || !o || !infos || nprob < 1) return fail(RF_EINVAL, "grids, u, H, opts, infos and nprob >= 1 are required");
+  for (int i = 0; i < nprob; ++i) {
+    if (!grids[i] || !u[i]) return fail(RF_EINVAL, "problem %d: grid and u are required", i);
+    for (int k = 0; k < i; ++k)
+      if (grids[k] == grids[i]) return fail(RF_EINVAL, "problem %d repeats the grid of problem %d", i, k);
+  }
+  int workers = max_concurrent > 0 ? max_concurrent : (nprob < 16 ? nprob : 16);
+  if (workers > nprob) workers = nprob;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  // every problem's work is ordered after `stream`
+  cudaEvent_t start;
+  CU(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CU(cudaEventRecord(start, (cudaStream_t)stream));
+  for (int i = 0; i < nprob; ++i) CU(cudaStreamWaitEvent(grids[i]->cs, start, 0));
+  std::vector<rf_status> st(nprob, RF_OK);
+  std::vector<std::string> msg(nprob);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (int i = next.fetch_add(1); i < nprob; i = next.fetch_add(1)) {
+      rf_grid* g = grids[i];
+      st[i] = rf_limex_step(g, u[i], H[i], &o[i], &infos[i], g->cs);
+      infos[i].status = st[i];
+      if (st[i] != RF_OK) msg[i] = t_err;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  // `stream` waits for every problem
+  for (int i = 0; i < nprob; ++i) {
+    CU(cudaEventRecord(grids[i]->join_out, grids[i]->cs));
+    CU(cudaStreamWaitEvent((cudaStream_t)stream, grids[i]->join_out, 0));
+  }
+  cudaEventDestroy(start);
+  for (int i = 0; i < nprob; ++i)
+    if (st[i] != RF_OK) return fail(st[i], "problem %d: %s", i, msg[i].c_str());
+  return RF_OK;
 }
 
 // ------------------------------------------------------------------ test hooks

@@ -89,6 +89,89 @@ __device__ __forceinline__ void spmv64_row(const Dims& d, const Nbr& nb, const d
   y1 = shift * m.y * xs - s1;
 }
 
+// Double-FP32 variant of the row product for an operand x that is exactly
+// representable in FP32 (the FP32 preconditioner's output).  J is stored as
+// FP32 pairs hi + lo with hi = fl32(a), lo = fl32(a - hi), |a - hi - lo| <=
+// 2^-48 |a|.  hi*x is made exact with an FMA (p + e), lo*x is rounded (error
+// <= 2^-48 |a x|), and the sum runs in a (sh, sl) pair with Knuth's two-sum.
+// Every operation runs on the FP32 pipe; only the final combination is FP64.
+__device__ __forceinline__ void df_acc(float& sh, float& sl, float hi, float lo, float x) {
+  const float p = hi * x;
+  const float e = fmaf(hi, x, -p);
+  const float q = lo * x;
+  const float s = sh + p;
+  const float bp = s - sh;
+  const float err = (sh - (s - bp)) + (p - bp);
+  sh = s;
+  sl += err + (e + q);
+}
+
+template <int NB>
+__device__ __forceinline__ void spmvdf_row(const Dims& d, const Nbr& nb, const float4* __restrict__ Jdf,
+                                           const double2* __restrict__ md, double shift,
+                                           const float2* __restrict__ x, int64_t p, double& y0, double& y1) {
+  const int par = (int)(p % d.nx) >= d.E;
+  float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const float4* q = Jdf + ((int64_t)b * d.nv + p) * 2;
+    const float4 hi = __ldcs(q), lo = __ldcs(q + 1);
+    const float2 xv = x[p + (par ? nb.off[1][b] : nb.off[0][b])];
+    df_acc(h0, l0, hi.x, lo.x, xv.x);
+    df_acc(h0, l0, hi.y, lo.y, xv.y);
+    df_acc(h1, l1, hi.z, lo.z, xv.x);
+    df_acc(h1, l1, hi.w, lo.w, xv.y);
+  }
+  const double2 m = md[p];
+  const double xs = (double)x[p].y;
+  y0 = shift * m.x * xs - ((double)h0 + (double)l0);
+  y1 = shift * m.y * xs - ((double)h1 + (double)l1);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(BS) k_bicg_v_df(Dims d, Nbr nb, const float4* __restrict__ Jdf,
+                                                  const double2* __restrict__ md, double shift,
+                                                  const float2* __restrict__ y, const double2* __restrict__ rh,
+                                                  double2* __restrict__ v, double* __restrict__ partial) {
+  double acc[1] = {0.0};
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
+    double y0, y1;
+    spmvdf_row<NB>(d, nb, Jdf, md, shift, y, p, y0, y1);
+    v[p] = make_double2(y0, y1);
+    const double2 r = rh[p];
+    acc[0] += r.x * y0 + r.y * y1;
+  }
+  block_reduce_store<1>(acc, partial + S_RHV * MAXB);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(BS) k_bicg_t_df(Dims d, Nbr nb, const float4* __restrict__ Jdf,
+                                                  const double2* __restrict__ md, double shift,
+                                                  const float2* __restrict__ z, const double2* __restrict__ s,
+                                                  double2* __restrict__ t, double* __restrict__ partial) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
+    double y0, y1;
+    spmvdf_row<NB>(d, nb, Jdf, md, shift, z, p, y0, y1);
+    t[p] = make_double2(y0, y1);
+    const double2 sv = s[p];
+    acc[0] += y0 * sv.x + y1 * sv.y;
+    acc[1] += y0 * y0 + y1 * y1;
+  }
+  block_reduce_store<2>(acc, partial + S_TS * MAXB);
+}
+
+// split J (FP64) into hi/lo FP32 pairs, layout [b][p][hi4, lo4]
+__global__ void k_split_df(int64_t nblocks, const double4_16a* __restrict__ J, float4* __restrict__ Jdf) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nblocks; q += (int64_t)gridDim.x * blockDim.x) {
+    const double4_16a a = J[q];
+    const float h0 = (float)a.x, h1 = (float)a.y, h2 = (float)a.z, h3 = (float)a.w;
+    Jdf[2 * q] = make_float4(h0, h1, h2, h3);
+    Jdf[2 * q + 1] = make_float4((float)(a.x - (double)h0), (float)(a.y - (double)h1), (float)(a.z - (double)h2),
+                                 (float)(a.w - (double)h3));
+  }
+}
+
 template <typename XV, int NB>
 __global__ void __launch_bounds__(BS) k_spmv64(Dims d, Nbr nb, const double* __restrict__ J,
                                                const double2* __restrict__ md, double shift,
@@ -338,6 +421,29 @@ void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* 
   if (d.nb == 27) RF_LAUNCH((k_bicg_v<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
   else RF_LAUNCH((k_bicg_v<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
   fin(1, g, K, 0.0, s);
+}
+
+void launch_split_df(const Dims& d, const double* J, float* Jdf, void* s) {
+  const int64_t nblocks = (int64_t)d.nb * d.nv;
+  RF_LAUNCH(k_split_df, grid_for(nblocks, 256), 256, 0, s, nblocks, (const double4_16a*)J, (float4*)Jdf);
+}
+
+void launch_bicg_v_df(const Dims& d, const Nbr& nb, const float* Jdf, const double* mdiag, double shift,
+                      KrylovVecs& K, void* s) {
+  const int g = krylov_blocks(d.nv);
+  const double2* md = (const double2*)mdiag;
+  if (d.nb == 27) RF_LAUNCH(k_bicg_v_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
+  else RF_LAUNCH(k_bicg_v_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
+  fin(1, g, K, 0.0, s);
+}
+
+void launch_bicg_t_df(const Dims& d, const Nbr& nb, const float* Jdf, const double* mdiag, double shift,
+                      KrylovVecs& K, void* s) {
+  const int g = krylov_blocks(d.nv);
+  const double2* md = (const double2*)mdiag;
+  if (d.nb == 27) RF_LAUNCH(k_bicg_t_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
+  else RF_LAUNCH(k_bicg_t_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
+  fin(2, g, K, 0.0, s);
 }
 
 void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s) {

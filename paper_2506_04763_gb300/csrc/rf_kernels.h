@@ -119,6 +119,12 @@ void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool first, void* 
 void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    KrylovVecs& K, bool y_is_f32, void* s);
 void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s);
+// double-FP32 outer operator (FP32 operands y, z; J as FP32 hi/lo pairs)
+void launch_split_df(const Dims& d, const double* J, float* Jdf, void* s);
+void launch_bicg_v_df(const Dims& d, const Nbr& nb, const float* Jdf, const double* mdiag, double shift,
+                      KrylovVecs& K, void* s);
+void launch_bicg_t_df(const Dims& d, const Nbr& nb, const float* Jdf, const double* mdiag, double shift,
+                      KrylovVecs& K, void* s);
 void launch_bicg_t(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    KrylovVecs& K, bool z_is_f32, void* s);
 void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, void* s);

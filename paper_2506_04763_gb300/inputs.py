@@ -174,9 +174,10 @@ def lognormal_box(nvert, seed, lenses=0, name=None, ell=8.0):
 
 
 def levels_for(nvert):
-    """Vertex-nested levels down to a coarsest grid of at most 7 vertices per axis."""
+    """Vertex-nested levels down to a coarsest grid of at most 5 vertices per axis
+    (257 -> 7 levels, 385 -> 8, 97 -> 6, 65 -> 5, 49 -> 5, 33 -> 4)."""
     L, m = 1, int(nvert)
-    while (m - 1) % 2 == 0 and m > 7:
+    while (m - 1) % 2 == 0 and m > 5:
         m = (m - 1) // 2 + 1
         L += 1
     return L

@@ -286,6 +286,30 @@ def test_solve_matches_oracle(case, precision, smoother):
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress", "3d-config3-33"])
+def test_solve_with_double_fp32_operator_matches_oracle(case, precision):
+    """RF_OUTER_DF32: the iteration's operator applications in double-FP32;
+    the FP64 true residual still decides convergence."""
+    prob = CASES[case]()
+    g, F = _assembled(prob)
+    shift = 1.0 / prob["H"]
+    L = _levels(prob)
+    g.gmg_setup([shift], rf.gmg_opts(L, "gs8", precision=precision))
+    b = torch.tensor(F, device="cuda")
+    x = torch.empty_like(b)
+    info = g.solve(0, b, x, rtol=1e-12, max_it=300, outer="df32")
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["relres"] <= 1e-12, info
+    m = O.Model(prob)
+    _, J_o, md_o = O.assemble(m, prob["u0"])
+    A = O.make_A(J_o, md_o, shift)
+    xs = x.cpu().numpy()
+    r = F - O.spmv(m.dim, m.n, A, xs)
+    assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(F)
+    g.close()
+
+
 def test_solve_host_buffers_and_zero_rhs():
     prob = CASES["2d-config1"]()
     g, F = _assembled(prob)
@@ -357,6 +381,35 @@ def test_limex_step_matches_oracle(kappa):
         assert info["eps"] == pytest.approx(inf_o["eps"], rel=1e-5)
         assert info["H_new"] == pytest.approx(inf_o["H_new"], rel=1e-5)
     g.close()
+
+
+def test_batched_ensemble_equals_sequential_steps():
+    """rf_limex_step_batched runs uneven problems concurrently; every member's
+    result is bitwise the one of its own sequential rf_limex_step."""
+    probs = [I.random_problem(3, (17, 17, 17), 41), I.random_problem(3, (9, 9, 9), 42),
+             I.random_problem(2, (33, 33), 43), I.random_problem(3, (33, 17, 9), 44),
+             I.random_problem(3, (17, 9, 9), 45)]
+    gm = [rf.gmg_opts(_levels(p), "jacobi", precision="fp32") for p in probs]
+    seq = []
+    for p, o in zip(probs, gm):
+        g = _grid(p)
+        u = torch.tensor(p["u0"], device="cuda")
+        info = g.limex_step(u, 5.0, kappa=3, tol=1e9, gmg=o, rtol=1e-11)
+        torch.cuda.synchronize()
+        seq.append((u.cpu().numpy(), info))
+        g.close()
+    grids = [_grid(p) for p in probs]
+    us = [torch.tensor(p["u0"], device="cuda") for p in probs]
+    st, infos = rf.limex_step_batched(grids, us, 5.0, kappa=3, tol=1e9, gmg=gm, rtol=1e-11, max_concurrent=3)
+    torch.cuda.synchronize()
+    assert st == max(i["status"] for _, i in seq)
+    assert sum(i["status"] == 0 for _, i in seq) >= 4
+    for (u_s, i_s), u_b, i_b in zip(seq, us, infos):
+        assert i_b["status"] == i_s["status"]
+        assert np.array_equal(u_s, u_b.cpu().numpy())
+        assert i_b["iterations"] == i_s["iterations"] and i_b["eps"] == i_s["eps"]
+    for g in grids:
+        g.close()
 
 
 def test_limex_rejects_and_keeps_state():
