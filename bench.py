@@ -53,6 +53,9 @@ def args_():
                     help="extra solve variants to time: precision[+outer], comma separated")
     ap.add_argument("--sample-nvert", type=int, default=65, help="oracle sample size (vertices per axis)")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-realisation ensemble (1/0)")
+    ap.add_argument("--config5-nvert", type=int, default=0,
+                    help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
+    ap.add_argument("--config5-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -391,6 +394,41 @@ def main():
         except rf.RFError as e:
             ensemble = {"error": str(e)}
 
+    # ---- config5: adaptive LIMEX on the DNAPL infiltration recipe, mass check
+    config5 = None
+    if a.config5_nvert:
+        try:
+            g.close()
+            torch.cuda.empty_cache()
+            p5 = I.config5(a.config5_nvert)
+            g5 = rf.Grid(p5)
+            u5 = torch.tensor(p5["u0"], device=dev)
+            m0 = g5.phase_mass(u5)[1]
+            q5 = float(p5["q_in"][1::2].sum())
+            opts5 = rf.gmg_opts(p5["nlevels"], "gs8", precision="fp32")
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t5, hist = g5.limex_run(u5, 10.0, steps=a.config5_steps, tol=1e-3, gmg=opts5, rtol=1e-10, max_it=300)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+            m1 = g5.phase_mass(u5)[1]
+            dof5 = 2 * g5.nv
+            nstep = len(hist)
+            config5 = {"workload": "config5: %d^3 DNAPL infiltration (inlet 0.1 kg m^-2 s^-1, lognormal K seed 3 + "
+                                   "lenses), adaptive LIMEX kappa = 4, TOL 1e-3, H0 = 10 s, FP32 GMG (8-colour GS) / "
+                                   "FP64 outer, rel.res 1e-10" % a.config5_nvert,
+                       "accepted": sum(h["accepted"] for h in hist), "rejected": sum(1 - h["accepted"] for h in hist),
+                       "t_end_s": t5, "wall_s": round(wall, 2), "ms_per_step": round(wall * 1e3 / nstep, 1),
+                       "dofs_per_s_per_step": dof5 / (wall / nstep), "dofs": dof5,
+                       "stage_solves": sum(h["solves"] for h in hist),
+                       "iterations": sum(h["iterations"] for h in hist),
+                       "napl_mass_kg": m1, "injected_kg": q5 * t5,
+                       "mass_error_rel": abs(m1 - m0 - q5 * t5) / m1,
+                       "H_history": [round(h["H"], 3) for h in hist]}
+            g5.close()
+        except (rf.RFError, RuntimeError) as e:
+            config5 = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1:
         v, dt, sdof, sit = oracle_sample(a.sample_nvert, a.smoother)
@@ -419,6 +457,7 @@ def main():
             "variants": variants,
             "limex_step": limex,
             "ensemble": ensemble,
+            "config5": config5,
             "e2e": {"value": world * dof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": 16 * g.nv,
                     "d2h_bytes_per_step": 16 * g.nv},
             "gpu_launches": launches,

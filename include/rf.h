@@ -161,6 +161,14 @@ rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* op
 rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
                                 const rf_limex_opts* opts, rf_limex_info* infos, int max_concurrent, void* stream);
 
+/* Total phase masses (kg) of state u [2nv] with the lumped storage of Eqs.
+ * (dsW),(dpN): mass_out[0] = sum_i rho_w (Phi V)_i (1 - S_n,i), mass_out[1] =
+ * sum_i rho_n (Phi V)_i S_n,i (host array of 2; synchronises the stream).
+ * Each linearly implicit Euler stage changes the NAPL mass by exactly h times
+ * its sources plus the linear solve's residual, so the difference between two
+ * states checks discrete mass conservation. */
+rf_status rf_phase_mass(rf_grid* g, const double* u, double* mass_out, void* stream);
+
 /* ---- test and inspection hooks (host buffers, natural vertex order) ---- */
 
 /* Copy out J as [nv][nb][4] (entries (w,p_w),(w,S_n),(n,p_w),(n,S_n)) and the

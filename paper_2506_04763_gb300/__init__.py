@@ -102,6 +102,7 @@ SIGNATURES = {
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_limex_step_batched": (_I, [_P, _P, _P, _I, _P, _P, _I, _P]),
+    "rf_phase_mass": (_I, [_P, _P, _P, _P]),
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
     "rf_export_rows": (_I, [_P, _P, _I, _P, _P, _P]),
@@ -345,6 +346,32 @@ class Grid:
         st, info = rf_limex_step(self.handle, _ptr(u), H, o, self.stream)
         return dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted, solves=info.solves,
                     iterations=info.iterations)
+
+    def limex_run(self, u, H0, steps, tol=1e-3, rho=0.75, H_max=None, gmg=None, rtol=1e-10, max_it=200,
+                  outer="fp64", kappa=4, max_rejects=50):
+        """Adaptive LIMEX integration (step control of Sec. 4, q = 2): takes
+        `steps` accepted steps from state u (updated in place); a rejected
+        step is retried with the proposed smaller H.  Returns (t, history)."""
+        H, t, hist, rejects = float(H0), 0.0, [], 0
+        while sum(h["accepted"] for h in hist) < steps:
+            info = self.limex_step(u, H, kappa=kappa, tol=tol, rho=rho, gmg=gmg, rtol=rtol, max_it=max_it,
+                                   outer=outer)
+            info.update(H=H, t=t)
+            hist.append(info)
+            if info["accepted"]:
+                t += H
+            else:
+                rejects += 1
+                if rejects > max_rejects:
+                    raise RuntimeError("LIMEX: more than %d rejected steps" % max_rejects)
+            H = info["H_new"] if H_max is None else min(info["H_new"], H_max)
+        return t, hist
+
+    def phase_mass(self, u):
+        """(water, NAPL) mass in kg of state u (lumped storage)."""
+        out = np.zeros(2)
+        _check(lib().rf_phase_mass(self.handle, _ptr(u), _ptr(out), self.stream))
+        return float(out[0]), float(out[1])
 
     def profile(self, enable):
         rf_profile(self.handle, enable)

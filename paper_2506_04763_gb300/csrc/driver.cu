@@ -1094,6 +1094,16 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
   return worst;
 }
 
+extern "C" rf_status rf_phase_mass(rf_grid* g, const double* u, double* mass_out, void* s) {
+  if (!g || !u || !mass_out) return fail(RF_EINVAL, "grid, u and mass_out are required");
+  rf_status st = pairs_in(g, g->d, u, g->u_p, s);
+  if (st) return st;
+  launch_phase_mass(g->d.nv, g->pp.rho_w, g->pp.rho_n, g->phiv, g->u_p, g->norms, g->K.partial, s);
+  CU(cudaMemcpyAsync(mass_out, g->norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return RF_OK;
+}
+
 // ------------------------------------------------------------------ ensembles
 extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
                                            const rf_limex_opts* o, rf_limex_info* infos, int max_concurrent,

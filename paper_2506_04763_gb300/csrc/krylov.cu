@@ -578,6 +578,34 @@ __global__ void __launch_bounds__(BS) k_error_norms(Dims d, double h0, double h1
   block_reduce_store<4>(acc, partial);
 }
 
+// Phase masses of a state (lumped storage, Eq. dsW/dpN): sum_i rho_w (Phi V)_i
+// (1 - S_n,i) and sum_i rho_n (Phi V)_i S_n,i; slots 0 and 1 of `partial`.
+__global__ void __launch_bounds__(BS) k_phase_mass(int64_t nv, double rho_w, double rho_n,
+                                                   const double* __restrict__ phiv, const double2* __restrict__ u,
+                                                   double* __restrict__ partial) {
+  double acc[2] = {0.0, 0.0};
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < nv; p += (int64_t)gridDim.x * BS) {
+    const double pv = phiv[p], sn = u[p].y;
+    acc[0] += rho_w * pv * (1.0 - sn);
+    acc[1] += rho_n * pv * sn;
+  }
+  block_reduce_store<2>(acc, partial);
+}
+
+__global__ void k_sum2(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
+  for (int q = 0; q < 2; ++q) {
+    const double t = sum_partials(partial, q, nblk);
+    if (threadIdx.x == 0) out[q] = t;
+  }
+}
+
+void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, double* out2,
+                       double* partial, void* s) {
+  const int g = krylov_blocks(nv);
+  RF_LAUNCH(k_phase_mass, g, BS, 0, s, nv, rho_w, rho_n, phiv, (const double2*)u, partial);
+  RF_LAUNCH(k_sum2, 1, 32, 0, s, g, partial, out2);
+}
+
 __global__ void k_sum4(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
   for (int q = 0; q < 4; ++q) {
     const double t = sum_partials(partial, q, nblk);

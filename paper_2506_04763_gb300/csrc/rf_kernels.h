@@ -133,6 +133,9 @@ void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const d
 void launch_restart(int64_t nv, KrylovVecs& K, void* s);
 void launch_axpy_pairs(int64_t nv, double2* u, const double2* du, void* s);
 
+void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, double* out2,
+                       double* partial, void* s);
+
 // ---- LIMEX (krylov.cu) ----
 void launch_extrapolate(int64_t n2, int kappa, double* T, void* s);
 void launch_error_norms(const Dims& d, const double* h, const double* Tkk, const double* Tkk1, double* out4,

@@ -412,6 +412,26 @@ def test_batched_ensemble_equals_sequential_steps():
         g.close()
 
 
+def test_adaptive_limex_conserves_napl_mass():
+    """DNAPL infiltration recipe (Neumann NAPL inlet on top, Dirichlet p_w
+    elsewhere) at 33^3: over adaptive LIMEX steps the NAPL mass grows exactly
+    by the injected mass (every stage is a divergence-form balance, the
+    extrapolation weights sum to one), up to the linear solves' residuals."""
+    prob = I.config5(33)
+    g = _grid(prob)
+    u = torch.tensor(prob["u0"], device="cuda")
+    m0 = g.phase_mass(u)[1]
+    q = prob["q_in"][1::2].sum()
+    t, hist = g.limex_run(u, 10.0, steps=4, tol=1e-3, gmg=rf.gmg_opts(prob["nlevels"], "gs8", precision="fp32"),
+                          rtol=1e-12, max_it=400)
+    torch.cuda.synchronize()
+    m1 = g.phase_mass(u)[1]
+    assert sum(h["accepted"] for h in hist) == 4 and t > 0
+    err = abs(m1 - m0 - q * t) / m1
+    assert err <= 1e-10, err
+    g.close()
+
+
 def test_limex_rejects_and_keeps_state():
     prob = I.random_problem(2, (17, 17), 32)
     g = _grid(prob)
