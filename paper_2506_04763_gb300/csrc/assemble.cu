@@ -1,10 +1,15 @@
 // assemble.cu — grid set-up (K0) and vertex-centred finite-volume assembly
 // (K1: F, exact Jacobian J = F_u and lumped M; K1r: F only).
 //
-// Compiled with -fmad=false: every product and sum of the discrete fluxes is
-// rounded separately, in the order written, so that the upwind decisions
-// (sign of T_w, T_n), the interface-condition cap and the k_r clamps are taken
-// on exactly the values that the order of operations below defines.
+// Compiled with -fmad=false: every product and sum is rounded separately, in
+// the order written.  The quantities on which a discrete decision rests — S_e
+// (k_r clamps), p_c and p_n = p_w + p_c, the face gradients G, T_w and T_n
+// (upwind directions), S_e at x_M and the S hat cap test — are in addition
+// written with explicit round-to-nearest intrinsics (__dadd_rn, __dmul_rn, ...),
+// so the decisions are taken on exactly the values that order defines.  The
+// derivatives stay unfused too: several Jacobian entries are sums of nearly
+// cancelling terms (e.g. the NAPL rows where k_rn ~ 0), whose rounding a fused
+// multiply-add would change by far more than 1e-12 of the row.
 //
 // Method (arXiv 2506.04763):
 //   Sec. 3.1, Eqs. (dsW),(dpN): dual-mesh control volumes b_i; storage lumped
@@ -41,24 +46,26 @@ struct Phys {
 // ---- constitutive laws (Brooks-Corey; J continued linearly outside [0.01, 1])
 __device__ __forceinline__ void leverett_pow(double lam, double S, double& J, double& dJ) {
   if (lam == 2.0) {
-    double r = sqrt(S);
-    J = 1.0 / r;
-    dJ = -0.5 / (S * r);
+    double r = __dsqrt_rn(S);
+    J = __ddiv_rn(1.0, r);
+    dJ = __ddiv_rn(-0.5, __dmul_rn(S, r));
   } else {
     J = pow(S, -1.0 / lam);
     dJ = (-1.0 / lam) * pow(S, -1.0 / lam - 1.0);
   }
 }
 
+// J(S_e) (decides nothing by itself but feeds p_c, p_n and T: exact rounding)
 __device__ __forceinline__ void leverett(double lam, double Se, double& J, double& dJ) {
   if (Se < 0.01) {
     double j0, d0;
     leverett_pow(lam, 0.01, j0, d0);
-    J = j0 + d0 * (Se - 0.01);
+    J = __dadd_rn(j0, __dmul_rn(d0, __dsub_rn(Se, 0.01)));
     dJ = d0;
   } else if (Se > 1.0) {
-    J = 1.0 + (-1.0 / lam) * (Se - 1.0);
-    dJ = -1.0 / lam;
+    const double sl = __ddiv_rn(-1.0, lam);
+    J = __dadd_rn(1.0, __dmul_rn(sl, __dsub_rn(Se, 1.0)));
+    dJ = sl;
   } else {
     leverett_pow(lam, Se, J, dJ);
   }
@@ -97,9 +104,9 @@ __device__ __forceinline__ void krn_of(double lam, double Se, double& k, double&
 // Eq. (hSw): S_e hat of vertex i inside an element of entry pressure pdc.
 __device__ __forceinline__ void shat_of(double lam, double Se, double pdc, double pdmin, double& s, double& ds) {
   if (pdc == pdmin) { s = Se; ds = 1.0; return; }
-  double r = pdc / pdmin;
-  double rl = (lam == 2.0) ? r * r : pow(r, lam);
-  double t = rl * Se;
+  double r = __ddiv_rn(pdc, pdmin);
+  double rl = (lam == 2.0) ? __dmul_rn(r, r) : pow(r, lam);
+  double t = __dmul_rn(rl, Se);
   if (t >= 1.0) { s = 1.0; ds = 0.0; }
   else { s = t; ds = rl; }
 }
@@ -168,16 +175,16 @@ __global__ void k_vertex_state(Dims d, Phys ph, const double2* __restrict__ u, c
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= d.nv) return;
   double2 uv = u[p];
-  double se = (1.0 - uv.y - ph.S_wr) / ph.den;
+  double se = __ddiv_rn(__dsub_rn(__dsub_rn(1.0, uv.y), ph.S_wr), ph.den);
   double J, dJ, k, dk;
   leverett(ph.lam, se, J, dJ);
   krw_of(ph.lam, se, k, dk);
   double pdm = pdmin[p];
-  double c = pdm * J;
+  double c = __dmul_rn(pdm, J);
   Se[p] = se;
   pc[p] = c;
   dpc[p] = -(pdm * dJ) / ph.den;
-  pn[p] = uv.x + c;
+  pn[p] = __dadd_rn(uv.x, c);
   krw[p] = k;
   dkrw[p] = -dk / ph.den;
 }
@@ -238,8 +245,8 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
         if (m != kk) oth[no++] = m;
       double Af = 1.0;
 #pragma unroll
-      for (int t = 0; t < DIM - 1; ++t) Af = Af * (ph.h[oth[t]] * 0.5);
-      const double KA = Kc * Af;
+      for (int t = 0; t < DIM - 1; ++t) Af = __dmul_rn(Af, __dmul_rn(ph.h[oth[t]], 0.5));
+      const double KA = __dmul_rn(Kc, Af);
       int o[2] = {0, 0};
 #pragma unroll
       for (int t = 0; t < DIM - 1; ++t) o[t] = (c >> oth[t]) & 1;
@@ -257,11 +264,11 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
           a2 |= o2[t] << oth[t];
         }
         const int b2 = a2 | (1 << kk);
-        gpn = gpn + w * (pnq[b2] - pnq[a2]);
-        gpc = gpc + w * (pcq[b2] - pcq[a2]);
+        gpn = __dadd_rn(gpn, __dmul_rn(w, __dsub_rn(pnq[b2], pnq[a2])));
+        gpc = __dadd_rn(gpc, __dmul_rn(w, __dsub_rn(pcq[b2], pcq[a2])));
       }
-      gpn = gpn / ph.h[kk];
-      gpc = gpc / ph.h[kk];
+      gpn = __ddiv_rn(gpn, ph.h[kk]);
+      gpc = __ddiv_rn(gpc, ph.h[kk]);
       double wM[NC], SeM = 0.0;
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
@@ -269,11 +276,11 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
 #pragma unroll
         for (int t = 0; t < DIM - 1; ++t) w = w * ((((q >> oth[t]) & 1) == o[t]) ? 0.75 : 0.25);
         wM[q] = w;
-        SeM = SeM + w * se[q];
+        SeM = __dadd_rn(SeM, __dmul_rn(w, se[q]));
       }
-      const double Tw = -KA * (gpn - ph.rho_w * ph.g[kk]);
-      const double Tn = -KA * (gpn - ph.rho_n * ph.g[kk]);
-      const double Tc = -KA * gpc;
+      const double Tw = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_w, ph.g[kk])));
+      const double Tn = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_n, ph.g[kk])));
+      const double Tc = __dmul_rn(-KA, gpc);
       const bool wa = Tw >= 0.0, na = Tn >= 0.0;
       const int64_t vw = wa ? vq[a] : vq[b];
       const int64_t vn = na ? vq[a] : vq[b];
