@@ -56,6 +56,8 @@ def args_():
     ap.add_argument("--config5-nvert", type=int, default=0,
                     help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
     ap.add_argument("--config5-steps", type=int, default=20)
+    ap.add_argument("--autotune", type=int, default=0,
+                    help="time block sizes of the level kernels during the set-up (1/0)")
     return ap.parse_args()
 
 
@@ -210,7 +212,7 @@ def main():
         torch.cuda.synchronize()
         s0, s1 = ev(), ev()
         s0.record(stream)
-        g.gmg_setup([shift], rf.gmg_opts(L, a.smoother, precision=precision))
+        g.gmg_setup([shift], rf.gmg_opts(L, a.smoother, precision=precision, autotune=a.autotune))
         s1.record(stream)
         torch.cuda.synchronize()
         return s0.elapsed_time(s1)
@@ -445,7 +447,7 @@ def main():
                                    "(h = 10 s) at u0, b = F(u0); FP64 BiCGSTAB (%s operator) + %s GMG (%d levels, %s, "
                                    "V(2,2)), x0 = 0, true rel.res <= 1e-10" % (a.nvert, a.outer.upper(), a.precision.upper(), L,
                                                                             "8-colour block GS" if a.smoother == "gs8" else "block Jacobi w=0.8"),
-                       "dofs": dof, "vertices": [a.nvert] * 3, "levels": L,
+                       "dofs": dof, "vertices": [a.nvert] * 3, "levels": L, "autotune": bool(a.autotune),
                        "l2": "no flush: inputs larger than L2 (FP64 Jacobian %.1f GB)" % (dof / 2 * 864 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "iterations": iters, "relres": infos[-1]["relres"],

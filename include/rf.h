@@ -92,8 +92,12 @@ enum { RF_PREC_FP64 = 0, RF_PREC_FP32 = 1, RF_PREC_FP16 = 2 };
  * (4 colours 2D / 8 colours 3D) block Gauss-Seidel; nu1/nu2 pre/post sweeps;
  * omega: Jacobi damping; precision: storage and arithmetic of the
  * preconditioner (FP64; FP32; FP16 storage with per-block-row FP32 scales and
- * FP32 arithmetic).  The coarsest level is solved exactly in FP64. */
-typedef struct { int nlevels, smoother, nu1, nu2; double omega; int precision; } rf_gmg_opts;
+ * FP32 arithmetic).  The coarsest level is solved exactly in FP64.
+ * autotune = 1 times candidate thread-block sizes (64..512) for each level's
+ * smoothing and residual kernels during the set-up and keeps the fastest
+ * (cached per level shape for the process, and in the file named by the
+ * environment variable RF_TUNE_CACHE, one JSON object per line). */
+typedef struct { int nlevels, smoother, nu1, nu2; double omega; int precision; int autotune; } rf_gmg_opts;
 
 /* Stop when the TRUE FP64 residual |b - A x|_2 <= rtol |b|_2.  outer selects
  * the arithmetic of the two operator applications inside each iteration:

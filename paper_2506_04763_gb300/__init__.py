@@ -64,7 +64,8 @@ class rf_allocator(ctypes.Structure):
 
 class rf_gmg_opts(ctypes.Structure):
     _fields_ = [("nlevels", ctypes.c_int), ("smoother", ctypes.c_int), ("nu1", ctypes.c_int),
-                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int)]
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("precision", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 RF_OUTER_FP64, RF_OUTER_DF32 = 0, 1
@@ -282,9 +283,9 @@ SMOOTHERS = {"jacobi": RF_SMOOTH_JACOBI, "gs8": RF_SMOOTH_GS8, "gs": RF_SMOOTH_G
 PRECISIONS = {"fp64": RF_PREC_FP64, "fp32": RF_PREC_FP32, "fp16": RF_PREC_FP16}
 
 
-def gmg_opts(nlevels, smoother="jacobi", nu1=2, nu2=2, omega=0.8, precision="fp32"):
+def gmg_opts(nlevels, smoother="jacobi", nu1=2, nu2=2, omega=0.8, precision="fp32", autotune=False):
     return rf_gmg_opts(int(nlevels), SMOOTHERS.get(smoother, smoother), int(nu1), int(nu2), float(omega),
-                       PRECISIONS.get(precision, precision))
+                       PRECISIONS.get(precision, precision), int(bool(autotune)))
 
 
 class Grid:

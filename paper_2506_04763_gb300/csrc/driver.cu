@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -71,6 +73,7 @@ struct Level {
   float* scale[RF_MAXSHIFT] = {};
   void* Dinv[RF_MAXSHIFT] = {};
   void *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+  int block = 256;   // threads per block of the smoothing / residual kernels
 };
 
 struct Alloc {
@@ -481,7 +484,105 @@ static LevelOp level_op(rf_grid* g, int l, int sh) {
   op.shift = g->shifts[sh];
   op.Dinv = Lv.Dinv[sh];
   op.dmask = Lv.dmask;
+  op.block = Lv.block;
   return op;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Chooses, per level, the thread-block size of the smoothing and residual
+// kernels by timing one sweep plus one residual for each candidate on the
+// level's own data (CUDA events).  Choices are cached per (device, level
+// dimensions, storage kind, smoother, finest-or-not) for the process and, when
+// RF_TUNE_CACHE names a file, in that file as one JSON object per line.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_key(const Dims& d, int kind, int smoother, bool fine) {
+  static std::string dev;
+  if (dev.empty()) {
+    cudaDeviceProp p;
+    int id = 0;
+    cudaGetDevice(&id);
+    dev = (cudaGetDeviceProperties(&p, id) == cudaSuccess) ? p.name : "gpu";
+  }
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|%dx%dx%d|k%d|s%d|f%d", dev.c_str(), d.nx, d.ny, d.nz, kind, smoother, fine ? 1 : 0);
+  return buf;
+}
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("RF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    // {"key": "<key>", "block": <n>}
+    char* k = strstr(line, "\"key\": \"");
+    char* b = strstr(line, "\"block\": ");
+    if (!k || !b) continue;
+    k += 8;
+    char* e = strchr(k, '"');
+    if (!e) continue;
+    g_tune[std::string(k, e - k)] = atoi(b + 9);
+  }
+  fclose(f);
+}
+
+static void tune_store_locked(const std::string& key, int block) {
+  g_tune[key] = block;
+  const char* path = getenv("RF_TUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"key\": \"%s\", \"block\": %d}\n", key.c_str(), block);
+  fclose(f);
+}
+
+static rf_status autotune_levels(rf_grid* g, void* s) {
+  static const int cand[4] = {64, 128, 256, 512};
+  const int last = g->nl - 1;   // the coarsest level is a dense solve
+  for (int l = 0; l < last; ++l) {
+    Level& Lv = g->L[l];
+    const std::string key = tune_key(Lv.d, g->kind, g->gopt.smoother, l == 0);
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_load_locked();
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) { Lv.block = it->second; continue; }
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_bs = 256;
+    for (int c = 0; c < 4; ++c) {
+      Lv.block = cand[c];
+      LevelOp op = level_op(g, l, 0);
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        CU(cudaEventRecord(e0, (cudaStream_t)s));
+        if (g->gopt.smoother == RF_SMOOTH_JACOBI) launch_jacobi(op, Lv.b, Lv.x, Lv.t, g->gopt.omega, false, s);
+        else launch_gs_sweep(op, Lv.b, Lv.x, true, false, s);
+        launch_residual(op, Lv.b, Lv.x, Lv.r, s);
+        CU(cudaEventRecord(e1, (cudaStream_t)s));
+        CU(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && ms < tmin) tmin = ms;   // first repetition warms up
+      }
+      if (tmin < best) { best = tmin; best_bs = cand[c]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    Lv.block = best_bs;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_store_locked(key, best_bs);
+  }
+  return RF_OK;
 }
 
 static void dfree_ptr(rf_grid* g, void* p, void* s) {
@@ -659,6 +760,10 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       GNEED(g->K.y64 = (double2*)dvec(g, g->d, sizeof(double), s, true));
       GNEED(g->K.z64 = (double2*)dvec(g, g->d, sizeof(double), s, true));
     }
+  }
+  if (o->autotune) {
+    rf_status ts = autotune_levels(g, s);
+    if (ts) { dfree_all(g, g->gbufs, s); return ts; }
   }
   // Optionally the small levels (<= RF_TAIL_NV vertices) run as one cluster
   // kernel.  Off by default: measured on GB300 it saves < 1% of a 257^3 solve

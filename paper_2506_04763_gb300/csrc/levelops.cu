@@ -127,7 +127,7 @@ __device__ __forceinline__ void residual_point(const LevelOp& L, const typename 
 }
 
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+__global__ void __launch_bounds__(512) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                   const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -162,7 +162,7 @@ __device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2
 }
 
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+__global__ void __launch_bounds__(512) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                 const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
                                                 typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
                                                 int zero_x) {
@@ -199,7 +199,7 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
 }
 
 template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(256) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+__global__ void __launch_bounds__(512) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                    typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
                                                    int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -789,22 +789,24 @@ __global__ void k_cast_f32_f64(const float* __restrict__ in, double* __restrict_
 template <int KIND, bool FINE>
 static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, void* s) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
-  const int g = (int)((L.d.nv + 255) / 256);
+  const int bs = L.block > 0 ? L.block : 256;
+  const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.d.nb == 27)
-    RF_LAUNCH((k_residual<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    RF_LAUNCH((k_residual<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   else
-    RF_LAUNCH((k_residual<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    RF_LAUNCH((k_residual<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
 }
 
 template <int KIND, bool FINE>
 static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x,
                      void* s) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
-  const int g = (int)((L.d.nv + 255) / 256);
+  const int bs = L.block > 0 ? L.block : 256;
+  const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.d.nb == 27)
-    RF_LAUNCH((k_jacobi<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    RF_LAUNCH((k_jacobi<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   else
-    RF_LAUNCH((k_jacobi<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    RF_LAUNCH((k_jacobi<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
 }
 
 // First forward sweep from x = 0: the neighbours of colour c that have a
@@ -833,11 +835,12 @@ static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool ze
     const int lines_z = L.d.dim == 3 ? (L.d.nz - pz + 1) / 2 : 1;
     const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
     if (count == 0) continue;
-    const int g = (int)((count + 255) / 256);
+    const int bs = L.block > 0 ? L.block : 256;
+    const int g = (int)((count + bs - 1) / bs);
     if (L.d.nb == 27)
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
     else
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, 256, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
   }
 }
 

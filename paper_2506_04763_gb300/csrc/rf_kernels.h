@@ -50,6 +50,7 @@ struct LevelOp {
   double shift;          // fine: 1/h_j
   const void* Dinv;      // [nv][4] inverse diagonal blocks (T)
   const uint8_t* dmask;  // [nv]
+  int block = 256;       // threads per block of the smoothing / residual kernels (autotuned)
 };
 
 // Vectors are T2 pointers to the first interior element of padded buffers.

@@ -286,6 +286,35 @@ def test_solve_matches_oracle(case, precision, smoother):
     g.close()
 
 
+@pytest.mark.parametrize("precision,smoother", [("fp32", "gs8"), ("fp64", "jacobi"), ("fp16", "gs8")])
+def test_autotuned_block_sizes_give_identical_solves(precision, smoother, tmp_path, monkeypatch):
+    """The autotuner only changes the thread-block size of the smoothing and
+    residual kernels; every vertex's arithmetic is the same, so the solve is
+    bitwise identical.  Its choices are appended to the RF_TUNE_CACHE file."""
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("RF_TUNE_CACHE", str(cache))
+    prob = I.random_problem(3, (25, 13, 9), 11 + len(precision) + len(smoother))
+    shift = 1.0 / prob["H"]
+    L = _levels(prob)
+    xs = []
+    for tune in (False, True):
+        g, F = _assembled(prob)
+        g.gmg_setup([shift], rf.gmg_opts(L, smoother, precision=precision, autotune=tune))
+        b = torch.tensor(F, device="cuda")
+        x = torch.empty_like(b)
+        info = g.solve(0, b, x, rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, info
+        xs.append(x.cpu().numpy())
+        g.close()
+    assert np.array_equal(xs[0], xs[1])
+    if cache.exists():
+        import json
+        for line in cache.read_text().splitlines():
+            e = json.loads(line)
+            assert e["block"] in (64, 128, 256, 512), e
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 @pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress", "3d-config3-33"])
 def test_solve_with_double_fp32_operator_matches_oracle(case, precision):
