@@ -133,6 +133,20 @@ int64_t rf_grid_nv(const rf_grid* g);
  * Sec. 3 (Eqs. dsW, dpN, up_krw, up_krn, hSw, krn_ip, krw_ip), Sec. 4 (J=F_u). */
 rf_status rf_assemble(rf_grid* g, const double* u, int want_jacobian, double* F_out, void* stream);
 
+/* Discretisation variants (bits; 0, the default, is the scheme of Sec. 3):
+ * RF_SCHEME_SHAT_STORAGE: the storage of each sub-control volume b_i^j uses
+ *   the interface saturation S hat of Eq. (hSw) (Sec. 3.3 applies it "as
+ *   well" beyond k_rn); M becomes diag(d m / d S_n) with the S hat slopes and
+ *   the storage is no longer linear in S_n.
+ * RF_SCHEME_DARCY_UPWIND: the whole water flux, capillary-diffusion part
+ *   included, is upwinded by the sign of the Darcy velocity u_w . n, the
+ *   scheme Sec. 3.2 sets its own against; the NAPL flux is unchanged.
+ * Changing the scheme drops the assembled Jacobian and multigrid set-up.
+ * RF_EINVAL for unknown bits. */
+#define RF_SCHEME_SHAT_STORAGE 1
+#define RF_SCHEME_DARCY_UPWIND 2
+rf_status rf_grid_set_scheme(rf_grid* g, int scheme);
+
 /* Build the multigrid hierarchy for the stage matrices A_j = shift[j] M - J,
  * j < nshift <= 4 (shift = 1/h_j), from the last assembled J, M: Galerkin
  * coarse operators P^T A P with trilinear P (FP64), the preconditioner copies
@@ -165,9 +179,27 @@ rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* op
 rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
                                 const rf_limex_opts* opts, rf_limex_info* infos, int max_concurrent, void* stream);
 
+/* One implicit Euler step of size H solved by Newton's method — the fixed-step
+ * scheme the paper compares LIMEX with (Sec. 6, Case 4, Table case4_2; Newton
+ * tolerances 1e-8 absolute / 1e-6 relative there).  Finds u with
+ *   R(u) = F(u) - (m(u) - m(u_old)) / H = 0
+ * (m the storage of Eqs. (dsW),(dpN); no storage in Dirichlet p_w rows) by
+ * Newton iterations (M(u_k)/H - J(u_k)) d = R(u_k), u_{k+1} = u_k + d: each
+ * iteration assembles J, M and F at u_k, rebuilds the multigrid hierarchy
+ * (opts->gmg) and solves with BiCGSTAB (opts->solve).  Converged when
+ * ||R||_2 <= atol or ||R||_2 <= rtol ||R(u_old)||_2.  u [2nv] (host or device)
+ * is updated in place only on success; info (host, may be NULL) receives the
+ * Newton and linear iteration counts and the first and last residual norms.
+ * RF_ENOTCONV when max_newton iterations do not converge; a linear solver
+ * failure is returned as is. */
+typedef struct { double atol, rtol; int max_newton; rf_gmg_opts gmg; rf_solve_opts solve; } rf_ie_opts;
+typedef struct { int newton, linear; double res0, res; rf_status status; } rf_ie_info;
+rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opts* opts, rf_ie_info* info, void* stream);
+
 /* Total phase masses (kg) of state u [2nv] with the lumped storage of Eqs.
  * (dsW),(dpN): mass_out[0] = sum_i rho_w (Phi V)_i (1 - S_n,i), mass_out[1] =
- * sum_i rho_n (Phi V)_i S_n,i (host array of 2; synchronises the stream).
+ * sum_i rho_n (Phi V)_i S_n,i (host array of 2; synchronises the stream);
+ * with RF_SCHEME_SHAT_STORAGE each sub-control volume's S hat saturation.
  * Each linearly implicit Euler stage changes the NAPL mass by exactly h times
  * its sources plus the linear solve's residual, so the difference between two
  * states checks discrete mass conservation. */

@@ -51,7 +51,8 @@ class _Model(ctypes.Structure):
                 ("mu_w", ctypes.c_double), ("mu_n", ctypes.c_double), ("S_wr", ctypes.c_double),
                 ("S_nr", ctypes.c_double), ("lam", ctypes.c_double),
                 ("K", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("pd", ctypes.c_void_p),
-                ("dir", ctypes.c_void_p), ("pw_dir", ctypes.c_void_p), ("q_in", ctypes.c_void_p)]
+                ("dir", ctypes.c_void_p), ("pw_dir", ctypes.c_void_p), ("q_in", ctypes.c_void_p),
+                ("scheme", ctypes.c_int)]
 
 
 class _LimexOpts(ctypes.Structure):
@@ -78,6 +79,8 @@ def _declare(L):
         "rfo_pdmin": (None, [_P, _P]),
         "rfo_phiv": (None, [_P, _P]),
         "rfo_assemble": (None, [_P, _P, _P, _P, _P]),
+        "rfo_storage": (None, [_P, _P, _P]),
+        "rfo_ie_step": (_I, [_P, _P, _D, _P, _P, _P]),
         "rfo_make_A": (None, [_I, _I, _P, _P, _D, _P]),
         "rfo_spmv": (None, [_I, _P, _P, _P, _P]),
         "rfo_residual": (None, [_I, _P, _P, _P, _P, _P]),
@@ -141,6 +144,7 @@ class Model:
         s.lam = float(prob["lam"])
         for k in ("K", "phi", "pd", "dir", "pw_dir", "q_in"):
             setattr(s, k, _p(self._keep[k]))
+        s.scheme = int(prob.get("scheme", 0))
         self.s = s
 
     @property
@@ -169,6 +173,14 @@ def pdmin(model):
 def phiv(model):
     out = np.zeros(model.nv)
     lib().rfo_phiv(model.ref, _p(out))
+    return out
+
+
+def storage(model, u):
+    """Storage terms [nv, 2] = (m_w, m_n) per vertex (kg)."""
+    u = _f64(u)
+    out = np.zeros((model.nv, 2))
+    lib().rfo_storage(model.ref, _p(u), _p(out))
     return out
 
 
@@ -318,3 +330,25 @@ def limex_step(model, u0, H, kappa=4, tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4
     st = lib().rfo_limex_step(model.ref, _p(_f64(u0)), float(H), ctypes.byref(o), _p(u_out), ctypes.byref(info))
     return u_out, dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted,
                        solves=info.solves, iterations=info.iterations)
+
+
+class _IeOpts(ctypes.Structure):
+    _fields_ = [("atol", ctypes.c_double), ("rtol", ctypes.c_double), ("max_newton", ctypes.c_int),
+                ("nlevels", ctypes.c_int), ("smoother", ctypes.c_int), ("nu1", ctypes.c_int),
+                ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("lin_rtol", ctypes.c_double),
+                ("lin_maxit", ctypes.c_int)]
+
+
+class _IeInfo(ctypes.Structure):
+    _fields_ = [("newton", ctypes.c_int), ("linear", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double)]
+
+
+def ie_step(model, u_old, H, atol=1e-8, rtol=1e-6, max_newton=20, nlevels=4, smoother=JACOBI, nu1=2, nu2=2,
+            omega=0.8, lin_rtol=1e-10, lin_maxit=400):
+    """One implicit Euler step solved by Newton's method (rfo_ie_step)."""
+    o = _IeOpts(atol, rtol, max_newton, nlevels, smoother, nu1, nu2, omega, lin_rtol, lin_maxit)
+    info = _IeInfo()
+    u_out = np.zeros(2 * model.nv)
+    st = lib().rfo_ie_step(model.ref, _p(_f64(u_old)), float(H), ctypes.byref(o), _p(u_out), ctypes.byref(info))
+    return u_out, dict(status=st, newton=info.newton, linear=info.linear, res0=info.res0, res=info.res)

@@ -150,6 +150,57 @@ void rfo_phiv(const rfo_model* m, double* phiv) {
       }
 }
 
+/* Sum over the sub-control volumes b_i^j of vertex v (one per element j around
+ * it) of Phi_j |b_i^j| times, for want = 0, the water saturation of b_i^j and,
+ * for want = 1, d S hat_e / d S_e (Eq. (hSw)).  With the S hat storage variant
+ * the water saturation of b_i^j is S_wr + S hat_e (1 - S_wr - S_nr).        */
+static double storage_weight(const rfo_model* m, const double* pdmin, double Se, int v, int want) {
+  const int nx = m->n[0], ny = m->n[1];
+  const int cx = nx - 1, cy = ny - 1, cz = (m->dim == 3) ? m->n[2] - 1 : 1;
+  const int i = v % nx, j = (v / nx) % ny, k = v / (nx * ny);
+  const double vol = m->h[0] * m->h[1] * (m->dim == 3 ? m->h[2] : 1.0);
+  const double frac = (m->dim == 3) ? 0.125 : 0.25;
+  const double den = 1.0 - m->S_wr - m->S_nr;
+  double s = 0.0;
+  for (int c2 = 0; c2 < (m->dim == 3 ? 2 : 1); ++c2)
+    for (int c1 = 0; c1 < 2; ++c1)
+      for (int c0 = 0; c0 < 2; ++c0) {
+        int ci = i - c0, cj = j - c1, ck = (m->dim == 3) ? k - c2 : 0;
+        if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+        const int cell = ci + cx * (cj + cy * ck);
+        double sh[2];
+        rfo_shat(m, Se, m->pd[cell], pdmin[v], sh);
+        const double w = m->phi[cell] * vol * frac;
+        s += w * (want ? sh[1] : m->S_wr + sh[0] * den);
+      }
+  return s;
+}
+
+/* Storage terms m_w,i and m_n,i of Eqs. (dsW),(dpN): rho_alpha times the sum
+ * over b_i^j of Phi_j |b_i^j| S_alpha.  The discretisation of Sec. 3 uses the
+ * vertex saturation in every b_i^j; the S hat storage variant uses S hat.   */
+void rfo_storage(const rfo_model* m, const double* u, double* mass) {
+  const int nv = nverts(m->n);
+  const double den = 1.0 - m->S_wr - m->S_nr;
+  double* pdmin = malloc(sizeof(double) * nv);
+  double* phiv = malloc(sizeof(double) * nv);
+  rfo_pdmin(m, pdmin);
+  rfo_phiv(m, phiv);
+  for (int v = 0; v < nv; ++v) {
+    const double Sn = u[2 * v + 1];
+    if (m->scheme & RFO_SCHEME_SHAT_STORAGE) {
+      const double Se = (1.0 - Sn - m->S_wr) / den;
+      const double sw = storage_weight(m, pdmin, Se, v, 0);   /* sum Phi |b| S_w */
+      mass[2 * v] = m->rho_w * sw;
+      mass[2 * v + 1] = m->rho_n * (phiv[v] - sw);
+    } else {
+      mass[2 * v] = m->rho_w * (phiv[v] * (1.0 - Sn));
+      mass[2 * v + 1] = m->rho_n * (phiv[v] * Sn);
+    }
+  }
+  free(pdmin); free(phiv);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Assembly of F(u), J = F_u and M.  Loop over elements; inside each element
  * over its d*2^(d-1) sub-control-volume faces (one per element edge a->b,
@@ -230,7 +281,7 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
             for (int t = 0; t < no; ++t) a |= o[t] << oth[t];
             const int b = a | (1 << k);
             /* gradient along k at x_M, canonical edge order e' = 0..nedge-1 */
-            double gpn = 0.0, gpc = 0.0;
+            double gpn = 0.0, gpc = 0.0, gpw = 0.0;
             for (int e2 = 0; e2 < nedge; ++e2) {
               int o2[2] = {e2 & 1, (e2 >> 1) & 1};
               double w = 1.0;
@@ -242,9 +293,11 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
               int b2 = a2 | (1 << k);
               gpn = gpn + w * (pn[vq[b2]] - pn[vq[a2]]);
               gpc = gpc + w * (pc[vq[b2]] - pc[vq[a2]]);
+              gpw = gpw + w * (u[2 * vq[b2]] - u[2 * vq[a2]]);
             }
             gpn = gpn / m->h[k];
             gpc = gpc / m->h[k];
+            gpw = gpw / m->h[k];
             /* Q1 interpolation weights at x_M, and the saturation there */
             double wM[8], SeM = 0.0;
             for (int q = 0; q < ncorner; ++q) {
@@ -256,14 +309,18 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
             const double Tw = -KA * (gpn - m->rho_w * m->g[k]);
             const double Tn = -KA * (gpn - m->rho_n * m->g[k]);
             const double Tc = -KA * gpc;
-            const int uw = (Tw >= 0.0) ? a : b;
+            /* Darcy-velocity upwinding of the whole water flux (scheme variant):
+             * T_pw = -K A_f (G(p_w) - rho_w g_k), equal to T_w - T_c up to rounding */
+            const int darcy = (m->scheme & RFO_SCHEME_DARCY_UPWIND) != 0;
+            const double Tpw = -KA * (gpw - m->rho_w * m->g[k]);
+            const int uw = darcy ? ((Tpw >= 0.0) ? a : b) : ((Tw >= 0.0) ? a : b);
             const int un = (Tn >= 0.0) ? a : b;
             double bcM[6];
             rfo_brooks_corey(m, SeM, bcM);
             const double lw_up = krw[vq[uw]] / m->mu_w;
             const double lwM = bcM[0] / m->mu_w;
             const double ln_up = krn_h[un] / m->mu_n;
-            const double Fw = m->rho_w * (lw_up * Tw - lwM * Tc);
+            const double Fw = darcy ? m->rho_w * (lw_up * Tpw) : m->rho_w * (lw_up * Tw - lwM * Tc);
             const double Fn = m->rho_n * (ln_up * Tn);
             F[2 * vq[a]] -= Fw; F[2 * vq[a] + 1] -= Fn;
             F[2 * vq[b]] += Fw; F[2 * vq[b] + 1] += Fn;
@@ -284,6 +341,9 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
                                  - dlwM * Tc - lwM * dT * dpc[vq[q]]);
               d[2] = m->rho_n * ln_up * dT;
               d[3] = m->rho_n * ((q == un ? dln_up * Tn : 0.0) + ln_up * dT * dpc[vq[q]]);
+              if (darcy) {   /* T_pw depends on p_w only */
+                d[1] = m->rho_w * (q == uw ? dlw_up * Tpw : 0.0);
+              }
               for (int side = 0; side < 2; ++side) {
                 const int r = side ? b : a;
                 const double sg = side ? 1.0 : -1.0;
@@ -299,6 +359,11 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
 
   double* phiv = malloc(sizeof(double) * nv);
   rfo_phiv(m, phiv);
+  if (m->scheme & RFO_SCHEME_SHAT_STORAGE) {
+    /* S hat storage: d m_n,i / d S_n,i = rho_n sum_j Phi_j |b_i^j| d S hat_e / d S_e
+     * (S_n of b_i^j is 1 - S_wr - S hat_e (1 - S_wr - S_nr)); kept in phiv */
+    for (int v = 0; v < nv; ++v) phiv[v] = storage_weight(m, pdmin, Se[v], v, 1);
+  }
   for (int v = 0; v < nv; ++v) {
     int dirv = m->dir ? m->dir[v] : 0;
     if (mdiag) {
@@ -868,5 +933,61 @@ int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_lim
   memcpy(u_out, acc ? Tkk : u0, sizeof(double) * N);
   if (info) { info->eps = eps; info->H_new = H * fac; info->accepted = acc; info->solves = solves; info->iterations = iters_total; }
   free(J); free(A); free(md); free(F0); free(F); free(du); free(T1); free(Tkk); free(Tkk1); free(nseq); free(dm);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Implicit Euler with Newton's method, the fixed-step scheme the paper sets
+ * LIMEX against (Sec. 6, Case 4; nonlinear tolerances 1e-8 abs / 1e-6 rel).
+ * One step: find u with F(u) - (m(u) - m(u_old))/H = 0, where m is the
+ * storage (rfo_storage) and F the flux residual (rfo_assemble); Dirichlet p_w
+ * rows keep their algebraic equation.  The Newton matrix is M(u_k)/H - J(u_k)
+ * with M = dm/dS_n from the assembly.                                      */
+int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_opts* o, double* u_out,
+                rfo_ie_info* info) {
+  const int dim = m->dim, nv = nverts(m->n), nb = nblk(dim), N = 2 * nv;
+  double* J = malloc(sizeof(double) * (size_t)nv * nb * 4);
+  double* A = malloc(sizeof(double) * (size_t)nv * nb * 4);
+  double* md = malloc(sizeof(double) * N);
+  double* F = malloc(sizeof(double) * N);
+  double* R = malloc(sizeof(double) * N);
+  double* d = malloc(sizeof(double) * N);
+  double* m0 = malloc(sizeof(double) * N);
+  double* mk = malloc(sizeof(double) * N);
+  unsigned char* dm = calloc(nv, 1);
+  if (m->dir) memcpy(dm, m->dir, nv);
+  memcpy(u_out, u_old, sizeof(double) * N);
+  rfo_storage(m, u_old, m0);
+  int status = 1, newton = 0, linear = 0;
+  double r0 = 0.0, r = 0.0;
+  for (;;) {
+    rfo_assemble(m, u_out, F, J, md);
+    rfo_storage(m, u_out, mk);
+    double s2 = 0.0;
+    for (int v = 0; v < nv; ++v) {
+      for (int a = 0; a < 2; ++a) {
+        const int q = 2 * v + a;
+        const int storage = !(a == 0 && dm[v]);
+        R[q] = F[q] - (storage ? (mk[q] - m0[q]) / H : 0.0);
+        s2 += R[q] * R[q];
+      }
+    }
+    r = sqrt(s2);
+    if (newton == 0) r0 = r;
+    if (r <= o->atol || r <= o->rtol * r0) { status = 0; break; }
+    if (newton >= o->max_newton) break;
+    rfo_make_A(nv, nb, J, md, 1.0 / H, A);
+    rfo_gmg* g = rfo_gmg_create(dim, m->n, A, dm, o->nlevels, o->smoother, o->nu1, o->nu2, o->omega);
+    int it = 0; double rr = 0.0;
+    int st = rfo_bicgstab(dim, m->n, A, g, R, d, o->lin_rtol, o->lin_maxit, &it, &rr);
+    rfo_gmg_free(g);
+    linear += it;
+    ++newton;
+    if (st != 0) { status = st; break; }
+    for (int q = 0; q < N; ++q) u_out[q] += d[q];
+  }
+  if (status != 0) memcpy(u_out, u_old, sizeof(double) * N);   /* a failed step keeps the state */
+  if (info) { info->newton = newton; info->linear = linear; info->res0 = r0; info->res = r; }
+  free(J); free(A); free(md); free(F); free(R); free(d); free(m0); free(mk); free(dm);
   return status;
 }

@@ -36,7 +36,18 @@ typedef struct {
   const unsigned char* dir;  /* per vertex: 1 = Dirichlet p_w (may be NULL) */
   const double* pw_dir;      /* per vertex Dirichlet value (used where dir=1) */
   const double* q_in;        /* per vertex [2] mass source kg/s (may be NULL) */
+  int scheme;                /* RFO_SCHEME_* bits; 0 = the discretisation of Sec. 3 */
 } rfo_model;
+
+/* Discretisation variants (bits of rfo_model.scheme):
+ *   RFO_SCHEME_SHAT_STORAGE: the storage term of sub-control volume b_i^j uses
+ *     the interface saturation S hat_{w,i,N} of Eq. (hSw) instead of the vertex
+ *     saturation (Sec. 3.3 asks for Eq. (hSw) "as well" beyond k_rn).
+ *   RFO_SCHEME_DARCY_UPWIND: the water flux is upwinded as a whole by the sign
+ *     of its Darcy velocity u_w . n (phase-potential upwinding, the scheme
+ *     Sec. 3.2 contrasts with its own), i.e. the capillary-diffusion part is
+ *     upwinded too. The NAPL flux is unchanged (u_n and v_n share their sign). */
+enum { RFO_SCHEME_SHAT_STORAGE = 1, RFO_SCHEME_DARCY_UPWIND = 2 };
 
 /* ---- constitutive laws (Brooks-Corey; interface condition) ---- */
 void rfo_brooks_corey(const rfo_model* m, double Se, double out[6]);
@@ -49,6 +60,8 @@ void rfo_pdmin(const rfo_model* m, double* pdmin);   /* [nv] */
 void rfo_phiv(const rfo_model* m, double* phiv);     /* [nv] */
 void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, double* mdiag);
 /* J, mdiag may be NULL (residual only) */
+void rfo_storage(const rfo_model* m, const double* u, double* mass);
+/* mass[2v] = m_w,i, mass[2v+1] = m_n,i (kg): the storage terms of Eqs. (dsW),(dpN) */
 
 /* ---- algebra on the stencil format ---- */
 void rfo_make_A(int nv, int nb, const double* J, const double* mdiag, double shift, double* A);
@@ -93,5 +106,21 @@ typedef struct {
 typedef struct { double eps, H_new; int accepted, solves, iterations; } rfo_limex_info;
 int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_limex_opts* o,
                    double* u_out, rfo_limex_info* info);
+
+/* ---- implicit Euler + Newton (the comparison scheme of Sec. 6, Case 4) ----
+ * Solves R(u) = F(u) - (m(u) - m(u_old))/H = 0 (storage m of rfo_storage;
+ * Dirichlet p_w rows have no storage) by Newton: (M(u_k)/H - J(u_k)) d = R(u_k),
+ * u_{k+1} = u_k + d, each linear system by BiCGSTAB + GMG to rtol.  Stops when
+ * ||R||_2 <= atol or ||R||_2 <= rtol_newton ||R(u_old)||_2 (Sec. 6: 1e-8 / 1e-6).
+ * Returns 0, or 1 if Newton did not converge in max_newton iterations, or the
+ * linear solver's status; on failure u_out = u_old. */
+typedef struct {
+  double atol, rtol; int max_newton;
+  int nlevels, smoother, nu1, nu2; double omega;
+  double lin_rtol; int lin_maxit;
+} rfo_ie_opts;
+typedef struct { int newton, linear; double res0, res; } rfo_ie_info;
+int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_opts* o, double* u_out,
+                rfo_ie_info* info);
 
 #endif

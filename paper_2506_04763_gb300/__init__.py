@@ -20,6 +20,7 @@ RF_SMOOTH_JACOBI, RF_SMOOTH_GS8 = 0, 1
 RF_PREC_FP64, RF_PREC_FP32, RF_PREC_FP16 = 0, 1, 2
 RF_OP_SPMV, RF_OP_VCYCLE, RF_OP_SMOOTH, RF_OP_RESIDUAL, RF_OP_RESTRICT, RF_OP_PROLONG, RF_OP_COARSE = range(7)
 RF_NOALLOC_MAX_N = 512
+RF_SCHEME_SHAT_STORAGE, RF_SCHEME_DARCY_UPWIND = 1, 2
 PROF_CLASSES = ["spmv64", "smooth_fine", "resid_fine", "transfer", "coarse_levels", "vector"]
 
 
@@ -87,6 +88,16 @@ class rf_limex_opts(ctypes.Structure):
                 ("solve", rf_solve_opts)]
 
 
+class rf_ie_opts(ctypes.Structure):
+    _fields_ = [("atol", ctypes.c_double), ("rtol", ctypes.c_double), ("max_newton", ctypes.c_int),
+                ("gmg", rf_gmg_opts), ("solve", rf_solve_opts)]
+
+
+class rf_ie_info(ctypes.Structure):
+    _fields_ = [("newton", ctypes.c_int), ("linear", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("status", ctypes.c_int)]
+
+
 class rf_limex_info(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("H_new", ctypes.c_double), ("accepted", ctypes.c_int),
                 ("solves", ctypes.c_int), ("iterations", ctypes.c_int), ("status", ctypes.c_int)]
@@ -99,10 +110,12 @@ SIGNATURES = {
     "rf_grid_destroy": (None, [_P]),
     "rf_grid_nv": (_I64, [_P]),
     "rf_assemble": (_I, [_P, _P, _I, _P, _P]),
+    "rf_grid_set_scheme": (_I, [_P, _I]),
     "rf_gmg_setup": (_I, [_P, _P, _I, _P, _P]),
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_limex_step_batched": (_I, [_P, _P, _P, _I, _P, _P, _I, _P]),
+    "rf_ie_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_phase_mass": (_I, [_P, _P, _P, _P]),
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
     "rf_export_level": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -157,6 +170,10 @@ def rf_assemble(grid, u_ptr, want_jacobian, F_ptr, stream):
     _check(lib().rf_assemble(grid, u_ptr, int(want_jacobian), F_ptr, stream))
 
 
+def rf_grid_set_scheme(grid, scheme):
+    _check(lib().rf_grid_set_scheme(grid, int(scheme)))
+
+
 def rf_gmg_setup(grid, shifts, opts, stream):
     arr = (ctypes.c_double * len(shifts))(*[float(s) for s in shifts])
     _check(lib().rf_gmg_setup(grid, arr, len(shifts), ctypes.byref(opts), stream))
@@ -173,6 +190,14 @@ def rf_solve(grid, shift, b_ptr, x_ptr, opts, stream):
 def rf_limex_step(grid, u_ptr, H, opts, stream):
     info = rf_limex_info()
     st = lib().rf_limex_step(grid, u_ptr, float(H), ctypes.byref(opts), ctypes.byref(info), stream)
+    if st not in (RF_OK, RF_ENOTCONV):
+        _check(st)
+    return st, info
+
+
+def rf_ie_step(grid, u_ptr, H, opts, stream):
+    info = rf_ie_info()
+    st = lib().rf_ie_step(grid, u_ptr, float(H), ctypes.byref(opts), ctypes.byref(info), stream)
     if st not in (RF_OK, RF_ENOTCONV):
         _check(st)
     return st, info
@@ -314,6 +339,8 @@ class Grid:
         bc = rf_bc(_ptr(keep["dir"]), _ptr(keep["pw_dir"]), _ptr(keep["q_in"]))
         self._alloc = _torch_allocator() if allocator == "torch" else None
         self.handle = rf_grid_create(desc, fl, mat, bc, self._alloc, self.stream)
+        if int(prob.get("scheme", 0)):
+            self.set_scheme(prob["scheme"])
 
     def close(self):
         if getattr(self, "handle", None):
@@ -330,6 +357,10 @@ class Grid:
     def assemble(self, u, jacobian=True, F=None):
         rf_assemble(self.handle, _ptr(u), jacobian, _ptr(F), self.stream)
         return F
+
+    def set_scheme(self, scheme):
+        """Discretisation variant bits (SCHEME_SHAT_STORAGE, SCHEME_DARCY_UPWIND)."""
+        rf_grid_set_scheme(self.handle, scheme)
 
     def gmg_setup(self, shifts, opts):
         rf_gmg_setup(self.handle, list(shifts), opts, self.stream)
@@ -348,19 +379,35 @@ class Grid:
         return dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted, solves=info.solves,
                     iterations=info.iterations)
 
-    def limex_run(self, u, H0, steps, tol=1e-3, rho=0.75, H_max=None, gmg=None, rtol=1e-10, max_it=200,
-                  outer="fp64", kappa=4, max_rejects=50):
+    def ie_step(self, u, H, atol=1e-8, rtol=1e-6, max_newton=20, gmg=None, lin_rtol=1e-10, max_it=200,
+                outer="fp64"):
+        """One implicit Euler step solved by Newton's method (rf_ie_step)."""
+        gmg = gmg if gmg is not None else gmg_opts(4)
+        o = rf_ie_opts(float(atol), float(rtol), int(max_newton), gmg,
+                       rf_solve_opts(float(lin_rtol), int(max_it), OUTERS.get(outer, outer)))
+        st, info = rf_ie_step(self.handle, _ptr(u), H, o, self.stream)
+        return dict(status=st, newton=info.newton, linear=info.linear, res0=info.res0, res=info.res)
+
+    def limex_run(self, u, H0, steps=None, tol=1e-3, rho=0.75, H_max=None, gmg=None, rtol=1e-10, max_it=200,
+                  outer="fp64", kappa=4, max_rejects=50, t_end=None):
         """Adaptive LIMEX integration (step control of Sec. 4, q = 2): takes
-        `steps` accepted steps from state u (updated in place); a rejected
-        step is retried with the proposed smaller H.  Returns (t, history)."""
-        H, t, hist, rejects = float(H0), 0.0, [], 0
-        while sum(h["accepted"] for h in hist) < steps:
+        `steps` accepted steps, or integrates up to time `t_end` (the last step
+        is shortened to land on it), from state u (updated in place); a
+        rejected step is retried with the proposed smaller H.  Returns
+        (t, history)."""
+        if steps is None and t_end is None:
+            raise ValueError("give steps or t_end")
+        H, t, hist, rejects, acc = float(H0), 0.0, [], 0, 0
+        while (steps is None or acc < steps) and (t_end is None or t < t_end * (1.0 - 1e-12)):
+            if t_end is not None:
+                H = min(H, t_end - t)
             info = self.limex_step(u, H, kappa=kappa, tol=tol, rho=rho, gmg=gmg, rtol=rtol, max_it=max_it,
                                    outer=outer)
             info.update(H=H, t=t)
             hist.append(info)
             if info["accepted"]:
                 t += H
+                acc += 1
             else:
                 rejects += 1
                 if rejects > max_rejects:

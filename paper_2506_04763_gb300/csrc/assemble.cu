@@ -41,6 +41,7 @@ namespace rf {
 struct Phys {
   double rho_w, rho_n, mu_w, mu_n, S_wr, S_nr, lam, den;
   double h[3], g[3];
+  int scheme;   // SCHEME_* bits (0: the discretisation of Sec. 3)
 };
 
 // ---- constitutive laws (Brooks-Corey; J continued linearly outside [0.01, 1])
@@ -193,7 +194,8 @@ __global__ void k_vertex_state(Dims d, Phys ph, const double2* __restrict__ u, c
 struct AsmIn {
   const double2* u;
   const double *Se, *pn, *pc, *dpc, *krw, *dkrw, *pdmin, *phiv;
-  const double *K, *pd;           // per cell (natural cell order)
+  const double *K, *pd, *phi;     // per cell (natural cell order)
+  double vol;                     // cell volume
   const uint8_t* dir;             // parity-split
   const double* pw_dir;           // parity-split
   const double2* q_in;            // parity-split (may be null)
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
   double F0 = 0.0, F1 = 0.0;
   if (in.q_in) { double2 q = in.q_in[p]; F0 = q.x; F1 = q.y; }
   const double neg_inv_den = -1.0 / ph.den;
+  const bool darcy = (ph.scheme & SCHEME_DARCY_UPWIND) != 0;
 
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
     const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
     const double Kc = in.K[cell], pdc = in.pd[cell];
     int64_t vq[NC];
-    double se[NC], pnq[NC], pcq[NC], dpcq[NC];
+    double se[NC], pnq[NC], pcq[NC], dpcq[NC], pwq[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
       vq[q] = pidx(d, ci + (q & 1), cj + ((q >> 1) & 1), DIM == 3 ? ck + ((q >> 2) & 1) : 0);
@@ -235,6 +238,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       pnq[q] = in.pn[vq[q]];
       pcq[q] = in.pc[vq[q]];
       dpcq[q] = in.dpc[vq[q]];
+      pwq[q] = darcy ? in.u[vq[q]].x : 0.0;
     }
 #pragma unroll
     for (int kk = 0; kk < DIM; ++kk) {
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       for (int t = 0; t < DIM - 1; ++t) o[t] = (c >> oth[t]) & 1;
       const int a = c & ~(1 << kk), b = c | (1 << kk);
       const double sgn = ((c >> kk) & 1) ? 1.0 : -1.0;  // this vertex is b: +flux, a: -flux
-      double gpn = 0.0, gpc = 0.0;
+      double gpn = 0.0, gpc = 0.0, gpw = 0.0;
 #pragma unroll
       for (int e2 = 0; e2 < NE; ++e2) {
         int o2[2] = {e2 & 1, (e2 >> 1) & 1};
@@ -266,9 +270,11 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
         const int b2 = a2 | (1 << kk);
         gpn = __dadd_rn(gpn, __dmul_rn(w, __dsub_rn(pnq[b2], pnq[a2])));
         gpc = __dadd_rn(gpc, __dmul_rn(w, __dsub_rn(pcq[b2], pcq[a2])));
+        if (darcy) gpw = __dadd_rn(gpw, __dmul_rn(w, __dsub_rn(pwq[b2], pwq[a2])));
       }
       gpn = __ddiv_rn(gpn, ph.h[kk]);
       gpc = __ddiv_rn(gpc, ph.h[kk]);
+      gpw = __ddiv_rn(gpw, ph.h[kk]);
       double wM[NC], SeM = 0.0;
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
@@ -281,7 +287,10 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       const double Tw = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_w, ph.g[kk])));
       const double Tn = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_n, ph.g[kk])));
       const double Tc = __dmul_rn(-KA, gpc);
-      const bool wa = Tw >= 0.0, na = Tn >= 0.0;
+      // Darcy-velocity upwinding variant: the whole water flux by the sign of
+      // T_pw = -K A_f (G(p_w) - rho_w g_k) (= T_w - T_c in exact arithmetic)
+      const double Tpw = __dmul_rn(-KA, __dsub_rn(gpw, __dmul_rn(ph.rho_w, ph.g[kk])));
+      const bool wa = darcy ? Tpw >= 0.0 : Tw >= 0.0, na = Tn >= 0.0;
       const int64_t vw = wa ? vq[a] : vq[b];
       const int64_t vn = na ? vq[a] : vq[b];
       const double lw_up = in.krw[vw] / ph.mu_w;
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       shat_of(ph.lam, in.Se[vn], pdc, in.pdmin[vn], sh, dsh);
       krn_of(ph.lam, sh, kn, dkn);
       const double ln_up = kn / ph.mu_n;
-      const double Fw = ph.rho_w * (lw_up * Tw - lwM * Tc);
+      const double Fw = darcy ? ph.rho_w * (lw_up * Tpw) : ph.rho_w * (lw_up * Tw - lwM * Tc);
       const double Fn = ph.rho_n * (ln_up * Tn);
       F0 += sgn * Fw;
       F1 += sgn * Fn;
@@ -310,8 +319,9 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
           const double dT = -KA * gq;
           const double dlwM = wM[q] * dlwM_dSeM * neg_inv_den;
           const double d0 = ph.rho_w * lw_up * dT;
-          const double d1 = ph.rho_w * ((q == qw ? dlw_up * Tw : 0.0) + lw_up * dT * dpcq[q] - dlwM * Tc -
-                                        lwM * dT * dpcq[q]);
+          const double d1 = darcy ? ph.rho_w * (q == qw ? dlw_up * Tpw : 0.0)
+                                  : ph.rho_w * ((q == qw ? dlw_up * Tw : 0.0) + lw_up * dT * dpcq[q] - dlwM * Tc -
+                                                lwM * dT * dpcq[q]);
           const double d2 = ph.rho_n * ln_up * dT;
           const double d3 = ph.rho_n * ((q == qn ? dln_up * Tn : 0.0) + ln_up * dT * dpcq[q]);
           const int dx = (q & 1) - (c & 1), dy = ((q >> 1) & 1) - ((c >> 1) & 1),
@@ -330,7 +340,20 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
   if (dirv) F0 = in.pw_dir[p] - in.u[p].x;
   F[p] = make_double2(F0, F1);
   if (WANT_J) {
-    const double pv = in.phiv[p];
+    double pv = in.phiv[p];
+    if (ph.scheme & SCHEME_SHAT_STORAGE) {
+      // S hat storage: d m_n / d S_n = rho_n sum_j Phi_j |b_i^j| d S hat_e / d S_e
+      const double frac = DIM == 3 ? 0.125 : 0.25, se = in.Se[p], pdm = in.pdmin[p];
+      pv = 0.0;
+      for (int c = 0; c < NC; ++c) {
+        const int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = DIM == 3 ? k - ((c >> 2) & 1) : 0;
+        if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+        const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+        double sh, dsh;
+        shat_of(ph.lam, se, in.pd[cell], pdm, sh, dsh);
+        pv += in.phi[cell] * in.vol * frac * dsh;
+      }
+    }
     mdiag[p] = make_double2(dirv ? 0.0 : -ph.rho_w * pv, ph.rho_n * pv);
     const int centre = DIM == 3 ? 13 : 4;
 #pragma unroll 3
@@ -343,6 +366,31 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       dst[1] = make_double2(e2, e3);
     }
   }
+}
+
+// ---------------------------------------------------------------- storage (S hat variant)
+// sw[p] = sum over the sub-control volumes b_i^j of vertex p of Phi_j |b_i^j|
+// S_w(b_i^j), with S_w = S_wr + S hat_e (1 - S_wr - S_nr) (Eq. (hSw)).
+__global__ void k_storage_sw(Dims d, Phys ph, const double2* __restrict__ u, const double* __restrict__ pdmin,
+                             const double* __restrict__ phi, const double* __restrict__ pd, double vol,
+                             double* __restrict__ sw) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= d.nv) return;
+  int i, j, k;
+  pcoords(d, p, i, j, k);
+  const int cx = d.nx - 1, cy = d.ny - 1, cz = d.dim == 3 ? d.nz - 1 : 1;
+  const double frac = d.dim == 3 ? 0.125 : 0.25;
+  const double se = __ddiv_rn(__dsub_rn(__dsub_rn(1.0, u[p].y), ph.S_wr), ph.den), pdm = pdmin[p];
+  double s = 0.0;
+  for (int c = 0; c < (1 << d.dim); ++c) {
+    const int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = d.dim == 3 ? k - ((c >> 2) & 1) : 0;
+    if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+    const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+    double sh, dsh;
+    shat_of(ph.lam, se, pd[cell], pdm, sh, dsh);
+    s += phi[cell] * vol * frac * (ph.S_wr + sh * ph.den);
+  }
+  sw[p] = s;
 }
 
 // ---------------------------------------------------------------- launchers
@@ -369,13 +417,15 @@ cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays
   ph.rho_w = pp.rho_w; ph.rho_n = pp.rho_n; ph.mu_w = pp.mu_w; ph.mu_n = pp.mu_n;
   ph.S_wr = pp.S_wr; ph.S_nr = pp.S_nr; ph.lam = pp.lambda;
   ph.den = 1.0 - pp.S_wr - pp.S_nr;
+  ph.scheme = pp.scheme;
   for (int t = 0; t < 3; ++t) { ph.h[t] = pp.h[t]; ph.g[t] = pp.g[t]; }
   const int nblk = (int)((d.nv + 255) / 256);
   RF_LAUNCH(k_vertex_state, nblk, 256, 0, s, d, ph, (const double2*)a.u, a.pdmin, a.Se, a.pn, a.pc, a.dpc,
             a.krw, a.dkrw);
   AsmIn in;
   in.u = (const double2*)a.u; in.Se = a.Se; in.pn = a.pn; in.pc = a.pc; in.dpc = a.dpc; in.krw = a.krw;
-  in.dkrw = a.dkrw; in.pdmin = a.pdmin; in.phiv = a.phiv; in.K = a.K; in.pd = a.pd; in.dir = a.dir;
+  in.dkrw = a.dkrw; in.pdmin = a.pdmin; in.phiv = a.phiv; in.K = a.K; in.pd = a.pd; in.phi = a.phi;
+  in.vol = a.vol; in.dir = a.dir;
   in.pw_dir = a.pw_dir; in.q_in = (const double2*)a.q_in;
   const int BS = 128;
   const int grid = (int)((d.nv + BS - 1) / BS);
@@ -397,6 +447,17 @@ cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays
     }
   }
   return cudaGetLastError();
+}
+
+void launch_storage_sw(const Dims& d, const PhysParams& pp, const double* u, const double* pdmin,
+                       const double* phi, const double* pd, double vol, double* sw, void* s) {
+  Phys ph;
+  ph.rho_w = pp.rho_w; ph.rho_n = pp.rho_n; ph.mu_w = pp.mu_w; ph.mu_n = pp.mu_n;
+  ph.S_wr = pp.S_wr; ph.S_nr = pp.S_nr; ph.lam = pp.lambda;
+  ph.den = 1.0 - pp.S_wr - pp.S_nr;
+  ph.scheme = pp.scheme;
+  for (int t = 0; t < 3; ++t) { ph.h[t] = pp.h[t]; ph.g[t] = pp.g[t]; }
+  RF_LAUNCH(k_storage_sw, (int)((d.nv + 255) / 256), 256, 0, s, d, ph, (const double2*)u, pdmin, phi, pd, vol, sw);
 }
 
 }  // namespace rf

@@ -73,8 +73,27 @@ struct Level {
   float* scale[RF_MAXSHIFT] = {};
   void* Dinv[RF_MAXSHIFT] = {};
   void *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
-  int block = 256;   // threads per block of the smoothing / residual kernels
+  // Shape of the smoothing / residual kernels (default_shape; the autotuner
+  // may change it): threads per block, and whether a thread issues its
+  // stencil loads 9 blocks per memory round trip.
+  int block = 128;
+  bool batched = true;
 };
+
+// Default kernel shape per level, from the autotuner's timings at 257^3 (one
+// sweep + one residual per candidate, GB300):
+//   FP32 storage: batched loads win everywhere — GS 2.62 -> 2.48 ms on the
+//     finest level, about 2x on levels of 65^3 and below (their time is one
+//     thread's chain of round trips), equal at 129^3; Jacobi 2.51 -> 2.27 ms
+//     on the finest level and 0.32 -> 0.29 ms at 129^3.
+//   FP64 storage: equal on the two finest levels, batched 1.2-1.6x faster on
+//     the levels below.
+//   FP16 storage: batched loads are 1.8-2x slower on the two finest levels
+//     and equal below, so never.
+static void default_shape(Level& Lv, int l, int kind) {
+  Lv.block = 128;
+  Lv.batched = kind == STORE_F32 || (kind == STORE_F64 && l >= 2);
+}
 
 struct Alloc {
   void* p;
@@ -92,6 +111,9 @@ struct rf_grid {
   double h[3], g[3];
   int64_t ncell = 0;
   double *Kcell = nullptr, *phi = nullptr, *pd = nullptr;
+  double vol = 0.0;   // cell volume
+  double* ie_old = nullptr;     // implicit Euler: u_old (parity-split pairs), allocated on first use
+  double* ie_swold = nullptr;   // implicit Euler, S hat storage: water pore volume sums of u_old
   uint8_t* dir = nullptr;
   double *pw_dir = nullptr, *q_in = nullptr;
   double *pdmin = nullptr, *phiv = nullptr;
@@ -373,6 +395,7 @@ extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* f
   for (int a = 0; a < 3; ++a) { g->h[a] = desc->h[a]; g->g[a] = desc->g[a]; g->pp.h[a] = desc->h[a]; g->pp.g[a] = desc->g[a]; }
   g->pp.rho_w = fl->rho_w; g->pp.rho_n = fl->rho_n; g->pp.mu_w = fl->mu_w; g->pp.mu_n = fl->mu_n;
   g->pp.S_wr = mat->S_wr; g->pp.S_nr = mat->S_nr; g->pp.lambda = mat->lambda;
+  g->pp.scheme = 0;
   g->ncell = (int64_t)(n[0] - 1) * (n[1] - 1) * (desc->dim == 3 ? n[2] - 1 : 1);
   const Dims& d = g->d;
   const size_t cb = sizeof(double) * g->ncell;
@@ -409,6 +432,7 @@ extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* f
   NEED(g->pdmin = (double*)dalloc(g, sizeof(double) * nv, stream, false));
   NEED(g->phiv = (double*)dalloc(g, sizeof(double) * nv, stream, false));
   const double vol = g->h[0] * g->h[1] * (d.dim == 3 ? g->h[2] : 1.0);
+  g->vol = vol;
   launch_vertex_setup(d, g->pd, g->phi, vol, g->pdmin, g->phiv, stream);
 
   NEED(g->J = (double*)dalloc(g, sizeof(double) * 4 * d.nb * nv, stream, false));
@@ -450,7 +474,8 @@ extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* f
 static rf_status assemble_p(rf_grid* g, bool want_j, void* s) {
   AsmArrays a;
   a.u = g->u_p; a.Se = g->Se; a.pn = g->pn; a.pc = g->pc; a.dpc = g->dpc; a.krw = g->krw; a.dkrw = g->dkrw;
-  a.pdmin = g->pdmin; a.phiv = g->phiv; a.K = g->Kcell; a.pd = g->pd; a.dir = g->dir; a.pw_dir = g->pw_dir;
+  a.pdmin = g->pdmin; a.phiv = g->phiv; a.K = g->Kcell; a.pd = g->pd; a.phi = g->phi; a.vol = g->vol;
+  a.dir = g->dir; a.pw_dir = g->pw_dir;
   a.q_in = g->q_in; a.F = g->F_p; a.J = want_j ? g->J : nullptr; a.mdiag = want_j ? g->mdiag : nullptr;
   cudaError_t e = launch_assemble(g->d, g->pp, a, want_j, s);
   if (e != cudaSuccess) return fail(RF_ECUDA, "assembly launch: %s", cudaGetErrorString(e));
@@ -464,6 +489,16 @@ extern "C" rf_status rf_assemble(rf_grid* g, const double* u, int want_jacobian,
   if (st) return st;
   if ((st = assemble_p(g, want_jacobian != 0, s))) return st;
   if (F_out) return pairs_out(g, g->d, g->F_p, F_out, s);
+  return RF_OK;
+}
+
+static_assert(RF_SCHEME_SHAT_STORAGE == SCHEME_SHAT_STORAGE && RF_SCHEME_DARCY_UPWIND == SCHEME_DARCY_UPWIND,
+              "scheme bits of the C ABI and the kernels agree");
+extern "C" rf_status rf_grid_set_scheme(rf_grid* g, int scheme) {
+  if (!g) return fail(RF_EINVAL, "grid is required");
+  if (scheme & ~(RF_SCHEME_SHAT_STORAGE | RF_SCHEME_DARCY_UPWIND)) return fail(RF_EINVAL, "unknown scheme bits 0x%x", scheme);
+  if (g->pp.scheme != scheme) { g->have_J = false; g->gmg_ready = false; g->jdf_valid = false; }
+  g->pp.scheme = scheme;
   return RF_OK;
 }
 
@@ -485,17 +520,21 @@ static LevelOp level_op(rf_grid* g, int l, int sh) {
   op.Dinv = Lv.Dinv[sh];
   op.dmask = Lv.dmask;
   op.block = Lv.block;
+  op.batched = Lv.batched;
   return op;
 }
 
 // ------------------------------------------------------------------ autotuner
-// Chooses, per level, the thread-block size of the smoothing and residual
-// kernels by timing one sweep plus one residual for each candidate on the
-// level's own data (CUDA events).  Choices are cached per (device, level
+// Chooses, per level, the shape of the smoothing and residual kernels — the
+// thread-block size and whether a thread issues its stencil loads in batches
+// of 9 blocks — by timing one sweep plus one residual for each candidate on
+// the level's own data (CUDA events).  Choices are cached per (device, level
 // dimensions, storage kind, smoother, finest-or-not) for the process and, when
 // RF_TUNE_CACHE names a file, in that file as one JSON object per line.
+// RF_TUNE_VERBOSE=1 prints every candidate's time to stderr.
+struct TuneChoice { int block; bool batched; };
 static std::mutex g_tune_mu;
-static std::map<std::string, int> g_tune;
+static std::map<std::string, TuneChoice> g_tune;
 static bool g_tune_loaded = false;
 
 static std::string tune_key(const Dims& d, int kind, int smoother, bool fine) {
@@ -520,30 +559,37 @@ static void tune_load_locked() {
   if (!f) return;
   char line[512];
   while (fgets(line, sizeof line, f)) {
-    // {"key": "<key>", "block": <n>}
+    // {"key": "<key>", "block": <n>, "batched": <0|1>}
     char* k = strstr(line, "\"key\": \"");
     char* b = strstr(line, "\"block\": ");
+    char* t = strstr(line, "\"batched\": ");
     if (!k || !b) continue;
     k += 8;
     char* e = strchr(k, '"');
     if (!e) continue;
-    g_tune[std::string(k, e - k)] = atoi(b + 9);
+    const int bs = atoi(b + 9);
+    if (bs != 64 && bs != 128 && bs != 256 && bs != 512) continue;
+    const bool bt = t ? atoi(t + 11) != 0 : false;
+    if (bt && bs > 256) continue;
+    g_tune[std::string(k, e - k)] = TuneChoice{bs, bt};
   }
   fclose(f);
 }
 
-static void tune_store_locked(const std::string& key, int block) {
-  g_tune[key] = block;
+static void tune_store_locked(const std::string& key, TuneChoice c) {
+  g_tune[key] = c;
   const char* path = getenv("RF_TUNE_CACHE");
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "{\"key\": \"%s\", \"block\": %d}\n", key.c_str(), block);
+  fprintf(f, "{\"key\": \"%s\", \"block\": %d, \"batched\": %d}\n", key.c_str(), c.block, c.batched ? 1 : 0);
   fclose(f);
 }
 
 static rf_status autotune_levels(rf_grid* g, void* s) {
-  static const int cand[4] = {64, 128, 256, 512};
+  static const TuneChoice cand[7] = {{64, false}, {128, false}, {256, false}, {512, false},
+                                     {64, true}, {128, true}, {256, true}};
+  const bool verbose = getenv("RF_TUNE_VERBOSE") && atoi(getenv("RF_TUNE_VERBOSE")) > 0;
   const int last = g->nl - 1;   // the coarsest level is a dense solve
   for (int l = 0; l < last; ++l) {
     Level& Lv = g->L[l];
@@ -552,15 +598,16 @@ static rf_status autotune_levels(rf_grid* g, void* s) {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       tune_load_locked();
       auto it = g_tune.find(key);
-      if (it != g_tune.end()) { Lv.block = it->second; continue; }
+      if (it != g_tune.end()) { Lv.block = it->second.block; Lv.batched = it->second.batched; continue; }
     }
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_bs = 256;
-    for (int c = 0; c < 4; ++c) {
-      Lv.block = cand[c];
+    TuneChoice best_c{256, false};
+    for (int c = 0; c < 7; ++c) {
+      Lv.block = cand[c].block;
+      Lv.batched = cand[c].batched;
       LevelOp op = level_op(g, l, 0);
       float tmin = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
@@ -574,13 +621,17 @@ static rf_status autotune_levels(rf_grid* g, void* s) {
         CU(cudaEventElapsedTime(&ms, e0, e1));
         if (rep > 0 && ms < tmin) tmin = ms;   // first repetition warms up
       }
-      if (tmin < best) { best = tmin; best_bs = cand[c]; }
+      if (verbose)
+        fprintf(stderr, "rf autotune %s: block %d batched %d: %.4f ms\n", key.c_str(), cand[c].block,
+                cand[c].batched ? 1 : 0, tmin);
+      if (tmin < best) { best = tmin; best_c = cand[c]; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    Lv.block = best_bs;
+    Lv.block = best_c.block;
+    Lv.batched = best_c.batched;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    tune_store_locked(key, best_bs);
+    tune_store_locked(key, best_c);
   }
   return RF_OK;
 }
@@ -680,6 +731,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
   for (int l = 0; l < g->nl; ++l) {
     Level& Lv = g->L[l];
     Lv.nb = make_nbr(Lv.d);
+    default_shape(Lv, l, kind);
     const Dims& d = Lv.d;
     if (l == 0) {
       Lv.dmask = g->dir;
@@ -1199,11 +1251,73 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
   return worst;
 }
 
+// ------------------------------------------------------------------ implicit Euler
+extern "C" rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opts* o, rf_ie_info* info, void* s) {
+  if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
+  if (!(H > 0.0) || !std::isfinite(H)) return fail(RF_EINVAL, "H must be positive");
+  if (!(o->atol >= 0.0) || !(o->rtol >= 0.0) || o->max_newton < 1) return fail(RF_EINVAL, "bad Newton parameters");
+  const Dims& d = g->d;
+  const size_t vb = sizeof(double) * 2 * d.nv;
+  const bool shat = (g->pp.scheme & SCHEME_SHAT_STORAGE) != 0;
+  if (!g->ie_old) {
+    g->ie_old = (double*)dalloc(g, vb, s, false);
+    if (!g->ie_old) return fail(RF_ENOMEM, "implicit Euler state allocation failed");
+  }
+  if (shat && !g->ie_swold) {
+    g->ie_swold = (double*)dalloc(g, sizeof(double) * d.nv, s, false);
+    if (!g->ie_swold) return fail(RF_ENOMEM, "implicit Euler storage allocation failed");
+  }
+  rf_status st = pairs_in(g, d, u, g->u_p, s);
+  if (st) return st;
+  CU(cudaMemcpyAsync(g->ie_old, g->u_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  if (shat) launch_storage_sw(d, g->pp, g->ie_old, g->pdmin, g->phi, g->pd, g->vol, g->ie_swold, s);
+  const double shift = 1.0 / H;
+  int newton = 0, linear = 0;
+  double r0 = 0.0, r = 0.0;
+  rf_status res = RF_OK;
+  for (;;) {
+    if ((st = assemble_p(g, true, s))) return st;   // F, J, M at the iterate
+    const double* sw = nullptr;
+    if (shat) {
+      launch_storage_sw(d, g->pp, g->u_p, g->pdmin, g->phi, g->pd, g->vol, g->pn, s);   // pn: assembly scratch
+      sw = g->pn;
+    }
+    launch_ie_residual(d.nv, g->F_p, g->u_p, g->ie_old, g->mdiag, sw, g->ie_swold, g->dir, g->pp.rho_w,
+                       g->pp.rho_n, shift, (double*)g->b_p, g->norms, g->K.partial, s);
+    double r2 = 0.0;
+    CU(cudaMemcpyAsync(&r2, g->norms, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaStreamSynchronize((cudaStream_t)s));
+    if (!std::isfinite(r2)) { res = fail(RF_ENONFINITE, "implicit Euler residual is not finite"); break; }
+    r = std::sqrt(r2);
+    if (newton == 0) r0 = r;
+    if (r <= o->atol || r <= o->rtol * r0) break;
+    if (newton >= o->max_newton) { res = RF_ENOTCONV; break; }
+    if ((st = rf_gmg_setup(g, &shift, 1, &o->gmg, s))) return st;
+    rf_solve_info si{};
+    rf_status ls = solve_p(g, 0, g->b_p, o->solve.rtol, o->solve.max_it, o->solve.outer, &si, s);
+    linear += si.iterations;
+    ++newton;
+    if (ls != RF_OK) { res = ls; break; }
+    launch_axpy_pairs(d.nv, (double2*)g->u_p, g->K.x, s);
+  }
+  if (info) { info->newton = newton; info->linear = linear; info->res0 = r0; info->res = r; info->status = res; }
+  if (res != RF_OK) {
+    if (res == RF_ENOTCONV) return fail(res, "Newton did not converge in %d iterations (|R| %.3e of %.3e)", newton, r, r0);
+    return res;
+  }
+  return pairs_out(g, d, g->u_p, u, s);
+}
+
 extern "C" rf_status rf_phase_mass(rf_grid* g, const double* u, double* mass_out, void* s) {
   if (!g || !u || !mass_out) return fail(RF_EINVAL, "grid, u and mass_out are required");
   rf_status st = pairs_in(g, g->d, u, g->u_p, s);
   if (st) return st;
-  launch_phase_mass(g->d.nv, g->pp.rho_w, g->pp.rho_n, g->phiv, g->u_p, g->norms, g->K.partial, s);
+  const double* sw = nullptr;
+  if (g->pp.scheme & SCHEME_SHAT_STORAGE) {
+    launch_storage_sw(g->d, g->pp, g->u_p, g->pdmin, g->phi, g->pd, g->vol, g->Se, s);   // Se: scratch
+    sw = g->Se;
+  }
+  launch_phase_mass(g->d.nv, g->pp.rho_w, g->pp.rho_n, g->phiv, g->u_p, sw, g->norms, g->K.partial, s);
   CU(cudaMemcpyAsync(mass_out, g->norms, sizeof(double) * 2, cudaMemcpyDeviceToHost, (cudaStream_t)s));
   CU(cudaStreamSynchronize((cudaStream_t)s));
   return RF_OK;

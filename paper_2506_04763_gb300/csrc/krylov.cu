@@ -498,6 +498,55 @@ void launch_axpy_pairs(int64_t nv, double2* u, const double2* du, void* s) {
   RF_LAUNCH(k_axpy_pairs, krylov_blocks(nv), BS, 0, s, nv, u, du);
 }
 
+// ----------------------------------------------------------------- implicit Euler
+// Newton residual of one implicit Euler step: R = F(u) - (m(u) - m(u_old))/H.
+// Linear storage: m(u) - m(u_old) = M (S_n - S_n,old) exactly (M = mdiag,
+// zero in Dirichlet p_w rows).  S hat storage (sw, sw_old given): the water
+// pore volume sums give dm_w = rho_w (sw - sw_old), dm_n = -rho_n (sw - sw_old),
+// and Dirichlet p_w rows take no storage.  Also sums ||R||^2 (block partials).
+__global__ void __launch_bounds__(BS) k_ie_residual(int64_t nv, const double2* __restrict__ F,
+                                                    const double2* __restrict__ u, const double2* __restrict__ u_old,
+                                                    const double2* __restrict__ mdiag, const double* __restrict__ sw,
+                                                    const double* __restrict__ sw_old, const uint8_t* __restrict__ dir,
+                                                    double rho_w, double rho_n, double inv_h, double2* __restrict__ R,
+                                                    double* __restrict__ partial) {
+  double acc[1] = {0.0};
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < nv; p += (int64_t)gridDim.x * BS) {
+    const double2 f = F[p];
+    double dw, dn;
+    if (sw) {
+      const double dsw = sw[p] - sw_old[p];
+      dw = dir[p] ? 0.0 : rho_w * dsw;
+      dn = -(rho_n * dsw);
+    } else {
+      const double2 m = mdiag[p];
+      const double ds = u[p].y - u_old[p].y;
+      dw = m.x * ds;
+      dn = m.y * ds;
+    }
+    double2 r;
+    r.x = f.x - dw * inv_h;
+    r.y = f.y - dn * inv_h;
+    R[p] = r;
+    acc[0] += r.x * r.x + r.y * r.y;
+  }
+  block_reduce_store<1>(acc, partial);
+}
+
+__global__ void k_sum1(int nblk, const double* __restrict__ partial, double* __restrict__ out) {
+  const double t = sum_partials(partial, 0, nblk);
+  if (threadIdx.x == 0) out[0] = t;
+}
+
+void launch_ie_residual(int64_t nv, const double* F, const double* u, const double* u_old, const double* mdiag,
+                        const double* sw, const double* sw_old, const uint8_t* dir, double rho_w, double rho_n,
+                        double inv_h, double* R, double* out1, double* partial, void* s) {
+  const int g = krylov_blocks(nv);
+  RF_LAUNCH(k_ie_residual, g, BS, 0, s, nv, (const double2*)F, (const double2*)u, (const double2*)u_old,
+            (const double2*)mdiag, sw, sw_old, dir, rho_w, rho_n, inv_h, (double2*)R, partial);
+  RF_LAUNCH(k_sum1, 1, 32, 0, s, g, partial, out1);
+}
+
 // ----------------------------------------------------------------- LIMEX
 // Aitken-Neville on the kappa column results T[j][q] (j = 0..kappa-1, n_j =
 // j+1), element by element; T[0] <- T_kk, T[1] <- T_{k,k-1}.
@@ -582,12 +631,19 @@ __global__ void __launch_bounds__(BS) k_error_norms(Dims d, double h0, double h1
 // (1 - S_n,i) and sum_i rho_n (Phi V)_i S_n,i; slots 0 and 1 of `partial`.
 __global__ void __launch_bounds__(BS) k_phase_mass(int64_t nv, double rho_w, double rho_n,
                                                    const double* __restrict__ phiv, const double2* __restrict__ u,
-                                                   double* __restrict__ partial) {
+                                                   const double* __restrict__ sw, double* __restrict__ partial) {
   double acc[2] = {0.0, 0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < nv; p += (int64_t)gridDim.x * BS) {
-    const double pv = phiv[p], sn = u[p].y;
-    acc[0] += rho_w * pv * (1.0 - sn);
-    acc[1] += rho_n * pv * sn;
+    const double pv = phiv[p];
+    if (sw) {
+      const double w = sw[p];
+      acc[0] += rho_w * w;
+      acc[1] += rho_n * (pv - w);
+    } else {
+      const double sn = u[p].y;
+      acc[0] += rho_w * (pv * (1.0 - sn));
+      acc[1] += rho_n * (pv * sn);
+    }
   }
   block_reduce_store<2>(acc, partial);
 }
@@ -599,10 +655,10 @@ __global__ void k_sum2(int nblk, const double* __restrict__ partial, double* __r
   }
 }
 
-void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, double* out2,
-                       double* partial, void* s) {
+void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, const double* sw,
+                       double* out2, double* partial, void* s) {
   const int g = krylov_blocks(nv);
-  RF_LAUNCH(k_phase_mass, g, BS, 0, s, nv, rho_w, rho_n, phiv, (const double2*)u, partial);
+  RF_LAUNCH(k_phase_mass, g, BS, 0, s, nv, rho_w, rho_n, phiv, (const double2*)u, sw, partial);
   RF_LAUNCH(k_sum2, 1, 32, 0, s, g, partial, out2);
 }
 

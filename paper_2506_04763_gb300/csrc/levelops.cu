@@ -88,13 +88,73 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
   s0 = a0; s1 = a1;
 }
 
+// stencil_sum with the loads of CH blocks (and their x values) issued before
+// any is used: one memory round trip per CH blocks instead of one per block.
+// The block loads are the `volatile` streaming loads of load_block, which the
+// compiler keeps in source order, so placing all CH of them ahead of the sums
+// is what batches them (ordinary loads get sunk back next to their uses).
+// Skipped blocks contribute exact zeros, so the sums equal stencil_sum's.
+// This is what the small levels need, where a thread's chain of round trips,
+// not bandwidth, sets the time.
+template <int KIND, int NB, int CH>
+__device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p, int par,
+                                                    const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                                    bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
+                                                    typename Ty<KIND>::T& s1) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  constexpr int C = NB == 27 ? 13 : 4;
+  float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (KIND == STORE_F16) sc = reinterpret_cast<const float4*>(L.scale)[p];
+  T a0 = 0, a1 = 0;
+#pragma unroll
+  for (int b0 = 0; b0 < NB; b0 += CH) {
+    T a[CH][4];
+    V xv[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int b = b0 + c;
+      if (b >= NB) break;
+      const bool skip = (skip_centre && b == C) || ((skipmask >> b) & 1u);
+      if (!skip) {
+        load_block<KIND>(L.A, L.d.nv, b, p, sc, a[c]);
+        xv[c] = x[p + (par ? L.nb.off[1][b] : L.nb.off[0][b])];
+      } else {
+        a[c][0] = a[c][1] = a[c][2] = a[c][3] = 0;
+        xv[c].x = 0;
+        xv[c].y = 0;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      if (b0 + c >= NB) break;
+      a0 += a[c][0] * xv[c].x + a[c][1] * xv[c].y;
+      a1 += a[c][2] * xv[c].x + a[c][3] * xv[c].y;
+    }
+  }
+  s0 = a0; s1 = a1;
+}
+
+template <int KIND, int NB, int CH>
+__device__ __forceinline__ void stencil_sum_any(const LevelOp& L, int64_t p, int par,
+                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                                bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
+                                                typename Ty<KIND>::T& s1) {
+  if (CH > 0) stencil_sum_batched<KIND, NB, (CH > 0 ? CH : 1)>(L, p, par, x, skip_centre, skipmask, s0, s1);
+  else stencil_sum<KIND, NB>(L, p, par, x, skip_centre, skipmask, s0, s1);
+}
+
 // (A x)_p, with A = shift*M - J on the fine level (blocks hold J)
-template <int KIND, bool FINE, int NB>
+template <int KIND, bool FINE, int NB, int CH = 0>
 __device__ __forceinline__ void apply_row(const LevelOp& L, int64_t p, int par,
                                           const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                           typename Ty<KIND>::T& s0, typename Ty<KIND>::T& s1) {
   typedef typename Ty<KIND>::T T;
-  stencil_sum<KIND, NB>(L, p, par, x, false, 0u, s0, s1);
+  // batched: the mask is L.nomask (always zero) read at run time, which keeps
+  // each block's load in its own conditional branch and so stops the compiler
+  // from interleaving the batch's loads with the sums (it does that with a
+  // constant zero mask, and the batch is lost)
+  stencil_sum_any<KIND, NB, CH>(L, p, par, x, false, CH > 0 ? L.nomask : 0u, s0, s1);
   if (FINE) {
     const double2 m = reinterpret_cast<const double2*>(L.mdiag)[p];
     const T xs = x[p].y, sh = (T)L.shift;
@@ -111,32 +171,32 @@ __device__ __forceinline__ void dinv_apply(const T* Dinv, int64_t p, T r0, T r1,
 }
 
 // ----------------------------------------------------------------- residual
-template <int KIND, bool FINE, int NB>
+template <int KIND, bool FINE, int NB, int CH = 0>
 __device__ __forceinline__ void residual_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                typename V2<typename Ty<KIND>::T>::t* __restrict__ r, int64_t p) {
   typedef typename Ty<KIND>::T T;
   const int par = (int)(p % L.d.nx) >= L.d.E;
-  T s0, s1;
-  apply_row<KIND, FINE, NB>(L, p, par, x, s0, s1);
   const typename V2<T>::t bv = b[p];
+  T s0, s1;
+  apply_row<KIND, FINE, NB, CH>(L, p, par, x, s0, s1);
   typename V2<T>::t o;
   o.x = bv.x - s0;
   o.y = bv.y - s1;
   r[p] = o;
 }
 
-template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(512) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                   const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= L.d.nv) return;
-  residual_point<KIND, FINE, NB>(L, b, x, r, p);
+  residual_point<KIND, FINE, NB, CH>(L, b, x, r, p);
 }
 
 // ----------------------------------------------------------------- Jacobi
-template <int KIND, bool FINE, int NB>
+template <int KIND, bool FINE, int NB, int CH = 0>
 __device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                              const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
                                              typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
@@ -147,7 +207,7 @@ __device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2
   if (!zero_x) {
     const int par = (int)(p % L.d.nx) >= L.d.E;
     T s0, s1;
-    apply_row<KIND, FINE, NB>(L, p, par, xin, s0, s1);
+    apply_row<KIND, FINE, NB, CH>(L, p, par, xin, s0, s1);
     r0 -= s0;
     r1 -= s1;
     x0 = xin[p].x;
@@ -161,20 +221,20 @@ __device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2
   xout[p] = o;
 }
 
-template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(512) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_jacobi(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                 const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
                                                 typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
                                                 int zero_x) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= L.d.nv) return;
-  jacobi_point<KIND, FINE, NB>(L, b, xin, xout, omega, zero_x, p);
+  jacobi_point<KIND, FINE, NB, CH>(L, b, xin, xout, omega, zero_x, p);
 }
 
 // ----------------------------------------------------------------- multicolour GS
 // One colour (px,py,pz) of the sweep: x_p <- D_p^-1 (b_p - sum_{q != p} A_pq x_q).
 // Work item t of the colour: t enumerates the colour's x-runs line by line.
-template <int KIND, bool FINE, int NB>
+template <int KIND, bool FINE, int NB, int CH = 0>
 __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                          typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py, int pz,
                                          int cnt_x, int lines_y, int64_t t, uint32_t skipmask) {
@@ -184,9 +244,9 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
   const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
-  T s0, s1;
-  stencil_sum<KIND, NB>(L, p, px, x, true, skipmask, s0, s1);
   const typename V2<T>::t bv = b[p];
+  T s0, s1;
+  stencil_sum_any<KIND, NB, CH>(L, p, px, x, true, skipmask, s0, s1);
   // off-diagonal part of A: fine level A_pq = -J_pq (q != p), coarse A_pq
   const T r0 = FINE ? bv.x + s0 : bv.x - s0;
   const T r1 = FINE ? bv.y + s1 : bv.y - s1;
@@ -198,13 +258,13 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
   x[p] = o;
 }
 
-template <int KIND, bool FINE, int NB>
-__global__ void __launch_bounds__(512) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                    typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
                                                    int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
-  gs_point<KIND, FINE, NB>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
+  gs_point<KIND, FINE, NB, CH>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
 }
 
 // ----------------------------------------------------------------- transfers
@@ -791,10 +851,15 @@ static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, 
   typedef typename V2<typename Ty<KIND>::T>::t V;
   const int bs = L.block > 0 ? L.block : 256;
   const int g = (int)((L.d.nv + bs - 1) / bs);
-  if (L.d.nb == 27)
-    RF_LAUNCH((k_residual<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+  if (L.batched) {
+    if (L.d.nb == 27)
+      RF_LAUNCH((k_residual<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    else
+      RF_LAUNCH((k_residual<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+  } else if (L.d.nb == 27)
+    RF_LAUNCH((k_residual<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   else
-    RF_LAUNCH((k_residual<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    RF_LAUNCH((k_residual<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
 }
 
 template <int KIND, bool FINE>
@@ -803,10 +868,15 @@ static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xou
   typedef typename V2<typename Ty<KIND>::T>::t V;
   const int bs = L.block > 0 ? L.block : 256;
   const int g = (int)((L.d.nv + bs - 1) / bs);
-  if (L.d.nb == 27)
-    RF_LAUNCH((k_jacobi<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+  if (L.batched) {
+    if (L.d.nb == 27)
+      RF_LAUNCH((k_jacobi<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    else
+      RF_LAUNCH((k_jacobi<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+  } else if (L.d.nb == 27)
+    RF_LAUNCH((k_jacobi<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   else
-    RF_LAUNCH((k_jacobi<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    RF_LAUNCH((k_jacobi<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
 }
 
 // First forward sweep from x = 0: the neighbours of colour c that have a
@@ -837,10 +907,15 @@ static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool ze
     if (count == 0) continue;
     const int bs = L.block > 0 ? L.block : 256;
     const int g = (int)((count + bs - 1) / bs);
-    if (L.d.nb == 27)
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 27>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+    if (L.batched) {
+      if (L.d.nb == 27)
+        RF_LAUNCH((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      else
+        RF_LAUNCH((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+    } else if (L.d.nb == 27)
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
     else
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH((k_gs_colour<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
   }
 }
 

@@ -7,16 +7,21 @@
 
 namespace rf {
 
+// discretisation variants (bits of PhysParams::scheme)
+enum { SCHEME_SHAT_STORAGE = 1, SCHEME_DARCY_UPWIND = 2 };
+
 struct PhysParams {
   double rho_w, rho_n, mu_w, mu_n, S_wr, S_nr, lambda;
   double h[3], g[3];
+  int scheme;
 };
 
 struct AsmArrays {
   const double* u;                 // [2nv] parity-split
   double *Se, *pn, *pc, *dpc, *krw, *dkrw;  // [nv] scratch
   const double *pdmin, *phiv;      // [nv]
-  const double *K, *pd;            // per cell
+  const double *K, *pd, *phi;      // per cell
+  double vol;                      // cell volume
   const uint8_t* dir;              // [nv]
   const double* pw_dir;            // [nv]
   const double* q_in;              // [2nv] or null
@@ -33,6 +38,9 @@ void launch_perm_from_p(const Dims& d, const double* pl, double* nat, void* s);
 void launch_perm_bytes_to_p(const Dims& d, const uint8_t* nat, uint8_t* out, void* s);
 void launch_perm_scalar_to_p(const Dims& d, const double* nat, double* out, void* s);
 cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays& a, bool want_j, void* s);
+// S hat storage variant: sw[p] = sum over the sub-control volumes of p of Phi |b| S_w (S hat)
+void launch_storage_sw(const Dims& d, const PhysParams& pp, const double* u, const double* pdmin,
+                       const double* phi, const double* pd, double vol, double* sw, void* s);
 
 // ---- multigrid level operators (levelops.cu) ----
 enum StoreKind { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2 };
@@ -51,6 +59,8 @@ struct LevelOp {
   const void* Dinv;      // [nv][4] inverse diagonal blocks (T)
   const uint8_t* dmask;  // [nv]
   int block = 256;       // threads per block of the smoothing / residual kernels (autotuned)
+  bool batched = false;  // smoothing / residual kernels issue 9 blocks' loads per round trip
+  uint32_t nomask = 0;   // always 0: a stencil skip mask the compiler cannot fold (see apply_row)
 };
 
 // Vectors are T2 pointers to the first interior element of padded buffers.
@@ -134,8 +144,15 @@ void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const d
 void launch_restart(int64_t nv, KrylovVecs& K, void* s);
 void launch_axpy_pairs(int64_t nv, double2* u, const double2* du, void* s);
 
-void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, double* out2,
-                       double* partial, void* s);
+// sw (may be null): per-vertex water pore volume sum Phi |b| S_w; null: phiv (1 - S_n)
+void launch_phase_mass(int64_t nv, double rho_w, double rho_n, const double* phiv, const double* u, const double* sw,
+                       double* out2, double* partial, void* s);
+
+// implicit Euler Newton residual R = F - (m(u) - m(u_old))/H (sw, sw_old: S hat storage, else null)
+// and ||R||^2 into out1[0]
+void launch_ie_residual(int64_t nv, const double* F, const double* u, const double* u_old, const double* mdiag,
+                        const double* sw, const double* sw_old, const uint8_t* dir, double rho_w, double rho_n,
+                        double inv_h, double* R, double* out1, double* partial, void* s);
 
 // ---- LIMEX (krylov.cu) ----
 void launch_extrapolate(int64_t n2, int kappa, double* T, void* s);

@@ -252,3 +252,98 @@ def random_problem(dim, nvert, seed, stress=False, dirichlet=True, gravity=True)
         prob["g"] = (0.0, 0.0, 0.0)
     prob.update(name="random-%dd-%s-seed%d" % (dim, "x".join(map(str, n[:dim])), seed), H=10.0)
     return prob
+
+
+# The layered Case-4 analogue (Sec. 6, Table case4): four horizontal layers,
+# a light NAPL injected into the bottom layer at 0.05 pore volumes per year.
+CASE4 = dict(K=(1e-13, 1e-12, 8e-13, 7e-13), phi=0.1, rho_w=1000.0, rho_n=700.0, mu_w=1e-3, mu_n=5.654e-5,
+             S_wr=0.2, S_nr=0.1, lam=2.0, p_bottom=5e7, rate_pv_per_year=0.05)
+YEAR = 365.0 * 86400.0
+
+
+def case4_analogue(nverts=(129, 65), injecting=True):
+    """2D unit square (R3) standing in for Case 4's 500 m x 200 m section: four
+    equal layers stacked in y (bottom first) with Case 4's permeabilities,
+    p_d = 7.37 K^-0.43 Pa, Phi = 0.1 and its fluids and residual saturations,
+    under this model's Brooks-Corey laws (Case 4's own k_r tables are not part
+    of the model).  The state starts at S_w = 1 - S_nr (S_n = S_nr, immobile)
+    with p_w hydrostatic from p_n = 5e7 Pa at the bottom, and p_w is held there
+    (Dirichlet on the bottom row; Case 4 fixes p_n and S_w on that face).  NAPL
+    enters through the vertices of the bottom layer's centre line with
+    |x - 0.5| <= 0.05 at 0.05 pore volumes per year (mass rate rho_n Phi |Omega|
+    0.05 / year, unit thickness) when `injecting`."""
+    c = CASE4
+    dim = 2
+    n, h, _ = grid(dim, nverts)
+    nc = ncells(dim, n)
+    jc = (np.arange(nc) // (n[0] - 1))
+    yc = (jc + 0.5) * h[1]
+    layer = np.minimum((yc * 4).astype(int), 3)
+    K = np.asarray(c["K"])[layer]
+    pd = 7.37 * K ** -0.43
+    phi = np.full(nc, c["phi"])
+    x, y, _ = _coords(dim, n, h)
+    nv = x.size
+    bottom = np.rint(y / h[1]).astype(int) == 0
+    # S_e = 1 everywhere: p_c = p_d of the vertex's lowest-entry-pressure cell
+    # (the p_dmin of the interface condition), so p_w = p_n - p_c at the bottom
+    pd_bottom = pd[layer == 0].max()
+    pw = (c["p_bottom"] - pd_bottom) - c["rho_w"] * GRAV * y
+    u = np.empty(2 * nv)
+    u[0::2] = pw
+    u[1::2] = c["S_nr"]
+    dm = bottom.astype(np.uint8)
+    prob = problem(dim, nverts, K, phi, pd, u, dirmask=dm)
+    prob["pw_dir"] = np.where(bottom, pw, 0.0)
+    prob.update(rho_w=c["rho_w"], rho_n=c["rho_n"], mu_w=c["mu_w"], mu_n=c["mu_n"], S_wr=c["S_wr"],
+                S_nr=c["S_nr"], lam=c["lam"])
+    q = np.zeros(2 * nv)
+    if injecting:
+        j_src = int(round(0.125 / h[1]))
+        src = (np.rint(y / h[1]).astype(int) == j_src) & (np.abs(x - 0.5) <= 0.05 + 1e-12)
+        rate = c["rho_n"] * c["phi"] * 1.0 * c["rate_pv_per_year"] / YEAR
+        q[1::2] = np.where(src, rate / src.sum(), 0.0)
+    prob["q_in"] = q
+    prob.update(name="case4-analogue-%dx%d" % (n[0], n[1]), nlevels=levels_for(min(n[0], n[1])),
+                smoother="gs8")
+    return prob
+
+
+# Case 1 (Sec. 6, Table case1): Buckley-Leverett displacement, p_c = 0.
+CASE1 = dict(L=300.0, W=75.0, K=1e-7, phi=0.2, rho=1000.0, mu=1e-3, p_in=2e5, q_out=3e-4, T=1500 * 86400.0)
+
+
+def case1_buckley_leverett(nx, ny=9):
+    """Table case1's 300 m x 75 m strip with nx elements along x (ny vertices
+    across, so that the multigrid hierarchy can coarsen), K = 1e-7 m^2,
+    Phi = 0.2, equal densities and viscosities, S_wr = S_nr = 0, p_c = 0
+    (p_d = 0), no gravity.  The model has no saturation Dirichlet condition,
+    so the inlet column starts water-filled (S_n = 0, where k_rn = 0 keeps it
+    so) with p_w = 2e5 Pa held (Dirichlet), and the outlet takes the table's
+    NAPL outflow 3e-4 kg m^-2 s^-1 as a sink spread over its column by face
+    share; everything else starts at S_n = 1.  Valid until the water front
+    reaches the outlet (about 238 m at 1500 days)."""
+    c = CASE1
+    dim = 2
+    n = (nx + 1, ny, 1)
+    h = (c["L"] / nx, c["W"] / (ny - 1), 1.0)
+    nc = nx * (ny - 1)
+    nv = n[0] * n[1]
+    i = np.arange(nv) % n[0]
+    j = np.arange(nv) // n[0]
+    u = np.empty(2 * nv)
+    u[0::2] = c["p_in"]
+    u[1::2] = np.where(i == 0, 0.0, 1.0)
+    dm = (i == 0).astype(np.uint8)
+    share = np.where((j == 0) | (j == ny - 1), 0.5, 1.0) * h[1]
+    q = np.zeros(2 * nv)
+    q[1::2] = np.where(i == nx, -c["q_out"] * share, 0.0)
+    prob = dict(dim=dim, n=n, h=h, g=(0.0, 0.0, 0.0), K=np.full(nc, c["K"]), phi=np.full(nc, c["phi"]),
+                pd=np.zeros(nc), dir=dm, pw_dir=np.where(i == 0, c["p_in"], 0.0), q_in=q, u0=u,
+                rho_w=c["rho"], rho_n=c["rho"], mu_w=c["mu"], mu_n=c["mu"], S_wr=0.0, S_nr=0.0, lam=2.0)
+    L, m = 1, list(n[:2])
+    while all((t - 1) % 2 == 0 and t >= 3 for t in m):
+        m = [(t - 1) // 2 + 1 for t in m]
+        L += 1
+    prob.update(name="case1-buckley-leverett-%d" % nx, nlevels=L, smoother="gs8")
+    return prob

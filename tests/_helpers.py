@@ -82,3 +82,41 @@ def colour(dim, n):
     v = np.arange(nx * ny * nz)
     i, j, k = v % nx, (v // nx) % ny, v // (nx * ny)
     return (i & 1) | ((j & 1) << 1) | ((k & 1) << 2)
+
+
+def buckley_leverett_sw(x, t, q, phi, mu_w, mu_n, lam=2.0):
+    """Textbook Buckley-Leverett solution (no gravity, no capillarity) for water
+    injected at total Darcy velocity q into a medium at S_w = 0 (S_wr = S_nr =
+    0): fractional flow f = lam_w / (lam_w + lam_n) with the Brooks-Corey
+    relative permeabilities k_rw = S^((2+3lam)/lam), k_rn = (1-S)^2 (1 -
+    S^((2+lam)/lam)); the front saturation S_f is Welge's tangent point,
+    max f(S)/S; behind the front x(S) = q t f'(S) / phi (S_f <= S <= 1)."""
+    S = np.linspace(0.0, 1.0, 200001)
+    krw = S ** ((2 + 3 * lam) / lam)
+    krn = (1 - S) ** 2 * (1 - S ** ((2 + lam) / lam))
+    f = (krw / mu_w) / (krw / mu_w + krn / mu_n)
+    df = np.gradient(f, S)
+    ratio = np.where(S > 0, f / np.where(S > 0, S, 1.0), 0.0)
+    k = int(np.argmax(ratio))
+    Sf = S[k]
+    xs = q * t * df[k:] / phi           # decreasing from the front to 0 at S = 1
+    Ss = S[k:]
+    x = np.asarray(x, dtype=float)
+    out = np.zeros_like(x)
+    behind = x <= xs[0]
+    # x(S) is monotone decreasing on [S_f, 1]: interpolate S as a function of x
+    out[behind] = np.interp(x[behind], xs[::-1], Ss[::-1])
+    return out, Sf, xs[0]
+
+
+def lp_error_1d(xv, sv, exact, p, samples=40):
+    """(integral over [x0, x_end] of |s_h - s|^p dx)^(1/p) with s_h the piecewise
+    linear interpolant of vertex values sv at xv and s = exact(x), by the
+    midpoint rule on `samples` points per element."""
+    tot = 0.0
+    for a in range(len(xv) - 1):
+        h = xv[a + 1] - xv[a]
+        xm = xv[a] + (np.arange(samples) + 0.5) / samples * h
+        sh = sv[a] + (sv[a + 1] - sv[a]) * (xm - xv[a]) / h
+        tot += (np.abs(sh - exact(xm)) ** p).sum() * h / samples
+    return tot ** (1.0 / p)

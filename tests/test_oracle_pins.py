@@ -169,12 +169,15 @@ def test_p1_laplacian_stencil_closed_form(oracle, dim, nv, expect):
 
 
 # ---------------------------------------------------------------- P3 exact J
+@pytest.mark.parametrize("scheme", [0, 2])
 @pytest.mark.parametrize("dim,nv,seed", [(2, (7, 6), 11), (3, (5, 4, 5), 12)])
-def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed):
+def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed, scheme):
     """J = F_u exactly (Sec. 4): central differences of the oracle's own F,
     entry by entry; columns where one-sided differences disagree (a kink or an
-    upwind switch inside the step) are skipped."""
+    upwind switch inside the step) are skipped.  scheme 2: Darcy-velocity
+    upwinding of the water flux."""
     p = I.random_problem(dim, nv, seed)
+    p["scheme"] = scheme
     m = oracle.Model(p)
     u = p["u0"].copy()
     F0, J, md = oracle.assemble(m, u)
@@ -199,12 +202,14 @@ def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed):
 
 
 # ---------------------------------------------------------------- P4 conservation
+@pytest.mark.parametrize("scheme", [0, 2])
 @pytest.mark.parametrize("dim,nv", [(2, (9, 7)), (3, (5, 6, 5))])
-def test_p4_discrete_conservation(oracle, dim, nv):
+def test_p4_discrete_conservation(oracle, dim, nv, scheme):
     """Without Dirichlet rows: sum_i F_alpha,i = sum_i q_alpha,i (every face
     flux leaves one control volume and enters its neighbour), and every column
     of J sums to zero."""
     p = I.random_problem(dim, nv, 5, stress=True, dirichlet=False)
+    p["scheme"] = scheme
     rng = np.random.default_rng(9)
     p["q_in"] = rng.normal(0, 1e-6, 2 * int(np.prod(p["n"])))
     m = oracle.Model(p)
@@ -220,8 +225,9 @@ def test_p4_discrete_conservation(oracle, dim, nv):
 
 
 # ---------------------------------------------------------------- P5 equilibrium
+@pytest.mark.parametrize("scheme", [0, 3])
 @pytest.mark.parametrize("dim,nv", [(2, (17, 17)), (3, (9, 9, 9))])
-def test_p5_hydrostatic_equilibrium(oracle, dim, nv):
+def test_p5_hydrostatic_equilibrium(oracle, dim, nv, scheme):
     """Exact hydrostatic p_w with S_n = 0 in heterogeneous K and p_d: F = 0 up
     to rounding, and a LIMEX step leaves the state unchanged."""
     p = I.random_problem(dim, nv, 21)
@@ -233,6 +239,7 @@ def test_p5_hydrostatic_equilibrium(oracle, dim, nv):
     u[0::2] = I.P_TOP + p["rho_w"] * I.GRAV * (1.0 - vert)
     u[1::2] = 0.0
     p["u0"] = u
+    p["scheme"] = scheme
     m = oracle.Model(p)
     F, J, md = oracle.assemble(m, u)
     flux = p["K"].max() * p["rho_w"] ** 2 * I.GRAV / p["mu_w"] * h[0] ** (dim - 1)
@@ -462,3 +469,276 @@ def test_pdmin_and_storage_invariants(oracle):
     phiv = oracle.phiv(m)
     vol = np.prod(p["h"])
     assert phiv.sum() == pytest.approx((p["phi"] * vol).sum(), rel=1e-13)
+
+
+# ---------------------------------------------------------------- discretisation variants
+def _cell_weights(p):
+    """Per vertex: list of (cell, Phi_c |c| / 2^d) of the cells around it."""
+    dim, n, h = p["dim"], p["n"], p["h"]
+    cx, cy = n[0] - 1, n[1] - 1
+    cz = n[2] - 1 if dim == 3 else 1
+    vol = h[0] * h[1] * (h[2] if dim == 3 else 1.0)
+    out = []
+    for v in range(n[0] * n[1] * n[2]):
+        i, j, k = v % n[0], (v // n[0]) % n[1], v // (n[0] * n[1])
+        cells = []
+        for dz in ((0, 1) if dim == 3 else (0,)):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    ci, cj, ck = i - dx, j - dy, k - dz
+                    if 0 <= ci < cx and 0 <= cj < cy and 0 <= ck < cz:
+                        c = ci + cx * (cj + cy * ck)
+                        cells.append((c, p["phi"][c] * vol / 2 ** dim))
+        out.append(cells)
+    return out
+
+
+def test_darcy_upwind_water_flux_needs_a_water_potential_gradient(oracle):
+    """Darcy-velocity upwinding moves water only along grad p_w - rho_w g: with
+    uniform p_w, no gravity and a varying S_n over two materials the water
+    residual is exactly zero, while the split scheme of Sec. 3.2 (capillary
+    diffusion not upwinded) gives a nonzero water flux."""
+    p = I.random_problem(2, (9, 8), 31, gravity=False, dirichlet=False)
+    p["u0"][0::2] = I.P_TOP
+    p["scheme"] = 2
+    F = oracle.assemble(oracle.Model(p), p["u0"], jacobian=False)[0]
+    assert np.all(F[0::2] == 0.0)
+    assert np.abs(F[1::2]).max() > 0.0
+    p["scheme"] = 0
+    F0 = oracle.assemble(oracle.Model(p), p["u0"], jacobian=False)[0]
+    assert np.abs(F0[0::2]).max() > 1e-3 * np.abs(F0[1::2]).max()
+
+
+@pytest.mark.parametrize("dim,nv", [(2, (9, 7)), (3, (5, 5, 4))])
+def test_darcy_upwind_equals_split_scheme_without_capillary_gradient(oracle, dim, nv):
+    """One material and uniform S_n: p_c is uniform, T_c = 0 and the two
+    upwindings coincide (T_pw and T_w differ by rounding only)."""
+    p = I.random_problem(dim, nv, 32)
+    p["pd"][:] = 755.0
+    p["u0"][1::2] = 0.25
+    out = []
+    for scheme in (0, 2):
+        p["scheme"] = scheme
+        out.append(oracle.assemble(oracle.Model(p), p["u0"]))
+    (F0, J0, m0), (F2, J2, m2) = out
+    assert np.abs(F2 - F0).max() <= 1e-12 * np.abs(F0).max()
+    assert np.abs(J2 - J0).max() <= 1e-12 * np.abs(J0).max()
+    assert np.array_equal(m0, m2)
+
+
+@pytest.mark.parametrize("dim,nv", [(2, (9, 7)), (3, (5, 6, 5))])
+def test_shat_storage_reduces_to_vertex_storage_in_one_material(oracle, dim, nv):
+    """With one entry pressure S hat = S (Eq. (hSw), first case): storage and
+    M of the S hat variant equal rho Phi V S of Eqs. (dsW),(dpN)."""
+    p = I.random_problem(dim, nv, 33, stress=True)
+    p["pd"][:] = 755.0
+    m0 = oracle.Model(p)
+    phiv = oracle.phiv(m0)
+    Sn = p["u0"][1::2]
+    p["scheme"] = 1
+    m1 = oracle.Model(p)
+    st = oracle.storage(m1, p["u0"])
+    np.testing.assert_allclose(st[:, 1], p["rho_n"] * phiv * Sn, rtol=0, atol=1e-14 * p["rho_n"] * phiv.max())
+    np.testing.assert_allclose(st[:, 0], p["rho_w"] * phiv * (1 - Sn), rtol=0,
+                               atol=1e-14 * p["rho_w"] * phiv.max())
+    _, _, md0 = oracle.assemble(m0, p["u0"])
+    _, _, md1 = oracle.assemble(m1, p["u0"])
+    np.testing.assert_allclose(md1, md0, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_mass_matrix_is_the_derivative_of_the_storage(oracle, scheme):
+    """M = d m / d S_n (Sec. 4), vertex by vertex, against central differences
+    of the storage terms; vertices where one-sided differences disagree (the S
+    hat cap inside the step) are skipped."""
+    p = I.random_problem(3, (5, 5, 4), 34, stress=True, dirichlet=False)
+    p["scheme"] = scheme
+    m = oracle.Model(p)
+    u = p["u0"]
+    _, _, md = oracle.assemble(m, u)
+    d = 1e-7
+    up, um = u.copy(), u.copy()
+    up[1::2] += d
+    um[1::2] -= d
+    st0, stp, stm = oracle.storage(m, u), oracle.storage(m, up), oracle.storage(m, um)
+    fwd, bwd, cen = (stp - st0) / d, (st0 - stm) / d, (stp - stm) / (2 * d)
+    ok = np.all(np.abs(fwd - bwd) <= 1e-4 * np.abs(md).max(), axis=1)
+    assert ok.mean() > 0.9
+    np.testing.assert_allclose(cen[ok], md[ok], rtol=0, atol=1e-6 * np.abs(md).max())
+
+
+def test_shat_storage_entry_pressure_barrier(oracle):
+    """Eq. (hSw), second case: where p_d(N) >= p_dmin J(S_w) the sub-control
+    volume holds S_w = 1 - S_nr, i.e. no NAPL.  At S_n = 0.2 (S_e = 0.667) the
+    lens sub-volumes around an interface vertex (p_d 1163 against 755) are at
+    the cap, so m_n,i = rho_n S_n,i times the pore volume of the sand
+    sub-volumes only, and m_w takes the rest."""
+    p = I.random_problem(3, (7, 7, 6), 35)
+    p["u0"][1::2] = 0.2
+    p["scheme"] = 1
+    m = oracle.Model(p)
+    st = oracle.storage(m, p["u0"])
+    W = _cell_weights(p)
+    pdm = oracle.pdmin(m)
+    mixed = 0
+    for v, cells in enumerate(W):
+        sand = sum(w for c, w in cells if p["pd"][c] == pdm[v])
+        total = sum(w for c, w in cells)
+        if sand < total:
+            mixed += 1
+        assert st[v, 1] == pytest.approx(p["rho_n"] * 0.2 * sand, rel=1e-14, abs=1e-300)
+        assert st[v, 0] == pytest.approx(p["rho_w"] * (total - 0.2 * sand), rel=1e-14)
+    assert mixed > 10
+
+
+# ---------------------------------------------------------------- implicit Euler + Newton
+def test_ie_hydrostatic_state_is_stationary(oracle):
+    """Exact hydrostatic p_w, S_n = 0: R(u_old) = 0 to rounding, so the step
+    takes no Newton iteration and returns the state."""
+    p = I.random_problem(2, (17, 17), 21)
+    n, h = p["n"], p["h"]
+    nvx = int(np.prod(n))
+    vert = ((np.arange(nvx) // n[0]) % n[1]) * h[1]
+    u = np.zeros(2 * nvx)
+    u[0::2] = I.P_TOP + p["rho_w"] * I.GRAV * (1.0 - vert)
+    m = oracle.Model(p)
+    u1, info = oracle.ie_step(m, u, 100.0, nlevels=3)
+    assert info["status"] == 0 and info["newton"] == 0
+    assert np.array_equal(u1, u)
+
+
+def test_ie_affine_problem_takes_one_newton_step(oracle):
+    """With S_n = 0 everywhere no NAPL moves (k_rn(1) = 0 with zero slope) and
+    the water residual is affine in p_w (uniform S: the same k_rw at every
+    vertex, a fixed capillary term): one Newton step solves the implicit Euler
+    equations up to the linear solver's tolerance."""
+    p = I.random_problem(2, (17, 17), 22)
+    p["u0"][1::2] = 0.0
+    m = oracle.Model(p)
+    u1, info = oracle.ie_step(m, p["u0"], 50.0, nlevels=3, rtol=1e-9, atol=0.0, lin_rtol=1e-13)
+    assert info["status"] == 0 and info["newton"] == 1, info
+    assert info["res"] <= 1e-9 * info["res0"]
+    assert np.all(u1[1::2] == 0.0)
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_ie_napl_mass_balance(oracle, scheme):
+    """Every implicit Euler step is a discrete balance: with a NAPL source and
+    no NAPL Dirichlet rows, sum_i (m_n,i(u1) - m_n,i(u0)) = H sum_i q_n,i up to
+    the Newton residual, also with the nonlinear S hat storage."""
+    p = I.config5(9)
+    p["scheme"] = scheme
+    m = oracle.Model(p)
+    H = 20.0
+    u1, info = oracle.ie_step(m, p["u0"], H, nlevels=3, atol=0.0, rtol=1e-13, lin_rtol=1e-14, max_newton=30)
+    assert info["status"] == 0, info
+    dm = oracle.storage(m, u1)[:, 1].sum() - oracle.storage(m, p["u0"])[:, 1].sum()
+    q = p["q_in"][1::2].sum() * H
+    assert abs(dm - q) <= 1e-9 * q
+
+
+def _consistent_start(oracle, m, u):
+    """The recipes' noisy p_w does not satisfy the pressure constraint (M has
+    no p_w column, so the summed volume balance is algebraic); one short
+    implicit Euler step projects the state onto it."""
+    u0, inf = oracle.ie_step(m, u, 1e-3, nlevels=2, atol=0.0, rtol=1e-11, lin_rtol=1e-14, max_newton=40)
+    assert inf["status"] == 0, inf
+    return u0
+
+
+def test_ie_is_first_order_in_time(oracle):
+    """Implicit Euler is first order: successive differences of 16, 32, 64
+    and 128 steps over the same interval halve (ratios within [1.8, 2.2])."""
+    p = I.random_problem(2, (9, 9), 23)
+    m = oracle.Model(p)
+    u0 = _consistent_start(oracle, m, p["u0"])
+    T, out = 0.5, {}
+    for nsteps in (16, 32, 64, 128):
+        u = u0.copy()
+        for _ in range(nsteps):
+            u, inf = oracle.ie_step(m, u, T / nsteps, nlevels=2, atol=0.0, rtol=1e-11, lin_rtol=1e-14, max_newton=40)
+            assert inf["status"] == 0, inf
+        out[nsteps] = u
+    d = [np.abs(out[a][1::2] - out[2 * a][1::2]).max() for a in (16, 32, 64)]
+    assert 1.8 <= d[0] / d[1] <= 2.2 and 1.8 <= d[1] / d[2] <= 2.2, d
+
+
+def test_limex_and_implicit_euler_share_their_limit(oracle):
+    """Two independent time integrators of the same semi-discretisation: from a
+    consistent state, LIMEX (kappa = 4, two steps) lands within twice implicit
+    Euler's own error at 128 steps (its successive difference) of the 128-step
+    result, and kappa = 1 (linearly implicit Euler) converges to that limit at
+    first order."""
+    p = I.random_problem(2, (9, 9), 23)
+    m = oracle.Model(p)
+    u0 = _consistent_start(oracle, m, p["u0"])
+    T = 0.5
+
+    def ie(n):
+        u = u0.copy()
+        for _ in range(n):
+            u, inf = oracle.ie_step(m, u, T / n, nlevels=2, atol=0.0, rtol=1e-11, lin_rtol=1e-14, max_newton=40)
+            assert inf["status"] == 0
+        return u
+
+    def limex(n, kappa):
+        u = u0.copy()
+        for _ in range(n):
+            u, inf = oracle.limex_step(m, u, T / n, kappa=kappa, tol=1e9, nlevels=2, rtol=1e-14, maxit=400)
+            assert inf["status"] == 0
+        return u
+
+    a, b = ie(64), ie(128)
+    ie_err = np.abs(a[1::2] - b[1::2]).max()
+    assert np.abs(limex(2, 4)[1::2] - b[1::2]).max() <= 2.0 * ie_err
+    e = [np.abs(limex(n, 1)[1::2] - b[1::2]).max() for n in (2, 8)]
+    assert 3.0 <= e[0] / e[1] <= 5.0, e
+
+
+# ---------------------------------------------------------------- Case 1 (Buckley-Leverett)
+def _case1_table():
+    rows = {}
+    with open(os.path.join(GOLDEN, "case1_error1.txt")) as f:
+        for line in f:
+            t = line.split()
+            if t and t[0] in ("ie", "limex"):
+                rows[(t[0], int(t[1]))] = (int(t[2]), float(t[3]), float(t[4]))
+    return rows
+
+
+def test_buckley_leverett_solution_closed_form():
+    """The textbook solution used below: with Brooks-Corey lambda = 2 and equal
+    viscosities the Welge front saturation is 3/4 (f(S)/S is maximal there),
+    and the front speed q f'(S_f)/phi reproduces the paper's v = 1.84e-6 m/s."""
+    c = I.CASE1
+    q = c["q_out"] / c["rho"]
+    _, Sf, xf = H.buckley_leverett_sw(np.array([0.0]), c["T"], q, c["phi"], c["mu"], c["mu"])
+    assert Sf == pytest.approx(0.75, abs=1e-4)
+    assert xf / c["T"] == pytest.approx(1.84e-6, rel=5e-3)
+
+
+def test_case1_implicit_euler_errors_match_the_paper(oracle):
+    """The whole discretisation against printed numbers: implicit Euler on
+    Case 1 with 64 elements at Courant number 0.8 (65 steps in the paper, 64
+    here from T / dt rounded up) gives the L1 and L2 errors of Table error1
+    within 3%."""
+    c = I.CASE1
+    rows = _case1_table()
+    nx = 64
+    p = I.case1_buckley_leverett(nx)
+    m = oracle.Model(p)
+    nst = int(np.ceil(c["T"] / (0.8 * (c["L"] / nx) / 1.84e-6)))
+    u = p["u0"].copy()
+    for _ in range(nst):
+        u, inf = oracle.ie_step(m, u, c["T"] / nst, nlevels=p["nlevels"], atol=1e-9, rtol=1e-6, lin_rtol=1e-8,
+                                max_newton=30)
+        assert inf["status"] == 0, inf
+    sw = 1.0 - u[1::2].reshape(p["n"][1], p["n"][0])
+    assert np.abs(sw - sw[0]).max() <= 1e-9          # one-dimensional flow
+    xv = np.arange(nx + 1) * c["L"] / nx
+    q = c["q_out"] / c["rho"]
+    exact = lambda x: H.buckley_leverett_sw(x, c["T"], q, c["phi"], c["mu"], c["mu"])[0]
+    steps, L1, L2 = rows[("ie", nx)]
+    assert abs(nst - steps) <= 1
+    assert H.lp_error_1d(xv, sw[0], exact, 1) == pytest.approx(L1, rel=0.03)
+    assert H.lp_error_1d(xv, sw[0], exact, 2) == pytest.approx(L2, rel=0.03)
