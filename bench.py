@@ -56,6 +56,10 @@ def args_():
     ap.add_argument("--config5-nvert", type=int, default=0,
                     help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
     ap.add_argument("--config5-steps", type=int, default=20)
+    ap.add_argument("--case4-days", type=float, default=0.0,
+                    help="also run the layered Case-4 analogue for this many days with implicit Euler (1-day steps) "
+                         "and adaptive LIMEX (0 = off)")
+    ap.add_argument("--case4-nvert", default="257x129", help="Case-4 analogue vertices (x by y)")
     ap.add_argument("--autotune", type=int, default=0,
                     help="time block sizes of the level kernels during the set-up (1/0)")
     return ap.parse_args()
@@ -431,6 +435,64 @@ def main():
         except (rf.RFError, RuntimeError) as e:
             config5 = {"error": str(e)}
 
+    # ---- Case-4 analogue: fixed-step implicit Euler + Newton against adaptive
+    # LIMEX over the same simulated time (the structure of the paper's Table
+    # case4_2: time steps, Newton and linear iterations, wall time)
+    case4 = None
+    if a.case4_days > 0:
+        try:
+            torch.cuda.empty_cache()
+            nv4 = tuple(int(t) for t in a.case4_nvert.split("x"))
+            p4 = I.case4_analogue(nv4)
+            T4 = a.case4_days * 86400.0
+            q4 = float(p4["q_in"][1::2].sum())
+            gm4 = rf.gmg_opts(p4["nlevels"], "gs8", precision="fp64")
+            case4 = {"workload": "layered Case-4 analogue, %dx%d vertices (500 m x 200 m, 4 layers), NAPL injection "
+                                 "0.05 PV/year, %.0f days; FP64 GMG (8-colour GS) in BiCGSTAB, linear rel.res 1e-6"
+                                 % (nv4[0], nv4[1], a.case4_days)}
+            g4 = rf.Grid(p4)
+            u4 = torch.tensor(p4["u0"], device=dev)
+            m0 = g4.phase_mass(u4)[1]
+            nst = int(round(a.case4_days))
+            nn = nl = 0
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            for k in range(nst):
+                inf4 = g4.ie_step(u4, T4 / nst, atol=1e-8, rtol=1e-6, max_newton=50, gmg=gm4, lin_rtol=1e-6,
+                                  max_it=500)
+                if inf4["status"] != 0:
+                    raise RuntimeError("implicit Euler step %d failed: %s" % (k, inf4))
+                nn += inf4["newton"]
+                nl += inf4["linear"]
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+            m1 = g4.phase_mass(u4)[1]
+            s_ie = u4.cpu().numpy()[1::2]
+            case4["implicit_euler"] = {"T_total_s": round(wall, 3), "time_steps": nst, "newton": nn, "linear": nl,
+                                       "dt_s": T4 / nst, "mass_error_rel": abs(m1 - m0 - q4 * T4) / (q4 * T4),
+                                       "tolerances": "Newton abs 1e-8 / rel 1e-6"}
+            g4.close()
+            g4 = rf.Grid(p4)
+            u4 = torch.tensor(p4["u0"], device=dev)
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t4, hist = g4.limex_run(u4, 32.0, t_end=T4, tol=5e-3, rho=0.75, H_max=100 * 86400.0, gmg=gm4, rtol=1e-6,
+                                    max_it=500, max_rejects=1000000)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+            m1 = g4.phase_mass(u4)[1]
+            acc = sum(h["accepted"] for h in hist)
+            case4["limex"] = {"T_total_s": round(wall, 3), "time_steps": acc, "rejected": len(hist) - acc,
+                              "linear": sum(h["iterations"] for h in hist), "stage_solves": sum(h["solves"] for h in hist),
+                              "H_max_used_s": max(h["H"] for h in hist),
+                              "mass_error_rel": abs(m1 - m0 - q4 * T4) / (q4 * T4),
+                              "tolerances": "TOL 5e-3, rho 0.75, H0 32 s, H_max 100 days"}
+            case4["max_abs_dSn_ie_vs_limex"] = float(np.abs(s_ie - u4.cpu().numpy()[1::2]).max())
+            case4["Sn_max"] = float(s_ie.max())
+            g4.close()
+        except (rf.RFError, RuntimeError) as e:
+            case4 = {"error": str(e)}
+
     cpu = None
     if rank == 0 and world == 1:
         v, dt, sdof, sit = oracle_sample(a.sample_nvert, a.smoother)
@@ -452,6 +514,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "iterations": iters, "relres": infos[-1]["relres"],
             "setup_ms": round(setup_ms, 1), "assembly_ms": round(asm_ms, 1),
+            "stage": {"dofs_per_s": world * dof / ((asm_ms + setup_ms + ms) / 1e3), "unit": "DoF/s",
+                      "ms": round(asm_ms + setup_ms + ms, 1),
+                      "note": "one LIMEX stage from scratch: assembly of J, M, F + multigrid set-up + solve"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm"],
                          "unit": "GB/s", "frac": round(achieved / pk["hbm"], 4), "traffic": traffic,
                          "peak_source": pk["src"], "note": "of %s HBM copy bandwidth" % pk["src"]},
@@ -460,6 +525,7 @@ def main():
             "limex_step": limex,
             "ensemble": ensemble,
             "config5": config5,
+            "case4_analogue": case4,
             "e2e": {"value": world * dof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": 16 * g.nv,
                     "d2h_bytes_per_step": 16 * g.nv},
             "gpu_launches": launches,

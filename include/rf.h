@@ -190,9 +190,12 @@ rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const d
  * ||R||_2 <= atol or ||R||_2 <= rtol ||R(u_old)||_2.  u [2nv] (host or device)
  * is updated in place only on success; info (host, may be NULL) receives the
  * Newton and linear iteration counts and the first and last residual norms.
+ * max_ls > 0 damps each correction by backtracking: lambda = 1, 1/2, ... (at
+ * most max_ls halvings, one residual evaluation each) until ||R(u + lambda d)||
+ * <= (1 - 1e-4 lambda) ||R(u)||, else the last lambda is kept.
  * RF_ENOTCONV when max_newton iterations do not converge; a linear solver
  * failure is returned as is. */
-typedef struct { double atol, rtol; int max_newton; rf_gmg_opts gmg; rf_solve_opts solve; } rf_ie_opts;
+typedef struct { double atol, rtol; int max_newton; rf_gmg_opts gmg; rf_solve_opts solve; int max_ls; } rf_ie_opts;
 typedef struct { int newton, linear; double res0, res; rf_status status; } rf_ie_info;
 rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opts* opts, rf_ie_info* info, void* stream);
 

@@ -336,7 +336,7 @@ class _IeOpts(ctypes.Structure):
     _fields_ = [("atol", ctypes.c_double), ("rtol", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("smoother", ctypes.c_int), ("nu1", ctypes.c_int),
                 ("nu2", ctypes.c_int), ("omega", ctypes.c_double), ("lin_rtol", ctypes.c_double),
-                ("lin_maxit", ctypes.c_int)]
+                ("lin_maxit", ctypes.c_int), ("max_ls", ctypes.c_int)]
 
 
 class _IeInfo(ctypes.Structure):
@@ -345,9 +345,9 @@ class _IeInfo(ctypes.Structure):
 
 
 def ie_step(model, u_old, H, atol=1e-8, rtol=1e-6, max_newton=20, nlevels=4, smoother=JACOBI, nu1=2, nu2=2,
-            omega=0.8, lin_rtol=1e-10, lin_maxit=400):
+            omega=0.8, lin_rtol=1e-10, lin_maxit=400, max_ls=0):
     """One implicit Euler step solved by Newton's method (rfo_ie_step)."""
-    o = _IeOpts(atol, rtol, max_newton, nlevels, smoother, nu1, nu2, omega, lin_rtol, lin_maxit)
+    o = _IeOpts(atol, rtol, max_newton, nlevels, smoother, nu1, nu2, omega, lin_rtol, lin_maxit, max_ls)
     info = _IeInfo()
     u_out = np.zeros(2 * model.nv)
     st = lib().rfo_ie_step(model.ref, _p(_f64(u_old)), float(H), ctypes.byref(o), _p(u_out), ctypes.byref(info))

@@ -943,6 +943,23 @@ int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_lim
  * storage (rfo_storage) and F the flux residual (rfo_assemble); Dirichlet p_w
  * rows keep their algebraic equation.  The Newton matrix is M(u_k)/H - J(u_k)
  * with M = dm/dS_n from the assembly.                                      */
+/* R = F(u) - (m(u) - m_old)/H with no storage in Dirichlet p_w rows; returns ||R||_2 */
+static double ie_residual(const rfo_model* m, const unsigned char* dm, const double* u, const double* m_old,
+                          double H, const double* F, double* mk, double* R) {
+  const int nv = nverts(m->n);
+  rfo_storage(m, u, mk);
+  double s2 = 0.0;
+  for (int v = 0; v < nv; ++v) {
+    for (int a = 0; a < 2; ++a) {
+      const int q = 2 * v + a;
+      const int storage = !(a == 0 && dm[v]);
+      R[q] = F[q] - (storage ? (mk[q] - m_old[q]) / H : 0.0);
+      s2 += R[q] * R[q];
+    }
+  }
+  return sqrt(s2);
+}
+
 int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_opts* o, double* u_out,
                 rfo_ie_info* info) {
   const int dim = m->dim, nv = nverts(m->n), nb = nblk(dim), N = 2 * nv;
@@ -954,6 +971,7 @@ int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_
   double* d = malloc(sizeof(double) * N);
   double* m0 = malloc(sizeof(double) * N);
   double* mk = malloc(sizeof(double) * N);
+  double* uk = malloc(sizeof(double) * N);
   unsigned char* dm = calloc(nv, 1);
   if (m->dir) memcpy(dm, m->dir, nv);
   memcpy(u_out, u_old, sizeof(double) * N);
@@ -962,17 +980,7 @@ int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_
   double r0 = 0.0, r = 0.0;
   for (;;) {
     rfo_assemble(m, u_out, F, J, md);
-    rfo_storage(m, u_out, mk);
-    double s2 = 0.0;
-    for (int v = 0; v < nv; ++v) {
-      for (int a = 0; a < 2; ++a) {
-        const int q = 2 * v + a;
-        const int storage = !(a == 0 && dm[v]);
-        R[q] = F[q] - (storage ? (mk[q] - m0[q]) / H : 0.0);
-        s2 += R[q] * R[q];
-      }
-    }
-    r = sqrt(s2);
+    r = ie_residual(m, dm, u_out, m0, H, F, mk, R);
     if (newton == 0) r0 = r;
     if (r <= o->atol || r <= o->rtol * r0) { status = 0; break; }
     if (newton >= o->max_newton) break;
@@ -984,10 +992,20 @@ int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_
     linear += it;
     ++newton;
     if (st != 0) { status = st; break; }
-    for (int q = 0; q < N; ++q) u_out[q] += d[q];
+    /* backtracking on the residual norm (max_ls halvings of the correction) */
+    memcpy(uk, u_out, sizeof(double) * N);
+    double lam = 1.0;
+    for (int ls = 0;; ++ls) {
+      for (int q = 0; q < N; ++q) u_out[q] = uk[q] + lam * d[q];
+      if (o->max_ls <= 0) break;
+      rfo_assemble(m, u_out, F, NULL, NULL);
+      const double rt = ie_residual(m, dm, u_out, m0, H, F, mk, R);
+      if (rt <= (1.0 - 1e-4 * lam) * r || ls >= o->max_ls) break;
+      lam = 0.5 * lam;
+    }
   }
   if (status != 0) memcpy(u_out, u_old, sizeof(double) * N);   /* a failed step keeps the state */
   if (info) { info->newton = newton; info->linear = linear; info->res0 = r0; info->res = r; }
-  free(J); free(A); free(md); free(F); free(R); free(d); free(m0); free(mk); free(dm);
+  free(J); free(A); free(md); free(F); free(R); free(d); free(m0); free(mk); free(uk); free(dm);
   return status;
 }

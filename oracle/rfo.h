@@ -112,12 +112,16 @@ int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_lim
  * Dirichlet p_w rows have no storage) by Newton: (M(u_k)/H - J(u_k)) d = R(u_k),
  * u_{k+1} = u_k + d, each linear system by BiCGSTAB + GMG to rtol.  Stops when
  * ||R||_2 <= atol or ||R||_2 <= rtol_newton ||R(u_old)||_2 (Sec. 6: 1e-8 / 1e-6).
+ * With max_ls > 0 each Newton correction is damped by backtracking: lambda =
+ * 1, 1/2, ... (at most max_ls halvings) until ||R(u + lambda d)|| <= (1 -
+ * 1e-4 lambda) ||R(u)||; if no lambda passes, the last one is taken.
  * Returns 0, or 1 if Newton did not converge in max_newton iterations, or the
  * linear solver's status; on failure u_out = u_old. */
 typedef struct {
   double atol, rtol; int max_newton;
   int nlevels, smoother, nu1, nu2; double omega;
   double lin_rtol; int lin_maxit;
+  int max_ls;
 } rfo_ie_opts;
 typedef struct { int newton, linear; double res0, res; } rfo_ie_info;
 int rfo_ie_step(const rfo_model* m, const double* u_old, double H, const rfo_ie_opts* o, double* u_out,

@@ -90,7 +90,7 @@ class rf_limex_opts(ctypes.Structure):
 
 class rf_ie_opts(ctypes.Structure):
     _fields_ = [("atol", ctypes.c_double), ("rtol", ctypes.c_double), ("max_newton", ctypes.c_int),
-                ("gmg", rf_gmg_opts), ("solve", rf_solve_opts)]
+                ("gmg", rf_gmg_opts), ("solve", rf_solve_opts), ("max_ls", ctypes.c_int)]
 
 
 class rf_ie_info(ctypes.Structure):
@@ -380,11 +380,11 @@ class Grid:
                     iterations=info.iterations)
 
     def ie_step(self, u, H, atol=1e-8, rtol=1e-6, max_newton=20, gmg=None, lin_rtol=1e-10, max_it=200,
-                outer="fp64"):
+                outer="fp64", max_ls=0):
         """One implicit Euler step solved by Newton's method (rf_ie_step)."""
         gmg = gmg if gmg is not None else gmg_opts(4)
         o = rf_ie_opts(float(atol), float(rtol), int(max_newton), gmg,
-                       rf_solve_opts(float(lin_rtol), int(max_it), OUTERS.get(outer, outer)))
+                       rf_solve_opts(float(lin_rtol), int(max_it), OUTERS.get(outer, outer)), int(max_ls))
         st, info = rf_ie_step(self.handle, _ptr(u), H, o, self.stream)
         return dict(status=st, newton=info.newton, linear=info.linear, res0=info.res0, res=info.res)
 

@@ -22,6 +22,13 @@ namespace rf {
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("RF_PDL");
+    return !(e && atoi(e) == 0);
+  }();
+  return on;
+}
 
 int num_sms() {
   static int n = 0;
@@ -114,6 +121,7 @@ struct rf_grid {
   double vol = 0.0;   // cell volume
   double* ie_old = nullptr;     // implicit Euler: u_old (parity-split pairs), allocated on first use
   double* ie_swold = nullptr;   // implicit Euler, S hat storage: water pore volume sums of u_old
+  double* ie_uk = nullptr;      // implicit Euler line search: the Newton iterate before the update
   uint8_t* dir = nullptr;
   double *pw_dir = nullptr, *q_in = nullptr;
   double *pdmin = nullptr, *phiv = nullptr;
@@ -1267,16 +1275,17 @@ extern "C" rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opt
     g->ie_swold = (double*)dalloc(g, sizeof(double) * d.nv, s, false);
     if (!g->ie_swold) return fail(RF_ENOMEM, "implicit Euler storage allocation failed");
   }
+  if (o->max_ls > 0 && !g->ie_uk) {
+    g->ie_uk = (double*)dalloc(g, vb, s, false);
+    if (!g->ie_uk) return fail(RF_ENOMEM, "implicit Euler line-search allocation failed");
+  }
   rf_status st = pairs_in(g, d, u, g->u_p, s);
   if (st) return st;
   CU(cudaMemcpyAsync(g->ie_old, g->u_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
   if (shat) launch_storage_sw(d, g->pp, g->ie_old, g->pdmin, g->phi, g->pd, g->vol, g->ie_swold, s);
   const double shift = 1.0 / H;
-  int newton = 0, linear = 0;
-  double r0 = 0.0, r = 0.0;
-  rf_status res = RF_OK;
-  for (;;) {
-    if ((st = assemble_p(g, true, s))) return st;   // F, J, M at the iterate
+  // ||R(u_p)||^2 into *r2 (F_p must hold F(u_p)); R into b_p
+  auto residual = [&](double* r2) -> rf_status {
     const double* sw = nullptr;
     if (shat) {
       launch_storage_sw(d, g->pp, g->u_p, g->pdmin, g->phi, g->pd, g->vol, g->pn, s);   // pn: assembly scratch
@@ -1284,9 +1293,17 @@ extern "C" rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opt
     }
     launch_ie_residual(d.nv, g->F_p, g->u_p, g->ie_old, g->mdiag, sw, g->ie_swold, g->dir, g->pp.rho_w,
                        g->pp.rho_n, shift, (double*)g->b_p, g->norms, g->K.partial, s);
-    double r2 = 0.0;
-    CU(cudaMemcpyAsync(&r2, g->norms, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaMemcpyAsync(r2, g->norms, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)s));
     CU(cudaStreamSynchronize((cudaStream_t)s));
+    return RF_OK;
+  };
+  int newton = 0, linear = 0;
+  double r0 = 0.0, r = 0.0;
+  rf_status res = RF_OK;
+  for (;;) {
+    if ((st = assemble_p(g, true, s))) return st;   // F, J, M at the iterate
+    double r2 = 0.0;
+    if ((st = residual(&r2))) return st;
     if (!std::isfinite(r2)) { res = fail(RF_ENONFINITE, "implicit Euler residual is not finite"); break; }
     r = std::sqrt(r2);
     if (newton == 0) r0 = r;
@@ -1298,7 +1315,22 @@ extern "C" rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opt
     linear += si.iterations;
     ++newton;
     if (ls != RF_OK) { res = ls; break; }
-    launch_axpy_pairs(d.nv, (double2*)g->u_p, g->K.x, s);
+    if (o->max_ls <= 0) {
+      launch_axpy_pairs(d.nv, (double2*)g->u_p, g->K.x, s);
+      continue;
+    }
+    // backtracking on ||R||: lambda = 1, 1/2, ... (mdiag stays that of u_k:
+    // the linear storage does not depend on u, the S hat one is recomputed)
+    CU(cudaMemcpyAsync(g->ie_uk, g->u_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    double lam = 1.0;
+    for (int k = 0;; ++k) {
+      launch_axpby_pairs(d.nv, g->u_p, g->ie_uk, g->K.x, lam, s);
+      if ((st = assemble_p(g, false, s))) return st;
+      double rt2 = 0.0;
+      if ((st = residual(&rt2))) return st;
+      if ((std::isfinite(rt2) && std::sqrt(rt2) <= (1.0 - 1e-4 * lam) * r) || k >= o->max_ls) break;
+      lam *= 0.5;
+    }
   }
   if (info) { info->newton = newton; info->linear = linear; info->res0 = r0; info->res = r; info->status = res; }
   if (res != RF_OK) {

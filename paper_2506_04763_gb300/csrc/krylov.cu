@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(BS) k_bicg_v_df(Dims d, Nbr nb, const float4* 
                                                   const double2* __restrict__ md, double shift,
                                                   const float2* __restrict__ y, const double2* __restrict__ rh,
                                                   double2* __restrict__ v, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[1] = {0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
     double y0, y1;
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(BS) k_bicg_t_df(Dims d, Nbr nb, const float4* 
                                                   const double2* __restrict__ md, double shift,
                                                   const float2* __restrict__ z, const double2* __restrict__ s,
                                                   double2* __restrict__ t, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[2] = {0.0, 0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
     double y0, y1;
@@ -189,6 +191,7 @@ __global__ void __launch_bounds__(BS) k_bicg_v(Dims d, Nbr nb, const double* __r
                                                const double2* __restrict__ md, double shift,
                                                const XV* __restrict__ y, const double2* __restrict__ rh,
                                                double2* __restrict__ v, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[1] = {0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
     double y0, y1;
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(BS) k_bicg_t(Dims d, Nbr nb, const double* __r
                                                const double2* __restrict__ md, double shift,
                                                const XV* __restrict__ z, const double2* __restrict__ s,
                                                double2* __restrict__ t, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[2] = {0.0, 0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
     double y0, y1;
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(BS) k_true_res(Dims d, Nbr nb, const double* _
                                                  const double2* __restrict__ md, double shift,
                                                  const double2* __restrict__ x, const double2* __restrict__ b,
                                                  double2* __restrict__ r, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[1] = {0.0};
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
     double y0, y1;
@@ -247,6 +252,7 @@ __global__ void __launch_bounds__(BS) k_bicg_init(int64_t nv, const double2* __r
                                                   double2* __restrict__ r, double2* __restrict__ rh,
                                                   double2* __restrict__ p, double2* __restrict__ v,
                                                   double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[1] = {0.0};
   for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
     const double2 bv = b[q];
@@ -263,6 +269,7 @@ __global__ void __launch_bounds__(BS) k_bicg_init(int64_t nv, const double2* __r
 __global__ void __launch_bounds__(BS) k_bicg_restart(int64_t nv, const double2* __restrict__ r,
                                                      double2* __restrict__ rh, double2* __restrict__ p,
                                                      double2* __restrict__ v, double* __restrict__ partial) {
+  rf_pdl_begin();
   double acc[1] = {0.0};
   for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
     const double2 rv = r[q];
@@ -278,6 +285,7 @@ template <typename LV>
 __global__ void __launch_bounds__(BS) k_bicg_p(int64_t nv, const double* __restrict__ scal,
                                                const double2* __restrict__ r, const double2* __restrict__ v,
                                                double2* __restrict__ p, LV* __restrict__ plo) {
+  rf_pdl_begin();
   const double beta = scal[S_BETA], omega = scal[S_OMEGA];
   for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
     const double2 rv = r[q], vv = v[q], pv = p[q];
@@ -292,6 +300,7 @@ template <typename LV>
 __global__ void __launch_bounds__(BS) k_bicg_s(int64_t nv, const double* __restrict__ scal,
                                                const double2* __restrict__ r, const double2* __restrict__ v,
                                                double2* __restrict__ s, LV* __restrict__ slo) {
+  rf_pdl_begin();
   const double alpha = scal[S_ALPHA];
   for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
     const double2 rv = r[q], vv = v[q];
@@ -307,6 +316,7 @@ __global__ void __launch_bounds__(BS) k_bicg_xr(int64_t nv, const double* __rest
                                                 const double2* __restrict__ s, const double2* __restrict__ t,
                                                 const double2* __restrict__ rh, double2* __restrict__ x,
                                                 double2* __restrict__ r, double* __restrict__ partial) {
+  rf_pdl_begin();
   const double alpha = scal[S_ALPHA], omega = scal[S_OMEGA];
   double acc[2] = {0.0, 0.0};
   for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
@@ -329,6 +339,7 @@ static_assert(S_RR + 1 == S_BB, "slots");  // k_bicg_xr writes (rr, <rh,r>) into
 // stage: 0 init, 1 alpha, 2 omega, 3 x/r update, 4 true residual, 5 restart
 __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const double* __restrict__ partial,
                            double rtol) {
+  rf_pdl_begin();
   if (threadIdx.x >= 32) return;
   if (stage == 0) {
     const double bb = sum_partials(partial, S_BB, nblk);
@@ -383,7 +394,7 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
 
 // ----------------------------------------------------------------- launchers
 static inline void fin(int stage, int nblk, KrylovVecs& K, double rtol, void* s) {
-  RF_LAUNCH(k_finalize, 1, 32, 0, s, stage, nblk, K.scal, K.partial, rtol);
+  RF_LAUNCH_PDL(k_finalize, 1, 32, 0, s, stage, nblk, K.scal, K.partial, rtol);
 }
 
 void launch_spmv64(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
@@ -401,14 +412,14 @@ void launch_spmv64(const Dims& d, const Nbr& nb, const double* J, const double* 
 
 void launch_bicg_init(int64_t nv, const double2* b, KrylovVecs& K, double rtol, void* s) {
   const int g = krylov_blocks(nv);
-  RF_LAUNCH(k_bicg_init, g, BS, 0, s, nv, b, K.x, K.r, K.rh, K.p, K.v, K.partial);
+  RF_LAUNCH_PDL(k_bicg_init, g, BS, 0, s, nv, b, K.x, K.r, K.rh, K.p, K.v, K.partial);
   fin(0, g, K, rtol, s);
 }
 
 void launch_bicg_p(int64_t nv, KrylovVecs& K, bool lo_is_f32, bool /*first*/, void* s) {
   const int g = krylov_blocks(nv);
-  if (lo_is_f32) RF_LAUNCH(k_bicg_p<float2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.p, (float2*)K.p_lo);
-  else RF_LAUNCH(k_bicg_p<double2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.p, (double2*)K.p_lo);
+  if (lo_is_f32) RF_LAUNCH_PDL(k_bicg_p<float2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.p, (float2*)K.p_lo);
+  else RF_LAUNCH_PDL(k_bicg_p<double2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.p, (double2*)K.p_lo);
 }
 
 // The operand is the FP64 copy y64 of the preconditioned vector: converting
@@ -418,8 +429,8 @@ void launch_bicg_v(const Dims& d, const Nbr& nb, const double* J, const double* 
                    KrylovVecs& K, bool /*y_is_f32*/, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) RF_LAUNCH((k_bicg_v<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
-  else RF_LAUNCH((k_bicg_v<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
+  if (d.nb == 27) RF_LAUNCH_PDL((k_bicg_v<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
+  else RF_LAUNCH_PDL((k_bicg_v<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.y64, K.rh, K.v, K.partial);
   fin(1, g, K, 0.0, s);
 }
 
@@ -432,8 +443,8 @@ void launch_bicg_v_df(const Dims& d, const Nbr& nb, const float* Jdf, const doub
                       KrylovVecs& K, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) RF_LAUNCH(k_bicg_v_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
-  else RF_LAUNCH(k_bicg_v_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
+  if (d.nb == 27) RF_LAUNCH_PDL(k_bicg_v_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
+  else RF_LAUNCH_PDL(k_bicg_v_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.y, K.rh, K.v, K.partial);
   fin(1, g, K, 0.0, s);
 }
 
@@ -441,32 +452,32 @@ void launch_bicg_t_df(const Dims& d, const Nbr& nb, const float* Jdf, const doub
                       KrylovVecs& K, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) RF_LAUNCH(k_bicg_t_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
-  else RF_LAUNCH(k_bicg_t_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
+  if (d.nb == 27) RF_LAUNCH_PDL(k_bicg_t_df<27>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
+  else RF_LAUNCH_PDL(k_bicg_t_df<9>, g, BS, 0, s, d, nb, (const float4*)Jdf, md, shift, (const float2*)K.z, K.s, K.t, K.partial);
   fin(2, g, K, 0.0, s);
 }
 
 void launch_bicg_s(int64_t nv, KrylovVecs& K, bool lo_is_f32, void* s) {
   const int g = krylov_blocks(nv);
-  if (lo_is_f32) RF_LAUNCH(k_bicg_s<float2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.s, (float2*)K.s_lo);
-  else RF_LAUNCH(k_bicg_s<double2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.s, (double2*)K.s_lo);
+  if (lo_is_f32) RF_LAUNCH_PDL(k_bicg_s<float2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.s, (float2*)K.s_lo);
+  else RF_LAUNCH_PDL(k_bicg_s<double2>, g, BS, 0, s, nv, K.scal, K.r, K.v, K.s, (double2*)K.s_lo);
 }
 
 void launch_bicg_t(const Dims& d, const Nbr& nb, const double* J, const double* mdiag, double shift,
                    KrylovVecs& K, bool /*z_is_f32*/, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) RF_LAUNCH((k_bicg_t<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
-  else RF_LAUNCH((k_bicg_t<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
+  if (d.nb == 27) RF_LAUNCH_PDL((k_bicg_t<double2, 27>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
+  else RF_LAUNCH_PDL((k_bicg_t<double2, 9>), g, BS, 0, s, d, nb, J, md, shift, (const double2*)K.z64, K.s, K.t, K.partial);
   fin(2, g, K, 0.0, s);
 }
 
 void launch_bicg_xr(int64_t nv, KrylovVecs& K, bool yz_is_f32, void* s) {
   const int g = krylov_blocks(nv);
   if (yz_is_f32)
-    RF_LAUNCH(k_bicg_xr<float2>, g, BS, 0, s, nv, K.scal, (const float2*)K.y, (const float2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
+    RF_LAUNCH_PDL(k_bicg_xr<float2>, g, BS, 0, s, nv, K.scal, (const float2*)K.y, (const float2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
   else
-    RF_LAUNCH(k_bicg_xr<double2>, g, BS, 0, s, nv, K.scal, (const double2*)K.y, (const double2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
+    RF_LAUNCH_PDL(k_bicg_xr<double2>, g, BS, 0, s, nv, K.scal, (const double2*)K.y, (const double2*)K.z, K.s, K.t, K.rh, K.x, K.r, K.partial);
   fin(3, g, K, 0.0, s);
 }
 
@@ -474,14 +485,14 @@ void launch_true_residual(const Dims& d, const Nbr& nb, const double* J, const d
                           const double2* b, KrylovVecs& K, void* s) {
   const int g = krylov_blocks(d.nv);
   const double2* md = (const double2*)mdiag;
-  if (d.nb == 27) RF_LAUNCH(k_true_res<27>, g, BS, 0, s, d, nb, J, md, shift, K.x, b, K.r, K.partial);
-  else RF_LAUNCH(k_true_res<9>, g, BS, 0, s, d, nb, J, md, shift, K.x, b, K.r, K.partial);
+  if (d.nb == 27) RF_LAUNCH_PDL(k_true_res<27>, g, BS, 0, s, d, nb, J, md, shift, K.x, b, K.r, K.partial);
+  else RF_LAUNCH_PDL(k_true_res<9>, g, BS, 0, s, d, nb, J, md, shift, K.x, b, K.r, K.partial);
   fin(4, g, K, 0.0, s);
 }
 
 void launch_restart(int64_t nv, KrylovVecs& K, void* s) {
   const int g = krylov_blocks(nv);
-  RF_LAUNCH(k_bicg_restart, g, BS, 0, s, nv, K.r, K.rh, K.p, K.v, K.partial);
+  RF_LAUNCH_PDL(k_bicg_restart, g, BS, 0, s, nv, K.r, K.rh, K.p, K.v, K.partial);
   fin(5, g, K, 0.0, s);
 }
 
@@ -531,6 +542,19 @@ __global__ void __launch_bounds__(BS) k_ie_residual(int64_t nv, const double2* _
     acc[0] += r.x * r.x + r.y * r.y;
   }
   block_reduce_store<1>(acc, partial);
+}
+
+// out = a + lam * d (pairs): a damped Newton update
+__global__ void k_axpby_pairs(int64_t nv, double2* __restrict__ out, const double2* __restrict__ a,
+                              const double2* __restrict__ d, double lam) {
+  for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
+    const double2 x = a[q], y = d[q];
+    out[q] = make_double2(x.x + lam * y.x, x.y + lam * y.y);
+  }
+}
+
+void launch_axpby_pairs(int64_t nv, double* out, const double* a, const double2* d, double lam, void* s) {
+  RF_LAUNCH(k_axpby_pairs, krylov_blocks(nv), BS, 0, s, nv, (double2*)out, (const double2*)a, d, lam);
 }
 
 __global__ void k_sum1(int nblk, const double* __restrict__ partial, double* __restrict__ out) {

@@ -190,6 +190,7 @@ template <int KIND, bool FINE, int NB, int CH>
 __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_residual(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                   const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                   typename V2<typename Ty<KIND>::T>::t* __restrict__ r) {
+  rf_pdl_begin();
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= L.d.nv) return;
   residual_point<KIND, FINE, NB, CH>(L, b, x, r, p);
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_jacobi(LevelOp L, const 
                                                 const typename V2<typename Ty<KIND>::T>::t* __restrict__ xin,
                                                 typename V2<typename Ty<KIND>::T>::t* __restrict__ xout, double omega,
                                                 int zero_x) {
+  rf_pdl_begin();
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= L.d.nv) return;
   jacobi_point<KIND, FINE, NB, CH>(L, b, xin, xout, omega, zero_x, p);
@@ -262,6 +264,7 @@ template <int KIND, bool FINE, int NB, int CH>
 __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                    typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
                                                    int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+  rf_pdl_begin();
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= count) return;
   gs_point<KIND, FINE, NB, CH>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
@@ -306,6 +309,7 @@ __global__ void __launch_bounds__(256) k_restrict(Dims df, Dims dc, const uint8_
                                                   const uint8_t* __restrict__ dmc,
                                                   const typename V2<T>::t* __restrict__ rf,
                                                   typename V2<T>::t* __restrict__ bc) {
+  rf_pdl_begin();
   int64_t pc = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pc >= dc.nv) return;
   restrict_point<T>(df, dc, dmf, dmc, rf, bc, pc);
@@ -346,6 +350,7 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
                                                  const uint8_t* __restrict__ dmc,
                                                  const typename V2<T>::t* __restrict__ xc,
                                                  typename V2<T>::t* __restrict__ xf) {
+  rf_pdl_begin();
   int64_t pf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pf >= df.nv) return;
   prolong_point<T>(df, dc, dmf, dmc, xc, xf, pf);
@@ -355,6 +360,7 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
                                                       const T* __restrict__ b, T* __restrict__ x) {
+  rf_pdl_begin();
   extern __shared__ double sb[];
   for (int t = threadIdx.x; t < N; t += blockDim.x) sb[t] = (double)b[t];
   __syncthreads();
@@ -841,6 +847,7 @@ __global__ void k_cast_f64_f32(const double* __restrict__ in, float* __restrict_
     out[t] = (float)in[t];
 }
 __global__ void k_cast_f32_f64(const float* __restrict__ in, double* __restrict__ out, int64_t n) {
+  rf_pdl_begin();
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     out[t] = (double)in[t];
 }
@@ -853,13 +860,13 @@ static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, 
   const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.batched) {
     if (L.d.nb == 27)
-      RF_LAUNCH((k_residual<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+      RF_LAUNCH_PDL((k_residual<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
     else
-      RF_LAUNCH((k_residual<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+      RF_LAUNCH_PDL((k_residual<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   } else if (L.d.nb == 27)
-    RF_LAUNCH((k_residual<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    RF_LAUNCH_PDL((k_residual<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   else
-    RF_LAUNCH((k_residual<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+    RF_LAUNCH_PDL((k_residual<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
 }
 
 template <int KIND, bool FINE>
@@ -870,13 +877,13 @@ static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xou
   const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.batched) {
     if (L.d.nb == 27)
-      RF_LAUNCH((k_jacobi<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
     else
-      RF_LAUNCH((k_jacobi<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   } else if (L.d.nb == 27)
-    RF_LAUNCH((k_jacobi<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   else
-    RF_LAUNCH((k_jacobi<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+    RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
 }
 
 // First forward sweep from x = 0: the neighbours of colour c that have a
@@ -909,13 +916,13 @@ static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool ze
     const int g = (int)((count + bs - 1) / bs);
     if (L.batched) {
       if (L.d.nb == 27)
-        RF_LAUNCH((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
       else
-        RF_LAUNCH((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
     } else if (L.d.nb == 27)
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
     else
-      RF_LAUNCH((k_gs_colour<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
   }
 }
 
@@ -946,17 +953,17 @@ void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, boo
 void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s) {
   const int g = (int)((C.d.nv + 255) / 256);
   if (F.kind == STORE_F64)
-    RF_LAUNCH(k_restrict<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
+    RF_LAUNCH_PDL(k_restrict<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
   else
-    RF_LAUNCH(k_restrict<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
+    RF_LAUNCH_PDL(k_restrict<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
 }
 
 void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s) {
   const int g = (int)((F.d.nv + 255) / 256);
   if (F.kind == STORE_F64)
-    RF_LAUNCH(k_prolong<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
+    RF_LAUNCH_PDL(k_prolong<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
   else
-    RF_LAUNCH(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
+    RF_LAUNCH_PDL(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
 }
 
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s) {
@@ -964,9 +971,9 @@ void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, vo
   const int g = (N + 255) / 256;
   const size_t smem = sizeof(double) * N;
   if (C.kind == STORE_F64)
-    RF_LAUNCH(k_coarse_solve<double>, g, 256, smem, s, N, Ainv, (const double*)b, (double*)x);
+    RF_LAUNCH_PDL(k_coarse_solve<double>, g, 256, smem, s, N, Ainv, (const double*)b, (double*)x);
   else
-    RF_LAUNCH(k_coarse_solve<float>, g, 256, smem, s, N, Ainv, (const float*)b, (float*)x);
+    RF_LAUNCH_PDL(k_coarse_solve<float>, g, 256, smem, s, N, Ainv, (const float*)b, (float*)x);
 }
 
 
@@ -1009,7 +1016,7 @@ void launch_cast_f64_to_f32(const double* in, float* out, int64_t n, void* s) {
   RF_LAUNCH(k_cast_f64_f32, grid_for(n, 256), 256, 0, s, in, out, n);
 }
 void launch_cast_f32_to_f64(const float* in, double* out, int64_t n, void* s) {
-  RF_LAUNCH(k_cast_f32_f64, grid_for(n, 256), 256, 0, s, in, out, n);
+  RF_LAUNCH_PDL(k_cast_f32_f64, grid_for(n, 256), 256, 0, s, in, out, n);
 }
 
 }  // namespace rf

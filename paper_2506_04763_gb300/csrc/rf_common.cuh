@@ -19,6 +19,7 @@
 // halo of `pad` pairs on both sides, so neighbour loads never leave the
 // allocation; a neighbour outside the grid is multiplied by a zero block.
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -90,6 +91,43 @@ inline int64_t vec_pad(const Dims& d) {
 void count_launch();
 int grid_for(int64_t n, int block, int max_blocks_per_sm = 8);
 int num_sms();
+// Programmatic dependent launch for the solve-path kernels (RF_PDL=0 turns it off).
+bool pdl_enabled();
+
+// Every kernel launched through RF_LAUNCH_PDL starts with rf_pdl_begin(): it
+// waits until the preceding kernel in the stream has completed and its writes
+// are visible (griddepcontrol.wait; a no-op without a programmatic
+// dependency), then lets the next kernel be launched early
+// (griddepcontrol.launch_dependents takes effect once every block of this grid
+// has issued it, i.e. when its last wave is resident, so the next grid's blocks
+// only fill SMs that this grid no longer needs, and they wait in turn).
+__device__ __forceinline__ void rf_pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch with the programmatic-stream-serialisation attribute (the kernel
+// must begin with rf_pdl_begin())
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args) {
+  count_launch();
+  if (!pdl_enabled()) {
+    kernel<<<grid, block, smem, stream>>>(std::forward<Args>(args)...);
+    return;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 }  // namespace rf
 
@@ -98,3 +136,6 @@ int num_sms();
     ::rf::count_launch();                                                 \
     kernel<<<(grid), (block), (smem), (cudaStream_t)(stream)>>>(__VA_ARGS__); \
   } while (0)
+
+#define RF_LAUNCH_PDL(kernel, grid, block, smem, stream, ...) \
+  ::rf::launch_pdl(kernel, dim3(grid), dim3(block), (size_t)(smem), (cudaStream_t)(stream), __VA_ARGS__)

@@ -154,6 +154,8 @@ void launch_ie_residual(int64_t nv, const double* F, const double* u, const doub
                         const double* sw, const double* sw_old, const uint8_t* dir, double rho_w, double rho_n,
                         double inv_h, double* R, double* out1, double* partial, void* s);
 
+void launch_axpby_pairs(int64_t nv, double* out, const double* a, const double2* d, double lam, void* s);
+
 // ---- LIMEX (krylov.cu) ----
 void launch_extrapolate(int64_t n2, int kappa, double* T, void* s);
 void launch_error_norms(const Dims& d, const double* h, const double* Tkk, const double* Tkk1, double* out4,

@@ -262,29 +262,33 @@ YEAR = 365.0 * 86400.0
 
 
 def case4_analogue(nverts=(129, 65), injecting=True):
-    """2D unit square (R3) standing in for Case 4's 500 m x 200 m section: four
-    equal layers stacked in y (bottom first) with Case 4's permeabilities,
-    p_d = 7.37 K^-0.43 Pa, Phi = 0.1 and its fluids and residual saturations,
-    under this model's Brooks-Corey laws (Case 4's own k_r tables are not part
-    of the model).  The state starts at S_w = 1 - S_nr (S_n = S_nr, immobile)
-    with p_w hydrostatic from p_n = 5e7 Pa at the bottom, and p_w is held there
-    (Dirichlet on the bottom row; Case 4 fixes p_n and S_w on that face).  NAPL
-    enters through the vertices of the bottom layer's centre line with
-    |x - 0.5| <= 0.05 at 0.05 pore volumes per year (mass rate rho_n Phi |Omega|
-    0.05 / year, unit thickness) when `injecting`."""
+    """Case 4's 500 m x 200 m vertical section (Table case4), with nverts
+    vertices: four equal layers stacked in y (bottom first) with Case 4's
+    permeabilities, p_d = 7.37 K^-0.43 Pa, Phi = 0.1 and its fluids and
+    residual saturations, under this model's Brooks-Corey laws (Case 4's own
+    k_r tables are not part of the model).  The state starts at S_w = 1 - S_nr
+    (S_n = S_nr, immobile) with p_w hydrostatic from p_n = 5e7 Pa at the
+    bottom, and p_w is held there (Dirichlet on the bottom row; Case 4 fixes
+    p_n and S_w on that face).  NAPL enters through the vertices of the bottom
+    layer's centre line with |x - 250 m| <= 25 m at 0.05 pore volumes per year
+    (unit thickness) when `injecting`."""
     c = CASE4
     dim = 2
-    n, h, _ = grid(dim, nverts)
+    n = (int(nverts[0]), int(nverts[1]), 1)
+    Lx, Ly = 500.0, 200.0
+    h = (Lx / (n[0] - 1), Ly / (n[1] - 1), 1.0)
     nc = ncells(dim, n)
     jc = (np.arange(nc) // (n[0] - 1))
     yc = (jc + 0.5) * h[1]
-    layer = np.minimum((yc * 4).astype(int), 3)
+    layer = np.minimum((yc / Ly * 4).astype(int), 3)
     K = np.asarray(c["K"])[layer]
     pd = 7.37 * K ** -0.43
     phi = np.full(nc, c["phi"])
-    x, y, _ = _coords(dim, n, h)
-    nv = x.size
-    bottom = np.rint(y / h[1]).astype(int) == 0
+    nv = n[0] * n[1]
+    x = (np.arange(nv) % n[0]) * h[0]
+    jv = np.arange(nv) // n[0]
+    y = jv * h[1]
+    bottom = jv == 0
     # S_e = 1 everywhere: p_c = p_d of the vertex's lowest-entry-pressure cell
     # (the p_dmin of the interface condition), so p_w = p_n - p_c at the bottom
     pd_bottom = pd[layer == 0].max()
@@ -292,18 +296,15 @@ def case4_analogue(nverts=(129, 65), injecting=True):
     u = np.empty(2 * nv)
     u[0::2] = pw
     u[1::2] = c["S_nr"]
-    dm = bottom.astype(np.uint8)
-    prob = problem(dim, nverts, K, phi, pd, u, dirmask=dm)
-    prob["pw_dir"] = np.where(bottom, pw, 0.0)
-    prob.update(rho_w=c["rho_w"], rho_n=c["rho_n"], mu_w=c["mu_w"], mu_n=c["mu_n"], S_wr=c["S_wr"],
-                S_nr=c["S_nr"], lam=c["lam"])
     q = np.zeros(2 * nv)
     if injecting:
-        j_src = int(round(0.125 / h[1]))
-        src = (np.rint(y / h[1]).astype(int) == j_src) & (np.abs(x - 0.5) <= 0.05 + 1e-12)
-        rate = c["rho_n"] * c["phi"] * 1.0 * c["rate_pv_per_year"] / YEAR
+        j_src = int(round(0.125 * Ly / h[1]))
+        src = (jv == j_src) & (np.abs(x - 0.5 * Lx) <= 0.05 * Lx + 1e-9)
+        rate = c["rho_n"] * c["phi"] * Lx * Ly * c["rate_pv_per_year"] / YEAR
         q[1::2] = np.where(src, rate / src.sum(), 0.0)
-    prob["q_in"] = q
+    prob = dict(dim=dim, n=n, h=h, g=(0.0, -GRAV, 0.0), K=K, phi=phi, pd=pd, dir=bottom.astype(np.uint8),
+                pw_dir=np.where(bottom, pw, 0.0), q_in=q, u0=u, rho_w=c["rho_w"], rho_n=c["rho_n"], mu_w=c["mu_w"],
+                mu_n=c["mu_n"], S_wr=c["S_wr"], S_nr=c["S_nr"], lam=c["lam"])
     prob.update(name="case4-analogue-%dx%d" % (n[0], n[1]), nlevels=levels_for(min(n[0], n[1])),
                 smoother="gs8")
     return prob

@@ -89,3 +89,23 @@ def test_ie_nonconvergence_keeps_the_state():
     assert info["status"] == rf.RF_ENOTCONV and info["newton"] == 1
     assert np.array_equal(u.cpu().numpy(), prob["u0"])
     g.close()
+
+
+@pytest.mark.parametrize("case,H", [("2d-17", 1000.0), ("3d-config5-9", 1000.0)])
+def test_ie_line_search_matches_oracle(case, H):
+    """Steps where the undamped Newton iteration fails and backtracking (at
+    most 4 halvings) converges: same Newton count and solution on both sides."""
+    prob = I.config5(9) if case == "3d-config5-9" else CASES[case]()
+    g = rf.Grid(prob)
+    u = torch.tensor(prob["u0"], device="cuda")
+    info = g.ie_step(u, H, atol=0.0, rtol=1e-9, max_newton=40, gmg=rf.gmg_opts(2, precision="fp64"),
+                     lin_rtol=1e-12, max_it=400, max_ls=4)
+    torch.cuda.synchronize()
+    u_o, inf_o = O.ie_step(O.Model(prob), prob["u0"], H, atol=0.0, rtol=1e-9, max_newton=40, nlevels=2,
+                           lin_rtol=1e-12, lin_maxit=400, max_ls=4)
+    assert info["status"] == 0 and inf_o["status"] == 0, (info, inf_o)
+    assert info["newton"] == inf_o["newton"]
+    us = u.cpu().numpy()
+    assert np.abs(us[0::2] - u_o[0::2]).max() <= 1e-8 * np.abs(u_o[0::2]).max()
+    assert np.abs(us[1::2] - u_o[1::2]).max() <= 1e-8
+    g.close()

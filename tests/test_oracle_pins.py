@@ -742,3 +742,22 @@ def test_case1_implicit_euler_errors_match_the_paper(oracle):
     assert abs(nst - steps) <= 1
     assert H.lp_error_1d(xv, sw[0], exact, 1) == pytest.approx(L1, rel=0.03)
     assert H.lp_error_1d(xv, sw[0], exact, 2) == pytest.approx(L2, rel=0.03)
+
+
+def test_ie_line_search_converges_where_plain_newton_fails(oracle):
+    """A 1000 s step of the DNAPL-inlet recipe at 9^3: undamped Newton does
+    not converge in 40 iterations, backtracking (at most 4 halvings) does, and
+    the result solves the implicit Euler equations, checked here from the
+    oracle's flux residual and storage rather than the step's own report."""
+    p = I.config5(9)
+    m = oracle.Model(p)
+    H = 1000.0
+    _, plain = oracle.ie_step(m, p["u0"], H, nlevels=2, atol=0.0, rtol=1e-9, lin_rtol=1e-12, max_newton=40)
+    assert plain["status"] != 0
+    u1, inf = oracle.ie_step(m, p["u0"], H, nlevels=2, atol=0.0, rtol=1e-9, lin_rtol=1e-12, max_newton=40, max_ls=4)
+    assert inf["status"] == 0, inf
+    F = oracle.assemble(m, u1, jacobian=False)[0]
+    dm = oracle.storage(m, u1) - oracle.storage(m, p["u0"])
+    R = F - dm.ravel() / H
+    R[0::2][p["dir"].astype(bool)] = F[0::2][p["dir"].astype(bool)]
+    assert np.linalg.norm(R) <= 1e-9 * inf["res0"] * 1.0000001
