@@ -186,8 +186,10 @@ __global__ void k_vertex_state(Dims d, Phys ph, const double2* __restrict__ u, c
   pc[p] = c;
   dpc[p] = -(pdm * dJ) / ph.den;
   pn[p] = __dadd_rn(uv.x, c);
-  krw[p] = k;
-  dkrw[p] = -dk / ph.den;
+  // the upwinded water mobility lambda_w = k_rw / mu_w and its S_n-derivative,
+  // divided here once per vertex instead of once per face visit
+  krw[p] = k / ph.mu_w;
+  dkrw[p] = (-dk / ph.den) / ph.mu_w;
 }
 
 // ---------------------------------------------------------------- K1 / K1r
@@ -221,6 +223,20 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
   if (in.q_in) { double2 q = in.q_in[p]; F0 = q.x; F1 = q.y; }
   const double neg_inv_den = -1.0 / ph.den;
   const bool darcy = (ph.scheme & SCHEME_DARCY_UPWIND) != 0;
+  // d G / d q_q = +-w / h_k takes one of DIM magnitudes per axis (w is a
+  // product of DIM-1 factors 3/4 or 1/4): divide once per thread.  gtab[k][m]
+  // = w / h_k with m = the number of 1/4 factors; IEEE division is correctly
+  // rounded and sign-symmetric, so +-gtab equals the per-corner (+-w) / h_k.
+  double gtab[DIM][DIM];
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk)
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      double w = 1.0;
+#pragma unroll
+      for (int t = 0; t < DIM - 1; ++t) w = w * (t < m ? 0.25 : 0.75);
+      gtab[kk][m] = w / ph.h[kk];
+    }
 
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
@@ -293,7 +309,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       const bool wa = darcy ? Tpw >= 0.0 : Tw >= 0.0, na = Tn >= 0.0;
       const int64_t vw = wa ? vq[a] : vq[b];
       const int64_t vn = na ? vq[a] : vq[b];
-      const double lw_up = in.krw[vw] / ph.mu_w;
+      const double lw_up = in.krw[vw];   // k_rw / mu_w
       double kM, dkM;
       krw_of(ph.lam, SeM, kM, dkM);
       const double lwM = kM / ph.mu_w;
@@ -306,16 +322,16 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       F0 += sgn * Fw;
       F1 += sgn * Fn;
       if (WANT_J) {
-        const double dlw_up = in.dkrw[vw] / ph.mu_w;
+        const double dlw_up = in.dkrw[vw];
         const double dlwM_dSeM = dkM / ph.mu_w;
         const double dln_up = dkn * dsh * neg_inv_den / ph.mu_n;
         const int qw = wa ? a : b, qn = na ? a : b;
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          double w = 1.0;
+          int nq = 0;   // number of 1/4 factors of this corner's weight
 #pragma unroll
-          for (int t = 0; t < DIM - 1; ++t) w = w * ((((q >> oth[t]) & 1) == o[t]) ? 0.75 : 0.25);
-          const double gq = (((q >> kk) & 1) ? w : -w) / ph.h[kk];
+          for (int t = 0; t < DIM - 1; ++t) nq += (((q >> oth[t]) & 1) == o[t]) ? 0 : 1;
+          const double gq = ((q >> kk) & 1) ? gtab[kk][nq] : -gtab[kk][nq];
           const double dT = -KA * gq;
           const double dlwM = wM[q] * dlwM_dSeM * neg_inv_den;
           const double d0 = ph.rho_w * lw_up * dT;

@@ -26,7 +26,21 @@ template <> struct Ty<STORE_F64> { typedef double T; typedef double S; };
 template <> struct Ty<STORE_F32> { typedef float T; typedef float S; };
 template <> struct Ty<STORE_F16> { typedef float T; typedef __half S; };
 
-// Streaming read of matrix data: read-only path, do not keep in L1.
+// Streaming read of matrix data: read-only path, not kept in L1, and first in
+// line for eviction from L2 (an L2 cache-hint policy), so that the x vector,
+// which every colour launch gathers from its neighbours, keeps its place
+// there.  -DRF_NO_L2_HINTS builds the loads without the L2 policies.
+__device__ __forceinline__ uint64_t l2_policy_first() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_last() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+#ifdef RF_NO_L2_HINTS
 __device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
   float4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
@@ -43,6 +57,41 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2* p) {
   asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
+template <typename V>
+__device__ __forceinline__ V ld_keep(const V* p) { return *p; }
+#else
+__device__ __forceinline__ float4 ld_stream_f4(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p), "l"(l2_policy_first()));
+  return v;
+}
+__device__ __forceinline__ double2 ld_stream_d2(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(l2_policy_first()));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+               : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(l2_policy_first()));
+  return v;
+}
+// Neighbour values of x: kept in L1 (neighbouring threads share them) and
+// last in line for eviction from L2.  Only values this launch does not write
+// are read this way (GS reads other colours; residual / Jacobi read an input).
+__device__ __forceinline__ float2 ld_keep(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(l2_policy_last()));
+  return v;
+}
+__device__ __forceinline__ double2 ld_keep(const double2* p) {
+  double2 v;
+  asm("ld.global.nc.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(l2_policy_last()));
+  return v;
+}
+#endif
 
 template <int KIND>
 __device__ __forceinline__ void load_block(const void* A, int64_t nv, int b, int64_t p, const float4& sc,
@@ -118,7 +167,7 @@ __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p,
       const bool skip = (skip_centre && b == C) || ((skipmask >> b) & 1u);
       if (!skip) {
         load_block<KIND>(L.A, L.d.nv, b, p, sc, a[c]);
-        xv[c] = x[p + (par ? L.nb.off[1][b] : L.nb.off[0][b])];
+        xv[c] = ld_keep(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]));
       } else {
         a[c][0] = a[c][1] = a[c][2] = a[c][3] = 0;
         xv[c].x = 0;
