@@ -33,6 +33,8 @@
 // and, in each, the d faces that touch it, and accumulates its own block row
 // (27 or 9 2x2 blocks) in shared memory; no atomics, no second pass.  The row
 // is written once with 1 KB-per-warp coalesced stores.
+#include <cstdlib>
+
 #include "rf_common.cuh"
 #include "rf_kernels.h"
 
@@ -384,6 +386,218 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
   }
 }
 
+// ---------------------------------------------------------------- K1, one thread per element
+// Each SCV face is evaluated once, by the thread of its element, and its flux
+// and derivatives go to both end vertices (a: -, b: +).  The one-thread-per-
+// vertex kernel above evaluates every face twice, once from each end, and K1
+// is FP64-pipe-bound on GB300, so this halves most of its FP64 work.
+// Elements are processed in 2^DIM colours (parities of their lower corner):
+// elements of one colour share no vertex, so each thread owns the rows of its
+// corners for the launch and adds into them without atomics, face by face in
+// a fixed order (deterministic).  J is zeroed before the first colour; the
+// adds go straight to global memory (coalesced across the warp: neighbouring
+// threads own neighbouring rows), which keeps the kernel free of shared
+// memory and its occupancy at what its registers allow (K1 is FP64-latency-
+// bound below ~8 warps per SM).  k_assemble_finish then adds the sources and
+// applies the Dirichlet rows and M.  The face arithmetic is
+// the vertex kernel's, expression by expression, so every upwind, cap and
+// clamp decision and every flux and derivative value are bitwise the same;
+// only the order in which a row's contributions are summed differs.
+template <int DIM, bool WANT_J>
+__global__ void __launch_bounds__(128) k_assemble_cells(Dims d, Phys ph, AsmIn in, int colour, int64_t ncol,
+                                                        double2* __restrict__ F, double* __restrict__ J) {
+  constexpr int NC = 1 << DIM, NE = 1 << (DIM - 1);
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ncol) return;
+  const int cx = d.nx - 1, cy = d.ny - 1;
+  const int px = colour & 1, py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
+  const int nxp = (cx - px + 1) / 2, nyp = (cy - py + 1) / 2;
+  const int64_t line = t / nxp;
+  const int ci = 2 * (int)(t - line * nxp) + px;
+  const int cj = 2 * (int)(line % nyp) + py;
+  const int ck = DIM == 3 ? 2 * (int)(line / nyp) + pz : 0;
+  const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+  const double Kc = in.K[cell], pdc = in.pd[cell];
+  const double neg_inv_den = -1.0 / ph.den;
+  const bool darcy = (ph.scheme & SCHEME_DARCY_UPWIND) != 0;
+  double gtab[DIM][DIM];   // +-w / h_k by the number of 1/4 factors (see k_assemble)
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk)
+#pragma unroll
+    for (int m = 0; m < DIM; ++m) {
+      double w = 1.0;
+#pragma unroll
+      for (int tt = 0; tt < DIM - 1; ++tt) w = w * (tt < m ? 0.25 : 0.75);
+      gtab[kk][m] = w / ph.h[kk];
+    }
+  int64_t vq[NC];
+  double se[NC], pnq[NC], pcq[NC], dpcq[NC], pwq[NC], Fl[NC][2];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    vq[q] = pidx(d, ci + (q & 1), cj + ((q >> 1) & 1), DIM == 3 ? ck + ((q >> 2) & 1) : 0);
+    se[q] = in.Se[vq[q]];
+    pnq[q] = in.pn[vq[q]];
+    pcq[q] = in.pc[vq[q]];
+    dpcq[q] = in.dpc[vq[q]];
+    pwq[q] = darcy ? in.u[vq[q]].x : 0.0;
+    Fl[q][0] = 0.0;
+    Fl[q][1] = 0.0;
+  }
+#pragma unroll
+  for (int kk = 0; kk < DIM; ++kk) {
+    int oth[2], no = 0;
+#pragma unroll
+    for (int m = 0; m < DIM; ++m)
+      if (m != kk) oth[no++] = m;
+    double Af = 1.0;
+#pragma unroll
+    for (int tt = 0; tt < DIM - 1; ++tt) Af = __dmul_rn(Af, __dmul_rn(ph.h[oth[tt]], 0.5));
+    const double KA = __dmul_rn(Kc, Af);
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+      int o[2] = {0, 0};
+#pragma unroll
+      for (int tt = 0; tt < DIM - 1; ++tt) o[tt] = (e >> tt) & 1;
+      int a = 0;
+#pragma unroll
+      for (int tt = 0; tt < DIM - 1; ++tt) a |= o[tt] << oth[tt];
+      const int b = a | (1 << kk);
+      double gpn = 0.0, gpc = 0.0, gpw = 0.0;
+#pragma unroll
+      for (int e2 = 0; e2 < NE; ++e2) {
+        int o2[2] = {e2 & 1, (e2 >> 1) & 1};
+        double w = 1.0;
+        int a2 = 0;
+#pragma unroll
+        for (int tt = 0; tt < DIM - 1; ++tt) {
+          w = w * (o2[tt] == o[tt] ? 0.75 : 0.25);
+          a2 |= o2[tt] << oth[tt];
+        }
+        const int b2 = a2 | (1 << kk);
+        gpn = __dadd_rn(gpn, __dmul_rn(w, __dsub_rn(pnq[b2], pnq[a2])));
+        gpc = __dadd_rn(gpc, __dmul_rn(w, __dsub_rn(pcq[b2], pcq[a2])));
+        if (darcy) gpw = __dadd_rn(gpw, __dmul_rn(w, __dsub_rn(pwq[b2], pwq[a2])));
+      }
+      gpn = __ddiv_rn(gpn, ph.h[kk]);
+      gpc = __ddiv_rn(gpc, ph.h[kk]);
+      gpw = __ddiv_rn(gpw, ph.h[kk]);
+      double wM[NC], SeM = 0.0;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        double w = 0.5;
+#pragma unroll
+        for (int tt = 0; tt < DIM - 1; ++tt) w = w * ((((q >> oth[tt]) & 1) == o[tt]) ? 0.75 : 0.25);
+        wM[q] = w;
+        SeM = __dadd_rn(SeM, __dmul_rn(w, se[q]));
+      }
+      const double Tw = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_w, ph.g[kk])));
+      const double Tn = __dmul_rn(-KA, __dsub_rn(gpn, __dmul_rn(ph.rho_n, ph.g[kk])));
+      const double Tc = __dmul_rn(-KA, gpc);
+      const double Tpw = __dmul_rn(-KA, __dsub_rn(gpw, __dmul_rn(ph.rho_w, ph.g[kk])));
+      const bool wa = darcy ? Tpw >= 0.0 : Tw >= 0.0, na = Tn >= 0.0;
+      const int qw = wa ? a : b, qn = na ? a : b;
+      const int64_t vw = wa ? vq[a] : vq[b], vn = na ? vq[a] : vq[b];   // selects, not indexing
+      const double lw_up = in.krw[vw];   // k_rw / mu_w
+      double kM, dkM;
+      krw_of(ph.lam, SeM, kM, dkM);
+      const double lwM = kM / ph.mu_w;
+      double sh, dsh, kn, dkn;
+      shat_of(ph.lam, na ? se[a] : se[b], pdc, in.pdmin[vn], sh, dsh);
+      krn_of(ph.lam, sh, kn, dkn);
+      const double ln_up = kn / ph.mu_n;
+      const double Fw = darcy ? ph.rho_w * (lw_up * Tpw) : ph.rho_w * (lw_up * Tw - lwM * Tc);
+      const double Fn = ph.rho_n * (ln_up * Tn);
+      Fl[a][0] -= Fw;
+      Fl[a][1] -= Fn;
+      Fl[b][0] += Fw;
+      Fl[b][1] += Fn;
+      if (WANT_J) {
+        const double dlw_up = in.dkrw[vw];
+        const double dlwM_dSeM = dkM / ph.mu_w;
+        const double dln_up = dkn * dsh * neg_inv_den / ph.mu_n;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          int nq = 0;
+#pragma unroll
+          for (int tt = 0; tt < DIM - 1; ++tt) nq += (((q >> oth[tt]) & 1) == o[tt]) ? 0 : 1;
+          const double gq = ((q >> kk) & 1) ? gtab[kk][nq] : -gtab[kk][nq];
+          const double dT = -KA * gq;
+          const double dlwM = wM[q] * dlwM_dSeM * neg_inv_den;
+          const double d0 = ph.rho_w * lw_up * dT;
+          const double d1 = darcy ? ph.rho_w * (q == qw ? dlw_up * Tpw : 0.0)
+                                  : ph.rho_w * ((q == qw ? dlw_up * Tw : 0.0) + lw_up * dT * dpcq[q] - dlwM * Tc -
+                                                lwM * dT * dpcq[q]);
+          const double d2 = ph.rho_n * ln_up * dT;
+          const double d3 = ph.rho_n * ((q == qn ? dln_up * Tn : 0.0) + ln_up * dT * dpcq[q]);
+          const int bia = blk_of(DIM, (q & 1) - (a & 1), ((q >> 1) & 1) - ((a >> 1) & 1),
+                                 DIM == 3 ? ((q >> 2) & 1) - ((a >> 2) & 1) : 0);
+          const int bib = blk_of(DIM, (q & 1) - (b & 1), ((q >> 1) & 1) - ((b >> 1) & 1),
+                                 DIM == 3 ? ((q >> 2) & 1) - ((b >> 2) & 1) : 0);
+          double2* ja = reinterpret_cast<double2*>(J + ((int64_t)bia * d.nv + vq[a]) * 4);
+          double2* jb = reinterpret_cast<double2*>(J + ((int64_t)bib * d.nv + vq[b]) * 4);
+          double2 a0 = ja[0], a1 = ja[1], b0 = jb[0], b1 = jb[1];
+          a0.x -= d0; a0.y -= d1; a1.x -= d2; a1.y -= d3;
+          b0.x += d0; b0.y += d1; b1.x += d2; b1.y += d3;
+          ja[0] = a0; ja[1] = a1;
+          jb[0] = b0; jb[1] = b1;
+        }
+      }
+    }
+  }
+  // add this element's residual contributions to its corners' rows
+#pragma unroll
+  for (int r = 0; r < NC; ++r) {
+    double2 f = F[vq[r]];
+    f.x += Fl[r][0];
+    f.y += Fl[r][1];
+    F[vq[r]] = f;
+  }
+}
+
+// After all colours: sources, Dirichlet p_w rows (0 = p_dir - p_w: J row -e,
+// M row 0) and the mass diagonal, per vertex.
+template <int DIM, bool WANT_J>
+__global__ void k_assemble_finish(Dims d, Phys ph, AsmIn in, double2* __restrict__ F, double* __restrict__ J,
+                                  double2* __restrict__ mdiag) {
+  constexpr int NC = 1 << DIM, NB = DIM == 3 ? 27 : 9;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= d.nv) return;
+  double2 f = F[p];
+  if (in.q_in) {
+    const double2 q = in.q_in[p];
+    f.x += q.x;
+    f.y += q.y;
+  }
+  const bool dirv = in.dir[p] != 0;
+  if (dirv) f.x = in.pw_dir[p] - in.u[p].x;
+  F[p] = f;
+  if (!WANT_J) return;
+  double pv = in.phiv[p];
+  if (ph.scheme & SCHEME_SHAT_STORAGE) {
+    int i, j, k;
+    pcoords(d, p, i, j, k);
+    const int cx = d.nx - 1, cy = d.ny - 1, cz = DIM == 3 ? d.nz - 1 : 1;
+    const double frac = DIM == 3 ? 0.125 : 0.25, se = in.Se[p], pdm = in.pdmin[p];
+    pv = 0.0;
+    for (int c = 0; c < NC; ++c) {
+      const int ci = i - (c & 1), cj = j - ((c >> 1) & 1), ck = DIM == 3 ? k - ((c >> 2) & 1) : 0;
+      if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
+      const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
+      double sh, dsh;
+      shat_of(ph.lam, se, in.pd[cell], pdm, sh, dsh);
+      pv += in.phi[cell] * in.vol * frac * dsh;
+    }
+  }
+  mdiag[p] = make_double2(dirv ? 0.0 : -ph.rho_w * pv, ph.rho_n * pv);
+  if (dirv) {
+    const int centre = DIM == 3 ? 13 : 4;
+    for (int bi = 0; bi < NB; ++bi) {
+      double2* dst = reinterpret_cast<double2*>(J + ((int64_t)bi * d.nv + p) * 4);
+      dst[0] = make_double2(bi == centre ? -1.0 : 0.0, 0.0);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- storage (S hat variant)
 // sw[p] = sum over the sub-control volumes b_i^j of vertex p of Phi_j |b_i^j|
 // S_w(b_i^j), with S_w = S_wr + S hat_e (1 - S_wr - S_nr) (Eq. (hSw)).
@@ -428,6 +642,36 @@ void launch_perm_scalar_to_p(const Dims& d, const double* nat, double* out, void
   RF_LAUNCH(k_perm_scalar_to_p, (int)((d.nv + 255) / 256), 256, 0, s, d, nat, out);
 }
 
+template <int DIM, bool WANT_J>
+static void cells_t(const Dims& d, const Phys& ph, const AsmIn& in, const AsmArrays& a, void* s) {
+  const int BS = 128;
+  const int NC = 1 << DIM;
+  const size_t smem = 0;
+  if (WANT_J) cudaMemsetAsync(a.J, 0, sizeof(double) * 4 * (size_t)d.nb * d.nv, (cudaStream_t)s);
+  cudaMemsetAsync(a.F, 0, sizeof(double) * 2 * (size_t)d.nv, (cudaStream_t)s);
+  const int cx = d.nx - 1, cy = d.ny - 1, cz = DIM == 3 ? d.nz - 1 : 1;
+  for (int c = 0; c < NC; ++c) {
+    const int px = c & 1, py = (c >> 1) & 1, pz = (c >> 2) & 1;
+    const int64_t ncol = (int64_t)((cx - px + 1) / 2) * ((cy - py + 1) / 2) * (DIM == 3 ? (cz - pz + 1) / 2 : 1);
+    if (ncol <= 0) continue;
+    RF_LAUNCH((k_assemble_cells<DIM, WANT_J>), (int)((ncol + BS - 1) / BS), BS, smem, s, d, ph, in, c, ncol,
+              (double2*)a.F, a.J);
+  }
+  RF_LAUNCH((k_assemble_finish<DIM, WANT_J>), (int)((d.nv + 255) / 256), 256, 0, s, d, ph, in, (double2*)a.F, a.J,
+            (double2*)a.mdiag);
+}
+
+static void launch_assemble_cells(const Dims& d, const Phys& ph, const AsmIn& in, const AsmArrays& a, bool want_j,
+                                  void* s) {
+  if (d.dim == 3) {
+    if (want_j) cells_t<3, true>(d, ph, in, a, s);
+    else cells_t<3, false>(d, ph, in, a, s);
+  } else {
+    if (want_j) cells_t<2, true>(d, ph, in, a, s);
+    else cells_t<2, false>(d, ph, in, a, s);
+  }
+}
+
 cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays& a, bool want_j, void* s) {
   Phys ph;
   ph.rho_w = pp.rho_w; ph.rho_n = pp.rho_n; ph.mu_w = pp.mu_w; ph.mu_n = pp.mu_n;
@@ -443,6 +687,11 @@ cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays
   in.dkrw = a.dkrw; in.pdmin = a.pdmin; in.phiv = a.phiv; in.K = a.K; in.pd = a.pd; in.phi = a.phi;
   in.vol = a.vol; in.dir = a.dir;
   in.pw_dir = a.pw_dir; in.q_in = (const double2*)a.q_in;
+  static const bool per_vertex = getenv("RF_ASM_VERTEX") && atoi(getenv("RF_ASM_VERTEX")) != 0;
+  if (!per_vertex) {
+    launch_assemble_cells(d, ph, in, a, want_j, s);
+    return cudaGetLastError();
+  }
   const int BS = 128;
   const int grid = (int)((d.nv + BS - 1) / BS);
   const int nb = d.dim == 3 ? 27 : 9;

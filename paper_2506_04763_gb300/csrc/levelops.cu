@@ -406,6 +406,8 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
 }
 
 // ----------------------------------------------------------------- coarsest solve
+// x = A^-1 b on the coarsest level: one warp per row of the explicit
+// inverse, lanes over its columns (coalesced), FP64 sums.
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
                                                       const T* __restrict__ b, T* __restrict__ x) {
@@ -413,12 +415,15 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __res
   extern __shared__ double sb[];
   for (int t = threadIdx.x; t < N; t += blockDim.x) sb[t] = (double)b[t];
   __syncthreads();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (r >= N) return;
   const double* row = Ainv + (int64_t)r * N;
   double s = 0.0;
-  for (int c = 0; c < N; ++c) s += row[c] * sb[c];
-  x[r] = (T)s;
+  for (int c = lane; c < N; c += 32) s += row[c] * sb[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[r] = (T)s;
 }
 
 // ----------------------------------------------------------------- V-cycle tail
@@ -767,31 +772,36 @@ __global__ void k_dense(Dims d, Nbr nb, const double* __restrict__ J, const doub
   D[(2 * p + 1) * N + 2 * q + 1] = e3;
 }
 
-// LU with partial pivoting in one CTA (first maximal pivot on ties).
+// LU with partial pivoting in one CTA (first maximal pivot on ties).  Per
+// column: pick the pivot from the candidates gathered while updating the
+// previous column, swap rows, then each warp takes whole rows of the trailing
+// matrix (multiplier by lane 0, row update over lanes, coalesced) and records
+// the next column's candidate.  Four barriers per column.
 __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int* __restrict__ piv,
                                              int* __restrict__ status) {
   __shared__ double sval[32];
   __shared__ int sidx[32];
   __shared__ int sp;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double best = -1.0;
+  int bi = N;
+  for (int r = tid; r < N; r += nt) {
+    const double v = fabs(D[(int64_t)r * N]);
+    if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+  }
   for (int c = 0; c < N; ++c) {
-    double best = -1.0;
-    int bi = N;
-    for (int r = c + tid; r < N; r += nt) {
-      double v = fabs(D[(int64_t)r * N + c]);
-      if (v > best || (v == best && r < bi)) { best = v; bi = r; }
-    }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      const double ov = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
     }
-    if ((tid & 31) == 0) { sval[tid >> 5] = best; sidx[tid >> 5] = bi; }
+    if (lane == 0) { sval[warp] = best; sidx[warp] = bi; }
     __syncthreads();
     if (tid == 0) {
       double bv = sval[0];
       int bidx = sidx[0];
-      for (int w = 1; w < (nt + 31) / 32; ++w)
+      for (int w = 1; w < nw; ++w)
         if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
       if (!(bv > 0.0)) { status[0] = 1; bidx = c; }
       sp = bidx;
@@ -801,45 +811,68 @@ __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int*
     const int pr = sp;
     if (pr != c)
       for (int t = tid; t < N; t += nt) {
-        double tmp = D[(int64_t)c * N + t];
+        const double tmp = D[(int64_t)c * N + t];
         D[(int64_t)c * N + t] = D[(int64_t)pr * N + t];
         D[(int64_t)pr * N + t] = tmp;
       }
     __syncthreads();
     const double dc = D[(int64_t)c * N + c];
-    for (int r = c + 1 + tid; r < N; r += nt) D[(int64_t)r * N + c] = (dc != 0.0) ? D[(int64_t)r * N + c] / dc : 0.0;
-    __syncthreads();
-    const int rem = N - c - 1;
-    for (int64_t e = tid; e < (int64_t)rem * rem; e += nt) {
-      const int r = c + 1 + (int)(e / rem), t = c + 1 + (int)(e % rem);
-      D[(int64_t)r * N + t] -= D[(int64_t)r * N + c] * D[(int64_t)c * N + t];
+    best = -1.0;
+    bi = N;
+    for (int r = c + 1 + warp; r < N; r += nw) {
+      double* Dr = D + (int64_t)r * N;
+      const double l = (dc != 0.0) ? Dr[c] / dc : 0.0;
+      for (int t = c + 1 + lane; t < N; t += 32) Dr[t] -= l * D[(int64_t)c * N + t];
+      __syncwarp();
+      if (lane == 0) {
+        Dr[c] = l;
+        if (c + 1 < N) {
+          const double v = fabs(Dr[c + 1]);
+          if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+        }
+      }
     }
     __syncthreads();
   }
 }
 
-// column `col` of the inverse from the LU factors: solve L U x = P e_col
-__global__ void k_lu_inverse_cols(int N, const double* __restrict__ LU, const int* __restrict__ piv,
-                                  double* __restrict__ work, double* __restrict__ Ainv) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+// Columns of the inverse from the LU factors, one warp per column: x = P e_col,
+// then L y = x and U z = y row by row, each row's dot product over the lanes
+// with x kept in shared memory.
+__global__ void __launch_bounds__(128) k_lu_inverse_cols(int N, const double* __restrict__ LU,
+                                                         const int* __restrict__ piv, double* __restrict__ Ainv) {
+  extern __shared__ double xs_all[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * (blockDim.x >> 5) + warp;
   if (col >= N) return;
-  double* x = work + (int64_t)col * N;
-  for (int r = 0; r < N; ++r) x[r] = (r == col) ? 1.0 : 0.0;
-  for (int c = 0; c < N; ++c) {
-    const int p = piv[c];
-    if (p != c) { double t = x[c]; x[c] = x[p]; x[p] = t; }
-  }
-  for (int r = 0; r < N; ++r) {
-    double s = x[r];
-    for (int c = 0; c < r; ++c) s -= LU[(int64_t)r * N + c] * x[c];
-    x[r] = s;
+  double* x = xs_all + (int64_t)warp * N;
+  for (int r = lane; r < N; r += 32) x[r] = (r == col) ? 1.0 : 0.0;
+  __syncwarp();
+  if (lane == 0)
+    for (int c = 0; c < N; ++c) {
+      const int p = piv[c];
+      if (p != c) { const double t = x[c]; x[c] = x[p]; x[p] = t; }
+    }
+  __syncwarp();
+  for (int r = 1; r < N; ++r) {
+    const double* Lr = LU + (int64_t)r * N;
+    double s = 0.0;
+    for (int c = lane; c < r; c += 32) s += Lr[c] * x[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] -= s;
+    __syncwarp();
   }
   for (int r = N - 1; r >= 0; --r) {
-    double s = x[r];
-    for (int c = r + 1; c < N; ++c) s -= LU[(int64_t)r * N + c] * x[c];
-    x[r] = s / LU[(int64_t)r * N + r];
+    const double* Ur = LU + (int64_t)r * N;
+    double s = 0.0;
+    for (int c = r + 1 + lane; c < N; c += 32) s += Ur[c] * x[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[r] = (x[r] - s) / Ur[r];
+    __syncwarp();
   }
-  for (int r = 0; r < N; ++r) Ainv[(int64_t)r * N + col] = x[r];
+  for (int r = lane; r < N; r += 32) Ainv[(int64_t)r * N + col] = x[r];
 }
 
 // natural-order FP64 export of a level operator
@@ -1017,7 +1050,7 @@ void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf
 
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s) {
   const int N = (int)(2 * C.d.nv);
-  const int g = (N + 255) / 256;
+  const int g = (N + 7) / 8;   // 8 rows (warps) per 256-thread block
   const size_t smem = sizeof(double) * N;
   if (C.kind == STORE_F64)
     RF_LAUNCH_PDL(k_coarse_solve<double>, g, 256, smem, s, N, Ainv, (const double*)b, (double*)x);
@@ -1051,8 +1084,11 @@ void launch_dense_coarsest(const Dims& d, const Nbr& nb, const double* Jc, const
 }
 
 cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status, void* s) {
+  (void)work;
   RF_LAUNCH(k_lu, 1, 1024, 0, s, N, D, piv, status);
-  RF_LAUNCH(k_lu_inverse_cols, (N + 31) / 32, 32, 0, s, N, D, piv, work, Ainv);
+  const size_t smem = sizeof(double) * 4 * (size_t)N;   // 4 warps per block, one x each (128 KB at N = 4096)
+  cudaFuncSetAttribute(k_lu_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  RF_LAUNCH(k_lu_inverse_cols, (N + 3) / 4, 128, smem, s, N, D, piv, Ainv);
   return cudaGetLastError();
 }
 
