@@ -94,7 +94,8 @@ struct Level {
 //     thread's chain of round trips), equal at 129^3; Jacobi 2.51 -> 2.27 ms
 //     on the finest level and 0.32 -> 0.29 ms at 129^3.
 //   FP64 storage: equal on the two finest levels, batched 1.2-1.6x faster on
-//     the levels below.
+//     the levels below.  (On the finest level of the 65^3 FP64 LIMEX step,
+//     batched Jacobi measured no faster either.)
 //   FP16 storage: batched loads are 1.8-2x slower on the two finest levels
 //     and equal below, so never.
 static void default_shape(Level& Lv, int l, int kind) {
@@ -785,26 +786,27 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     const Level& C = g->L[g->nl - 1];
     const int N = (int)(2 * C.d.nv);
     if (N > 4096) { dfree_all(g, g->gbufs, s); return fail(RF_EINVAL, "coarsest level too large (%d unknowns): use more levels", N); }
+    // all shifts at once: one LU per CTA, the inverse columns of every shift in one grid
     double* D;
-    double* work;
     int* piv;
     int* status;
-    GNEED(D = (double*)dalloc(g, sizeof(double) * N * N, s, true));
-    GNEED(work = (double*)dalloc(g, sizeof(double) * N * N, s, true));
-    GNEED(piv = (int*)dalloc(g, sizeof(int) * N, s, true));
-    GNEED(status = (int*)dalloc(g, sizeof(int), s, true));
+    const size_t NN = (size_t)N * N;
+    GNEED(D = (double*)dalloc(g, sizeof(double) * NN * nshift, s, true));
+    GNEED(piv = (int*)dalloc(g, sizeof(int) * N * nshift, s, true));
+    GNEED(status = (int*)dalloc(g, sizeof(int) * nshift, s, true));
+    CU(cudaMemsetAsync(D, 0, sizeof(double) * NN * nshift, (cudaStream_t)s));
+    CU(cudaMemsetAsync(status, 0, sizeof(int) * nshift, (cudaStream_t)s));
     for (int j = 0; j < nshift; ++j) {
-      GNEED(g->Ainv[j] = (double*)dalloc(g, sizeof(double) * N * N, s, true));
-      CU(cudaMemsetAsync(D, 0, sizeof(double) * N * N, (cudaStream_t)s));
-      CU(cudaMemsetAsync(status, 0, sizeof(int), (cudaStream_t)s));
-      if (g->nl == 1) launch_dense_coarsest(C.d, C.nb, g->J, nullptr, g->mdiag, true, shifts[j], D, s);
-      else launch_dense_coarsest(C.d, C.nb, C.Jc, C.Mc, nullptr, false, shifts[j], D, s);
-      CU(launch_dense_inverse(N, D, g->Ainv[j], piv, work, status, s));
-      int hst = 0;
-      CU(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)s));
-      CU(cudaStreamSynchronize((cudaStream_t)s));
-      if (hst) { dfree_all(g, g->gbufs, s); return fail(RF_ENONFINITE, "coarsest operator is singular (shift %d)", j); }
+      GNEED(g->Ainv[j] = (double*)dalloc(g, sizeof(double) * NN, s, true));
+      if (g->nl == 1) launch_dense_coarsest(C.d, C.nb, g->J, nullptr, g->mdiag, true, shifts[j], D + NN * j, s);
+      else launch_dense_coarsest(C.d, C.nb, C.Jc, C.Mc, nullptr, false, shifts[j], D + NN * j, s);
     }
+    CU(launch_dense_inverse_batched(N, nshift, D, g->Ainv, piv, status, s));
+    int hst[RF_MAXSHIFT] = {};
+    CU(cudaMemcpyAsync(hst, status, sizeof(int) * nshift, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+    CU(cudaStreamSynchronize((cudaStream_t)s));
+    for (int j = 0; j < nshift; ++j)
+      if (hst[j]) { dfree_all(g, g->gbufs, s); return fail(RF_ENONFINITE, "coarsest operator is singular (shift %d)", j); }
   }
   // Krylov preconditioned vectors in the preconditioner type
   {

@@ -773,12 +773,22 @@ __global__ void k_dense(Dims d, Nbr nb, const double* __restrict__ J, const doub
 }
 
 // LU with partial pivoting in one CTA (first maximal pivot on ties).  Per
-// column: pick the pivot from the candidates gathered while updating the
-// previous column, swap rows, then each warp takes whole rows of the trailing
-// matrix (multiplier by lane 0, row update over lanes, coalesced) and records
-// the next column's candidate.  Four barriers per column.
+// column: the pivot comes from candidates gathered while the previous column
+// was applied; after the row swap the pivot row (from c on) and the column's
+// multipliers go to shared memory, so the trailing update is a loop of
+// independent loads and stores (warps over rows, lanes over columns) with no
+// per-row dependency chain; the thread that updates column c+1 of a row
+// records it as a candidate for the next pivot.  Four barriers per column.
+// Dynamic shared memory: 2 N doubles.
 __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int* __restrict__ piv,
                                              int* __restrict__ status) {
+  // one matrix per block: D, piv, status of matrix blockIdx.x
+  D += (int64_t)blockIdx.x * N * N;
+  piv += (int64_t)blockIdx.x * N;
+  status += blockIdx.x;
+  extern __shared__ double lu_sh[];
+  double* prow = lu_sh;       // pivot row, columns c..N-1
+  double* mult = lu_sh + N;   // multipliers of column c
   __shared__ double sval[32];
   __shared__ int sidx[32];
   __shared__ int sp;
@@ -809,26 +819,33 @@ __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int*
     }
     __syncthreads();
     const int pr = sp;
-    if (pr != c)
-      for (int t = tid; t < N; t += nt) {
-        const double tmp = D[(int64_t)c * N + t];
-        D[(int64_t)c * N + t] = D[(int64_t)pr * N + t];
-        D[(int64_t)pr * N + t] = tmp;
+    for (int t = tid; t < N; t += nt) {
+      const double vc = D[(int64_t)c * N + t], vp = D[(int64_t)pr * N + t];
+      if (pr != c) {
+        D[(int64_t)c * N + t] = vp;
+        D[(int64_t)pr * N + t] = vc;
       }
+      if (t >= c) prow[t] = vp;
+    }
     __syncthreads();
-    const double dc = D[(int64_t)c * N + c];
+    const double dc = prow[c];
+    for (int r = c + 1 + tid; r < N; r += nt) {
+      const double l = (dc != 0.0) ? D[(int64_t)r * N + c] / dc : 0.0;
+      mult[r] = l;
+      D[(int64_t)r * N + c] = l;
+    }
+    __syncthreads();
     best = -1.0;
     bi = N;
     for (int r = c + 1 + warp; r < N; r += nw) {
       double* Dr = D + (int64_t)r * N;
-      const double l = (dc != 0.0) ? Dr[c] / dc : 0.0;
-      for (int t = c + 1 + lane; t < N; t += 32) Dr[t] -= l * D[(int64_t)c * N + t];
-      __syncwarp();
-      if (lane == 0) {
-        Dr[c] = l;
-        if (c + 1 < N) {
-          const double v = fabs(Dr[c + 1]);
-          if (v > best || (v == best && r < bi)) { best = v; bi = r; }
+      const double l = mult[r];
+      for (int t = c + 1 + lane; t < N; t += 32) {
+        const double v = Dr[t] - l * prow[t];
+        Dr[t] = v;
+        if (t == c + 1) {
+          const double av = fabs(v);
+          if (av > best || (av == best && r < bi)) { best = av; bi = r; }
         }
       }
     }
@@ -840,7 +857,11 @@ __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int*
 // then L y = x and U z = y row by row, each row's dot product over the lanes
 // with x kept in shared memory.
 __global__ void __launch_bounds__(128) k_lu_inverse_cols(int N, const double* __restrict__ LU,
-                                                         const int* __restrict__ piv, double* __restrict__ Ainv) {
+                                                         const int* __restrict__ piv, InvOut out) {
+  // matrix blockIdx.y of the batch
+  LU += (int64_t)blockIdx.y * N * N;
+  piv += (int64_t)blockIdx.y * N;
+  double* __restrict__ Ainv = out.Ainv[blockIdx.y];
   extern __shared__ double xs_all[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -1083,13 +1104,23 @@ void launch_dense_coarsest(const Dims& d, const Nbr& nb, const double* Jc, const
   RF_LAUNCH(k_dense, (int)((n + 127) / 128), 128, 0, s, d, nb, Jc, Mc, (const double2*)mdiag, fine, shift, D);
 }
 
-cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status, void* s) {
-  (void)work;
-  RF_LAUNCH(k_lu, 1, 1024, 0, s, N, D, piv, status);
+cudaError_t launch_dense_inverse_batched(int N, int nmat, double* D, double* const* Ainv, int* piv, int* status,
+                                         void* s) {
+  if (nmat < 1 || nmat > RF_MAXSHIFT) return cudaErrorInvalidValue;
+  InvOut out;
+  for (int j = 0; j < RF_MAXSHIFT; ++j) out.Ainv[j] = j < nmat ? Ainv[j] : nullptr;
+  const size_t lsm = sizeof(double) * 2 * (size_t)N;   // 64 KB at N = 4096
+  cudaFuncSetAttribute(k_lu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm);
+  RF_LAUNCH(k_lu, nmat, 1024, lsm, s, N, D, piv, status);
   const size_t smem = sizeof(double) * 4 * (size_t)N;   // 4 warps per block, one x each (128 KB at N = 4096)
   cudaFuncSetAttribute(k_lu_inverse_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  RF_LAUNCH(k_lu_inverse_cols, (N + 3) / 4, 128, smem, s, N, D, piv, Ainv);
+  RF_LAUNCH(k_lu_inverse_cols, dim3((N + 3) / 4, nmat), 128, smem, s, N, D, piv, out);
   return cudaGetLastError();
+}
+
+cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status, void* s) {
+  (void)work;
+  return launch_dense_inverse_batched(N, 1, D, &Ainv, piv, status, s);
 }
 
 void launch_export_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,

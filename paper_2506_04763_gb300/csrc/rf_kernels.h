@@ -105,6 +105,11 @@ void launch_dense_coarsest(const Dims& d, const Nbr& nb, const double* Jc, const
                            const double* mdiag, bool fine, double shift, double* D, void* s);
 cudaError_t launch_dense_inverse(int N, double* D, double* Ainv, int* piv, double* work, int* status,
                                  void* s);
+// nmat (<= RF_MAXSHIFT) independent inverses at once, one CTA each for the LU:
+// D = nmat consecutive N x N matrices (overwritten), piv = nmat x N, status = nmat
+struct InvOut { double* Ainv[RF_MAXSHIFT]; };
+cudaError_t launch_dense_inverse_batched(int N, int nmat, double* D, double* const* Ainv, int* piv, int* status,
+                                         void* s);
 void launch_export_level(const Dims& d, bool fine, const double* J, const double* M, const double* mdiag,
                          double shift, double* A_nat, void* s);
 void launch_gather_rows(const Dims& d, const double* J, const double* mdiag, const int64_t* verts, int count,
