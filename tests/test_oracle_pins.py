@@ -418,6 +418,25 @@ def test_p8_extrapolation_order_on_linear_ode(oracle):
         assert abs(slope - (kappa + 1)) < 0.1
 
 
+def test_p8_w_method_keeps_the_order_with_an_inexact_jacobian(oracle):
+    """LIMEX is a W-method (Sec. 4: no algebraic conditions on the matrix): for
+    y' = lam y, columns built with W = 1 - h J~, J~ = 1.3 lam != lam, i.e.
+    y_{k+1} = y_k + h (1 - h J~)^-1 lam y_k, still extrapolate to local order
+    kappa + 1.  (The order reduction to q = 2 that the step control assumes
+    comes from stiff DAE structure, not from the inexact matrix.)"""
+    lam = -1.3
+    Jt = 1.3 * lam
+    for kappa in (2, 3, 4):
+        errs = []
+        Hs = np.array([0.02, 0.01, 0.005])
+        for Hh in Hs:
+            T1 = np.array([[(1 + (Hh / j) * lam / (1 - (Hh / j) * Jt)) ** j] for j in range(1, kappa + 1)])
+            Tkk, _ = oracle.extrapolate(T1, list(range(1, kappa + 1)))
+            errs.append(abs(Tkk[0] - np.exp(lam * Hh)))
+        slope = np.polyfit(np.log(Hs), np.log(errs), 1)[0]
+        assert abs(slope - (kappa + 1)) < 0.1
+
+
 def test_limex_columns_match_dense_linearly_implicit_euler(oracle):
     """kappa = 2 LIMEX step of the oracle = dense reconstruction: columns of
     linearly implicit Euler with the frozen J(u0), M(u0) (numpy solves), then
