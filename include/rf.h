@@ -163,7 +163,12 @@ rf_status rf_solve(rf_grid* g, int shift, const double* b, double* x, const rf_s
  * u, multigrid setup for the kappa shifts n_j/H, the columns of linearly
  * implicit Euler steps (each an rf_solve), Aitken-Neville extrapolation, the
  * scaled error estimate and the step-size proposal (q = 2).  u is replaced by
- * the extrapolated state only when the step is accepted (eps <= tol). */
+ * the extrapolated state only when the step is accepted (eps <= tol).
+ * The columns are independent until the extrapolation.  On grids of at most
+ * 4M vertices (or as the environment variable RF_LIMEX_CONCURRENT=1/0 says)
+ * they run at the same time, each on its own stream and host thread, with
+ * vectors of their own and the operators shared. The results are bitwise
+ * those of running the columns in turn. */
 rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* opts, rf_limex_info* info,
                         void* stream);
 

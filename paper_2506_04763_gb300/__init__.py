@@ -389,15 +389,18 @@ class Grid:
         return dict(status=st, newton=info.newton, linear=info.linear, res0=info.res0, res=info.res)
 
     def limex_run(self, u, H0, steps=None, tol=1e-3, rho=0.75, H_max=None, gmg=None, rtol=1e-10, max_it=200,
-                  outer="fp64", kappa=4, max_rejects=50, t_end=None):
+                  outer="fp64", kappa=4, max_rejects=50, t_end=None, hold_after_reject=True):
         """Adaptive LIMEX integration (step control of Sec. 4, q = 2): takes
         `steps` accepted steps, or integrates up to time `t_end` (the last step
         is shortened to land on it), from state u (updated in place); a
-        rejected step is retried with the proposed smaller H.  Returns
-        (t, history)."""
+        rejected step is retried with the proposed smaller H.  With
+        hold_after_reject (the usual safeguard; the paper does not state its
+        rule) the step accepted right after a rejection does not propose a
+        larger H.  Returns (t, history)."""
         if steps is None and t_end is None:
             raise ValueError("give steps or t_end")
         H, t, hist, rejects, acc = float(H0), 0.0, [], 0, 0
+        last_rejected = False
         while (steps is None or acc < steps) and (t_end is None or t < t_end * (1.0 - 1e-12)):
             if t_end is not None:
                 H = min(H, t_end - t)
@@ -405,14 +408,19 @@ class Grid:
                                    outer=outer)
             info.update(H=H, t=t)
             hist.append(info)
+            H_new = info["H_new"]
             if info["accepted"]:
                 t += H
                 acc += 1
+                if hold_after_reject and last_rejected:
+                    H_new = min(H_new, H)
+                last_rejected = False
             else:
                 rejects += 1
+                last_rejected = True
                 if rejects > max_rejects:
                     raise RuntimeError("LIMEX: more than %d rejected steps" % max_rejects)
-            H = info["H_new"] if H_max is None else min(info["H_new"], H_max)
+            H = H_new if H_max is None else min(H_new, H_max)
         return t, hist
 
     def phase_mass(self, u):

@@ -174,6 +174,14 @@ struct rf_grid {
   IterGraph* cap = nullptr;
   cudaStream_t cs = nullptr;             // internal stream for the iteration
   cudaEvent_t join_in = nullptr, join_out = nullptr;
+  // LIMEX columns solved concurrently: column j > 0 runs on col[j], a grid
+  // that shares this grid's operator data and hierarchy (read-only) and owns
+  // its vectors, scratch, streams and graphs (refreshed after each set-up)
+  uint64_t hier_gen = 0;                 // incremented by every rf_gmg_setup
+  uint64_t gen = ~0ull;                  // (column grids) the hierarchy they mirror
+  bool is_column = false;
+  rf_grid* col[RF_MAXSHIFT] = {};
+  cudaStream_t col_s[RF_MAXSHIFT] = {};  // (column grids) the caller-side stream of the column
 };
 
 // ------------------------------------------------------------------ profiling
@@ -360,6 +368,12 @@ extern "C" rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* l
 extern "C" void rf_grid_destroy(rf_grid* g) {
   if (!g) return;
   cudaDeviceSynchronize();
+  for (int j = 0; j < RF_MAXSHIFT; ++j)
+    if (g->col[j]) {
+      if (g->col[j]->col_s[0]) cudaStreamDestroy(g->col[j]->col_s[0]);
+      rf_grid_destroy(g->col[j]);   // frees only what the column grid allocated
+      g->col[j] = nullptr;
+    }
   destroy_graphs(g);
   for (auto e : g->evpool) cudaEventDestroy(e);
   if (g->join_in) cudaEventDestroy(g->join_in);
@@ -711,6 +725,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
   CU(cudaStreamSynchronize(g->cs));
   destroy_graphs(g);
   dfree_all(g, g->gbufs, s);
+  ++g->hier_gen;
   for (int l = 0; l < RF_MAXL; ++l) g->L[l] = Level();
   for (int j = 0; j < RF_MAXSHIFT; ++j) g->Ainv[j] = nullptr;
   g->gmg_ready = false;
@@ -1183,6 +1198,122 @@ extern "C" rf_status rf_solve(rf_grid* g, int sh, const double* b, double* x, co
 }
 
 // ------------------------------------------------------------------ LIMEX
+// ------------------------------------------------------------------ LIMEX column grids
+// Column j of a LIMEX step (n_j = j+1 linearly implicit Euler substeps with
+// shift (j+1)/H) depends on the others only through the extrapolation at the
+// end, so the columns can run at the same time.  Column j > 0 runs on a
+// column grid: a shallow copy of this grid's operator data and multigrid
+// hierarchy (J, M, level operators, coarsest inverses; read-only during the
+// columns) with its own Krylov and level vectors, assembly scratch, pinned
+// scalars, internal stream and iteration graphs.  Same kernels, same shapes,
+// same order per column: the results are bitwise those of running the
+// columns one after another.
+static rf_status column_grid(rf_grid* g, int j, void* s, rf_grid** out) {
+  rf_grid* c = g->col[j];
+  if (!c) {
+    c = new rf_grid();
+    c->is_column = true;
+    c->alloc = g->alloc;
+    c->user_alloc = g->user_alloc;
+    c->d = g->d;
+    c->nb = g->nb;
+    const Dims& d = c->d;
+    const int64_t nv = d.nv;
+    bool ok = true;
+    double** scratch[6] = {&c->Se, &c->pn, &c->pc, &c->dpc, &c->krw, &c->dkrw};
+    for (auto p : scratch) ok = ok && (*p = (double*)dalloc(c, sizeof(double) * nv, s, false));
+    ok = ok && (c->u_p = (double*)dalloc(c, sizeof(double) * 2 * nv, s, false));
+    ok = ok && (c->F_p = (double*)dalloc(c, sizeof(double) * 2 * nv, s, false));
+    ok = ok && (c->K.x = (double2*)dvec(c, d, sizeof(double), s, false));
+    double2** kv[6] = {&c->K.r, &c->K.rh, &c->K.p, &c->K.v, &c->K.s, &c->K.t};
+    for (auto p : kv) ok = ok && (*p = (double2*)dalloc(c, sizeof(double2) * nv, s, false));
+    ok = ok && (c->K.partial = (double*)dalloc(c, sizeof(double) * 16 * 2048, s, false));
+    ok = ok && (c->K.scal = (double*)dalloc(c, sizeof(double) * 32, s, false));
+    ok = ok && (c->norms = (double*)dalloc(c, sizeof(double) * 8, s, false));
+    if (ok && cudaMallocHost((void**)&c->hscal, sizeof(double) * 32) != cudaSuccess) {
+      cudaGetLastError();
+      c->hscal = nullptr;
+      ok = false;
+    }
+    if (ok && (cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaStreamCreateWithFlags(&c->col_s[0], cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&c->join_in, cudaEventDisableTiming) != cudaSuccess ||
+               cudaEventCreateWithFlags(&c->join_out, cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      ok = false;
+    }
+    if (!ok) {
+      if (c->col_s[0]) cudaStreamDestroy(c->col_s[0]);
+      rf_grid_destroy(c);
+      return fail(RF_ENOMEM, "LIMEX column %d: allocation failed", j);
+    }
+    g->col[j] = c;
+  }
+  // the parent's operator data (read-only while the columns run)
+  c->pp = g->pp;
+  for (int a = 0; a < 3; ++a) { c->h[a] = g->h[a]; c->g[a] = g->g[a]; }
+  c->ncell = g->ncell;
+  c->Kcell = g->Kcell; c->phi = g->phi; c->pd = g->pd; c->vol = g->vol;
+  c->dir = g->dir; c->pw_dir = g->pw_dir; c->q_in = g->q_in; c->pdmin = g->pdmin; c->phiv = g->phiv;
+  c->J = g->J; c->mdiag = g->mdiag; c->have_J = g->have_J;
+  c->Jdf = g->Jdf; c->jdf_valid = g->jdf_valid;
+  if (c->gen != g->hier_gen) {
+    // new hierarchy: drop graphs and level vectors, mirror the levels, own vectors
+    CU(cudaStreamSynchronize(c->cs));
+    destroy_graphs(c);
+    dfree_all(c, c->gbufs, s);
+    c->gmg_ready = g->gmg_ready;
+    c->gopt = g->gopt;
+    c->kind = g->kind;
+    c->nshift = g->nshift;
+    for (int k = 0; k < RF_MAXSHIFT; ++k) { c->shifts[k] = g->shifts[k]; c->Ainv[k] = g->Ainv[k]; }
+    c->nl = g->nl;
+    c->tail_first = -1;
+    const size_t te = t_size(c->kind);
+    bool ok = true;
+    for (int l = 0; l < RF_MAXL; ++l) {
+      c->L[l] = g->L[l];
+      c->L[l].x = c->L[l].b = c->L[l].r = c->L[l].t = nullptr;
+      if (l >= c->nl) continue;
+      const Dims& dl = c->L[l].d;
+      ok = ok && (c->L[l].x = dvec(c, dl, te, s, true));
+      ok = ok && (c->L[l].b = dvec(c, dl, te, s, true));
+      ok = ok && (c->L[l].r = dvec(c, dl, te, s, true));
+      ok = ok && (c->L[l].t = dvec(c, dl, te, s, true));
+    }
+    ok = ok && (c->K.y = dvec(c, c->d, te, s, true));
+    ok = ok && (c->K.z = dvec(c, c->d, te, s, true));
+    ok = ok && (c->K.p_lo = dvec(c, c->d, te, s, true));
+    ok = ok && (c->K.s_lo = dvec(c, c->d, te, s, true));
+    if (c->kind == STORE_F64) {
+      c->K.y64 = (double2*)c->K.y;
+      c->K.z64 = (double2*)c->K.z;
+    } else {
+      ok = ok && (c->K.y64 = (double2*)dvec(c, c->d, sizeof(double), s, true));
+      ok = ok && (c->K.z64 = (double2*)dvec(c, c->d, sizeof(double), s, true));
+    }
+    if (!ok) {
+      dfree_all(c, c->gbufs, s);
+      c->gen = ~0ull;
+      return fail(RF_ENOMEM, "LIMEX column %d: vector allocation failed", j);
+    }
+    c->gen = g->hier_gen;
+  }
+  *out = c;
+  return RF_OK;
+}
+
+// Whether a LIMEX step runs its columns concurrently: RF_LIMEX_CONCURRENT=1/0
+// forces it; by default on grids of at most 4M vertices (the extra vectors
+// cost ~300 B per vertex and column; larger grids are bandwidth-bound).
+static thread_local bool t_in_batch = false;   // set by rf_limex_step_batched's workers
+static bool limex_concurrent(const rf_grid* g, int kap) {
+  if (kap < 2) return false;
+  const char* e = getenv("RF_LIMEX_CONCURRENT");
+  if (e) return atoi(e) != 0;
+  return !t_in_batch && g->d.nv <= 4000000;
+}
+
 extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* o, rf_limex_info* info,
                                    void* s) {
   if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
@@ -1209,30 +1340,85 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
   double shifts[RF_MAXSHIFT];
   for (int j = 0; j < kap; ++j) shifts[j] = (double)(j + 1) / H;
   if ((st = rf_gmg_setup(g, shifts, kap, &o->gmg, s))) return st;
-  int solves = 0, iters = 0;
-  rf_status worst = RF_OK;
-  for (int j = 0; j < kap; ++j) {
+  // column j on grid gj and stream sj: u0 -> n_j substeps -> T slot j
+  struct ColResult { rf_status st = RF_OK; int solves = 0, iters = 0; std::string msg; };
+  ColResult res[RF_MAXSHIFT];
+  auto column = [&](rf_grid* gj, int j, void* sj) {
+    ColResult& R = res[j];
     double* U = g->T + (size_t)j * 2 * d.nv;
-    CU(cudaMemcpyAsync(U, u0, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+    if (cudaMemcpyAsync(U, u0, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)sj) != cudaSuccess) {
+      R.st = fail(RF_ECUDA, "LIMEX column %d: copy failed", j);
+      R.msg = rf_last_error();
+      return;
+    }
     for (int k = 0; k <= j; ++k) {
       const double* F;
       if (k == 0) {
         F = F0;
       } else {
-        CU(cudaMemcpyAsync(g->u_p, U, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
-        if ((st = assemble_p(g, false, s))) return st;
-        F = g->F_p;
+        rf_status a2 = RF_OK;
+        if (cudaMemcpyAsync(gj->u_p, U, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)sj) != cudaSuccess)
+          a2 = fail(RF_ECUDA, "LIMEX column %d: copy failed", j);
+        if (!a2) a2 = assemble_p(gj, false, sj);
+        if (a2) { R.st = a2; R.msg = rf_last_error(); return; }
+        F = gj->F_p;
       }
       rf_solve_info si{};
-      rf_status r = solve_p(g, j, (const double2*)F, o->solve.rtol, o->solve.max_it, o->solve.outer, &si, s);
-      ++solves;
-      iters += si.iterations;
+      rf_status r = solve_p(gj, j, (const double2*)F, o->solve.rtol, o->solve.max_it, o->solve.outer, &si, sj);
+      ++R.solves;
+      R.iters += si.iterations;
       if (r != RF_OK) {
-        if (r != RF_ENOTCONV) return r;
-        worst = r;
+        if (r != RF_ENOTCONV) { R.st = r; R.msg = rf_last_error(); return; }
+        if (R.st == RF_OK) R.st = r;
       }
-      launch_axpy_pairs(d.nv, (double2*)U, g->K.x, s);
+      launch_axpy_pairs(d.nv, (double2*)U, gj->K.x, sj);
     }
+  };
+  if (limex_concurrent(g, kap)) {
+    // the double-FP32 operator copy is made once, before the columns share it
+    if (o->solve.outer == RF_OUTER_DF32 && g->kind != STORE_F64 && !g->jdf_valid) {
+      if (!g->Jdf) {
+        g->Jdf = (float*)dalloc(g, sizeof(double) * 4 * g->d.nb * g->d.nv, s, false);
+        if (!g->Jdf) return fail(RF_ENOMEM, "double-FP32 operator copy");
+      }
+      launch_split_df(g->d, g->J, g->Jdf, s);
+      g->jdf_valid = true;
+    }
+    rf_grid* cg[RF_MAXSHIFT] = {g};
+    for (int j = 1; j < kap; ++j)
+      if ((st = column_grid(g, j, s, &cg[j]))) return st;
+    cudaEvent_t ready;
+    CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CU(cudaEventRecord(ready, (cudaStream_t)s));
+    for (int j = 1; j < kap; ++j) CU(cudaStreamWaitEvent(cg[j]->col_s[0], ready, 0));
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    std::vector<std::thread> th;
+    for (int j = kap - 1; j >= 1; --j)   // longest columns first
+      th.emplace_back([&, j] {
+        cudaSetDevice(dev);
+        column(cg[j], j, cg[j]->col_s[0]);
+      });
+    column(g, 0, s);
+    for (auto& t : th) t.join();
+    for (int j = 1; j < kap; ++j) {
+      CU(cudaEventRecord(cg[j]->join_out, cg[j]->col_s[0]));
+      CU(cudaStreamWaitEvent((cudaStream_t)s, cg[j]->join_out, 0));
+    }
+    cudaEventDestroy(ready);
+  } else {
+    for (int j = 0; j < kap; ++j) {
+      column(g, j, s);
+      if (res[j].st != RF_OK && res[j].st != RF_ENOTCONV) break;
+    }
+  }
+  int solves = 0, iters = 0;
+  rf_status worst = RF_OK;
+  for (int j = 0; j < kap; ++j) {
+    solves += res[j].solves;
+    iters += res[j].iters;
+    if (res[j].st != RF_OK && res[j].st != RF_ENOTCONV) return fail(res[j].st, "%s", res[j].msg.c_str());
+    if (res[j].st == RF_ENOTCONV) worst = RF_ENOTCONV;
   }
   launch_extrapolate(2 * d.nv, kap, g->T, s);
   const double* Tkk = g->T;
@@ -1381,12 +1567,15 @@ extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const*
   std::atomic<int> next{0};
   auto work = [&]() {
     cudaSetDevice(dev);
+    const bool was = t_in_batch;
+    t_in_batch = true;   // the problems already run side by side: columns one after another
     for (int i = next.fetch_add(1); i < nprob; i = next.fetch_add(1)) {
       rf_grid* g = grids[i];
       st[i] = rf_limex_step(g, u[i], H[i], &o[i], &infos[i], g->cs);
       infos[i].status = st[i];
       if (st[i] != RF_OK) msg[i] = t_err;
     }
+    t_in_batch = was;
   };
   std::vector<std::thread> pool;
   for (int w = 1; w < workers; ++w) pool.emplace_back(work);
