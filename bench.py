@@ -166,6 +166,25 @@ def run_reference(a):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ multi-rank helpers
+def max_over_ranks(ms, world, device=None):
+    """The job's time is its slowest rank's: MAX all-reduce of a per-rank time
+    (ms) over the process group; a single process returns ms unchanged."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, ms):
+    """Whole-job throughput: every rank solves its own replica (weak scaling),
+    so the job processes world x units in the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     a = args_()
@@ -250,11 +269,7 @@ def main():
         if profile:
             g.profile(0)
             prof = g.profile_read()
-        ms = t0.elapsed_time(t1) / nsteps
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(t0.elapsed_time(t1) / nsteps, world, dev)
         return ms, infos, launches, prof
 
     # ---- headline: FP32 (or chosen) GMG
@@ -267,7 +282,7 @@ def main():
     bad = [i for i in infos if i["status"] != 0 or i["relres"] > RTOL]
     if bad:
         raise SystemExit("solve did not reach rel.res %g: %s" % (RTOL, bad[0]))
-    value = world * dof / (ms / 1e3)
+    value = job_rate(world, dof, ms)
     iters = infos[-1]["iterations"]
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
@@ -282,11 +297,7 @@ def main():
     for _ in range(a.steps):
         g.solve(0, bn, xn, rtol=RTOL, max_it=500, outer=a.outer)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - w0) * 1e3 / a.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks((time.perf_counter() - w0) * 1e3 / a.steps, world, dev)
 
     # ---- roofline of the dominant kernel class, from the live event timings
     pk = peaks()

@@ -270,10 +270,10 @@ rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, do
  * which may synchronise the device.  Inverts a dense FP64 N x N matrix
  * (row-major, DEVICE pointers A and Ainv, caller-owned; A is not modified) by
  * LU with partial pivoting, as the multigrid set-up does for the coarsest
- * operator, and allocates nothing: the LU factors, work vectors, pivots and
- * status live in a static device array of RF_NOALLOC_MAX_N^2 * 16 bytes plus a
- * little (about 4 MiB), reserved on every GPU that loads the library until the
- * process exits.  The first call on a device looks up the array's device
+ * operator, and allocates nothing: the LU factors, pivots and status live in
+ * a static device array of RF_NOALLOC_MAX_N^2 * 8 bytes plus a little (about
+ * 2 MiB), reserved on every GPU that loads the library until the process
+ * exits.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) and should therefore come before any stream
  * capture.  Calls share the array: calls that overlap on the GPU race and must
  * be serialised by the caller.  Returns RF_EINVAL for N outside

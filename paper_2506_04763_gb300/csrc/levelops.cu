@@ -324,30 +324,40 @@ template <typename T>
 __device__ __forceinline__ void restrict_point(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
                                                const uint8_t* __restrict__ dmc, const typename V2<T>::t* __restrict__ rf,
                                                typename V2<T>::t* __restrict__ bc, int64_t pc) {
+  typedef typename V2<T>::t V;
   int I, J, K;
   pcoords(dc, pc, I, J, K);
   const bool mc = dmc[pc] != 0;
-  T s0 = 0, s1 = 0;
-  const int zlo = df.dim == 3 ? -1 : 0, zhi = df.dim == 3 ? 1 : 0;
-  for (int dz = zlo; dz <= zhi; ++dz) {
-    const int fk = df.dim == 3 ? 2 * K + dz : 0;
-    if (fk < 0 || fk >= df.nz) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int fj = 2 * J + dy;
-      if (fj < 0 || fj >= df.ny) continue;
+  // all 3^d fine values and masks are loaded first (one memory round trip),
+  // then summed in the fixed (dz, dy, dx) order
+  V r[27];
+  uint8_t m[27];
+  bool in[27];
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int fi = 2 * I + dx;
-        if (fi < 0 || fi >= df.nx) continue;
-        const T w = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
-        const int64_t pf = pidx(df, fi, fj, fk);
-        const typename V2<T>::t r = rf[pf];
-        if (!(mc || dmf[pf])) s0 += w * r.x;
-        s1 += w * r.y;
-      }
+  for (int q = 0; q < 27; ++q) {
+    const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+    const int fi = 2 * I + dx, fj = 2 * J + dy, fk = df.dim == 3 ? 2 * K + dz : 0;
+    in[q] = (df.dim == 3 || dz == 0) && fi >= 0 && fi < df.nx && fj >= 0 && fj < df.ny && fk >= 0 && fk < df.nz;
+    if (in[q]) {
+      const int64_t pf = pidx(df, fi, fj, fk);
+      r[q] = rf[pf];
+      m[q] = dmf[pf];
+    } else {
+      r[q].x = 0;
+      r[q].y = 0;
+      m[q] = 1;
     }
   }
-  typename V2<T>::t o;
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (!in[q]) continue;
+    const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+    const T w = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+    if (!(mc || m[q])) s0 += w * r[q].x;
+    s1 += w * r[q].y;
+  }
+  V o;
   o.x = s0;
   o.y = s1;
   bc[pc] = o;
@@ -368,27 +378,40 @@ template <typename T>
 __device__ __forceinline__ void prolong_point(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
                                               const uint8_t* __restrict__ dmc, const typename V2<T>::t* __restrict__ xc,
                                               typename V2<T>::t* __restrict__ xf, int64_t pf) {
+  typedef typename V2<T>::t V;
   int fi, fj, fk;
   pcoords(df, pf, fi, fj, fk);
   const bool mf = dmf[pf] != 0;
-  T s0 = 0, s1 = 0;
-  for (int K = fk >> 1; K <= ((fk + 1) >> 1); ++K) {
-    if (K >= dc.nz) continue;
-    const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
-    for (int J = fj >> 1; J <= ((fj + 1) >> 1); ++J) {
-      if (J >= dc.ny) continue;
-      const T wy = (fj & 1) ? (T)0.5 : (T)1;
-      for (int I = fi >> 1; I <= ((fi + 1) >> 1); ++I) {
-        if (I >= dc.nx) continue;
-        const T w = ((fi & 1) ? (T)0.5 : (T)1) * wy * wz;
-        const int64_t pc = pidx(dc, I, J, K);
-        const typename V2<T>::t c = xc[pc];
-        if (!(mf || dmc[pc])) s0 += w * c.x;
-        s1 += w * c.y;
-      }
+  // the (up to) 2^d coarse parents, loaded first, summed in (K, J, I) order
+  V c[8];
+  uint8_t m[8];
+  bool in[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int K = (fk >> 1) + ((q >> 2) & 1), J = (fj >> 1) + ((q >> 1) & 1), I = (fi >> 1) + (q & 1);
+    in[q] = ((q & 1) == 0 || (fi & 1)) && (((q >> 1) & 1) == 0 || (fj & 1)) &&
+            (((q >> 2) & 1) == 0 || (fk & 1)) && K < dc.nz && J < dc.ny && I < dc.nx;
+    if (in[q]) {
+      const int64_t pc = pidx(dc, I, J, K);
+      c[q] = xc[pc];
+      m[q] = dmc[pc];
+    } else {
+      c[q].x = 0;
+      c[q].y = 0;
+      m[q] = 1;
     }
   }
-  typename V2<T>::t o = xf[pf];
+  const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
+  const T wy = (fj & 1) ? (T)0.5 : (T)1;
+  const T w = ((fi & 1) ? (T)0.5 : (T)1) * wy * wz;
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (!in[q]) continue;
+    if (!(mf || m[q])) s0 += w * c[q].x;
+    s1 += w * c[q].y;
+  }
+  V o = xf[pf];
   o.x += s0;
   o.y += s1;
   xf[pf] = o;

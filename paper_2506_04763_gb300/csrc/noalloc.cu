@@ -10,9 +10,10 @@
 // set-up applies to the coarsest-level operator) with its working storage in
 // a file-scope device array that the library reserves when it is loaded.
 //
-// The array holds the LU factors, the per-column work vectors, the pivots and
-// a status word for matrices up to RF_NOALLOC_MAX_N x RF_NOALLOC_MAX_N.  Every
-// GPU that loads the library keeps it (about 4 MiB) until the process exits.
+// The array holds the LU factors, the pivots and a status word for matrices up
+// to RF_NOALLOC_MAX_N x RF_NOALLOC_MAX_N (the inverse's per-column vectors live
+// in the kernel's shared memory).  Every GPU that loads the library keeps it
+// (about 2 MiB) until the process exits.
 // All calls on a device share it: two calls whose work overlaps on the GPU
 // (different streams, or different host threads) race on it and must be
 // serialised by the caller.  The status word is cleared by every call; the
@@ -27,8 +28,8 @@ namespace {
 
 constexpr int kMaxN = RF_NOALLOC_MAX_N;
 constexpr size_t kMat = (size_t)kMaxN * kMaxN;          // doubles per N x N matrix
-// layout in doubles: [LU: kMat][work: kMat][pivots: kMaxN ints][status: 1 int], padded
-constexpr size_t kWords = 2 * kMat + kMaxN / 2 + 64;
+// layout in doubles: [LU: kMat][pivots: kMaxN ints][status: 1 int], padded
+constexpr size_t kWords = kMat + kMaxN / 2 + 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kWords];
 
@@ -71,14 +72,13 @@ extern "C" rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ai
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return RF_ECUDA;
   double* LU = static_cast<double*>(base);
-  double* work = LU + kMat;
-  int* piv = reinterpret_cast<int*>(work + kMat);
+  int* piv = reinterpret_cast<int*>(LU + kMat);
   int* status = piv + kMaxN;
   cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(LU, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return RF_ECUDA;
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return RF_ECUDA;
-  if (rf::launch_dense_inverse(N, LU, Ainv, piv, work, status, stream) != cudaSuccess) return RF_ECUDA;
+  if (rf::launch_dense_inverse(N, LU, Ainv, piv, nullptr, status, stream) != cudaSuccess) return RF_ECUDA;
   int h = 0;
   if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RF_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return RF_ECUDA;

@@ -89,7 +89,8 @@ def lognormal_field(dim, n, seed, ell=8.0, mean=np.log(5e-11), sigma=1.0, rng=No
     f = ndimage.gaussian_filter(w, sigma=sig, mode="wrap", truncate=4.0)
     sl = tuple(slice(pad, pad + s) if s > 1 else slice(0, 1) for s in shape)
     f = f[sl]
-    f = (f - f.mean()) / f.std()
+    sd = f.std()
+    f = (f - f.mean()) / sd if sd > 0 else np.zeros_like(f)   # a single cell: the mean
     return np.exp(mean + sigma * f).ravel(), rng
 
 

@@ -496,3 +496,41 @@ def test_concurrent_limex_columns_equal_sequential(precision, smoother, outer, m
     assert np.array_equal(out["0"][0], out["1"][0])
     assert out["0"][1]["iterations"] == out["1"][1]["iterations"]
     assert out["0"][1]["eps"] == out["1"][1]["eps"]
+
+
+@pytest.mark.parametrize("dim,nv", [(2, (2, 2)), (2, (3, 2)), (3, (2, 2, 2)), (3, (3, 2, 3))])
+def test_smallest_grids_assemble_and_solve(dim, nv):
+    """Degenerate sizes: one element (2^d vertices) and one-element-thick
+    grids; a one-level hierarchy is the dense coarsest solve itself.  (Dirichlet
+    p_w on the top face: without any, the pressure is fixed only up to a
+    constant and A = M/h - J is singular.)"""
+    prob = I.random_problem(dim, nv, 45)
+    g, F = _assembled(prob)
+    J, md = g.export_jacobian()
+    m = O.Model(prob)
+    F_o, J_o, md_o = O.assemble(m, prob["u0"])
+    assert np.abs(J - J_o).max() <= 1e-12 * np.abs(J_o).max()
+    assert np.abs(F - F_o).max() <= 1e-12 * np.abs(F_o).max()
+    shift = 1.0 / prob["H"]
+    g.gmg_setup([shift], rf.gmg_opts(1, "jacobi", precision="fp64"))
+    b = torch.tensor(F, device="cuda")
+    x = torch.empty_like(b)
+    info = g.solve(0, b, x, rtol=1e-12, max_it=50)
+    torch.cuda.synchronize()
+    assert info["status"] == 0 and info["iterations"] <= 2, info
+    A = O.make_A(J_o, md_o, shift)
+    r = F - O.spmv(m.dim, m.n, A, x.cpu().numpy())
+    assert np.linalg.norm(r) <= 1e-11 * np.linalg.norm(F)
+    g.close()
+
+
+def test_coarsest_level_size_limit_is_enforced():
+    """A hierarchy whose coarsest level would exceed 4096 unknowns is refused
+    at set-up (the dense inverse is sized for that), not run."""
+    prob = I.random_problem(3, (17, 17, 17), 46)
+    g, _ = _assembled(prob)
+    with pytest.raises(rf.RFError) as e:
+        g.gmg_setup([0.1], rf.gmg_opts(1))   # 17^3 x 2 = 9826 unknowns on one level
+    assert e.value.status == rf.RF_EINVAL
+    g.gmg_setup([0.1], rf.gmg_opts(2))       # 9^3 x 2 = 1458: fine
+    g.close()
