@@ -91,8 +91,9 @@ enum { RF_PREC_FP64 = 0, RF_PREC_FP32 = 1, RF_PREC_FP16 = 2 };
  * at most this many); smoother: damped point-block Jacobi or multicolour
  * (4 colours 2D / 8 colours 3D) block Gauss-Seidel; nu1/nu2 pre/post sweeps;
  * omega: Jacobi damping; precision: storage and arithmetic of the
- * preconditioner (FP64; FP32; FP16 storage with per-block-row FP32 scales and
- * FP32 arithmetic).  The coarsest level is solved exactly in FP64.
+ * preconditioner (FP64; FP32; FP16 storage of the finest level's matrix
+ * with per-block-row FP32 scales, FP32 storage on the coarser levels, FP32
+ * arithmetic throughout).  The coarsest level is solved exactly in FP64.
  * autotune = 1 times candidate thread-block sizes (64..512) for each level's
  * smoothing and residual kernels during the set-up and keeps the fastest
  * (cached per level shape for the process, and in the file named by the

@@ -21,7 +21,13 @@
 namespace rf {
 
 static std::atomic<int64_t> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// this thread's launches: a graph capture counts its kernels with it, so that
+// LIMEX columns capturing on other threads do not add to the count
+static thread_local int64_t t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
 bool pdl_enabled() {
   static const bool on = [] {
     const char* e = getenv("RF_PDL");
@@ -85,6 +91,11 @@ struct Level {
   // stencil loads 9 blocks per memory round trip.
   int block = 128;
   bool batched = true;
+  // matrix storage of this level (STORE_*): the hierarchy's precision, except
+  // that FP16 storage applies to the finest level only and the coarser levels
+  // keep FP32 (their sweeps are latency-bound, and FP16 unpacking made them
+  // slower: 11.7 -> 17.8 ms of coarse-level time per 257^3 solve)
+  int kind = STORE_F64;
 };
 
 // Default kernel shape per level, from the autotuner's timings at 257^3 (one
@@ -534,7 +545,7 @@ static LevelOp level_op(rf_grid* g, int l, int sh) {
   const Level& Lv = g->L[l];
   op.d = Lv.d;
   op.nb = Lv.nb;
-  op.kind = g->kind;
+  op.kind = Lv.kind;
   op.fine = (l == 0);
   op.A = (l == 0) ? Lv.A[0] : Lv.A[sh];
   op.scale = (l == 0) ? Lv.scale[0] : Lv.scale[sh];
@@ -616,7 +627,7 @@ static rf_status autotune_levels(rf_grid* g, void* s) {
   const int last = g->nl - 1;   // the coarsest level is a dense solve
   for (int l = 0; l < last; ++l) {
     Level& Lv = g->L[l];
-    const std::string key = tune_key(Lv.d, g->kind, g->gopt.smoother, l == 0);
+    const std::string key = tune_key(Lv.d, Lv.kind, g->gopt.smoother, l == 0);
     {
       std::lock_guard<std::mutex> lk(g_tune_mu);
       tune_load_locked();
@@ -755,7 +766,8 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
   for (int l = 0; l < g->nl; ++l) {
     Level& Lv = g->L[l];
     Lv.nb = make_nbr(Lv.d);
-    default_shape(Lv, l, kind);
+    Lv.kind = (kind == STORE_F16 && l > 0) ? STORE_F32 : kind;
+    default_shape(Lv, l, Lv.kind);
     const Dims& d = Lv.d;
     if (l == 0) {
       Lv.dmask = g->dir;
@@ -767,7 +779,8 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       rf_status gst = galerkin_level(g, g->L[l - 1], Lv, l == 1, s);
       if (gst) { dfree_all(g, g->gbufs, s); return gst; }
     }
-    const size_t te = t_size(kind), se = s_size(kind);
+    const int lk = Lv.kind;
+    const size_t te = t_size(kind), se = s_size(lk);
     if (l < g->nl - 1 || g->nl == 1) {
       // smoothed levels: storage + inverse diagonal blocks per shift
       if (l == 0) {
@@ -785,9 +798,9 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       } else {
         for (int j = 0; j < nshift; ++j) {
           GNEED(Lv.A[j] = dalloc(g, se * 4 * d.nb * d.nv, s, true));
-          if (kind == STORE_F16) GNEED(Lv.scale[j] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
+          if (lk == STORE_F16) GNEED(Lv.scale[j] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
           GNEED(Lv.Dinv[j] = dalloc(g, te * 4 * d.nv, s, true));
-          launch_pack_level(d, false, Lv.Jc, Lv.Mc, nullptr, shifts[j], kind, Lv.A[j], Lv.scale[j], Lv.Dinv[j], s);
+          launch_pack_level(d, false, Lv.Jc, Lv.Mc, nullptr, shifts[j], lk, Lv.A[j], Lv.scale[j], Lv.Dinv[j], s);
         }
       }
     }
@@ -855,7 +868,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
       for (int l = 1; l < g->nl - 1; ++l)
         if (g->L[l].d.nv <= thr) { g->tail_first = l; break; }
     if (g->tail_first > 0) {
-      g->tail_cs = tail_cluster_size(kind, g->d.nb);
+      g->tail_cs = tail_cluster_size(g->L[g->tail_first].kind, g->d.nb);
       cudaGetLastError();
       if (g->tail_cs == 0) g->tail_first = -1;
     }
@@ -891,7 +904,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
 // bytes of one smoothing sweep on a level of nv vertices
 static double sweep_bytes(rf_grid* g, int l, bool zero_x) {
   const Dims& d = g->L[l].d;
-  const int k = g->kind;
+  const int k = g->L[l].kind;
   const double T = tb(k), nv = (double)d.nv;
   if (g->gopt.smoother == RF_SMOOTH_JACOBI) {
     if (zero_x) return nv * (4 * T + 4 * T);  // Dinv, b, x out
@@ -960,15 +973,16 @@ static void smooth_post(rf_grid* g, int l, int sh, const void* b, void* x_final,
 }
 
 static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void* s) {
-  const int k = g->kind;
+  const int k = g->L[l].kind;
   const double T = tb(k);
   if (l == g->tail_first) {
     // the whole remaining V-cycle in one cluster launch (x, b are level l's own vectors)
     double by = 4.0 * g->L[g->nl - 1].d.nv * g->L[g->nl - 1].d.nv * 8.0;
     for (int q = l; q < g->nl - 1; ++q) {
       const double nvq = (double)g->L[q].d.nv, nvc = (double)g->L[q + 1].d.nv;
+      const int kq = g->L[q].kind;
       by += sweep_bytes(g, q, true) + (g->gopt.nu1 - 1 + g->gopt.nu2) * sweep_bytes(g, q, false);
-      by += nvq * (g->L[q].d.nb * blk_bytes(k) + row_extra(k) + 6 * T) + nvq * (6 * T + 2) + nvc * (4 * T + 2);
+      by += nvq * (g->L[q].d.nb * blk_bytes(kq) + row_extra(kq) + 6 * T) + nvq * (6 * T + 2) + nvc * (4 * T + 2);
     }
     ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, by, 1);
     launch_vcycle_tail(g->tail[sh], k, g->d.nb, g->tail_cs, s);
@@ -1069,7 +1083,7 @@ static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
   const bool prof = g->prof_on;
   rf_grid::IterGraph& G = g->ig[sh][prof ? 1 : 0][g->outer_df];
   if (!G.exec) {
-    const int64_t c0 = g_launches.load();
+    const int64_t c0 = t_launches;
     CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     g->capturing = true;
     g->cap = &G;
@@ -1079,7 +1093,7 @@ static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
     g->cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    G.kernels = g_launches.load() - c0;   // counted again at every replay
+    G.kernels = t_launches - c0;   // counted again at every replay
     g_launches.fetch_sub(G.kernels);
     if (e != cudaSuccess) return fail(RF_ECUDA, "iteration capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&G.exec, graph, 0);
