@@ -428,6 +428,131 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
   prolong_point<T>(df, dc, dmf, dmc, xc, xf, pf);
 }
 
+// The same transfers with the vertex taken from the launch shape: a plane per
+// blockIdx.y and the position within it by one 32-bit division, with the
+// line offsets of the gathered values computed once per vertex instead of a
+// 64-bit pidx per value (and pcoords' 64-bit divisions per vertex), which made
+// the per-point kernels above integer-bound.  Loads, masks, weights and the
+// order of the sums are those of restrict_point / prolong_point.
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                         const uint8_t* __restrict__ dmc,
+                                                         const typename V2<T>::t* __restrict__ rf,
+                                                         typename V2<T>::t* __restrict__ bc) {
+  rf_pdl_begin();
+  typedef typename V2<T>::t V;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= dc.nx * dc.ny) return;
+  const int J = t / dc.nx, pos = t - J * dc.nx, K = blockIdx.y;
+  const int I = pos < dc.E ? 2 * pos : 2 * (pos - dc.E) + 1;
+  const int64_t pc = ((int64_t)J + (int64_t)dc.ny * K) * dc.nx + pos;
+  const bool mc = dmc[pc] != 0;
+  int xo[3];
+  bool xin[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int fi = 2 * I + a - 1;
+    xin[a] = fi >= 0 && fi < df.nx;
+    xo[a] = (fi & 1) ? df.E + (fi >> 1) : (fi >> 1);
+  }
+  int64_t lo[9];
+  bool lin[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int fj = 2 * J + b - 1, fk = df.dim == 3 ? 2 * K + c - 1 : 0;
+      lin[3 * c + b] = (df.dim == 3 || c == 1) && fj >= 0 && fj < df.ny && fk >= 0 && fk < df.nz;
+      lo[3 * c + b] = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx;
+    }
+  V r[27];
+  uint8_t m[27];
+  bool in[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int a = q % 3, bc3 = q / 3;   // bc3 = 3 * (dz + 1) + (dy + 1)
+    in[q] = lin[bc3] && xin[a];
+    if (in[q]) {
+      const int64_t pf = lo[bc3] + xo[a];
+      r[q] = rf[pf];
+      m[q] = dmf[pf];
+    } else {
+      r[q].x = 0;
+      r[q].y = 0;
+      m[q] = 1;
+    }
+  }
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    if (!in[q]) continue;
+    const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+    const T w = (T)((dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0));
+    if (!(mc || m[q])) s0 += w * r[q].x;
+    s1 += w * r[q].y;
+  }
+  V o;
+  o.x = s0;
+  o.y = s1;
+  bc[pc] = o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                        const uint8_t* __restrict__ dmc,
+                                                        const typename V2<T>::t* __restrict__ xc,
+                                                        typename V2<T>::t* __restrict__ xf) {
+  rf_pdl_begin();
+  typedef typename V2<T>::t V;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= df.nx * df.ny) return;
+  const int fj = t / df.nx, pos = t - fj * df.nx, fk = blockIdx.y;
+  const int fi = pos < df.E ? 2 * pos : 2 * (pos - df.E) + 1;
+  const int64_t pf = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx + pos;
+  const bool mf = dmf[pf] != 0;
+  const int I0 = fi >> 1, J0 = fj >> 1, K0 = fk >> 1;
+  int xo[2];
+  int64_t lo[4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a) xo[a] = ((I0 + a) & 1) ? dc.E + ((I0 + a) >> 1) : ((I0 + a) >> 1);
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) lo[2 * c + b] = ((int64_t)(J0 + b) + (int64_t)dc.ny * (K0 + c)) * dc.nx;
+  V c8[8];
+  uint8_t m[8];
+  bool in[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int K = K0 + ((q >> 2) & 1), J = J0 + ((q >> 1) & 1), I = I0 + (q & 1);
+    in[q] = ((q & 1) == 0 || (fi & 1)) && (((q >> 1) & 1) == 0 || (fj & 1)) &&
+            (((q >> 2) & 1) == 0 || (fk & 1)) && K < dc.nz && J < dc.ny && I < dc.nx;
+    if (in[q]) {
+      const int64_t pc = lo[q >> 1] + xo[q & 1];
+      c8[q] = xc[pc];
+      m[q] = dmc[pc];
+    } else {
+      c8[q].x = 0;
+      c8[q].y = 0;
+      m[q] = 1;
+    }
+  }
+  const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
+  const T wy = (fj & 1) ? (T)0.5 : (T)1;
+  const T w = ((fi & 1) ? (T)0.5 : (T)1) * wy * wz;
+  T s0 = 0, s1 = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    if (!in[q]) continue;
+    if (!(mf || m[q])) s0 += w * c8[q].x;
+    s1 += w * c8[q].y;
+  }
+  V o = xf[pf];
+  o.x += s0;
+  o.y += s1;
+  xf[pf] = o;
+}
+
 // ----------------------------------------------------------------- coarsest solve
 // x = A^-1 b on the coarsest level: one warp per row of the explicit
 // inverse, lanes over its columns (coalesced), FP64 sums.
@@ -1076,20 +1201,44 @@ void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, boo
   }
 }
 
+// one thread per vertex of the written level: x = its planes' vertices in
+// blocks of 256, y = its planes (RF_TRANSFER_POINT=1 selects the per-point
+// kernels with a flat grid)
+static bool transfer_point() {
+  static const bool on = getenv("RF_TRANSFER_POINT") && atoi(getenv("RF_TRANSFER_POINT")) == 1;
+  return on;
+}
+
 void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s) {
-  const int g = (int)((C.d.nv + 255) / 256);
+  if (transfer_point()) {
+    const int g = (int)((C.d.nv + 255) / 256);
+    if (F.kind == STORE_F64)
+      RF_LAUNCH_PDL(k_restrict<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
+    else
+      RF_LAUNCH_PDL(k_restrict<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
+    return;
+  }
+  const dim3 g((unsigned)((C.d.nx * C.d.ny + 255) / 256), (unsigned)C.d.nz);
   if (F.kind == STORE_F64)
-    RF_LAUNCH_PDL(k_restrict<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
+    RF_LAUNCH_PDL(k_restrict_planes<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)rf, (double2*)bc);
   else
-    RF_LAUNCH_PDL(k_restrict<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
+    RF_LAUNCH_PDL(k_restrict_planes<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)rf, (float2*)bc);
 }
 
 void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s) {
-  const int g = (int)((F.d.nv + 255) / 256);
+  if (transfer_point()) {
+    const int g = (int)((F.d.nv + 255) / 256);
+    if (F.kind == STORE_F64)
+      RF_LAUNCH_PDL(k_prolong<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
+    else
+      RF_LAUNCH_PDL(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
+    return;
+  }
+  const dim3 g((unsigned)((F.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz);
   if (F.kind == STORE_F64)
-    RF_LAUNCH_PDL(k_prolong<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
+    RF_LAUNCH_PDL(k_prolong_planes<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
   else
-    RF_LAUNCH_PDL(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
+    RF_LAUNCH_PDL(k_prolong_planes<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
 }
 
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s) {
