@@ -465,6 +465,10 @@ __global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const
       lin[3 * c + b] = (df.dim == 3 || c == 1) && fj >= 0 && fj < df.ny && fk >= 0 && fk < df.nz;
       lo[3 * c + b] = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx;
     }
+  // every load is issued, without a branch, before the first sum: a value
+  // outside the grid is read at the vertex's own fine position (always
+  // inside) and then skipped, so the 27 loads are one memory round trip
+  const int64_t pf0 = lo[4] + xo[1];
   V r[27];
   uint8_t m[27];
   bool in[27];
@@ -472,15 +476,9 @@ __global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const
   for (int q = 0; q < 27; ++q) {
     const int a = q % 3, bc3 = q / 3;   // bc3 = 3 * (dz + 1) + (dy + 1)
     in[q] = lin[bc3] && xin[a];
-    if (in[q]) {
-      const int64_t pf = lo[bc3] + xo[a];
-      r[q] = rf[pf];
-      m[q] = dmf[pf];
-    } else {
-      r[q].x = 0;
-      r[q].y = 0;
-      m[q] = 1;
-    }
+    const int64_t pf = in[q] ? lo[bc3] + xo[a] : pf0;
+    r[q] = rf[pf];
+    m[q] = dmf[pf];
   }
   T s0 = 0, s1 = 0;
 #pragma unroll
@@ -519,6 +517,9 @@ __global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const 
   for (int c = 0; c < 2; ++c)
 #pragma unroll
     for (int b = 0; b < 2; ++b) lo[2 * c + b] = ((int64_t)(J0 + b) + (int64_t)dc.ny * (K0 + c)) * dc.nx;
+  // as in the restriction, all loads go out before the first sum; a parent
+  // outside the coarse grid is read at coarse vertex 0 and skipped
+  const V xv = xf[pf];
   V c8[8];
   uint8_t m[8];
   bool in[8];
@@ -527,15 +528,9 @@ __global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const 
     const int K = K0 + ((q >> 2) & 1), J = J0 + ((q >> 1) & 1), I = I0 + (q & 1);
     in[q] = ((q & 1) == 0 || (fi & 1)) && (((q >> 1) & 1) == 0 || (fj & 1)) &&
             (((q >> 2) & 1) == 0 || (fk & 1)) && K < dc.nz && J < dc.ny && I < dc.nx;
-    if (in[q]) {
-      const int64_t pc = lo[q >> 1] + xo[q & 1];
-      c8[q] = xc[pc];
-      m[q] = dmc[pc];
-    } else {
-      c8[q].x = 0;
-      c8[q].y = 0;
-      m[q] = 1;
-    }
+    const int64_t pc = in[q] ? lo[q >> 1] + xo[q & 1] : 0;
+    c8[q] = xc[pc];
+    m[q] = dmc[pc];
   }
   const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
   const T wy = (fj & 1) ? (T)0.5 : (T)1;
@@ -547,7 +542,7 @@ __global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const 
     if (!(mf || m[q])) s0 += w * c8[q].x;
     s1 += w * c8[q].y;
   }
-  V o = xf[pf];
+  V o = xv;
   o.x += s0;
   o.y += s1;
   xf[pf] = o;
