@@ -1198,10 +1198,11 @@ void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, boo
 
 // one thread per vertex of the written level: x = its planes' vertices in
 // blocks of 256, y = its planes (RF_TRANSFER_POINT=1 selects the per-point
-// kernels with a flat grid)
+// kernels with a flat grid; read at every launch, so a graph keeps the choice
+// made when it was captured)
 static bool transfer_point() {
-  static const bool on = getenv("RF_TRANSFER_POINT") && atoi(getenv("RF_TRANSFER_POINT")) == 1;
-  return on;
+  const char* e = getenv("RF_TRANSFER_POINT");
+  return e && atoi(e) == 1;
 }
 
 void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s) {

@@ -534,3 +534,36 @@ def test_coarsest_level_size_limit_is_enforced():
     assert e.value.status == rf.RF_EINVAL
     g.gmg_setup([0.1], rf.gmg_opts(2))       # 9^3 x 2 = 1458: fine
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plane_and_point_transfers_are_bitwise_equal(precision, monkeypatch):
+    """The plane-indexed restriction / prolongation kernels gather the same
+    values, apply the same masks and weights and sum in the same order as the
+    per-point kernels (RF_TRANSFER_POINT=1): transfers on every level and a
+    whole solve agree bitwise."""
+    prob = I.random_problem(3, (17, 13, 9), 48)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RF_TRANSFER_POINT", mode)
+        g, F = _assembled(prob)
+        g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(3, "gs8", precision=precision))
+        res = []
+        dims = [(17, 13, 9), (9, 7, 5), (5, 4, 3)]   # vertex-nested: n -> (n - 1) / 2 + 1
+        for level in range(2):
+            nv, nvc = int(np.prod(dims[level])), int(np.prod(dims[level + 1]))
+            r = np.random.default_rng(7 + level).standard_normal(2 * nv)
+            res.append(g.apply(rf.RF_OP_RESTRICT, level, 0, r)[:2 * nvc])
+            xc = np.random.default_rng(9 + level).standard_normal(2 * nvc)
+            x = np.random.default_rng(11 + level).standard_normal(2 * nv)
+            res.append(g.apply(rf.RF_OP_PROLONG, level, 0, xc, x)[:2 * nv])
+        b = torch.tensor(F, device="cuda")
+        x = torch.empty_like(b)
+        info = g.solve(0, b, x, rtol=1e-12, max_it=200)
+        torch.cuda.synchronize()
+        res.append(x.cpu().numpy())
+        out[mode] = (res, info)
+        g.close()
+    assert out["0"][1] == out["1"][1] and out["0"][1]["status"] == 0
+    for a, b_ in zip(out["0"][0], out["1"][0]):
+        assert np.array_equal(a, b_)
