@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -53,9 +54,9 @@ def args_():
                     help="extra solve variants to time: precision[+outer], comma separated")
     ap.add_argument("--sample-nvert", type=int, default=65, help="oracle sample size (vertices per axis)")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-realisation ensemble (1/0)")
-    ap.add_argument("--config5-nvert", type=int, default=0,
+    ap.add_argument("--infiltration-nvert", type=int, default=0,
                     help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
-    ap.add_argument("--config5-steps", type=int, default=20)
+    ap.add_argument("--infiltration-steps", type=int, default=20)
     ap.add_argument("--case4-days", type=float, default=0.0,
                     help="also run the layered Case-4 analogue for this many days with implicit Euler (1-day steps) "
                          "and adaptive LIMEX (0 = off)")
@@ -81,8 +82,9 @@ class Clocks:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        # raw samples: RF_CLOCKS_CSV names the file (default: a temporary one)
+        self.path = os.environ.get("RF_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(), "rf_clocks_bench.csv")
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
         self.p = None
         try:
             self.f = open(self.path, "w")
@@ -128,7 +130,7 @@ def oracle_sample(nvert, smoother):
     size: returns (DoF/s of the solve, seconds, DoF, iterations)."""
     import oracle as O
     from paper_2506_04763_gb300 import inputs as I
-    prob = I.config3(nvert)
+    prob = I.lognormal_lenses_box(nvert)
     m = O.Model(prob)
     F, J, md = O.assemble(m, prob["u0"])
     A = O.make_A(J, md, 1.0 / prob["H"])
@@ -156,7 +158,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "config3 recipe (lognormal K seed 2 + 6 lenses), %d^3 vertices, FP64 "
+            "config": {"workload": "lognormal-lenses box recipe (lognormal K seed 2 + 6 lenses), %d^3 vertices, FP64 "
                                    "BiCGSTAB + FP64 GMG (8-colour GS V(2,2)), rel.res 1e-10" % a.sample_nvert,
                        "dofs": 2 * a.sample_nvert ** 3},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
@@ -211,7 +213,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    prob = I.config3(a.nvert)
+    prob = I.lognormal_lenses_box(a.nvert)
     L = I.levels_for(a.nvert)
     g = rf.Grid(prob)
     dof = 2 * g.nv
@@ -339,10 +341,10 @@ def main():
                                   "per_class_ms_per_solve": {k: round(v["ms"] / len(vinf), 3)
                                                              for k, v in vprof.items()}}
 
-    # ---- one full LIMEX step (config2: 65^3, kappa = 4, FP64 throughout)
+    # ---- one full LIMEX step (65^3 lognormal cube, kappa = 4, FP64 throughout)
     limex = None
     try:
-        p2 = I.config2()
+        p2 = I.lognormal_cube_65()
         g2 = rf.Grid(p2)
         u_ref = torch.tensor(p2["u0"], device=dev)
         opts2 = rf.gmg_opts(p2["nlevels"], "jacobi", precision="fp64")
@@ -360,7 +362,7 @@ def main():
             times.append(a0.elapsed_time(a1))
         lms = statistics.median(times)
         dof2 = 2 * g2.nv
-        limex = {"workload": "config2: 65^3 lognormal K (seed 1), one LIMEX step H = 10 s, kappa = 4 (10 stage "
+        limex = {"workload": "65^3 lognormal K (seed 1), one LIMEX step H = 10 s, kappa = 4 (10 stage "
                              "solves, one Jacobian), FP64 BiCGSTAB + FP64 GMG (5 levels, block Jacobi), rel.res 1e-10",
                  "ms_per_step": round(lms, 2), "dofs_per_s": dof2 / (lms / 1e3), "dofs": dof2,
                  "solves": info2["solves"], "iterations": info2["iterations"], "eps": info2["eps"],
@@ -369,7 +371,7 @@ def main():
     except rf.RFError as e:
         limex = {"error": str(e)}
 
-    # ---- ensemble (config4): 64 realisations on uneven grids, one LIMEX step each
+    # ---- ensemble: 64 realisations on uneven grids, one LIMEX step each
     ensemble = None
     if a.ensemble:
         try:
@@ -397,7 +399,7 @@ def main():
                 gg.limex_step(uu, 10.0, kappa=4, tol=1e-3, gmg=oo)
             torch.cuda.synchronize()
             ts_s = time.perf_counter() - w0
-            ensemble = {"workload": "config4: 64 lognormal realisations (seeds 100..163) on 33^3/49^3/65^3/97^3 "
+            ensemble = {"workload": "64 lognormal realisations (seeds 100..163) on 33^3/49^3/65^3/97^3 "
                                     "(16 each), one LIMEX step each (kappa = 4, 10 solves), FP32 GMG (block "
                                     "Jacobi) / FP64 outer, rel.res 1e-10",
                         "dofs_total": edof, "stage_solves": sum(i["solves"] for i in einfo),
@@ -411,13 +413,13 @@ def main():
         except rf.RFError as e:
             ensemble = {"error": str(e)}
 
-    # ---- config5: adaptive LIMEX on the DNAPL infiltration recipe, mass check
-    config5 = None
-    if a.config5_nvert:
+    # ---- adaptive LIMEX on the DNAPL infiltration recipe, mass check
+    infiltration = None
+    if a.infiltration_nvert:
         try:
             g.close()
             torch.cuda.empty_cache()
-            p5 = I.config5(a.config5_nvert)
+            p5 = I.dnapl_infiltration(a.infiltration_nvert)
             g5 = rf.Grid(p5)
             u5 = torch.tensor(p5["u0"], device=dev)
             m0 = g5.phase_mass(u5)[1]
@@ -425,15 +427,15 @@ def main():
             opts5 = rf.gmg_opts(p5["nlevels"], "gs8", precision="fp32")
             torch.cuda.synchronize()
             w0 = time.perf_counter()
-            t5, hist = g5.limex_run(u5, 10.0, steps=a.config5_steps, tol=1e-3, gmg=opts5, rtol=1e-10, max_it=300)
+            t5, hist = g5.limex_run(u5, 10.0, steps=a.infiltration_steps, tol=1e-3, gmg=opts5, rtol=1e-10, max_it=300)
             torch.cuda.synchronize()
             wall = time.perf_counter() - w0
             m1 = g5.phase_mass(u5)[1]
             dof5 = 2 * g5.nv
             nstep = len(hist)
-            config5 = {"workload": "config5: %d^3 DNAPL infiltration (inlet 0.1 kg m^-2 s^-1, lognormal K seed 3 + "
+            infiltration = {"workload": "%d^3 DNAPL infiltration (inlet 0.1 kg m^-2 s^-1, lognormal K seed 3 + "
                                    "lenses), adaptive LIMEX kappa = 4, TOL 1e-3, H0 = 10 s, FP32 GMG (8-colour GS) / "
-                                   "FP64 outer, rel.res 1e-10" % a.config5_nvert,
+                                   "FP64 outer, rel.res 1e-10" % a.infiltration_nvert,
                        "accepted": sum(h["accepted"] for h in hist), "rejected": sum(1 - h["accepted"] for h in hist),
                        "t_end_s": t5, "wall_s": round(wall, 2), "ms_per_step": round(wall * 1e3 / nstep, 1),
                        "dofs_per_s_per_step": dof5 / (wall / nstep), "dofs": dof5,
@@ -444,7 +446,7 @@ def main():
                        "H_history": [round(h["H"], 3) for h in hist]}
             g5.close()
         except (rf.RFError, RuntimeError) as e:
-            config5 = {"error": str(e)}
+            infiltration = {"error": str(e)}
 
     # ---- Case-4 analogue: fixed-step implicit Euler + Newton against adaptive
     # LIMEX over the same simulated time (the structure of the paper's Table
@@ -516,7 +518,7 @@ def main():
             "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64/%s" % a.precision.replace("fp", "f"), "data": "synthetic",
-            "config": {"workload": "config3: %d^3-vertex box, lognormal K (seed 2) + 6 lenses, A = M/h - J "
+            "config": {"workload": "%d^3-vertex box, lognormal K (seed 2) + 6 lenses, A = M/h - J "
                                    "(h = 10 s) at u0, b = F(u0); FP64 BiCGSTAB (%s operator) + %s GMG (%d levels, %s, "
                                    "V(2,2)), x0 = 0, true rel.res <= 1e-10" % (a.nvert, a.outer.upper(), a.precision.upper(), L,
                                                                             "8-colour block GS" if a.smoother == "gs8" else "block Jacobi w=0.8"),
@@ -535,7 +537,7 @@ def main():
             "variants": variants,
             "limex_step": limex,
             "ensemble": ensemble,
-            "config5": config5,
+            "dnapl_infiltration": infiltration,
             "case4_analogue": case4,
             "e2e": {"value": world * dof / (e2e_ms / 1e3), "unit": "DoF/s", "h2d_bytes_per_step": 16 * g.nv,
                     "d2h_bytes_per_step": 16 * g.nv},

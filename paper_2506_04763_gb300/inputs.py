@@ -11,12 +11,12 @@ Gravity points along -y in 2D and -z in 3D; the domain is the unit square or
 cube; Dirichlet p_w sits on the top face.
 
 Workloads:
-  config1    2D 33x33, sand with a 9x5-cell lens, h = 10 s, 4-level GMG.
-  config2    3D 65^3, lognormal K (ln K ~ N(ln 5e-11, 1), Gaussian covariance,
-             correlation length 8 cells, seed 1).
-  config3    3D 257^3, lognormal K (seed 2) plus 6 random low-K lenses.
-  ensemble   64 realisations (seeds 100..163) on 33^3, 49^3, 65^3, 97^3.
-  config5    3D 385^3, lognormal K (seed 3) plus lenses, NAPL inlet on top.
+  lens_square_2d         2D 33x33, sand with a 9x5-cell lens, h = 10 s, 4-level GMG.
+  lognormal_cube_65      3D 65^3, lognormal K (ln K ~ N(ln 5e-11, 1), Gaussian
+                         covariance, correlation length 8 cells, seed 1).
+  lognormal_lenses_box   3D 257^3, lognormal K (seed 2) plus 6 random low-K lenses.
+  ensemble_member        64 realisations (seeds 100..163) on 33^3, 49^3, 65^3, 97^3.
+  dnapl_infiltration     3D 385^3, lognormal K (seed 3) plus lenses, NAPL inlet on top.
 """
 import numpy as np
 
@@ -136,7 +136,7 @@ def problem(dim, nverts, K, phi, pd, u0, q_in=None, dirmask=None):
     return prob
 
 
-def config1():
+def lens_square_2d():
     """2D 33x33 unit square, sand with a centred 9x5-cell lens (x-cells
     [11,20), y-cells [13,18)); state seed 0; one stage with h = 10 s."""
     dim, nv = 2, (33, 33)
@@ -150,7 +150,7 @@ def config1():
     phi = _paint(dim, n, phi, box, LENS["phi"])
     pd = _paint(dim, n, pd, box, LENS["pd"])
     prob = problem(dim, nv, K, phi, pd, initial_state(dim, n, h, seed=0))
-    prob.update(name="config1-2d-33x33", H=10.0, nlevels=4, smoother="jacobi")
+    prob.update(name="lens-square-2d-33x33", H=10.0, nlevels=4, smoother="jacobi")
     return prob
 
 
@@ -184,14 +184,14 @@ def levels_for(nvert):
     return L
 
 
-def config2():
-    p = lognormal_box(65, seed=1, name="config2-65cube-fp64-limex")
+def lognormal_cube_65():
+    p = lognormal_box(65, seed=1, name="lognormal-cube-65")
     p.update(nlevels=5, smoother="jacobi")
     return p
 
 
-def config3(nvert=257):
-    p = lognormal_box(nvert, seed=2, lenses=6, name="config3-%dcube-lenses" % nvert)
+def lognormal_lenses_box(nvert=257):
+    p = lognormal_box(nvert, seed=2, lenses=6, name="lognormal-lenses-%dcube" % nvert)
     p.update(nlevels=levels_for(nvert), smoother="gs8")
     return p
 
@@ -208,10 +208,10 @@ def ensemble_member(seed, nvert):
     return p
 
 
-def config5(nvert=385, inflow=0.1, half_width=0.05):
+def dnapl_infiltration(nvert=385, inflow=0.1, half_width=0.05):
     """DNAPL infiltration: Neumann NAPL influx (kg m^-2 s^-1) through a top
     patch |x-.5|,|y-.5| <= half_width; Dirichlet p_w on the rest of the top."""
-    p = lognormal_box(nvert, seed=3, lenses=6, name="config5-%dcube-infiltration" % nvert)
+    p = lognormal_box(nvert, seed=3, lenses=6, name="dnapl-infiltration-%dcube" % nvert)
     dim, n, h = 3, p["n"], p["h"]
     x, y, z = _coords(dim, n, h)
     top = top_mask(dim, n).astype(bool)

@@ -14,7 +14,7 @@ def _declared():
     return names
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_boundary_entry_points():
     names = _declared()
     for n in ("rf_grid_create", "rf_assemble", "rf_gmg_setup", "rf_solve", "rf_limex_step", "rf_grid_destroy"):
         assert n in names

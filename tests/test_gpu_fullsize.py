@@ -29,7 +29,7 @@ def big():
     G.build()
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
-    prob = I.config3(NV)
+    prob = I.lognormal_lenses_box(NV)
     g = rf.Grid(prob)
     u = torch.tensor(prob["u0"], device="cuda")
     F = torch.empty_like(u)

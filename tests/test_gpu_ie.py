@@ -28,7 +28,7 @@ def _built():
 CASES = {
     "2d-17": lambda: I.random_problem(2, (17, 17), 41),
     "3d-9x9x5": lambda: I.random_problem(3, (9, 9, 5), 42),
-    "3d-config5-17": lambda: I.config5(17),
+    "3d-infiltration-17": lambda: I.dnapl_infiltration(17),
 }
 
 
@@ -62,7 +62,7 @@ def test_ie_conserves_napl_mass(scheme):
     sqrt(nv) ||R||_2).  The residual norm mixes kg/s rows with the Dirichlet
     rows' p_dir - p_w (Pa), whose rounding floor (~1e-11 Pa per row) is why
     the Newton tolerance is 1e-8 here."""
-    prob = I.config5(33)
+    prob = I.dnapl_infiltration(33)
     prob["scheme"] = scheme
     g = rf.Grid(prob)
     u = torch.tensor(prob["u0"], device="cuda")
@@ -91,11 +91,11 @@ def test_ie_nonconvergence_keeps_the_state():
     g.close()
 
 
-@pytest.mark.parametrize("case,H", [("2d-17", 1000.0), ("3d-config5-9", 1000.0)])
+@pytest.mark.parametrize("case,H", [("2d-17", 1000.0), ("3d-infiltration-9", 1000.0)])
 def test_ie_line_search_matches_oracle(case, H):
     """Steps where the undamped Newton iteration fails and backtracking (at
     most 4 halvings) converges: same Newton count and solution on both sides."""
-    prob = I.config5(9) if case == "3d-config5-9" else CASES[case]()
+    prob = I.dnapl_infiltration(9) if case == "3d-infiltration-9" else CASES[case]()
     g = rf.Grid(prob)
     u = torch.tensor(prob["u0"], device="cuda")
     info = g.ie_step(u, H, atol=0.0, rtol=1e-9, max_newton=40, gmg=rf.gmg_opts(2, precision="fp64"),

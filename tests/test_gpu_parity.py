@@ -24,7 +24,7 @@ torch = pytest.importorskip("torch")
 rf = pytest.importorskip("paper_2506_04763_gb300")
 
 CASES = {
-    "2d-config1": lambda: I.config1(),
+    "2d-lens-33": lambda: I.lens_square_2d(),
     "2d-17x13-stress": lambda: I.random_problem(2, (17, 13), 3, stress=True),
     "3d-9x7x5-stress": lambda: I.random_problem(3, (9, 7, 5), 4, stress=True),
     "3d-17cube": lambda: I.random_problem(3, (17, 17, 17), 5),
@@ -32,7 +32,7 @@ CASES = {
     "2d-even-10x8": lambda: I.random_problem(2, (10, 8), 8),
     # the full-size workload's recipe at 33^3: far-field S_n ~ 1e-13 gives k_rn
     # entries far below the FP32 normal range
-    "3d-config3-33": lambda: I.config3(33),
+    "3d-lenses-33": lambda: I.lognormal_lenses_box(33),
 }
 U32 = 2.0 ** -24
 
@@ -100,7 +100,7 @@ def test_assembly_host_and_device_pointers_agree():
 
 
 # ------------------------------------------------------------------ outer operator
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-9x7x5-stress"])
 def test_fp64_spmv_matches_oracle(case):
     prob = CASES[case]()
     g, F = _assembled(prob)
@@ -131,7 +131,7 @@ def _setup_both(prob, precision, smoother, levels=None):
     return g, F, m, A, gm
 
 
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-33x17x9-nodir"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-33x17x9-nodir"])
 def test_galerkin_levels_match_oracle(case):
     prob = CASES[case]()
     g, F, m, A, gm = _setup_both(prob, "fp64", "jacobi")
@@ -160,7 +160,7 @@ def _rel_bound(Ao, x, b, dim, n, prec):
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "2d-17x13-stress"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "2d-17x13-stress"])
 def test_level_kernels_match_oracle(case, smoother, precision):
     prob = CASES[case]()
     g, F, m, A, gm = _setup_both(prob, precision, smoother)
@@ -221,7 +221,7 @@ def _mask_chain(prob, m, gm, level):
 
 
 @pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube"])
 def test_vcycle_and_coarse_solve_match_oracle(case, smoother):
     prob = CASES[case]()
     g, F, m, A, gm = _setup_both(prob, "fp64", smoother)
@@ -258,7 +258,7 @@ def test_vcycle_cluster_tail_matches_oracle(smoother, precision, monkeypatch):
 # ------------------------------------------------------------------ solves
 @pytest.mark.parametrize("precision,smoother", [("fp64", "jacobi"), ("fp32", "jacobi"), ("fp32", "gs8"),
                                                 ("fp16", "gs8"), ("fp64", "gs8")])
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress", "2d-even-10x8", "3d-config3-33"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-9x7x5-stress", "2d-even-10x8", "3d-lenses-33"])
 def test_solve_matches_oracle(case, precision, smoother):
     prob = CASES[case]()
     g, F = _assembled(prob)
@@ -316,7 +316,7 @@ def test_autotuned_block_sizes_give_identical_solves(precision, smoother, tmp_pa
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-@pytest.mark.parametrize("case", ["2d-config1", "3d-17cube", "3d-9x7x5-stress", "3d-config3-33"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-9x7x5-stress", "3d-lenses-33"])
 def test_solve_with_double_fp32_operator_matches_oracle(case, precision):
     """RF_OUTER_DF32: the iteration's operator applications in double-FP32;
     the FP64 true residual still decides convergence."""
@@ -340,7 +340,7 @@ def test_solve_with_double_fp32_operator_matches_oracle(case, precision):
 
 
 def test_solve_host_buffers_and_zero_rhs():
-    prob = CASES["2d-config1"]()
+    prob = CASES["2d-lens-33"]()
     g, F = _assembled(prob)
     g.gmg_setup([0.1], rf.gmg_opts(4, precision="fp32"))
     x_host = np.zeros(2 * g.nv)
@@ -359,7 +359,7 @@ def test_solve_host_buffers_and_zero_rhs():
 
 
 def test_invalid_arguments_are_rejected():
-    prob = CASES["2d-config1"]()
+    prob = CASES["2d-lens-33"]()
     g = _grid(prob)
     with pytest.raises(rf.RFError) as e:
         g.solve(0, np.zeros(2 * g.nv), np.zeros(2 * g.nv))
@@ -379,7 +379,7 @@ def test_invalid_arguments_are_rejected():
 
 
 def test_nonfinite_state_is_reported():
-    prob = CASES["2d-config1"]()
+    prob = CASES["2d-lens-33"]()
     g, F = _assembled(prob)
     g.gmg_setup([0.1], rf.gmg_opts(4))
     b = F.copy()
@@ -446,7 +446,7 @@ def test_adaptive_limex_conserves_napl_mass():
     elsewhere) at 33^3: over adaptive LIMEX steps the NAPL mass grows exactly
     by the injected mass (every stage is a divergence-form balance, the
     extrapolation weights sum to one), up to the linear solves' residuals."""
-    prob = I.config5(33)
+    prob = I.dnapl_infiltration(33)
     g = _grid(prob)
     u = torch.tensor(prob["u0"], device="cuda")
     m0 = g.phase_mass(u)[1]

@@ -22,7 +22,7 @@ CASES = {
     "2d-17x13-stress": lambda: I.random_problem(2, (17, 13), 3, stress=True),
     "3d-9x7x5-stress": lambda: I.random_problem(3, (9, 7, 5), 4, stress=True),
     "3d-17cube": lambda: I.random_problem(3, (17, 17, 17), 5),
-    "3d-config5-17": lambda: I.config5(17),
+    "3d-infiltration-17": lambda: I.dnapl_infiltration(17),
 }
 
 
@@ -70,7 +70,7 @@ def test_scheme_change_drops_the_jacobian_and_rejects_unknown_bits():
 
 @pytest.mark.parametrize("scheme", [0, 1])
 def test_phase_mass_matches_oracle_storage(scheme):
-    prob = I.config5(17)
+    prob = I.dnapl_infiltration(17)
     prob["scheme"] = scheme
     g = rf.Grid(prob)
     u = torch.tensor(prob["u0"], device="cuda")
@@ -107,7 +107,7 @@ def test_variants_on_dnapl_infiltration_mass_and_solution():
     integration.  Both variants change the NAPL field, by a bounded amount."""
     out = {}
     for scheme in (0, 1, 2):
-        prob = I.config5(33)
+        prob = I.dnapl_infiltration(33)
         prob["scheme"] = scheme
         g = rf.Grid(prob)
         u = torch.tensor(prob["u0"], device="cuda")

@@ -1,5 +1,5 @@
-"""The workload configurations end to end against the oracle: config 2 (one
-full FP64 LIMEX step at 65^3) and ensemble members of config 4 (one LIMEX
+"""The workloads end to end against the oracle: the 65^3 lognormal cube (one
+full FP64 LIMEX step) and members of the 64-realisation ensemble (one LIMEX
 step with FP32 multigrid inside FP64 BiCGSTAB, at 33^3 and 49^3).  The 97^3
 members and the 257^3 / 385^3 configurations are checked by sampled rows and
 invariants in test_gpu_fullsize.py and test_gpu_parity.py (the oracle would
@@ -49,15 +49,15 @@ def _limex_parity(prob, precision, smoother, H=10.0):
     return info, inf_o
 
 
-def test_config2_limex_step_matches_oracle():
-    """Config 2: 65^3 lognormal field (seed 1), kappa = 4, H = 10 s, FP64
+def test_lognormal_cube_65_limex_step_matches_oracle():
+    """65^3 lognormal field (seed 1), kappa = 4, H = 10 s, FP64
     throughout with 5-level block-Jacobi multigrid."""
-    info, inf_o = _limex_parity(I.config2(), "fp64", "jacobi")
-    print("config2 GPU iterations", info["iterations"], "oracle", inf_o["iterations"])
+    info, inf_o = _limex_parity(I.lognormal_cube_65(), "fp64", "jacobi")
+    print("65^3 LIMEX step: GPU iterations", info["iterations"], "oracle", inf_o["iterations"])
 
 
 @pytest.mark.parametrize("seed,nvert", [(100, 33), (116, 49)])
 def test_ensemble_member_limex_step_matches_oracle(seed, nvert):
-    """Config 4 members (seed order: 33^3 for seeds 100..115, 49^3 for
+    """Ensemble members (seed order: 33^3 for seeds 100..115, 49^3 for
     116..131): one LIMEX step with FP32 multigrid inside FP64 BiCGSTAB."""
     _limex_parity(I.ensemble_member(seed, nvert), "fp32", "jacobi")

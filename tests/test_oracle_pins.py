@@ -51,7 +51,7 @@ def test_dof_counts_match_paper():
 
 # ---------------------------------------------------------------- laws
 def test_brooks_corey_special_values(oracle):
-    m = oracle.Model(I.config1())
+    m = oracle.Model(I.lens_square_2d())
     kr = oracle.brooks_corey(m, 1.0)
     assert kr[0] == 1.0 and kr[2] == 0.0 and kr[4] == 1.0     # krw(1)=1, krn(1)=0, J(1)=1
     kr = oracle.brooks_corey(m, 0.0)
@@ -66,7 +66,7 @@ def test_brooks_corey_special_values(oracle):
 def test_brooks_corey_lambda2_path_equals_general_pow_path(oracle):
     """The sqrt/integer-power special case for lambda=2 agrees with the general
     pow() path evaluated at lambda = 2 + 1e-12."""
-    p = I.config1()
+    p = I.lens_square_2d()
     m2 = oracle.Model(p)
     p2 = dict(p)
     p2["lam"] = 2.0 + 1e-12
@@ -78,7 +78,7 @@ def test_brooks_corey_lambda2_path_equals_general_pow_path(oracle):
 
 
 def test_brooks_corey_derivatives_by_finite_differences(oracle):
-    m = oracle.Model(I.config1())
+    m = oracle.Model(I.lens_square_2d())
     for s in np.linspace(0.02, 0.98, 25):
         d = 1e-6
         f0 = oracle.brooks_corey(m, s)
@@ -100,7 +100,7 @@ def test_case4_threshold_saturation(oracle):
     oracle's S hat (Eq. hSw) must switch from the capped branch (S_e hat = 1,
     NAPL blocked) to the open branch exactly at that wetting saturation."""
     g = _read_golden("case4_threshold.txt")
-    p = I.config1()
+    p = I.lens_square_2d()
     p["S_wr"], p["S_nr"], p["lam"] = float(g["S_wr"]), float(g["S_nr"]), float(g["lambda"])
     m = oracle.Model(p)
     pd2 = float(g["pd_coef"]) * float(g["K2"]) ** float(g["pd_exp"])
@@ -125,7 +125,7 @@ def test_case4_threshold_saturation(oracle):
 
 
 def test_shat_branches(oracle):
-    m = oracle.Model(I.config1())
+    m = oracle.Model(I.lens_square_2d())
     assert list(oracle.shat(m, 0.4, 755.0, 755.0)) == [0.4, 1.0]      # case 1
     r2 = (1163.0 / 755.0) ** 2
     out = oracle.shat(m, 0.3, 1163.0, 755.0)                           # case 3
@@ -645,7 +645,7 @@ def test_ie_napl_mass_balance(oracle, scheme):
     """Every implicit Euler step is a discrete balance: with a NAPL source and
     no NAPL Dirichlet rows, sum_i (m_n,i(u1) - m_n,i(u0)) = H sum_i q_n,i up to
     the Newton residual, also with the nonlinear S hat storage."""
-    p = I.config5(9)
+    p = I.dnapl_infiltration(9)
     p["scheme"] = scheme
     m = oracle.Model(p)
     H = 20.0
@@ -768,7 +768,7 @@ def test_ie_line_search_converges_where_plain_newton_fails(oracle):
     not converge in 40 iterations, backtracking (at most 4 halvings) does, and
     the result solves the implicit Euler equations, checked here from the
     oracle's flux residual and storage rather than the step's own report."""
-    p = I.config5(9)
+    p = I.dnapl_infiltration(9)
     m = oracle.Model(p)
     H = 1000.0
     _, plain = oracle.ie_step(m, p["u0"], H, nlevels=2, atol=0.0, rtol=1e-9, lin_rtol=1e-12, max_newton=40)
