@@ -462,6 +462,29 @@ def test_limex_columns_match_dense_linearly_implicit_euler(oracle):
     np.testing.assert_allclose(u_out[1::2], T22[1::2], atol=1e-11)
 
 
+def test_step_control_order_clamps_and_rejection(oracle):
+    """Step control of Sec. 4 with the order reduced to q = 2: the estimate eps
+    does not depend on TOL, the new step grows with TOL^(1/(q+1)) (eight times
+    the tolerance doubles it) and is clamped to [0.2, 4] times H; a step with
+    eps > TOL is rejected and leaves the state unchanged."""
+    p = I.random_problem(2, (9, 9), 18)
+    m = oracle.Model(p)
+    Hh, rho = 2.0, 0.75
+    kw = dict(kappa=3, rho=rho, nlevels=3, rtol=1e-13, maxit=300)
+    _, ref = oracle.limex_step(m, p["u0"], Hh, tol=1e9, **kw)
+    eps = ref["eps"]
+    assert eps > 0 and ref["H_new"] == 4.0 * Hh and ref["accepted"] == 1
+    t1 = 1.5 * eps / rho                 # (rho TOL / eps)^(1/3) = 1.5^(1/3), unclamped
+    _, a = oracle.limex_step(m, p["u0"], Hh, tol=t1, **kw)
+    _, b = oracle.limex_step(m, p["u0"], Hh, tol=8.0 * t1, **kw)
+    assert a["eps"] == eps and b["eps"] == eps
+    assert a["accepted"] == 1 and b["accepted"] == 1
+    assert b["H_new"] / a["H_new"] == pytest.approx(2.0, rel=1e-12)
+    u_r, r = oracle.limex_step(m, p["u0"], Hh, tol=1e-6 * eps, **kw)
+    assert r["accepted"] == 0 and r["H_new"] == pytest.approx(0.2 * Hh, rel=1e-15)
+    assert np.array_equal(u_r, p["u0"])
+
+
 def test_error_norm_quadratures(oracle):
     """H1 seminorm of a linear function = |a|^2 |Omega|; of x*y on the unit
     square = 2/3 (bilinear, exact); lumped L2 of 1 = |Omega|."""
