@@ -428,12 +428,15 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
   prolong_point<T>(df, dc, dmf, dmc, xc, xf, pf);
 }
 
-// The same transfers with the vertex taken from the launch shape: a plane per
-// blockIdx.y and the position within it by one 32-bit division, with the
-// line offsets of the gathered values computed once per vertex instead of a
-// 64-bit pidx per value (and pcoords' 64-bit divisions per vertex), which made
-// the per-point kernels above integer-bound.  Loads, masks, weights and the
-// order of the sums are those of restrict_point / prolong_point.
+// The same transfers, organised for memory-level parallelism.  The per-point
+// kernels above put each gathered load behind its own bounds branch.  These
+// issue every load before the first sum: a value outside the grid is read at
+// an in-grid address and then skipped.  They also take the vertex from the
+// launch shape (a plane per blockIdx.y, the position within it by one 32-bit
+// division) and compute the gathered lines' offsets once per vertex, instead
+// of pcoords and a 64-bit pidx per value.  Loads, masks, weights and the order
+// of the sums are those of restrict_point / prolong_point, so the results are
+// bitwise equal.  At 257^3 the transfers take 3.14 ms per solve against 4.14.
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
                                                          const uint8_t* __restrict__ dmc,
