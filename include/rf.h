@@ -278,10 +278,18 @@ rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, do
  * address (cudaGetSymbolAddress) and should therefore come before any stream
  * capture.  Calls share the array: calls that overlap on the GPU race and must
  * be serialised by the caller.  Returns RF_EINVAL for N outside
- * [1, RF_NOALLOC_MAX_N] or non-device pointers, RF_ENONFINITE for a singular
- * matrix; synchronises `stream` before returning. */
+ * [1, RF_NOALLOC_MAX_N] or for pointers that are not device (or managed)
+ * memory of the current device, RF_ENONFINITE for a singular matrix or one
+ * with non-finite entries; synchronises `stream` before returning. */
 #define RF_NOALLOC_MAX_N 512
 rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ainv, void* stream);
+
+/* FP64 fused multiply-add throughput of the current GPU (FMA per second),
+ * timed with CUDA events on `stream`: 8 independent FMA chains per thread, 8
+ * blocks of 256 threads per SM.  The roofline denominator of the kernels that
+ * the FP64 pipe, not HBM, bounds (outer operator, vector updates, assembly).
+ * Synchronises `stream`. */
+rf_status rf_fp64_fma_rate(void* stream, double* fma_per_s);
 
 /* Kernels launched by this library in this process so far. */
 int64_t rf_launch_count(void);

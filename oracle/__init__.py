@@ -27,7 +27,7 @@ def build(force=False):
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= newest:
         return _SO
     tmp = _SO + ".%d.tmp" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                            "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _SO)
     return _SO
@@ -74,6 +74,8 @@ _D = ctypes.c_double
 
 def _declare(L):
     sig = {
+        "rfo_set_threads": (None, [_I]),
+        "rfo_get_threads": (_I, []),
         "rfo_brooks_corey": (None, [_P, _D, _P]),
         "rfo_shat": (None, [_P, _D, _D, _D, _P]),
         "rfo_pdmin": (None, [_P, _P]),
@@ -150,6 +152,16 @@ class Model:
     @property
     def ref(self):
         return ctypes.byref(self.s)
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's per-vertex loops (results are bitwise
+    the same for any count)."""
+    lib().rfo_set_threads(int(n))
+
+
+def get_threads():
+    return int(lib().rfo_get_threads())
 
 
 def brooks_corey(model, Se):

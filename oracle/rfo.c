@@ -23,13 +23,41 @@
  *
  * Readings where the paper is silent are listed in the repository's design
  * notes and restated at each use below.
+ *
+ * Threads: loops whose iterations write disjoint outputs and read nothing
+ * another iteration writes (per-vertex rows of a mat-vec, a Jacobi sweep, one
+ * colour of the multicolour sweep, a transfer, an elementwise vector update)
+ * carry a plain "omp parallel for".  Each output is then computed by exactly
+ * the same operations in the same order as in a serial run, so results are
+ * bitwise independent of the thread count.  Sums over the whole grid (inner
+ * products, norms) and the element and Galerkin loops, which add into shared
+ * rows, stay serial.
  */
 #include "rfo.h"
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
 static int nverts(const int n[3]) { return n[0] * n[1] * n[2]; }
+
+void rfo_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+
+int rfo_get_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 static int nblk(int dim) { return dim == 3 ? 27 : 9; }
 static int blk_index(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
 /* In 2D dz is always 0, so the 2D index (dx+1)+3(dy+1) is blk_index - 9. */
@@ -238,6 +266,7 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
   double* krw = malloc(sizeof(double) * nv);
   double* dkrw = malloc(sizeof(double) * nv);
   rfo_pdmin(m, pdmin);
+#pragma omp parallel for schedule(static)
   for (int v = 0; v < nv; ++v) {
     double bc[6];
     Se[v] = (1.0 - u[2 * v + 1] - m->S_wr) / den;
@@ -388,6 +417,7 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
  * divided by tau).                                                          */
 void rfo_make_A(int nv, int nb, const double* J, const double* mdiag, double shift, double* A) {
   const int c = (nb == 27) ? 13 : 4;
+#pragma omp parallel for schedule(static)
   for (size_t t = 0; t < (size_t)nv * nb * 4; ++t) A[t] = -J[t];
   for (int v = 0; v < nv; ++v) {
     A[((size_t)v * nb + c) * 4 + 1] += shift * mdiag[2 * v];
@@ -416,6 +446,7 @@ static void row_apply(int dim, const int n[3], const double* A, const double* x,
 }
 
 void rfo_spmv(int dim, const int n[3], const double* A, const double* x, double* y) {
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < n[2]; ++k)
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
@@ -428,7 +459,9 @@ void rfo_spmv(int dim, const int n[3], const double* A, const double* x, double*
 
 void rfo_residual(int dim, const int n[3], const double* A, const double* b, const double* x, double* r) {
   rfo_spmv(dim, n, A, x, r);
-  for (int t = 0; t < 2 * nverts(n); ++t) r[t] = b[t] - r[t];
+  const int N = 2 * nverts(n);
+#pragma omp parallel for schedule(static)
+  for (int t = 0; t < N; ++t) r[t] = b[t] - r[t];
 }
 
 /* 2x2 diagonal-block inverse applied to s. */
@@ -442,6 +475,7 @@ static void dsolve(const double* a, const double s[2], double y[2]) {
 void rfo_jacobi(int dim, const int n[3], const double* A, const double* b, const double* xin,
                 double* xout, double omega) {
   const int nb = nblk(dim);
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < n[2]; ++k)
     for (int j = 0; j < n[1]; ++j)
       for (int i = 0; i < n[0]; ++i) {
@@ -463,6 +497,7 @@ void rfo_gs_sweep(int dim, const int n[3], const double* A, const double* b, dou
   const int nb = nblk(dim), ncol = 1 << dim;
   for (int cc = 0; cc < ncol; ++cc) {
     int col = forward ? cc : ncol - 1 - cc;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
         for (int i = 0; i < n[0]; ++i) {
@@ -494,6 +529,7 @@ static double pweight(int dim, int fi, int fj, int fk, int I, int J, int K) {
 
 void rfo_restrict(int dim, const int nf[3], const unsigned char* dmf, const int nc[3],
                   const unsigned char* dmc, const double* rf, double* bc) {
+#pragma omp parallel for collapse(2) schedule(static)
   for (int K = 0; K < nc[2]; ++K)
     for (int J = 0; J < nc[1]; ++J)
       for (int I = 0; I < nc[0]; ++I) {
@@ -515,6 +551,7 @@ void rfo_restrict(int dim, const int nf[3], const unsigned char* dmf, const int 
 
 void rfo_prolong_add(int dim, const int nf[3], const unsigned char* dmf, const int nc[3],
                      const unsigned char* dmc, const double* xc, double* xf) {
+#pragma omp parallel for collapse(2) schedule(static)
   for (int fk = 0; fk < nf[2]; ++fk)
     for (int fj = 0; fj < nf[1]; ++fj)
       for (int fi = 0; fi < nf[0]; ++fi) {
@@ -768,18 +805,27 @@ int rfo_bicgstab(int dim, const int n[3], const double* A, rfo_gmg* g, const dou
   for (it = 1; it <= maxit; ++it) {
     double rho = dot(N, rh, r);
     double beta = (rho / rho_old) * (alpha / omega);
+#pragma omp parallel for schedule(static)
     for (int q = 0; q < N; ++q) p[q] = r[q] + beta * (p[q] - omega * v[q]);
     if (g) rfo_gmg_vcycle(g, p, y); else memcpy(y, p, sizeof(double) * N);
     rfo_spmv(dim, n, A, y, v);
     alpha = rho / dot(N, rh, v);
+    /* Breakdown <r_hat, v> = 0 (a reading: the paper names BiCGSTAB only):
+     * no BiCG half step (alpha = 0, so x and r stay finite), and a restart
+     * from the current x after the minimal-residual half step below. */
+    const int broke = !isfinite(alpha);
+    if (broke) alpha = 0.0;
+#pragma omp parallel for schedule(static)
     for (int q = 0; q < N; ++q) s[q] = r[q] - alpha * v[q];
     if (g) rfo_gmg_vcycle(g, s, z); else memcpy(z, s, sizeof(double) * N);
     rfo_spmv(dim, n, A, z, t);
     double tt = dot(N, t, t);
     omega = (tt > 0.0) ? dot(N, t, s) / tt : 0.0;
+#pragma omp parallel for schedule(static)
     for (int q = 0; q < N; ++q) { x[q] += alpha * y[q] + omega * z[q]; r[q] = s[q] - omega * t[q]; }
     rho_old = rho;
-    int restart = !(omega != 0.0) || !isfinite(omega) || !isfinite(alpha);
+    /* the next <r_hat, r> vanishing is a breakdown as well */
+    int restart = !(omega != 0.0) || !isfinite(omega) || broke || !(dot(N, rh, r) != 0.0);
     if (sqrt(dot(N, r, r)) <= rtol * bn || restart) {
       rfo_residual(dim, n, A, b, x, r);
       rel = sqrt(dot(N, r, r)) / bn;

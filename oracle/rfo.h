@@ -49,6 +49,11 @@ typedef struct {
  *     upwinded too. The NAPL flux is unchanged (u_n and v_n share their sign). */
 enum { RFO_SCHEME_SHAT_STORAGE = 1, RFO_SCHEME_DARCY_UPWIND = 2 };
 
+/* ---- threads: OpenMP threads of the per-vertex loops (results do not depend
+ * on the count; see rfo.c) ---- */
+void rfo_set_threads(int n);
+int rfo_get_threads(void);
+
 /* ---- constitutive laws (Brooks-Corey; interface condition) ---- */
 void rfo_brooks_corey(const rfo_model* m, double Se, double out[6]);
 /* out = {krw, dkrw/dSe, krn, dkrn/dSe, J, dJ/dSe} */

@@ -124,6 +124,7 @@ SIGNATURES = {
     "rf_dense_inverse_noalloc": (_I, [_I, _P, _P, _P]),
     "rf_profile": (_I, [_P, _I]),
     "rf_profile_read": (_I, [_P, _I, _P, _P, _P]),
+    "rf_fp64_fma_rate": (_I, [_P, _P]),
     "rf_launch_count": (_I64, []),
     "rf_status_string": (ctypes.c_char_p, [_I]),
     "rf_last_error": (ctypes.c_char_p, []),
@@ -255,6 +256,13 @@ def rf_profile_read(grid, cls):
     return ms.value, n.value, by.value
 
 
+def rf_fp64_fma_rate(stream=None):
+    """Measured FP64 FMA/s of the current GPU (rf_fp64_fma_rate)."""
+    v = ctypes.c_double()
+    _check(lib().rf_fp64_fma_rate(_stream_handle(stream), ctypes.byref(v)))
+    return v.value
+
+
 def rf_launch_count():
     return int(lib().rf_launch_count())
 
@@ -337,7 +345,8 @@ class Grid:
         mat = rf_materials(prob["S_wr"], prob["S_nr"], prob["lam"], _ptr(keep["K"]), _ptr(keep["phi"]),
                            _ptr(keep["pd"]))
         bc = rf_bc(_ptr(keep["dir"]), _ptr(keep["pw_dir"]), _ptr(keep["q_in"]))
-        self._alloc = _torch_allocator() if allocator == "torch" else None
+        # "torch": PyTorch's caching allocator; None: cudaMalloc; or an rf_allocator
+        self._alloc = _torch_allocator() if allocator == "torch" else allocator
         self.handle = rf_grid_create(desc, fl, mat, bc, self._alloc, self.stream)
         if int(prob.get("scheme", 0)):
             self.set_scheme(prob["scheme"])

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "librf")
 LIB = os.path.join(PKG, "librf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"assemble.cu": ["-fmad=false"], "levelops.cu": [], "krylov.cu": [], "driver.cu": [], "noalloc.cu": []}
+UNITS = {"assemble.cu": ["-fmad=false"], "levelops.cu": [], "krylov.cu": [], "driver.cu": [], "noalloc.cu": [], "probe.cu": []}
 
 
 def nvcc():

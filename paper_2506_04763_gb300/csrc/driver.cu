@@ -834,7 +834,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     CU(cudaMemcpyAsync(hst, status, sizeof(int) * nshift, cudaMemcpyDeviceToHost, (cudaStream_t)s));
     CU(cudaStreamSynchronize((cudaStream_t)s));
     for (int j = 0; j < nshift; ++j)
-      if (hst[j]) { dfree_all(g, g->gbufs, s); return fail(RF_ENONFINITE, "coarsest operator is singular (shift %d)", j); }
+      if (hst[j]) { dfree_all(g, g->gbufs, s); return fail(RF_ENONFINITE, "coarsest operator is singular or not finite (shift %d)", j); }
   }
   // Krylov preconditioned vectors in the preconditioner type
   {

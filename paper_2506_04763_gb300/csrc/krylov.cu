@@ -353,9 +353,12 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
     const double rhv = sum_partials(partial, S_RHV, nblk);
     if (threadIdx.x == 0) {
       scal[S_RHV] = rhv;
-      const double a = scal[S_RHO] / rhv;
+      double a = scal[S_RHO] / rhv;
+      // <r_hat, v> = 0: no BiCG half step.  alpha = 0 keeps x and r finite
+      // (the iteration finishes as a minimal-residual step along z), and the
+      // flag sends the host to the true-residual check and a restart.
+      if (!isfinite(a)) { scal[S_BREAK] = 1.0; a = 0.0; }
       scal[S_ALPHA] = a;
-      if (!isfinite(a)) scal[S_BREAK] = 1.0;
     }
   } else if (stage == 2) {
     const double ts = sum_partials(partial, S_TS, nblk);

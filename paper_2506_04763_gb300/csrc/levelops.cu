@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int*
       int bidx = sidx[0];
       for (int w = 1; w < nw; ++w)
         if (sval[w] > bv || (sval[w] == bv && sidx[w] < bidx)) { bv = sval[w]; bidx = sidx[w]; }
-      if (!(bv > 0.0)) { status[0] = 1; bidx = c; }
+      if (!(bv > 0.0) || !isfinite(bv)) { status[0] = 1; bidx = c; }
       sp = bidx;
       piv[c] = bidx;
     }
@@ -977,6 +977,9 @@ __global__ void __launch_bounds__(1024) k_lu(int N, double* __restrict__ D, int*
     const double dc = prow[c];
     for (int r = c + 1 + tid; r < N; r += nt) {
       const double l = (dc != 0.0) ? D[(int64_t)r * N + c] / dc : 0.0;
+      // a NaN entry is never picked as pivot (fabs(NaN) > best is false) but
+      // reaches the factors through its multiplier: report it
+      if (!isfinite(l)) status[0] = 1;
       mult[r] = l;
       D[(int64_t)r * N + c] = l;
     }

@@ -55,20 +55,30 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// Whether p is memory the kernels of the CURRENT device may use: device memory
+// of that device, or managed memory.  Memory of another GPU is refused: the
+// copy into the scratch array would cross devices and the kernel would write
+// Ainv through a peer mapping that may not exist.
+bool on_this_device(const void* p) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
 
 extern "C" rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ainv, void* stream) {
   if (N < 1 || N > kMaxN) return RF_EINVAL;   // beyond the reserved scratch
-  if (!A || !Ainv || !on_device(A) || !on_device(Ainv)) return RF_EINVAL;
+  if (!A || !Ainv || !on_this_device(A) || !on_this_device(Ainv)) return RF_EINVAL;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return RF_ECUDA;
   double* LU = static_cast<double*>(base);
