@@ -37,6 +37,16 @@ RTOL = 1e-10
 # algorithmic count is 456 B.
 GS_TRAFFIC_PER_COLOUR_VERTEX = 560.0
 GS_ALGO_PER_COLOUR_VERTEX = 456.0
+# FP64 floating-point operations per vertex of one outer operator application
+# (k_bicg_v / k_bicg_t): 27 blocks x 4 FMA (216 flop), the shift*M diagonal
+# (4 flop) and the fused inner products (<rh, v>: 4 flop; <t, s>, <t, t>: 8
+# flop), averaged over the two applications of an iteration.
+SPMV64_FLOP_PER_VERTEX = 216.0 + 4.0 + 6.0
+# FP64 instructions (DADD + DMUL + DFMA) per vertex of one K1 assembly with the
+# Jacobian, from one ncu capture of this recipe at 129^3 (231 per cycle over
+# 18.6 ms per assembly); K1 is FP64-issue-bound, so its roofline is that
+# instruction rate against the FMA issue rate rf_fp64_fma_rate measures.
+K1_FP64_INST_PER_VERTEX = 4150.0
 
 
 def args_():
@@ -51,12 +61,13 @@ def args_():
     ap.add_argument("--outer", default="fp64", choices=["fp64", "df32"],
                     help="arithmetic of the operator applications inside the iteration")
     ap.add_argument("--variants", default="fp64,fp16,fp32+df32",
-                    help="extra solve variants to time: precision[+outer], comma separated")
-    ap.add_argument("--sample-nvert", type=int, default=65, help="oracle sample size (vertices per axis)")
+                    help="extra solve variants to time: precision[+outer], comma separated ('none': no variants)")
+    ap.add_argument("--sample-nvert", type=int, default=129, help="oracle sample size (vertices per axis)")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-realisation ensemble (1/0)")
-    ap.add_argument("--infiltration-nvert", type=int, default=0,
+    ap.add_argument("--infiltration-nvert", type=int, default=385,
                     help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
-    ap.add_argument("--infiltration-steps", type=int, default=20)
+    ap.add_argument("--infiltration-steps", type=int, default=3,
+                    help="accepted steps of the infiltration run (the workload's 20 take ~3 minutes)")
     ap.add_argument("--case4-days", type=float, default=0.0,
                     help="also run the layered Case-4 analogue for this many days with implicit Euler (1-day steps) "
                          "and adaptive LIMEX (0 = off)")
@@ -125,21 +136,37 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ oracle baseline
-def oracle_sample(nvert, smoother):
-    """The CPU oracle (as it stands, one thread) on the same recipe at a bounded
-    size: returns (DoF/s of the solve, seconds, DoF, iterations)."""
-    import oracle as O
-    from paper_2506_04763_gb300 import inputs as I
-    prob = I.lognormal_lenses_box(nvert)
-    m = O.Model(prob)
-    F, J, md = O.assemble(m, prob["u0"])
-    A = O.make_A(J, md, 1.0 / prob["H"])
-    gm = O.GMG(3, m.n, A, prob["dir"], I.levels_for(nvert), smoother=O.GS8 if smoother == "gs8" else O.JACOBI)
-    t0 = time.perf_counter()
-    x, info = O.bicgstab(3, m.n, A, gm, F, rtol=RTOL, maxit=200)
-    dt = time.perf_counter() - t0
-    dof = 2 * m.nv
-    return dof / dt, dt, dof, info["iterations"]
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+class OracleSample:
+    """The CPU oracle (as it stands) on the same recipe at a bounded size: the
+    system is assembled and the multigrid set up once; solve(threads) times one
+    BiCGSTAB-GMG solve from x0 = 0 to 1e-10 with that many OpenMP threads
+    (results are bitwise the same for any count).  Returns (DoF/s, seconds,
+    iterations)."""
+
+    def __init__(self, nvert, smoother):
+        import oracle as O
+        from paper_2506_04763_gb300 import inputs as I
+        self.O = O
+        O.set_threads(host_cores())
+        prob = I.lognormal_lenses_box(nvert)
+        self.m = O.Model(prob)
+        self.F, J, md = O.assemble(self.m, prob["u0"])
+        self.A = O.make_A(J, md, 1.0 / prob["H"])
+        del J
+        self.gm = O.GMG(3, self.m.n, self.A, prob["dir"], I.levels_for(nvert),
+                        smoother=O.GS8 if smoother == "gs8" else O.JACOBI)
+        self.dof = 2 * self.m.nv
+
+    def solve(self, threads):
+        self.O.set_threads(threads)
+        t0 = time.perf_counter()
+        x, info = self.O.bicgstab(3, self.m.n, self.A, self.gm, self.F, rtol=RTOL, maxit=200)
+        dt = time.perf_counter() - t0
+        return self.dof / dt, dt, info["iterations"]
 
 
 def run_reference(a):
@@ -148,9 +175,11 @@ def run_reference(a):
         return
     import oracle as O
     O.build()
+    cores = host_cores()
+    sample = OracleSample(a.sample_nvert, a.smoother)
     vals = []
     for k in range(a.warmup + a.steps):
-        v, dt, dof, it = oracle_sample(a.sample_nvert, a.smoother)
+        v, dt, it = sample.solve(cores)
         if k >= a.warmup:
             vals.append((v, dt, it))
     value = statistics.median([v for v, _, _ in vals])
@@ -161,14 +190,18 @@ def run_reference(a):
             "config": {"workload": "lognormal-lenses box recipe (lognormal K seed 2 + 6 lenses), %d^3 vertices, FP64 "
                                    "BiCGSTAB + FP64 GMG (8-colour GS V(2,2)), rel.res 1e-10" % a.sample_nvert,
                        "dofs": 2 * a.sample_nvert ** 3},
-            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-                             "sample": "oracle solve of the same recipe at %d^3 vertices (set-up excluded)"
-                                       % a.sample_nvert},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+                             "sample": "oracle solve of the same recipe at %d^3 vertices (set-up excluded), OpenMP "
+                                       "over vertices on %d host cores" % (a.sample_nvert, cores)},
             "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ------------------------------------------------------------------ multi-rank helpers
+def per_class_frac(v, hbm):
+    return round(v["bytes"] / (v["ms"] / 1e3) / 1e9 / hbm, 4) if v["ms"] > 0 else None
+
+
 def max_over_ranks(ms, world, device=None):
     """The job's time is its slowest rank's: MAX all-reduce of a per-rank time
     (ms) over the process group; a single process returns ms unchanged."""
@@ -212,6 +245,9 @@ def main():
         dist.barrier()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
+
+    fma_rate = rf.rf_fp64_fma_rate()        # FP64 FMA/s of this GPU, measured here
+    fp64_peak_tflops = 2.0 * fma_rate / 1e12
 
     prob = I.lognormal_lenses_box(a.nvert)
     L = I.levels_for(a.nvert)
@@ -314,6 +350,21 @@ def main():
                    "algorithmic_bytes_per_launch": GS_ALGO_PER_COLOUR_VERTEX * colour_vertices,
                    "launch": "one full-sweep colour (nv/8 vertices)",
                    "source": "ncu capture at 129^3 scaled by vertices"}
+    # the FP64 pipe's roofline of the outer operator (FP64-pipe-bound: 108 FMA
+    # per 864 B of J), against the FMA rate measured above
+    sp = prof["spmv64"]
+    spmv_tflops = SPMV64_FLOP_PER_VERTEX * g.nv * sp["launches"] / (sp["ms"] / 1e3) / 1e12 if sp["ms"] > 0 else None
+    roofline_fp64 = {"bound": "fp64", "kernel": "spmv64", "achieved": round(spmv_tflops, 4) if spmv_tflops else None,
+                     "peak": round(fp64_peak_tflops, 4), "unit": "TFLOP/s",
+                     "frac": round(spmv_tflops / fp64_peak_tflops, 4) if spmv_tflops else None,
+                     "flop_per_vertex": SPMV64_FLOP_PER_VERTEX,
+                     "hbm_frac_same_kernel": per_class_frac(sp, pk["hbm"]),
+                     "peak_source": "rf_fp64_fma_rate in this process (8 FMA chains per thread, 2 flop per FMA)"}
+    k1_rate = K1_FP64_INST_PER_VERTEX * g.nv / (asm_ms / 1e3)
+    roofline_fp64["k1_assembly"] = {"kernel": "k_assemble_cells", "achieved_inst_per_s": k1_rate,
+                                    "peak_inst_per_s": fma_rate, "frac": round(k1_rate / fma_rate, 4),
+                                    "inst_per_vertex": K1_FP64_INST_PER_VERTEX,
+                                    "source": "FP64 instruction count per vertex from ncu at 129^3; time measured here"}
     shares = {k: round(v["ms"] / sum(p["ms"] for p in prof.values()), 4) for k, v in prof.items()}
     per_class = {k: {"ms_per_step": round(v["ms"] / a.steps, 3), "launches": v["launches"],
                      "GB_per_s": round(v["bytes"] / (v["ms"] / 1e3) / 1e9, 1) if v["ms"] > 0 else None,
@@ -322,7 +373,7 @@ def main():
 
     # ---- variants of the same solve: all-FP64 GPU path, FP16 storage
     variants = {}
-    for var in [v for v in a.variants.split(",") if v and v != "%s+%s" % (a.precision, a.outer)]:
+    for var in [v for v in a.variants.split(",") if v and v != "none" and v != "%s+%s" % (a.precision, a.outer)]:
         vprec, _, vout = var.partition("+")
         vout = vout or "fp64"
         if vprec == a.precision and vout == a.outer:
@@ -348,25 +399,42 @@ def main():
         g2 = rf.Grid(p2)
         u_ref = torch.tensor(p2["u0"], device=dev)
         opts2 = rf.gmg_opts(p2["nlevels"], "jacobi", precision="fp64")
-        u2 = u_ref.clone()
-        g2.limex_step(u2, p2["H"], kappa=4, tol=1e-3, gmg=opts2)        # warm-up
-        times, info2 = [], None
-        for _ in range(3):
-            u2 = u_ref.clone()
-            torch.cuda.synchronize()
-            a0, a1 = ev(), ev()
-            a0.record(stream)
-            info2 = g2.limex_step(u2, p2["H"], kappa=4, tol=1e-3, gmg=opts2)
-            a1.record(stream)
-            torch.cuda.synchronize()
-            times.append(a0.elapsed_time(a1))
-        lms = statistics.median(times)
+        def limex_ms(env):
+            saved = {k: os.environ.pop(k, None) for k in ("RF_LIMEX_BATCH", "RF_LIMEX_CONCURRENT")}
+            os.environ.update(env)
+            try:
+                u2 = u_ref.clone()
+                g2.limex_step(u2, p2["H"], kappa=4, tol=1e-3, gmg=opts2)        # warm-up
+                times, inf = [], None
+                for _ in range(3):
+                    u2 = u_ref.clone()
+                    torch.cuda.synchronize()
+                    a0, a1 = ev(), ev()
+                    a0.record(stream)
+                    inf = g2.limex_step(u2, p2["H"], kappa=4, tol=1e-3, gmg=opts2)
+                    a1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(a0.elapsed_time(a1))
+                return statistics.median(times), inf, u2.cpu().numpy()
+            finally:
+                for k in ("RF_LIMEX_BATCH", "RF_LIMEX_CONCURRENT"):
+                    os.environ.pop(k, None)
+                os.environ.update({k: v for k, v in saved.items() if v is not None})
+
+        lms, info2, ub = limex_ms({})
+        sms, _, us = limex_ms({"RF_LIMEX_BATCH": "0", "RF_LIMEX_CONCURRENT": "0"})
+        bms, _, uc = limex_ms({"RF_LIMEX_BATCH": "1"})
         dof2 = 2 * g2.nv
         limex = {"workload": "65^3 lognormal K (seed 1), one LIMEX step H = 10 s, kappa = 4 (10 stage "
                              "solves, one Jacobian), FP64 BiCGSTAB + FP64 GMG (5 levels, block Jacobi), rel.res 1e-10",
                  "ms_per_step": round(lms, 2), "dofs_per_s": dof2 / (lms / 1e3), "dofs": dof2,
                  "solves": info2["solves"], "iterations": info2["iterations"], "eps": info2["eps"],
-                 "accepted": info2["accepted"], "H_new": info2["H_new"]}
+                 "accepted": info2["accepted"], "H_new": info2["H_new"],
+                 "schedule": "columns side by side on column grids and host threads (the default below 1M "
+                             "vertices)",
+                 "columns_sequential_ms": round(sms, 2), "batched_rounds_ms": round(bms, 2),
+                 "speedup_vs_sequential": round(sms / lms, 3),
+                 "bitwise_equal_to_sequential": bool(np.array_equal(ub, us) and np.array_equal(ub, uc))}
         g2.close()
     except rf.RFError as e:
         limex = {"error": str(e)}
@@ -392,6 +460,12 @@ def main():
 
             batched()                                   # warm-up (captures graphs)
             tb_s, einfo = batched()
+            os.environ["RF_LIMEX_BATCH"] = "0"          # the per-problem worker threads, for comparison
+            try:
+                batched()
+                tt_s, _ = batched()
+            finally:
+                os.environ.pop("RF_LIMEX_BATCH", None)
             us = [t.clone() for t in eu0]
             torch.cuda.synchronize()
             w0 = time.perf_counter()
@@ -407,6 +481,9 @@ def main():
                         "batched_s": round(tb_s, 3), "dofs_per_s_batched": edof / tb_s,
                         "sequential_s": round(ts_s, 3), "dofs_per_s_sequential": edof / ts_s,
                         "batching_speedup": round(ts_s / tb_s, 2),
+                        "threads_s": round(tt_s, 3),
+                        "schedule": "problems of equal grids in shared batched rounds (one launch per kernel for "
+                                    "up to 64 (member, column) systems; each member's J read once per round)",
                         "accepted": sum(i["accepted"] for i in einfo)}
             for gg in egrids:
                 gg.close()
@@ -439,11 +516,14 @@ def main():
                        "accepted": sum(h["accepted"] for h in hist), "rejected": sum(1 - h["accepted"] for h in hist),
                        "t_end_s": t5, "wall_s": round(wall, 2), "ms_per_step": round(wall * 1e3 / nstep, 1),
                        "dofs_per_s_per_step": dof5 / (wall / nstep), "dofs": dof5,
-                       "stage_solves": sum(h["solves"] for h in hist),
-                       "iterations": sum(h["iterations"] for h in hist),
+                       "stage_solves": g5.last_run["solves"],
+                       "iterations": g5.last_run["iterations"],
                        "napl_mass_kg": m1, "injected_kg": q5 * t5,
                        "mass_error_rel": abs(m1 - m0 - q5 * t5) / m1,
-                       "H_history": [round(h["H"], 3) for h in hist]}
+                       "H_history": [round(h["H"], 3) for h in hist],
+                       "eps_history": [float("%.4g" % h["eps"]) for h in hist],
+                       "note": "first %d accepted steps of the workload's 20 (bounded for the bench's time)"
+                               % a.infiltration_steps}
             g5.close()
         except (rf.RFError, RuntimeError) as e:
             infiltration = {"error": str(e)}
@@ -496,7 +576,7 @@ def main():
             m1 = g4.phase_mass(u4)[1]
             acc = sum(h["accepted"] for h in hist)
             case4["limex"] = {"T_total_s": round(wall, 3), "time_steps": acc, "rejected": len(hist) - acc,
-                              "linear": sum(h["iterations"] for h in hist), "stage_solves": sum(h["solves"] for h in hist),
+                              "linear": g4.last_run["iterations"], "stage_solves": g4.last_run["solves"],
                               "H_max_used_s": max(h["H"] for h in hist),
                               "mass_error_rel": abs(m1 - m0 - q4 * T4) / (q4 * T4),
                               "tolerances": "TOL 5e-3, rho 0.75, H0 32 s, H_max 100 days"}
@@ -508,10 +588,16 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1:
-        v, dt, sdof, sit = oracle_sample(a.sample_nvert, a.smoother)
-        cpu = {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
-               "sample": "oracle FP64 BiCGSTAB-GMG solve (set-up excluded) of the same recipe at %d^3 "
-                         "vertices (%d DoF, %d iterations, %.1f s)" % (a.sample_nvert, sdof, sit, dt)}
+        cores = host_cores()
+        sample = OracleSample(a.sample_nvert, a.smoother)
+        v1, dt1, it1 = sample.solve(1)
+        vn, dtn, itn = sample.solve(cores)
+        cpu = {"value": vn, "unit": "DoF/s", "cores": cores, "kind": "oracle",
+               "sample": "oracle FP64 BiCGSTAB-GMG solve (set-up excluded) of the same recipe at %d^3 vertices "
+                         "(%d DoF, %d iterations): %.2f s on %d cores (OpenMP over vertices), %.2f s on 1"
+                         % (a.sample_nvert, sample.dof, itn, dtn, cores, dt1),
+               "single_thread": {"value": v1, "unit": "DoF/s", "seconds": round(dt1, 3)}}
+        del sample
 
     if rank == 0:
         line = {
@@ -533,6 +619,9 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": pk["hbm"],
                          "unit": "GB/s", "frac": round(achieved / pk["hbm"], 4), "traffic": traffic,
                          "peak_source": pk["src"], "note": "of %s HBM copy bandwidth" % pk["src"]},
+            "roofline_fp64": roofline_fp64,
+            "fp64_peak": {"fma_per_s": fma_rate, "tflops": round(fp64_peak_tflops, 4),
+                          "source": "rf_fp64_fma_rate, measured in this process"},
             "per_class": per_class, "time_shares": shares,
             "variants": variants,
             "limex_step": limex,

@@ -185,6 +185,28 @@ rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* op
 rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
                                 const rf_limex_opts* opts, rf_limex_info* infos, int max_concurrent, void* stream);
 
+/* Adaptive LIMEX integration under the step control of Sec. 4: repeated
+ * rf_limex_step calls from t = 0 on state u (in/out).  Before each step H =
+ * min(H, t_end - t) when t_end > 0 (the last step lands on t_end).  An
+ * accepted step advances t by H and replaces u; a rejected one keeps u and is
+ * retried with the proposed smaller H.  The next H is the step's proposal
+ * H_new, but not larger than H after a step accepted right after a rejection
+ * when hold_after_reject (a common safeguard; the paper states no rule), and
+ * at most H_max when H_max > 0.  Stops after max_steps accepted steps (when >
+ * 0) or at t_end (when > 0), whichever comes first.  RF_ENOTCONV after more
+ * than max_rejects rejections; a step's own failure is returned as is (u then
+ * holds the last accepted state).  hist (host, may be NULL when hist_cap = 0)
+ * receives {H, eps, accepted} per attempted step, for at most hist_cap steps;
+ * info (host, may be NULL) the totals. */
+typedef struct {
+  rf_limex_opts step;
+  double t_end, H_max;
+  int max_steps, max_rejects, hold_after_reject;
+} rf_limex_run_opts;
+typedef struct { double t, H_next; int accepted, rejected, solves, iterations, steps, status; } rf_limex_run_info;
+rf_status rf_limex_run(rf_grid* g, double* u, double H0, const rf_limex_run_opts* opts, rf_limex_run_info* info,
+                       double* hist, int hist_cap, void* stream);
+
 /* One implicit Euler step of size H solved by Newton's method — the fixed-step
  * scheme the paper compares LIMEX with (Sec. 6, Case 4, Table case4_2; Newton
  * tolerances 1e-8 absolute / 1e-6 relative there).  Finds u with

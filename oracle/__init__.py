@@ -40,6 +40,9 @@ def lib():
     global _lib
     if _lib is None:
         build()
+        # idle OpenMP threads sleep instead of spinning, so that two processes
+        # running the oracle at once do not starve each other
+        os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
         _lib = ctypes.CDLL(_SO)
         _declare(_lib)
     return _lib
@@ -99,11 +102,15 @@ def _declare(L):
         "rfo_gmg_level_dims": (None, [_P, _I, _P]),
         "rfo_gmg_level_matrix": (None, [_P, _I, _P]),
         "rfo_gmg_vcycle": (None, [_P, _P, _P]),
+        "rfo_gmg32_create": (_P, [_P]),
+        "rfo_gmg32_free": (None, [_P]),
+        "rfo_gmg32_vcycle": (None, [_P, _P, _P]),
         "rfo_bicgstab": (_I, [_I, _P, _P, _P, _P, _P, _D, _I, _P, _P]),
         "rfo_extrapolate": (None, [_I, _P, _I, _P, _P, _P]),
         "rfo_h1_seminorm2": (_D, [_I, _P, _P, _P, _I]),
         "rfo_lumped_l2norm2": (_D, [_I, _P, _P, _P, _I]),
         "rfo_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
+        "rfo_limex_run": (_I, [_P, _P, _D, _P, _P, _P, _P, _I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -307,6 +314,25 @@ class GMG:
         return x
 
 
+class GMG32:
+    """FP32 emulation of a GMG hierarchy's V-cycle (float storage and sums)."""
+
+    def __init__(self, gmg):
+        self.gmg = gmg   # keeps the double hierarchy alive
+        self.h = lib().rfo_gmg32_create(gmg.h)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().rfo_gmg32_free(self.h)
+            self.h = None
+
+    def vcycle(self, b):
+        b32 = np.ascontiguousarray(b, dtype=np.float32)
+        x = np.zeros(len(b32), dtype=np.float32)
+        lib().rfo_gmg32_vcycle(self.h, _p(b32), _p(x))
+        return x.astype(np.float64)
+
+
 def bicgstab(dim, n, A, gmg, b, rtol=1e-10, maxit=200):
     x = np.zeros(len(b))
     it = ctypes.c_int(0)
@@ -342,6 +368,34 @@ def limex_step(model, u0, H, kappa=4, tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4
     st = lib().rfo_limex_step(model.ref, _p(_f64(u0)), float(H), ctypes.byref(o), _p(u_out), ctypes.byref(info))
     return u_out, dict(status=st, eps=info.eps, H_new=info.H_new, accepted=info.accepted,
                        solves=info.solves, iterations=info.iterations)
+
+
+class _LimexRunOpts(ctypes.Structure):
+    _fields_ = [("step", _LimexOpts), ("t_end", ctypes.c_double), ("H_max", ctypes.c_double),
+                ("max_steps", ctypes.c_int), ("max_rejects", ctypes.c_int), ("hold_after_reject", ctypes.c_int)]
+
+
+class _LimexRunInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("H_next", ctypes.c_double), ("accepted", ctypes.c_int),
+                ("rejected", ctypes.c_int), ("solves", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("steps", ctypes.c_int)]
+
+
+def limex_run(model, u0, H0, steps=0, t_end=0.0, H_max=0.0, max_rejects=50, hold_after_reject=True, kappa=4,
+              tol=1e-3, rho=0.75, fac_min=0.2, fac_max=4.0, nlevels=4, smoother=JACOBI, nu1=2, nu2=2, omega=0.8,
+              rtol=1e-10, maxit=200, hist_cap=1000):
+    """Adaptive LIMEX integration (rfo_limex_run): returns (u, info, history)
+    with history rows (H, eps, accepted) per attempted step."""
+    o = _LimexRunOpts(_LimexOpts(kappa, tol, rho, fac_min, fac_max, nlevels, smoother, nu1, nu2, omega, rtol, maxit),
+                      float(t_end), float(H_max), int(steps), int(max_rejects), int(bool(hold_after_reject)))
+    info = _LimexRunInfo()
+    u_out = np.zeros(2 * model.nv)
+    hist = np.zeros((hist_cap, 3))
+    st = lib().rfo_limex_run(model.ref, _p(_f64(u0)), float(H0), ctypes.byref(o), _p(u_out), ctypes.byref(info),
+                             _p(hist), int(hist_cap))
+    n = min(info.steps, hist_cap)
+    return u_out, dict(status=st, t=info.t, H_next=info.H_next, accepted=info.accepted, rejected=info.rejected,
+                       solves=info.solves, iterations=info.iterations, steps=info.steps), hist[:n].copy()
 
 
 class _IeOpts(ctypes.Structure):

@@ -619,6 +619,7 @@ void rfo_galerkin(int dim, const int nf[3], const unsigned char* dmf, const doub
 
 /* Dense LU with partial pivoting (row-major N x N), the textbook algorithm. */
 int rfo_lu_factor(int N, double* LU, int* piv) {
+  for (int c = 0; c < N; ++c) piv[c] = c;   /* defined even if a zero pivot stops the factorisation */
   for (int c = 0; c < N; ++c) {
     int p = c;
     double best = fabs(LU[(size_t)c * N + c]);
@@ -777,6 +778,211 @@ void rfo_gmg_vcycle(rfo_gmg* g, const double* b, double* x) {
   memcpy(g->b[0], b, sizeof(double) * 2 * nv);
   vcycle(g, 0);
   memcpy(x, g->x[0], sizeof(double) * 2 * nv);
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP32 emulation of the multigrid V-cycle: the same hierarchy, smoother and
+ * schedule as rfo_gmg_vcycle, with every level matrix and vector stored in
+ * float and every sum accumulated in float, as a reference for a
+ * preconditioner run in single precision.  The inverse 2x2 diagonal blocks are
+ * the float roundings of the double inverses of the double blocks; the
+ * coarsest level is solved in double (the LU of rfo_gmg_create) and rounded
+ * back to float.                                                            */
+struct rfo_gmg32 {
+  const rfo_gmg* g;
+  float* A[RFO_MAXL];
+  float* Dinv[RFO_MAXL];
+  float *x[RFO_MAXL], *b[RFO_MAXL], *r[RFO_MAXL], *t[RFO_MAXL];
+  double* xc;
+};
+
+static void row_apply32(int dim, const int n[3], const float* A, const float* x, int i, int j, int k,
+                        int skip_centre, float out[2]) {
+  const int nb = nblk(dim), v = i + n[0] * (j + n[1] * k);
+  float s0 = 0.0f, s1 = 0.0f;
+  for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        int ii = i + dx, jj = j + dy, kk = k + dz;
+        if (ii < 0 || ii >= n[0] || jj < 0 || jj >= n[1] || kk < 0 || kk >= n[2]) continue;
+        if (skip_centre && dx == 0 && dy == 0 && dz == 0) continue;
+        const float* a = A + ((size_t)v * nb + blk(dim, dx, dy, dz)) * 4;
+        const float* xv = x + 2 * (ii + n[0] * (jj + n[1] * kk));
+        s0 += a[0] * xv[0] + a[1] * xv[1];
+        s1 += a[2] * xv[0] + a[3] * xv[1];
+      }
+  out[0] = s0; out[1] = s1;
+}
+
+static void residual32(int dim, const int n[3], const float* A, const float* b, const float* x, float* r) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        int v = i + n[0] * (j + n[1] * k);
+        float s[2];
+        row_apply32(dim, n, A, x, i, j, k, 0, s);
+        r[2 * v] = b[2 * v] - s[0];
+        r[2 * v + 1] = b[2 * v + 1] - s[1];
+      }
+}
+
+static void dinv32(const float* D, const float r[2], float y[2]) {
+  y[0] = D[0] * r[0] + D[1] * r[1];
+  y[1] = D[2] * r[0] + D[3] * r[1];
+}
+
+static void jacobi32(int dim, const int n[3], const float* A, const float* Dinv, const float* b, const float* xin,
+                     float* xout, float omega) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int k = 0; k < n[2]; ++k)
+    for (int j = 0; j < n[1]; ++j)
+      for (int i = 0; i < n[0]; ++i) {
+        int v = i + n[0] * (j + n[1] * k);
+        float s[2], r[2], y[2];
+        row_apply32(dim, n, A, xin, i, j, k, 0, s);
+        r[0] = b[2 * v] - s[0]; r[1] = b[2 * v + 1] - s[1];
+        dinv32(Dinv + 4 * (size_t)v, r, y);
+        xout[2 * v] = xin[2 * v] + omega * y[0];
+        xout[2 * v + 1] = xin[2 * v + 1] + omega * y[1];
+      }
+}
+
+static void gs32(int dim, const int n[3], const float* A, const float* Dinv, const float* b, float* x, int forward) {
+  const int ncol = 1 << dim;
+  for (int cc = 0; cc < ncol; ++cc) {
+    int col = forward ? cc : ncol - 1 - cc;
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          if (((i & 1) | ((j & 1) << 1) | ((k & 1) << 2)) != col) continue;
+          int v = i + n[0] * (j + n[1] * k);
+          float s[2], r[2];
+          row_apply32(dim, n, A, x, i, j, k, 1, s);
+          r[0] = b[2 * v] - s[0]; r[1] = b[2 * v + 1] - s[1];
+          dinv32(Dinv + 4 * (size_t)v, r, x + 2 * v);
+        }
+  }
+}
+
+static void restrict32(int dim, const int nf[3], const unsigned char* dmf, const int nc[3], const unsigned char* dmc,
+                       const float* rf, float* bc) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int K = 0; K < nc[2]; ++K)
+    for (int J = 0; J < nc[1]; ++J)
+      for (int I = 0; I < nc[0]; ++I) {
+        int vc = I + nc[0] * (J + nc[1] * K);
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int dz = (dim == 3 ? -1 : 0); dz <= (dim == 3 ? 1 : 0); ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              int fi = 2 * I + dx, fj = 2 * J + dy, fk = (dim == 3) ? 2 * K + dz : 0;
+              if (fi < 0 || fi >= nf[0] || fj < 0 || fj >= nf[1] || fk < 0 || fk >= nf[2]) continue;
+              int vf = fi + nf[0] * (fj + nf[1] * fk);
+              float w = (float)pweight(dim, fi, fj, fk, I, J, (dim == 3) ? K : 0);
+              if (!(dmf[vf] || dmc[vc])) s0 += w * rf[2 * vf];
+              s1 += w * rf[2 * vf + 1];
+            }
+        bc[2 * vc] = s0; bc[2 * vc + 1] = s1;
+      }
+}
+
+static void prolong_add32(int dim, const int nf[3], const unsigned char* dmf, const int nc[3],
+                          const unsigned char* dmc, const float* xc, float* xf) {
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int fk = 0; fk < nf[2]; ++fk)
+    for (int fj = 0; fj < nf[1]; ++fj)
+      for (int fi = 0; fi < nf[0]; ++fi) {
+        int vf = fi + nf[0] * (fj + nf[1] * fk);
+        float s0 = 0.0f, s1 = 0.0f;
+        for (int K = fk / 2; K <= (fk + 1) / 2; ++K)
+          for (int J = fj / 2; J <= (fj + 1) / 2; ++J)
+            for (int I = fi / 2; I <= (fi + 1) / 2; ++I) {
+              if (I >= nc[0] || J >= nc[1] || K >= nc[2]) continue;
+              float w = (float)pweight(dim, fi, fj, fk, I, J, K);
+              if (w == 0.0f) continue;
+              int vc = I + nc[0] * (J + nc[1] * K);
+              if (!(dmf[vf] || dmc[vc])) s0 += w * xc[2 * vc];
+              s1 += w * xc[2 * vc + 1];
+            }
+        xf[2 * vf] += s0; xf[2 * vf + 1] += s1;
+      }
+}
+
+rfo_gmg32* rfo_gmg32_create(const rfo_gmg* g) {
+  rfo_gmg32* h = calloc(1, sizeof(rfo_gmg32));
+  const int nb = nblk(g->dim), c = centre(g->dim);
+  h->g = g;
+  for (int l = 0; l < g->nl; ++l) {
+    const size_t nv = (size_t)nverts(g->n[l]);
+    h->A[l] = malloc(sizeof(float) * nv * nb * 4);
+    h->Dinv[l] = malloc(sizeof(float) * nv * 4);
+    for (size_t t = 0; t < nv * nb * 4; ++t) h->A[l][t] = (float)g->A[l][t];
+    for (size_t v = 0; v < nv; ++v) {
+      const double* a = g->A[l] + (v * nb + c) * 4;
+      const double det = a[0] * a[3] - a[1] * a[2];
+      h->Dinv[l][4 * v] = (float)(a[3] / det);
+      h->Dinv[l][4 * v + 1] = (float)(-a[1] / det);
+      h->Dinv[l][4 * v + 2] = (float)(-a[2] / det);
+      h->Dinv[l][4 * v + 3] = (float)(a[0] / det);
+    }
+    h->x[l] = calloc(2 * nv, sizeof(float));
+    h->b[l] = calloc(2 * nv, sizeof(float));
+    h->r[l] = calloc(2 * nv, sizeof(float));
+    h->t[l] = calloc(2 * nv, sizeof(float));
+  }
+  h->xc = malloc(sizeof(double) * g->N);
+  return h;
+}
+
+void rfo_gmg32_free(rfo_gmg32* h) {
+  if (!h) return;
+  for (int l = 0; l < h->g->nl; ++l) {
+    free(h->A[l]); free(h->Dinv[l]); free(h->x[l]); free(h->b[l]); free(h->r[l]); free(h->t[l]);
+  }
+  free(h->xc);
+  free(h);
+}
+
+static void smooth32(rfo_gmg32* h, int l, int nsweep, int pre) {
+  const rfo_gmg* g = h->g;
+  const int* n = g->n[l];
+  const int nv = nverts(n);
+  for (int s = 0; s < nsweep; ++s) {
+    if (g->smoother == RFO_JACOBI) {
+      jacobi32(g->dim, n, h->A[l], h->Dinv[l], h->b[l], h->x[l], h->t[l], (float)g->omega);
+      memcpy(h->x[l], h->t[l], sizeof(float) * 2 * nv);
+    } else {
+      gs32(g->dim, n, h->A[l], h->Dinv[l], h->b[l], h->x[l], pre);
+    }
+  }
+}
+
+static void vcycle32(rfo_gmg32* h, int l) {
+  const rfo_gmg* g = h->g;
+  const int* n = g->n[l];
+  const int nv = nverts(n);
+  if (l == g->nl - 1) {
+    for (int q = 0; q < 2 * nv; ++q) h->xc[q] = (double)h->b[l][q];
+    rfo_lu_solve(g->N, g->lu, g->piv, h->xc);
+    for (int q = 0; q < 2 * nv; ++q) h->x[l][q] = (float)h->xc[q];
+    return;
+  }
+  memset(h->x[l], 0, sizeof(float) * 2 * nv);
+  smooth32(h, l, g->nu1, 1);
+  residual32(g->dim, n, h->A[l], h->b[l], h->x[l], h->r[l]);
+  restrict32(g->dim, n, g->dm[l], g->n[l + 1], g->dm[l + 1], h->r[l], h->b[l + 1]);
+  vcycle32(h, l + 1);
+  prolong_add32(g->dim, n, g->dm[l], g->n[l + 1], g->dm[l + 1], h->x[l + 1], h->x[l]);
+  smooth32(h, l, g->nu2, 0);
+}
+
+void rfo_gmg32_vcycle(rfo_gmg32* h, const float* b, float* x) {
+  const int nv = nverts(h->g->n[0]);
+  memcpy(h->b[0], b, sizeof(float) * 2 * nv);
+  vcycle32(h, 0);
+  memcpy(x, h->x[0], sizeof(float) * 2 * nv);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -979,6 +1185,54 @@ int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_lim
   memcpy(u_out, acc ? Tkk : u0, sizeof(double) * N);
   if (info) { info->eps = eps; info->H_new = H * fac; info->accepted = acc; info->solves = solves; info->iterations = iters_total; }
   free(J); free(A); free(md); free(F0); free(F); free(du); free(T1); free(Tkk); free(Tkk1); free(nseq); free(dm);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive integration with the step control of Sec. 4 (see rfo.h).        */
+int rfo_limex_run(const rfo_model* m, const double* u0, double H0, const rfo_limex_run_opts* o, double* u_out,
+                  rfo_limex_run_info* info, double* hist, int hist_cap) {
+  const int N = 2 * nverts(m->n);
+  double* u = malloc(sizeof(double) * N);
+  double* un = malloc(sizeof(double) * N);
+  memcpy(u, u0, sizeof(double) * N);
+  double t = 0.0, H = H0;
+  int acc = 0, rej = 0, solves = 0, iters = 0, steps = 0, status = 0, last_rejected = 0;
+  for (;;) {
+    if (o->max_steps > 0 && acc >= o->max_steps) break;
+    if (o->t_end > 0.0 && !(t < o->t_end * (1.0 - 1e-12))) break;
+    if (o->t_end > 0.0 && H > o->t_end - t) H = o->t_end - t;
+    rfo_limex_info si;
+    status = rfo_limex_step(m, u, H, &o->step, un, &si);
+    solves += si.solves;
+    iters += si.iterations;
+    if (hist && steps < hist_cap) {
+      hist[3 * steps] = H;
+      hist[3 * steps + 1] = si.eps;
+      hist[3 * steps + 2] = si.accepted;
+    }
+    ++steps;
+    if (status != 0) break;
+    double Hn = si.H_new;
+    if (si.accepted) {
+      memcpy(u, un, sizeof(double) * N);
+      t += H;
+      ++acc;
+      if (o->hold_after_reject && last_rejected && Hn > H) Hn = H;
+      last_rejected = 0;
+    } else {
+      ++rej;
+      last_rejected = 1;
+      if (rej > o->max_rejects) { status = 1; break; }
+    }
+    H = (o->H_max > 0.0 && Hn > o->H_max) ? o->H_max : Hn;
+  }
+  memcpy(u_out, u, sizeof(double) * N);
+  if (info) {
+    info->t = t; info->H_next = H; info->accepted = acc; info->rejected = rej;
+    info->solves = solves; info->iterations = iters; info->steps = steps;
+  }
+  free(u); free(un);
   return status;
 }
 

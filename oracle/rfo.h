@@ -95,6 +95,13 @@ void rfo_gmg_level_dims(const rfo_gmg* g, int level, int n[3]);
 void rfo_gmg_level_matrix(const rfo_gmg* g, int level, double* A);
 void rfo_gmg_vcycle(rfo_gmg* g, const double* b, double* x);
 
+/* ---- FP32 emulation of the V-cycle (float storage and accumulation; the
+ * hierarchy of g rounded to float, the coarsest level solved in double) ---- */
+typedef struct rfo_gmg32 rfo_gmg32;
+rfo_gmg32* rfo_gmg32_create(const rfo_gmg* g);
+void rfo_gmg32_free(rfo_gmg32* h);
+void rfo_gmg32_vcycle(rfo_gmg32* h, const float* b, float* x);
+
 /* ---- BiCGSTAB, right-preconditioned by one V-cycle (g may be NULL) ---- */
 int rfo_bicgstab(int dim, const int n[3], const double* A, rfo_gmg* g, const double* b, double* x,
                  double rtol, int maxit, int* iters, double* relres);
@@ -111,6 +118,24 @@ typedef struct {
 typedef struct { double eps, H_new; int accepted, solves, iterations; } rfo_limex_info;
 int rfo_limex_step(const rfo_model* m, const double* u0, double H, const rfo_limex_opts* o,
                    double* u_out, rfo_limex_info* info);
+
+/* ---- adaptive LIMEX integration: repeated steps under the step control of
+ * Sec. 4.  From t = 0: H = min(H, t_end - t) when t_end > 0; one step; if it
+ * is accepted t += H, else the state stays; the next H is the step's proposal
+ * H_new, not larger than H after a step accepted right after a rejection
+ * when hold_after_reject (a safeguard; the paper states no rule), and at
+ * most H_max when H_max > 0.  Stops after max_steps accepted steps (> 0) or
+ * at t_end (> 0), whichever comes first; returns 1 after more than
+ * max_rejects rejections, else the last step's status.  hist (may be NULL)
+ * receives per attempted step {H, eps, accepted} for at most hist_cap steps. */
+typedef struct {
+  rfo_limex_opts step;
+  double t_end, H_max;
+  int max_steps, max_rejects, hold_after_reject;
+} rfo_limex_run_opts;
+typedef struct { double t, H_next; int accepted, rejected, solves, iterations, steps; } rfo_limex_run_info;
+int rfo_limex_run(const rfo_model* m, const double* u0, double H0, const rfo_limex_run_opts* o, double* u_out,
+                  rfo_limex_run_info* info, double* hist, int hist_cap);
 
 /* ---- implicit Euler + Newton (the comparison scheme of Sec. 6, Case 4) ----
  * Solves R(u) = F(u) - (m(u) - m(u_old))/H = 0 (storage m of rfo_storage;

@@ -88,6 +88,17 @@ class rf_limex_opts(ctypes.Structure):
                 ("solve", rf_solve_opts)]
 
 
+class rf_limex_run_opts(ctypes.Structure):
+    _fields_ = [("step", rf_limex_opts), ("t_end", ctypes.c_double), ("H_max", ctypes.c_double),
+                ("max_steps", ctypes.c_int), ("max_rejects", ctypes.c_int), ("hold_after_reject", ctypes.c_int)]
+
+
+class rf_limex_run_info(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("H_next", ctypes.c_double), ("accepted", ctypes.c_int),
+                ("rejected", ctypes.c_int), ("solves", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("steps", ctypes.c_int), ("status", ctypes.c_int)]
+
+
 class rf_ie_opts(ctypes.Structure):
     _fields_ = [("atol", ctypes.c_double), ("rtol", ctypes.c_double), ("max_newton", ctypes.c_int),
                 ("gmg", rf_gmg_opts), ("solve", rf_solve_opts), ("max_ls", ctypes.c_int)]
@@ -115,6 +126,7 @@ SIGNATURES = {
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_limex_step_batched": (_I, [_P, _P, _P, _I, _P, _P, _I, _P]),
+    "rf_limex_run": (_I, [_P, _P, _D, _P, _P, _P, _I, _P]),
     "rf_ie_step": (_I, [_P, _P, _D, _P, _P, _P]),
     "rf_phase_mass": (_I, [_P, _P, _P, _P]),
     "rf_export_jacobian": (_I, [_P, _P, _P, _P]),
@@ -398,39 +410,30 @@ class Grid:
         return dict(status=st, newton=info.newton, linear=info.linear, res0=info.res0, res=info.res)
 
     def limex_run(self, u, H0, steps=None, tol=1e-3, rho=0.75, H_max=None, gmg=None, rtol=1e-10, max_it=200,
-                  outer="fp64", kappa=4, max_rejects=50, t_end=None, hold_after_reject=True):
-        """Adaptive LIMEX integration (step control of Sec. 4, q = 2): takes
-        `steps` accepted steps, or integrates up to time `t_end` (the last step
-        is shortened to land on it), from state u (updated in place); a
-        rejected step is retried with the proposed smaller H.  With
-        hold_after_reject (the usual safeguard; the paper does not state its
-        rule) the step accepted right after a rejection does not propose a
-        larger H.  Returns (t, history)."""
+                  outer="fp64", kappa=4, max_rejects=50, t_end=None, hold_after_reject=True, hist_cap=100000,
+                  fac_min=0.2, fac_max=4.0):
+        """Adaptive LIMEX integration (rf_limex_run): `steps` accepted steps
+        and/or up to time `t_end`, from state u (updated in place).  Returns
+        (t, history) with one dict per attempted step (H, eps, accepted)."""
         if steps is None and t_end is None:
             raise ValueError("give steps or t_end")
-        H, t, hist, rejects, acc = float(H0), 0.0, [], 0, 0
-        last_rejected = False
-        while (steps is None or acc < steps) and (t_end is None or t < t_end * (1.0 - 1e-12)):
-            if t_end is not None:
-                H = min(H, t_end - t)
-            info = self.limex_step(u, H, kappa=kappa, tol=tol, rho=rho, gmg=gmg, rtol=rtol, max_it=max_it,
-                                   outer=outer)
-            info.update(H=H, t=t)
-            hist.append(info)
-            H_new = info["H_new"]
-            if info["accepted"]:
-                t += H
-                acc += 1
-                if hold_after_reject and last_rejected:
-                    H_new = min(H_new, H)
-                last_rejected = False
-            else:
-                rejects += 1
-                last_rejected = True
-                if rejects > max_rejects:
-                    raise RuntimeError("LIMEX: more than %d rejected steps" % max_rejects)
-            H = H_new if H_max is None else min(H_new, H_max)
-        return t, hist
+        gmg = gmg if gmg is not None else gmg_opts(4)
+        step = rf_limex_opts(int(kappa), float(tol), float(rho), float(fac_min), float(fac_max), gmg,
+                             rf_solve_opts(float(rtol), int(max_it), OUTERS.get(outer, outer)))
+        o = rf_limex_run_opts(step, float(t_end or 0.0), float(H_max or 0.0), int(steps or 0), int(max_rejects),
+                              int(bool(hold_after_reject)))
+        info = rf_limex_run_info()
+        hist = np.zeros((int(hist_cap), 3))
+        st = lib().rf_limex_run(self.handle, _ptr(u), float(H0), ctypes.byref(o), ctypes.byref(info), _ptr(hist),
+                                int(hist_cap), self.stream)
+        if st == RF_ENOTCONV and info.rejected > max_rejects:
+            raise RuntimeError("LIMEX: more than %d rejected steps" % max_rejects)
+        if st not in (RF_OK, RF_ENOTCONV):
+            _check(st)
+        n = min(info.steps, int(hist_cap))
+        self.last_run = dict(t=info.t, H_next=info.H_next, accepted=info.accepted, rejected=info.rejected,
+                             solves=info.solves, iterations=info.iterations, steps=info.steps, status=st)
+        return info.t, [dict(H=float(h[0]), eps=float(h[1]), accepted=int(h[2])) for h in hist[:n]]
 
     def phase_mass(self, u):
         """(water, NAPL) mass in kg of state u (lumped storage)."""

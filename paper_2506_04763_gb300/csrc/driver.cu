@@ -3,7 +3,9 @@
 // LIMEX step.  Every arithmetic step on grid data runs in the kernels of
 // assemble.cu, levelops.cu and krylov.cu; this file only sequences launches
 // and moves scalars (convergence flags, the error estimate) to the host.
+#include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -176,8 +178,14 @@ struct rf_grid {
     int64_t kernels = 0;                 // kernel launches per replay
     std::vector<ProfRec> recs;           // event pairs recorded by the graph
     std::vector<cudaEvent_t> events;     // owned by the graph
+    bool stale = false;                  // the data it points to was reallocated: re-capture before use
   };
   IterGraph ig[RF_MAXSHIFT][2][2];       // [shift][profiling][outer operator]
+  // batched solves led by this grid: one captured iteration per batch
+  // (its systems, shifts and profiling flag), the gathered scalars
+  std::map<std::string, IterGraph> bgraph;
+  double* bscal = nullptr;               // device: 16 scalars per system
+  double* bscal_h = nullptr;             // pinned host copy (+ the constant 1.0 at [16 * RF_MAXSYS])
   int outer_df = 0;                      // the current solve's RF_OUTER_* mode
   float* Jdf = nullptr;                  // J as FP32 hi/lo pairs (RF_OUTER_DF32)
   bool jdf_valid = false;
@@ -245,6 +253,66 @@ static void destroy_graphs(rf_grid* g) {
         for (auto e : G.events) cudaEventDestroy(e);
         G = rf_grid::IterGraph();
       }
+  for (auto& kv : g->bgraph) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    for (auto e : kv.second.events) cudaEventDestroy(e);
+  }
+  g->bgraph.clear();
+}
+
+// After a new multigrid set-up the captured iterations point to freed data.
+// They are kept and marked stale: the next use captures the iteration again
+// and updates the instantiated graph in place (cudaGraphExecUpdate; the
+// schedule, hence the graph's topology, is the same), which costs far less
+// than instantiating it anew.
+static void stale_graphs(rf_grid* g) {
+  for (auto& row : g->ig)
+    for (auto& pair : row)
+      for (auto& G : pair) G.stale = G.exec != nullptr;
+  for (auto& kv : g->bgraph) kv.second.stale = kv.second.exec != nullptr;
+}
+
+// Capture `body` on stream cs into G: a new instantiation, or an in-place
+// update of a stale one (falling back to a new instantiation if the update is
+// refused).  Kernel launches counted during the capture are taken back (a
+// replay counts them).
+template <typename Body>
+static rf_status capture_graph(rf_grid* owner, rf_grid::IterGraph& G, cudaStream_t cs, const char* what, Body body) {
+  std::vector<cudaEvent_t> old_events;
+  old_events.swap(G.events);
+  G.recs.clear();
+  const int64_t c0 = t_launches;
+  CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  owner->capturing = true;
+  owner->cap = &G;
+  body();
+  owner->capturing = false;
+  owner->cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  G.kernels = t_launches - c0;
+  g_launches.fetch_sub(G.kernels);
+  if (e != cudaSuccess) {
+    for (auto ev : old_events) cudaEventDestroy(ev);
+    return fail(RF_ECUDA, "%s capture: %s", what, cudaGetErrorString(e));
+  }
+  if (G.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(G.exec, graph, &info) != cudaSuccess) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+  }
+  if (!G.exec) {
+    e = cudaGraphInstantiate(&G.exec, graph, 0);
+    if (e != cudaSuccess) G.exec = nullptr;
+  }
+  cudaGraphDestroy(graph);
+  for (auto ev : old_events) cudaEventDestroy(ev);
+  G.stale = false;
+  if (!G.exec) return fail(RF_ECUDA, "%s graph: %s", what, cudaGetErrorString(e));
+  return RF_OK;
 }
 
 // algorithmic bytes of the level kernels (each matrix entry / vector element once)
@@ -393,6 +461,7 @@ extern "C" void rf_grid_destroy(rf_grid* g) {
   dfree_all(g, g->gbufs, nullptr);
   dfree_all(g, g->bufs, nullptr);
   if (g->hscal) cudaFreeHost(g->hscal);
+  if (g->bscal_h) cudaFreeHost(g->bscal_h);
   delete g;
 }
 
@@ -734,7 +803,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     if (!(shifts[j] >= 0.0) || !std::isfinite(shifts[j])) return fail(RF_EINVAL, "shifts must be finite and >= 0");
   CU(cudaStreamSynchronize((cudaStream_t)s));
   CU(cudaStreamSynchronize(g->cs));
-  destroy_graphs(g);
+  stale_graphs(g);
   dfree_all(g, g->gbufs, s);
   ++g->hier_gen;
   for (int l = 0; l < RF_MAXL; ++l) g->L[l] = Level();
@@ -1082,26 +1151,12 @@ static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
   }
   const bool prof = g->prof_on;
   rf_grid::IterGraph& G = g->ig[sh][prof ? 1 : 0][g->outer_df];
-  if (!G.exec) {
-    const int64_t c0 = t_launches;
-    CU(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    g->capturing = true;
-    g->cap = &G;
-    iteration_body(g, sh, cs);
-    cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, cs);
-    g->capturing = false;
-    g->cap = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cs, &graph);
-    G.kernels = t_launches - c0;   // counted again at every replay
-    g_launches.fetch_sub(G.kernels);
-    if (e != cudaSuccess) return fail(RF_ECUDA, "iteration capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&G.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) {
-      G.exec = nullptr;
-      return fail(RF_ECUDA, "iteration graph: %s", cudaGetErrorString(e));
-    }
+  if (!G.exec || G.stale) {
+    rf_status st = capture_graph(g, G, cs, "iteration", [&] {
+      iteration_body(g, sh, cs);
+      cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, cs);
+    });
+    if (st) return st;
   }
   CU(cudaGraphLaunch(G.exec, cs));
   g_launches.fetch_add(G.kernels);
@@ -1211,6 +1266,435 @@ extern "C" rf_status rf_solve(rf_grid* g, int sh, const double* b, double* x, co
   return RF_OK;
 }
 
+// ------------------------------------------------------------------ batched solves
+// The systems of a batch (grid, shift index, right-hand side) have equal level
+// shapes, storage kind and smoother: the active LIMEX columns of a step, or the
+// (member, column) pairs of an ensemble group.  They run BiCGSTAB in lock-step:
+// every kernel of an iteration serves all of them in one launch (one system per
+// blockIdx.y; on the finest level of systems that share J, all of them per
+// thread with J read once), and one captured graph holds the whole batched
+// iteration.  A system that has finished is flagged in its scalars
+// (RF_SCAL_DONE) and skipped by every later launch, so each system performs
+// exactly the operations of its own solve: results equal solve_p's bit for bit.
+struct BatchSys {
+  rf_grid* g;
+  int sh;
+  const double2* b;
+};
+
+static SysLevel sys_level(rf_grid* g, int l, int sh) {
+  const LevelOp op = level_op(g, l, sh);
+  SysLevel P{};
+  P.A = op.A;
+  P.scale = op.scale;
+  P.Dinv = op.Dinv;
+  P.mdiag = op.mdiag;
+  P.dmask = op.dmask;
+  P.shift = op.shift;
+  P.scal = g->K.scal;
+  return P;
+}
+
+// bytes of one batched level launch: S systems, the matrix read once per group
+// of `share` systems that use the same one
+static double batch_bytes(double per_sys, double matrix, int S, int share) {
+  return S * per_sys - (S - S / share) * matrix;
+}
+
+static void vcycle_batch(rf_grid* lead, const std::vector<BatchSys>& bs, int l, const std::vector<const void*>& b,
+                         const std::vector<void*>& x, int share, void* s) {
+  const int S = (int)bs.size();
+  rf_grid* g0 = bs[0].g;
+  const int k = g0->L[l].kind;
+  const double T = tb(k);
+  const double nv = (double)g0->L[l].d.nv;
+  if (l == g0->nl - 1) {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = sys_level(bs[q].g, l, bs[q].sh);
+      B.s[q].A = bs[q].g->Ainv[bs[q].sh];
+      B.s[q].in0 = b[q];
+      B.s[q].out = x[q];
+    }
+    const double N = 2.0 * nv;
+    ProfScope ps(lead, s, RF_PROF_COARSE_LEVELS, S * (N * N * 8.0 + 2 * N * T), 1);
+    launch_coarse_solve_b(level_op(g0, l, bs[0].sh), B, s);
+    return;
+  }
+  const bool sh_l = share > 1 && l == 0;   // only the finest level stores the shared J
+  const int shl = sh_l ? share : 1;
+  const LevelOp op = level_op(g0, l, bs[0].sh);
+  const LevelOp opc = level_op(g0, l + 1, bs[0].sh);
+  const rf_gmg_opts& o = g0->gopt;
+  const int cls = l == 0 ? RF_PROF_SMOOTH_FINE : RF_PROF_COARSE_LEVELS;
+  const int ncol = 1 << op.d.dim;
+  const double mat = nv * (op.d.nb * blk_bytes(k) + row_extra(k));
+  auto base = [&](int q) {
+    SysLevel P = sys_level(bs[q].g, l, bs[q].sh);
+    return P;
+  };
+  std::vector<void*> cur(S), tmp(S);
+  for (int q = 0; q < S; ++q) tmp[q] = bs[q].g->L[l].t;
+  // pre-smoothing (the schedule of smooth_pre)
+  if (o.smoother == RF_SMOOTH_JACOBI) {
+    const int W = o.nu1 + o.nu2;
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].in0 = b[q];
+      B.s[q].in1 = nullptr;
+      cur[q] = (W % 2 == 1) ? x[q] : tmp[q];
+      B.s[q].out = cur[q];
+    }
+    {
+      ProfScope ps(lead, s, cls, S * sweep_bytes(g0, l, true), 1);
+      if (sh_l) launch_jacobi_shared(op, B, share, o.omega, true, s);
+      else launch_jacobi_b(op, B, o.omega, true, s);
+    }
+    for (int it = 1; it < o.nu1; ++it) {
+      for (int q = 0; q < S; ++q) {
+        void* dst = (cur[q] == x[q]) ? tmp[q] : x[q];
+        B.s[q].in1 = cur[q];
+        B.s[q].out = dst;
+        cur[q] = dst;
+      }
+      ProfScope ps(lead, s, cls, batch_bytes(sweep_bytes(g0, l, false), mat, S, shl), 1);
+      if (sh_l) launch_jacobi_shared(op, B, share, o.omega, false, s);
+      else launch_jacobi_b(op, B, o.omega, false, s);
+    }
+  } else {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].in0 = b[q];
+      B.s[q].in1 = x[q];
+      B.s[q].out = x[q];
+      cur[q] = x[q];
+    }
+    for (int it = 0; it < o.nu1; ++it) {
+      ProfScope ps(lead, s, cls, batch_bytes(sweep_bytes(g0, l, it == 0), it == 0 ? 0.5 * mat : mat, S, shl), ncol);
+      if (sh_l) launch_gs_sweep_shared(op, B, share, true, it == 0, s);
+      else launch_gs_sweep_b(op, B, true, it == 0, s);
+    }
+  }
+  // residual, restriction
+  {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].in0 = b[q];
+      B.s[q].in1 = cur[q];
+      B.s[q].out = bs[q].g->L[l].r;
+    }
+    ProfScope ps(lead, s, l == 0 ? RF_PROF_RESID_FINE : RF_PROF_COARSE_LEVELS,
+                 batch_bytes(nv * (op.d.nb * blk_bytes(k) + row_extra(k) + (l == 0 ? 16.0 : 0.0) + 6 * T), mat, S, shl),
+                 1);
+    if (sh_l) launch_residual_shared(op, B, share, s);
+    else launch_residual_b(op, B, s);
+  }
+  const double nvc = (double)g0->L[l + 1].d.nv;
+  {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].dmask = bs[q].g->L[l].dmask;
+      B.s[q].dmask_c = bs[q].g->L[l + 1].dmask;
+      B.s[q].in0 = bs[q].g->L[l].r;
+      B.s[q].out = bs[q].g->L[l + 1].b;
+    }
+    ProfScope ps(lead, s, RF_PROF_TRANSFER, S * (nv * (2 * T + 1) + nvc * (2 * T + 1)), 1);
+    launch_restrict_b(op, opc, B, s);
+  }
+  std::vector<const void*> bc(S);
+  std::vector<void*> xc(S);
+  for (int q = 0; q < S; ++q) {
+    bc[q] = bs[q].g->L[l + 1].b;
+    xc[q] = bs[q].g->L[l + 1].x;
+  }
+  vcycle_batch(lead, bs, l + 1, bc, xc, share, s);
+  {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].dmask = bs[q].g->L[l].dmask;
+      B.s[q].dmask_c = bs[q].g->L[l + 1].dmask;
+      B.s[q].in0 = xc[q];
+      B.s[q].out = cur[q];
+    }
+    ProfScope ps(lead, s, RF_PROF_TRANSFER, S * (nv * (4 * T + 1) + nvc * (2 * T + 1)), 1);
+    launch_prolong_b(op, opc, B, s);
+  }
+  // post-smoothing (the schedule of smooth_post)
+  if (o.smoother == RF_SMOOTH_JACOBI) {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].in0 = b[q];
+    }
+    for (int it = 0; it < o.nu2; ++it) {
+      for (int q = 0; q < S; ++q) {
+        void* dst = (cur[q] == x[q]) ? tmp[q] : x[q];
+        B.s[q].in1 = cur[q];
+        B.s[q].out = dst;
+        cur[q] = dst;
+      }
+      ProfScope ps(lead, s, cls, batch_bytes(sweep_bytes(g0, l, false), mat, S, shl), 1);
+      if (sh_l) launch_jacobi_shared(op, B, share, o.omega, false, s);
+      else launch_jacobi_b(op, B, o.omega, false, s);
+    }
+  } else {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) {
+      B.s[q] = base(q);
+      B.s[q].in0 = b[q];
+      B.s[q].in1 = x[q];
+      B.s[q].out = x[q];
+    }
+    for (int it = 0; it < o.nu2; ++it) {
+      ProfScope ps(lead, s, cls, batch_bytes(sweep_bytes(g0, l, false), mat, S, shl), ncol);
+      if (sh_l) launch_gs_sweep_shared(op, B, share, false, false, s);
+      else launch_gs_sweep_b(op, B, false, false, s);
+    }
+  }
+}
+
+static KBatch krylov_batch(const std::vector<BatchSys>& bs) {
+  KBatch KB{};
+  KB.n = (int)bs.size();
+  for (int q = 0; q < KB.n; ++q) {
+    KB.s[q].K = bs[q].g->K;
+    KB.s[q].J = bs[q].g->J;
+    KB.s[q].mdiag = bs[q].g->mdiag;
+    KB.s[q].shift = bs[q].g->shifts[bs[q].sh];
+  }
+  return KB;
+}
+
+// one batched BiCGSTAB iteration (both V-cycles), then the gathered scalars to the host
+static void batch_body(rf_grid* lead, const std::vector<BatchSys>& bs, int share, void* s) {
+  rf_grid* g0 = bs[0].g;
+  const int S = (int)bs.size();
+  const Dims& d = g0->d;
+  const bool lo32 = g0->kind != STORE_F64;
+  const double T = tb(g0->kind), nv = (double)d.nv;
+  const KBatch KB = krylov_batch(bs);
+  const double opmat = nv * d.nb * 32.0;
+  const double spmv_bytes = nv * (d.nb * 32.0 + 16.0 + 16.0 + 16.0 + 16.0);
+  {
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (16.0 * 4 + 2 * T), 1);
+    launch_bicg_p_b(d.nv, KB, lo32, s);
+  }
+  std::vector<const void*> in(S);
+  std::vector<void*> out(S);
+  for (int q = 0; q < S; ++q) { in[q] = bs[q].g->K.p_lo; out[q] = bs[q].g->K.y; }
+  vcycle_batch(lead, bs, 0, in, out, share, s);
+  if (lo32) {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) { B.s[q].scal = bs[q].g->K.scal; B.s[q].in0 = bs[q].g->K.y; B.s[q].out = bs[q].g->K.y64; }
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (2 * T + 16.0), 1);
+    launch_cast_f32_to_f64_b(2 * d.nv, B, s);
+  }
+  {
+    ProfScope ps(lead, s, RF_PROF_SPMV64, batch_bytes(spmv_bytes, opmat, S, share), 1);
+    launch_bicg_v_b(d, g0->nb, KB, share, s);
+  }
+  {
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (16.0 * 3 + 2 * T), 1);
+    launch_bicg_s_b(d.nv, KB, lo32, s);
+  }
+  for (int q = 0; q < S; ++q) { in[q] = bs[q].g->K.s_lo; out[q] = bs[q].g->K.z; }
+  vcycle_batch(lead, bs, 0, in, out, share, s);
+  if (lo32) {
+    SysBatch B{};
+    B.n = S;
+    for (int q = 0; q < S; ++q) { B.s[q].scal = bs[q].g->K.scal; B.s[q].in0 = bs[q].g->K.z; B.s[q].out = bs[q].g->K.z64; }
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (2 * T + 16.0), 1);
+    launch_cast_f32_to_f64_b(2 * d.nv, B, s);
+  }
+  {
+    ProfScope ps(lead, s, RF_PROF_SPMV64, batch_bytes(spmv_bytes, opmat, S, share), 1);
+    launch_bicg_t_b(d, g0->nb, KB, share, s);
+  }
+  {
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (4 * T + 16.0 * 6), 1);
+    launch_bicg_xr_b(d.nv, KB, lo32, s);
+  }
+  launch_gather_scalars(KB, lead->bscal, s);
+  cudaMemcpyAsync(lead->bscal_h, lead->bscal, sizeof(double) * 16 * S, cudaMemcpyDeviceToHost, (cudaStream_t)s);
+}
+
+static rf_status batch_gather(rf_grid* lead, const std::vector<BatchSys>& bs, cudaStream_t s) {
+  const KBatch KB = krylov_batch(bs);
+  launch_gather_scalars(KB, lead->bscal, s);
+  CU(cudaMemcpyAsync(lead->bscal_h, lead->bscal, sizeof(double) * 16 * bs.size(), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return RF_OK;
+}
+
+static rf_status run_batch_iteration(rf_grid* lead, const std::vector<BatchSys>& bs, int share, cudaStream_t cs) {
+  static const bool eager = getenv("RF_NO_GRAPHS") && getenv("RF_NO_GRAPHS")[0] == '1';
+  if (eager) {
+    batch_body(lead, bs, share, cs);
+    CU(cudaStreamSynchronize(cs));
+    return RF_OK;
+  }
+  std::string key = (lead->prof_on ? "p" : "n") + std::to_string(share);
+  char buf[64];
+  for (const auto& q : bs) {
+    snprintf(buf, sizeof buf, "|%p:%d", (void*)q.g, q.sh);
+    key += buf;
+  }
+  rf_grid::IterGraph& G = lead->bgraph[key];
+  if (!G.exec || G.stale) {
+    rf_status st = capture_graph(lead, G, cs, "batched iteration", [&] { batch_body(lead, bs, share, cs); });
+    if (st) return st;
+  }
+  CU(cudaGraphLaunch(G.exec, cs));
+  g_launches.fetch_add(G.kernels);
+  CU(cudaStreamSynchronize(cs));
+  if (lead->prof_on)
+    for (auto& r : G.recs) {
+      float e = 0.f;
+      CU(cudaEventElapsedTime(&e, r.a, r.b));
+      lead->acc_ms[r.cls] += e;
+      lead->acc_bytes[r.cls] += r.bytes;
+      lead->acc_launches[r.cls] += r.launches;
+    }
+  return RF_OK;
+}
+
+// the lead grid's gathered-scalar buffers (device, pinned host + the constant 1.0)
+static rf_status batch_buffers(rf_grid* lead, void* s) {
+  if (!lead->bscal) {
+    lead->bscal = (double*)dalloc(lead, sizeof(double) * 16 * RF_MAXSYS, s, false);
+    if (!lead->bscal) return fail(RF_ENOMEM, "batch scalars");
+  }
+  if (!lead->bscal_h) {
+    if (cudaMallocHost((void**)&lead->bscal_h, sizeof(double) * (16 * RF_MAXSYS + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      lead->bscal_h = nullptr;
+      return fail(RF_ENOMEM, "pinned batch scalars");
+    }
+    lead->bscal_h[16 * RF_MAXSYS] = 1.0;
+  }
+  return RF_OK;
+}
+
+// Solve the batch's systems A_{sh} x = b (x in each system's grid K.x) in lock-step
+// on the lead grid's internal stream, ordered after and before `s`.  st[q], info[q]
+// receive each system's result as solve_cs would return them.
+static rf_status solve_batch(rf_grid* lead, const std::vector<BatchSys>& bs, int share, double rtol, int max_it,
+                             std::vector<rf_status>& st, std::vector<rf_solve_info>& info, void* s) {
+  const int S = (int)bs.size();
+  if (S < 1 || S > RF_MAXSYS) return fail(RF_EINVAL, "batch of %d systems", S);
+  if (share < 1 || share > 4 || S % share) return fail(RF_EINVAL, "batch of %d systems in groups of %d", S, share);
+  rf_status bst = batch_buffers(lead, s);
+  if (bst) return bst;
+  const double* one = lead->bscal_h + 16 * RF_MAXSYS;
+  cudaStream_t cs = lead->cs;
+  CU(cudaEventRecord(lead->join_in, (cudaStream_t)s));
+  CU(cudaStreamWaitEvent(cs, lead->join_in, 0));
+  const Dims& d = bs[0].g->d;
+  st.assign(S, RF_ENOTCONV);
+  info.assign(S, rf_solve_info{});
+  std::vector<int> active(S, 0), restarts(S, 0), iters(S, 0);
+  std::vector<double> bn(S, 0.0), relres(S, 0.0);
+  rf_status err = RF_OK;
+  auto finish = [&](int q) -> rf_status {   // the system leaves the lock-step
+    active[q] = 0;
+    CU(cudaMemcpyAsync(bs[q].g->K.scal + RF_SCAL_DONE, one, sizeof(double), cudaMemcpyHostToDevice, cs));
+    return RF_OK;
+  };
+  for (int q = 0; q < S; ++q) {
+    rf_grid* g = bs[q].g;
+    ProfScope ps(lead, cs, RF_PROF_VECTOR, (double)d.nv * 16.0 * 6, 1);
+    launch_bicg_init(d.nv, bs[q].b, g->K, rtol, cs);
+  }
+  if ((err = batch_gather(lead, bs, cs))) return err;
+  int nact = 0;
+  for (int q = 0; q < S; ++q) {
+    const double bb = lead->bscal_h[16 * q + H_BB];
+    if (!std::isfinite(bb)) {
+      st[q] = RF_ENONFINITE;
+      if ((err = finish(q))) return err;
+    } else if (bb == 0.0) {
+      st[q] = RF_OK;
+      if ((err = finish(q))) return err;
+    } else {
+      bn[q] = std::sqrt(bb);
+      active[q] = 1;
+      ++nact;
+    }
+  }
+  for (int it = 1; it <= max_it && nact > 0; ++it) {
+    if ((err = run_batch_iteration(lead, bs, share, cs))) return err;
+    std::vector<int> check;
+    for (int q = 0; q < S; ++q) {
+      if (!active[q]) continue;
+      iters[q] = it;
+      const double* h = lead->bscal_h + 16 * q;
+      if (h[H_BAD] != 0.0) {
+        st[q] = RF_ENONFINITE;
+        if ((err = finish(q))) return err;
+        --nact;
+      } else if (h[H_CONV] != 0.0 || h[H_BREAK] != 0.0) {
+        check.push_back(q);
+      }
+    }
+    if (check.empty()) continue;
+    for (int q : check) {
+      rf_grid* g = bs[q].g;
+      const double shift = g->shifts[bs[q].sh];
+      ProfScope ps(lead, cs, RF_PROF_SPMV64, (double)d.nv * (d.nb * 32.0 + 64.0), 1);
+      launch_true_residual(d, g->nb, g->J, g->mdiag, shift, bs[q].b, g->K, cs);
+    }
+    if ((err = batch_gather(lead, bs, cs))) return err;
+    for (int q : check) {
+      rf_grid* g = bs[q].g;
+      relres[q] = std::sqrt(lead->bscal_h[16 * q + H_TRUE]) / bn[q];
+      if (!std::isfinite(relres[q])) st[q] = RF_ENONFINITE;
+      else if (relres[q] <= rtol) st[q] = RF_OK;
+      else if (++restarts[q] > 20) st[q] = RF_EBREAKDOWN;
+      else {
+        launch_restart(d.nv, g->K, cs);
+        continue;
+      }
+      if ((err = finish(q))) return err;
+      --nact;
+    }
+  }
+  // systems that used up max_it: their true residual
+  for (int q = 0; q < S; ++q) {
+    if (!active[q]) continue;
+    rf_grid* g = bs[q].g;
+    launch_true_residual(d, g->nb, g->J, g->mdiag, g->shifts[bs[q].sh], bs[q].b, g->K, cs);
+  }
+  if ((err = batch_gather(lead, bs, cs))) return err;
+  for (int q = 0; q < S; ++q) {
+    if (active[q] || st[q] == RF_EBREAKDOWN) relres[q] = std::sqrt(lead->bscal_h[16 * q + H_TRUE]) / bn[q];
+    if (active[q]) {
+      st[q] = RF_ENOTCONV;
+      if ((err = finish(q))) return err;
+    }
+    info[q].iterations = iters[q];
+    info[q].relres = relres[q];
+    info[q].status = st[q];
+    info[q].restarts = restarts[q];
+  }
+  CU(cudaEventRecord(lead->join_out, cs));
+  CU(cudaStreamWaitEvent((cudaStream_t)s, lead->join_out, 0));
+  return RF_OK;
+}
+
 // ------------------------------------------------------------------ LIMEX
 // ------------------------------------------------------------------ LIMEX column grids
 // Column j of a LIMEX step (n_j = j+1 linearly implicit Euler substeps with
@@ -1271,10 +1755,29 @@ static rf_status column_grid(rf_grid* g, int j, void* s, rf_grid** out) {
   c->dir = g->dir; c->pw_dir = g->pw_dir; c->q_in = g->q_in; c->pdmin = g->pdmin; c->phiv = g->phiv;
   c->J = g->J; c->mdiag = g->mdiag; c->have_J = g->have_J;
   c->Jdf = g->Jdf; c->jdf_valid = g->jdf_valid;
+  // a new hierarchy of the same shape (levels, storage kind, level sizes): keep
+  // the column's own level vectors (their zero halos are never written) and
+  // mirror the new operators
+  bool same_shape = c->gen != ~0ull && c->nl == g->nl && c->kind == g->kind;
+  for (int l = 0; same_shape && l < g->nl; ++l) same_shape = c->L[l].d.nv == g->L[l].d.nv && c->L[l].d.nx == g->L[l].d.nx;
+  if (c->gen != g->hier_gen && same_shape) {
+    CU(cudaStreamSynchronize(c->cs));
+    stale_graphs(c);
+    c->gmg_ready = g->gmg_ready;
+    c->gopt = g->gopt;
+    c->nshift = g->nshift;
+    for (int k = 0; k < RF_MAXSHIFT; ++k) { c->shifts[k] = g->shifts[k]; c->Ainv[k] = g->Ainv[k]; }
+    for (int l = 0; l < c->nl; ++l) {
+      Level keep = c->L[l];
+      c->L[l] = g->L[l];
+      c->L[l].x = keep.x; c->L[l].b = keep.b; c->L[l].r = keep.r; c->L[l].t = keep.t; c->L[l].pad = keep.pad;
+    }
+    c->gen = g->hier_gen;
+  }
   if (c->gen != g->hier_gen) {
     // new hierarchy: drop graphs and level vectors, mirror the levels, own vectors
     CU(cudaStreamSynchronize(c->cs));
-    destroy_graphs(c);
+    stale_graphs(c);
     dfree_all(c, c->gbufs, s);
     c->gmg_ready = g->gmg_ready;
     c->gopt = g->gopt;
@@ -1328,8 +1831,12 @@ static bool limex_concurrent(const rf_grid* g, int kap) {
   return !t_in_batch && g->d.nv <= 4000000;
 }
 
-extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* o, rf_limex_info* info,
-                                   void* s) {
+// The LIMEX step with its columns one after another (or side by side on
+// column grids and host threads, see limex_concurrent): the path taken when
+// RF_LIMEX_BATCH=0, with the double-FP32 outer operator, or when the column
+// grids of the batched path cannot be allocated.
+static rf_status limex_step_columns(rf_grid* g, double* u, double H, const rf_limex_opts* o, rf_limex_info* info,
+                                    void* s) {
   if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
   if (!(H > 0.0) || !std::isfinite(H)) return fail(RF_EINVAL, "H must be positive");
   if (o->kappa < 1 || o->kappa > RF_MAXSHIFT) return fail(RF_EINVAL, "kappa must be 1..4");
@@ -1461,6 +1968,256 @@ extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_lim
   return worst;
 }
 
+// ------------------------------------------------------------------ LIMEX in batched rounds
+// Column j of a step (n_j = j+1 substeps, shift (j+1)/H) runs on column grid
+// cg[j] (cg[0] = the grid itself).  Round r solves the r-th substep of every
+// column j >= r: the right-hand sides F(u_r^j) are assembled per column, then
+// all of them go to one batched solve (solve_batch), and each column adds its
+// increment.  Every column performs the same operations in the same order as
+// in limex_step_columns, so the step is bitwise the same; an ensemble group
+// puts the columns of all its members into the same rounds.
+struct LimexWork {
+  rf_grid* g = nullptr;
+  double* u = nullptr;
+  double H = 0.0;
+  const rf_limex_opts* o = nullptr;
+  rf_limex_info* info = nullptr;
+  rf_grid* cg[RF_MAXSHIFT] = {};
+  rf_status st = RF_OK;          // first hard failure of this problem
+  std::string msg;
+  rf_status worst = RF_OK;       // RF_ENOTCONV if a column solve did not converge
+  int solves = 0, iters = 0;
+};
+
+static rf_status limex_check(rf_grid* g, double* u, double H, const rf_limex_opts* o) {
+  if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
+  if (!(H > 0.0) || !std::isfinite(H)) return fail(RF_EINVAL, "H must be positive");
+  if (o->kappa < 1 || o->kappa > RF_MAXSHIFT) return fail(RF_EINVAL, "kappa must be 1..4");
+  if (!(o->tol > 0) || !(o->rho > 0) || !(o->fac_min > 0) || !(o->fac_max >= o->fac_min))
+    return fail(RF_EINVAL, "bad step-control parameters");
+  return RF_OK;
+}
+
+// state in, J, M and F(u0) assembled, hierarchy for the kappa shifts, column
+// grids, every column's slot of the table T set to u0 (u0 kept in nat_a, F0 in nat_b)
+static rf_status limex_prepare(LimexWork& w, void* s) {
+  rf_grid* g = w.g;
+  const Dims& d = g->d;
+  const int kap = w.o->kappa;
+  const size_t vb = sizeof(double) * 2 * d.nv;
+  if (!g->T || g->T_kappa < kap) {
+    g->T = (double*)dalloc(g, vb * kap, s, false);
+    if (!g->T) return fail(RF_ENOMEM, "LIMEX table allocation failed");
+    g->T_kappa = kap;
+  }
+  rf_status st = pairs_in(g, d, w.u, g->u_p, s);
+  if (st) return st;
+  CU(cudaMemcpyAsync(g->nat_a, g->u_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  if ((st = assemble_p(g, true, s))) return st;
+  CU(cudaMemcpyAsync(g->nat_b, g->F_p, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  double shifts[RF_MAXSHIFT];
+  for (int j = 0; j < kap; ++j) shifts[j] = (double)(j + 1) / w.H;
+  if ((st = rf_gmg_setup(g, shifts, kap, &w.o->gmg, s))) return st;
+  w.cg[0] = g;
+  for (int j = 1; j < kap; ++j)
+    if ((st = column_grid(g, j, s, &w.cg[j]))) return st;
+  for (int j = 0; j < kap; ++j)
+    CU(cudaMemcpyAsync(g->T + (size_t)j * 2 * d.nv, g->nat_a, vb, cudaMemcpyDeviceToDevice, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return RF_OK;
+}
+
+// the rounds of a group of steps whose grids have equal shapes and options
+static rf_status limex_rounds(std::vector<LimexWork*>& ws, void* s) {
+  rf_grid* lead = ws[0]->g;
+  // every problem of the batch was set up anew: the lead's batched iterations
+  // (which reach into all of them) are re-captured at their first use
+  stale_graphs(lead);
+  const Dims& d = lead->d;
+  const int kap = ws[0]->o->kappa;
+  const size_t vb = sizeof(double) * 2 * d.nv;
+  cudaEvent_t round_start;
+  CU(cudaEventCreateWithFlags(&round_start, cudaEventDisableTiming));
+  struct EvGuard { cudaEvent_t e; ~EvGuard() { cudaEventDestroy(e); } } guard{round_start};
+  for (int r = 0; r < kap; ++r) {
+    std::vector<BatchSys> bs;
+    std::vector<LimexWork*> owner;
+    std::vector<int> col;
+    // the right-hand sides F(u_r^j): each column assembles on its own stream
+    // (the assemblies are independent), after everything before on s
+    if (r > 0) CU(cudaEventRecord(round_start, (cudaStream_t)s));
+    for (LimexWork* w : ws) {
+      if (w->st != RF_OK) continue;
+      for (int j = r; j < kap; ++j) {
+        rf_grid* gj = w->cg[j];
+        const double* F = w->g->nat_b;   // F(u0): the first substep of every column
+        if (r > 0) {
+          double* U = w->g->T + (size_t)j * 2 * d.nv;
+          CU(cudaStreamWaitEvent(gj->cs, round_start, 0));
+          CU(cudaMemcpyAsync(gj->u_p, U, vb, cudaMemcpyDeviceToDevice, gj->cs));
+          rf_status a = assemble_p(gj, false, gj->cs);
+          if (a) return a;
+          CU(cudaEventRecord(gj->join_out, gj->cs));
+          CU(cudaStreamWaitEvent((cudaStream_t)s, gj->join_out, 0));
+          F = gj->F_p;
+        }
+        bs.push_back({gj, j, (const double2*)F});
+        owner.push_back(w);
+        col.push_back(j);
+      }
+    }
+    // every problem's active columns (kap - r consecutive systems) share its J;
+    // batches of at most RF_MAXSYS systems, whole groups each
+    const int share = kap - r;
+    const size_t chunk = (size_t)(RF_MAXSYS / share) * share;
+    for (size_t b0 = 0; b0 < bs.size(); b0 += chunk) {
+      const size_t b1 = std::min(bs.size(), b0 + chunk);
+      std::vector<BatchSys> part(bs.begin() + b0, bs.begin() + b1);
+      std::vector<rf_status> st;
+      std::vector<rf_solve_info> inf;
+      const rf_solve_opts& so = ws[0]->o->solve;
+      rf_status e = solve_batch(lead, part, share, so.rtol, so.max_it, st, inf, s);
+      if (e) return e;
+      for (size_t q = 0; q < part.size(); ++q) {
+        LimexWork* w = owner[b0 + q];
+        ++w->solves;
+        w->iters += inf[q].iterations;
+        if (st[q] == RF_ENOTCONV) {
+          w->worst = RF_ENOTCONV;
+        } else if (st[q] != RF_OK && w->st == RF_OK) {
+          w->st = st[q];
+          char buf[160];
+          snprintf(buf, sizeof buf, "LIMEX column %d: %s", col[b0 + q], rf_status_string(st[q]));
+          w->msg = buf;
+        }
+        if (st[q] == RF_OK || st[q] == RF_ENOTCONV)
+          launch_axpy_pairs(d.nv, (double2*)(w->g->T + (size_t)col[b0 + q] * 2 * d.nv), part[q].g->K.x, s);
+      }
+    }
+  }
+  return RF_OK;
+}
+
+// extrapolation, error estimate, step-size proposal, the state out if accepted
+static rf_status limex_finish(LimexWork& w, void* s) {
+  rf_grid* g = w.g;
+  const Dims& d = g->d;
+  const int kap = w.o->kappa;
+  launch_extrapolate(2 * d.nv, kap, g->T, s);
+  const double* Tkk = g->T;
+  const double* Tkk1 = g->T + 2 * d.nv;
+  launch_error_norms(d, g->h, Tkk, kap > 1 ? Tkk1 : Tkk, g->norms, g->K.partial, s);
+  double nrm[4];
+  CU(cudaMemcpyAsync(nrm, g->norms, sizeof nrm, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  double vol = 1.0;
+  for (int a = 0; a < d.dim; ++a) vol *= (double)((a == 0 ? d.nx : a == 1 ? d.ny : d.nz) - 1) * g->h[a];
+  const double alpha = 1.0 / (nrm[0] + 1e-30);
+  const double beta = 1.0 / (nrm[2] + 1e-4 * vol);
+  const double eps = std::sqrt((alpha * nrm[1] + beta * nrm[3]) / 2.0);
+  const rf_limex_opts* o = w.o;
+  double fac = (eps > 0.0) ? std::pow(o->rho * o->tol / eps, 1.0 / 3.0) : o->fac_max;
+  if (fac > o->fac_max) fac = o->fac_max;
+  if (fac < o->fac_min) fac = o->fac_min;
+  const int acc = (eps <= o->tol) && w.worst == RF_OK;
+  if (acc) {
+    rf_status st = pairs_out(g, d, Tkk, w.u, s);
+    if (st) return st;
+  }
+  if (w.info) {
+    w.info->eps = eps; w.info->H_new = w.H * fac; w.info->accepted = acc; w.info->solves = w.solves;
+    w.info->iterations = w.iters; w.info->status = w.worst;
+  }
+  if (!std::isfinite(eps)) return fail(RF_ENONFINITE, "error estimate is not finite");
+  return w.worst;
+}
+
+// Batched rounds (RF_LIMEX_BATCH=1/0 forces the choice; never with the
+// double-FP32 operator).  By default a single step takes them on grids of at
+// least 1M vertices and the concurrent column threads below that, as measured
+// on GB300 for one kappa = 4 step of the lognormal-lenses recipe: 129^3 FP32
+// GMG 206 ms batched against 220 ms concurrent and 264 ms sequential, 257^3
+// 1389 ms against 1661 ms sequential, but 65^3 FP64 105 ms against 90 ms
+// concurrent (there every kernel is latency-bound, and a round lasts as long
+// as its slowest column while the threads let each column run ahead).  An
+// ensemble is always batched (its groups fill the launches).
+static bool limex_batched(const rf_limex_opts* o, int64_t nv = -1) {
+  if (o->solve.outer != RF_OUTER_FP64) return false;
+  const char* e = getenv("RF_LIMEX_BATCH");
+  if (e) return atoi(e) != 0;
+  return nv < 0 || nv >= 1000000;
+}
+
+extern "C" rf_status rf_limex_step(rf_grid* g, double* u, double H, const rf_limex_opts* o, rf_limex_info* info,
+                                   void* s) {
+  rf_status st = limex_check(g, u, H, o);
+  if (st) return st;
+  if (!limex_batched(o, g->d.nv)) return limex_step_columns(g, u, H, o, info, s);
+  LimexWork w;
+  w.g = g; w.u = u; w.H = H; w.o = o; w.info = info;
+  st = limex_prepare(w, s);
+  if (st == RF_ENOMEM) {
+    cudaGetLastError();
+    return limex_step_columns(g, u, H, o, info, s);   // no room for the column grids
+  }
+  if (st) return st;
+  std::vector<LimexWork*> ws{&w};
+  if ((st = limex_rounds(ws, s))) return st;
+  if (w.st != RF_OK) return fail(w.st, "%s", w.msg.c_str());
+  return limex_finish(w, s);
+}
+
+// ------------------------------------------------------------------ adaptive runs
+extern "C" rf_status rf_limex_run(rf_grid* g, double* u, double H0, const rf_limex_run_opts* o,
+                                  rf_limex_run_info* info, double* hist, int hist_cap, void* s) {
+  if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
+  if (!(H0 > 0.0) || !std::isfinite(H0)) return fail(RF_EINVAL, "H0 must be positive");
+  if (o->max_steps <= 0 && !(o->t_end > 0.0)) return fail(RF_EINVAL, "give max_steps > 0 or t_end > 0");
+  if (o->max_rejects < 0 || (hist_cap > 0 && !hist)) return fail(RF_EINVAL, "bad max_rejects or history buffer");
+  rf_status st = limex_check(g, u, H0, &o->step);
+  if (st) return st;
+  double t = 0.0, H = H0;
+  int acc = 0, rej = 0, solves = 0, iters = 0, steps = 0;
+  bool last_rejected = false;
+  rf_status result = RF_OK;
+  for (;;) {
+    if (o->max_steps > 0 && acc >= o->max_steps) break;
+    if (o->t_end > 0.0 && !(t < o->t_end * (1.0 - 1e-12))) break;
+    if (o->t_end > 0.0 && H > o->t_end - t) H = o->t_end - t;
+    rf_limex_info si{};
+    result = rf_limex_step(g, u, H, &o->step, &si, s);
+    solves += si.solves;
+    iters += si.iterations;
+    if (hist && steps < hist_cap) {
+      hist[3 * steps] = H;
+      hist[3 * steps + 1] = si.eps;
+      hist[3 * steps + 2] = si.accepted;
+    }
+    ++steps;
+    if (result != RF_OK) break;
+    double Hn = si.H_new;
+    if (si.accepted) {
+      t += H;
+      ++acc;
+      if (o->hold_after_reject && last_rejected && Hn > H) Hn = H;
+      last_rejected = false;
+    } else {
+      ++rej;
+      last_rejected = true;
+      if (rej > o->max_rejects) {
+        result = fail(RF_ENOTCONV, "LIMEX step control: more than %d rejected steps", o->max_rejects);
+        break;
+      }
+    }
+    H = (o->H_max > 0.0 && Hn > o->H_max) ? o->H_max : Hn;
+  }
+  if (info) {
+    info->t = t; info->H_next = H; info->accepted = acc; info->rejected = rej; info->solves = solves;
+    info->iterations = iters; info->steps = steps; info->status = result;
+  }
+  return result;
+}
+
 // ------------------------------------------------------------------ implicit Euler
 extern "C" rf_status rf_ie_step(rf_grid* g, double* u, double H, const rf_ie_opts* o, rf_ie_info* info, void* s) {
   if (!g || !u || !o) return fail(RF_EINVAL, "grid, u and options are required");
@@ -1558,15 +2315,11 @@ extern "C" rf_status rf_phase_mass(rf_grid* g, const double* u, double* mass_out
 }
 
 // ------------------------------------------------------------------ ensembles
-extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
-                                           const rf_limex_opts* o, rf_limex_info* infos, int max_concurrent,
-                                           void* stream) {
-  if (!grids || !u || !H || !o || !infos || nprob < 1) return fail(RF_EINVAL, "grids, u, H, opts, infos and nprob >= 1 are required");
-  for (int i = 0; i < nprob; ++i) {
-    if (!grids[i] || !u[i]) return fail(RF_EINVAL, "problem %d: grid and u are required", i);
-    for (int k = 0; k < i; ++k)
-      if (grids[k] == grids[i]) return fail(RF_EINVAL, "problem %d repeats the grid of problem %d", i, k);
-  }
+// The ensemble with each problem's whole step on its own stream and host
+// worker (RF_LIMEX_BATCH=0, or any problem with the double-FP32 operator).
+static rf_status limex_batched_threads(rf_grid* const* grids, double* const* u, const double* H, int nprob,
+                                       const rf_limex_opts* o, rf_limex_info* infos, int max_concurrent,
+                                       void* stream) {
   int workers = max_concurrent > 0 ? max_concurrent : (nprob < 16 ? nprob : 16);
   if (workers > nprob) workers = nprob;
   int dev = 0;
@@ -1604,6 +2357,142 @@ extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const*
   for (int i = 0; i < nprob; ++i)
     if (st[i] != RF_OK) return fail(st[i], "problem %d: %s", i, msg[i].c_str());
   return RF_OK;
+}
+
+static double wall_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// problems whose columns can share batched launches: equal grid shapes, options
+static bool same_group(const rf_grid* a, const rf_limex_opts& oa, const rf_grid* b, const rf_limex_opts& ob) {
+  return a->d.nx == b->d.nx && a->d.ny == b->d.ny && a->d.nz == b->d.nz && a->d.dim == b->d.dim &&
+         oa.kappa == ob.kappa && oa.gmg.nlevels == ob.gmg.nlevels && oa.gmg.smoother == ob.gmg.smoother &&
+         oa.gmg.nu1 == ob.gmg.nu1 && oa.gmg.nu2 == ob.gmg.nu2 && oa.gmg.omega == ob.gmg.omega &&
+         oa.gmg.precision == ob.gmg.precision && oa.solve.rtol == ob.solve.rtol && oa.solve.max_it == ob.solve.max_it;
+}
+
+extern "C" rf_status rf_limex_step_batched(rf_grid* const* grids, double* const* u, const double* H, int nprob,
+                                           const rf_limex_opts* o, rf_limex_info* infos, int max_concurrent,
+                                           void* stream) {
+  if (!grids || !u || !H || !o || !infos || nprob < 1) return fail(RF_EINVAL, "grids, u, H, opts, infos and nprob >= 1 are required");
+  for (int i = 0; i < nprob; ++i) {
+    if (!grids[i] || !u[i]) return fail(RF_EINVAL, "problem %d: grid and u are required", i);
+    for (int k = 0; k < i; ++k)
+      if (grids[k] == grids[i]) return fail(RF_EINVAL, "problem %d repeats the grid of problem %d", i, k);
+    rf_status c = limex_check(grids[i], u[i], H[i], &o[i]);
+    if (c) return fail(c, "problem %d: %s", i, t_err.c_str());
+  }
+  bool batched = true;
+  for (int i = 0; i < nprob; ++i) batched = batched && limex_batched(&o[i]);
+  if (!batched) return limex_batched_threads(grids, u, H, nprob, o, infos, max_concurrent, stream);
+  int workers = max_concurrent > 0 ? max_concurrent : (nprob < 16 ? nprob : 16);
+  if (workers > nprob) workers = nprob;
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  const double t_start = wall_ms();
+  std::vector<LimexWork> W(nprob);
+  for (int i = 0; i < nprob; ++i) {
+    W[i].g = grids[i]; W[i].u = u[i]; W[i].H = H[i]; W[i].o = &o[i]; W[i].info = &infos[i];
+  }
+  // Groups of equal shapes share batched rounds.  Each group runs as a
+  // pipeline on its own host thread: its members' assembly and multigrid
+  // set-up (each on the member's stream, by a few worker threads), then its
+  // rounds and the members' extrapolation on the lead grid's stream.  Groups of
+  // larger grids start first, and the groups' launches overlap on the GPU.
+  std::vector<std::vector<LimexWork*>> groups;
+  {
+    std::vector<int> done(nprob, 0);
+    for (int i = 0; i < nprob; ++i) {
+      if (done[i]) continue;
+      std::vector<LimexWork*> grp;
+      for (int k = i; k < nprob; ++k)
+        if (!done[k] && same_group(grids[i], o[i], grids[k], o[k])) {
+          done[k] = 1;
+          grp.push_back(&W[k]);
+        }
+      groups.push_back(grp);
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const std::vector<LimexWork*>& a, const std::vector<LimexWork*>& b) {
+      return a[0]->g->d.nv * (int64_t)a.size() > b[0]->g->d.nv * (int64_t)b.size();
+    });
+  }
+  // everything is ordered after `stream`
+  cudaEvent_t start;
+  CU(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  CU(cudaEventRecord(start, (cudaStream_t)stream));
+  for (int i = 0; i < nprob; ++i) CU(cudaStreamWaitEvent(grids[i]->cs, start, 0));
+  const int per_group = std::max(1, workers / std::max<int>(1, (int)groups.size()));
+  std::vector<rf_status> gst(groups.size(), RF_OK);
+  std::vector<std::string> gmsg(groups.size());
+  std::vector<double> gms(groups.size(), 0.0), gprep(groups.size(), 0.0);
+  auto run_group = [&](size_t q) {
+    cudaSetDevice(dev);
+    const double t0 = wall_ms();
+    std::vector<LimexWork*>& all = groups[q];
+    std::atomic<int> next{0};
+    auto prep = [&]() {
+      cudaSetDevice(dev);
+      for (int i = next.fetch_add(1); i < (int)all.size(); i = next.fetch_add(1)) {
+        LimexWork* w = all[i];
+        rf_status st = limex_prepare(*w, w->g->cs);
+        if (st) { w->st = st; w->msg = t_err; }
+      }
+    };
+    {
+      std::vector<std::thread> pool;
+      for (int k = 1; k < std::min<int>(per_group, (int)all.size()); ++k) pool.emplace_back(prep);
+      prep();
+      for (auto& t : pool) t.join();
+    }
+    gprep[q] = wall_ms() - t0;
+    std::vector<LimexWork*> grp;
+    for (LimexWork* w : all)
+      if (w->st == RF_OK) grp.push_back(w);
+    if (!grp.empty()) {
+      cudaStream_t gs = grp[0]->g->cs;
+      rf_status st = limex_rounds(grp, gs);
+      if (st == RF_OK)
+        for (LimexWork* w : grp) {
+          const rf_status f = limex_finish(*w, gs);
+          if (f == RF_ENOTCONV) w->worst = RF_ENOTCONV;
+          else if (f != RF_OK) { w->st = f; w->msg = t_err; }
+        }
+      if (st != RF_OK) { gst[q] = st; gmsg[q] = t_err; }
+      cudaStreamSynchronize(gs);
+    }
+    gms[q] = wall_ms() - t0;
+  };
+  {
+    std::vector<std::thread> gt;
+    for (size_t q = 1; q < groups.size(); ++q) gt.emplace_back(run_group, q);
+    if (!groups.empty()) run_group(0);
+    for (auto& t : gt) t.join();
+  }
+  cudaEventDestroy(start);
+  if (getenv("RF_BATCH_VERBOSE")) {
+    fprintf(stderr, "rf batched LIMEX: %d problems, %zu groups:", nprob, groups.size());
+    for (size_t q = 0; q < groups.size(); ++q)
+      fprintf(stderr, " [%zu x %dx%dx%d: prepare %.1f ms, all %.1f ms]", groups[q].size(), groups[q][0]->g->d.nx,
+              groups[q][0]->g->d.ny, groups[q][0]->g->d.nz, gprep[q], gms[q]);
+    fprintf(stderr, " total %.1f ms\n", wall_ms() - t_start);
+  }
+  for (size_t q = 0; q < groups.size(); ++q)
+    if (gst[q] != RF_OK) return fail(gst[q], "%s", gmsg[q].c_str());
+  rf_status first = RF_OK;
+  for (int i = 0; i < nprob; ++i) {
+    const rf_status st = W[i].st != RF_OK ? W[i].st : W[i].worst;
+    infos[i].status = st;
+    if (st != RF_OK && first == RF_OK) {
+      first = st;
+      t_err = "problem " + std::to_string(i) + ": " + (W[i].msg.empty() ? rf_status_string(st) : W[i].msg);
+    }
+  }
+  // `stream` waits for every problem's stream
+  for (int i = 0; i < nprob; ++i) {
+    CU(cudaEventRecord(grids[i]->join_out, grids[i]->cs));
+    CU(cudaStreamWaitEvent((cudaStream_t)stream, grids[i]->join_out, 0));
+  }
+  return first;
 }
 
 // ------------------------------------------------------------------ test hooks

@@ -25,6 +25,7 @@ enum {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_BETA, S_RR, S_BB, S_RHV, S_TS, S_TT,
   S_CONV, S_BAD, S_TRUE_RR, S_BREAK, S_RTOL, S_NSLOTS
 };
+static_assert(S_NSLOTS <= RF_SCAL_DONE, "the batch flag slot follows the scalars");
 static constexpr int MAXB = 2048;   // max blocks of a reducing kernel
 static constexpr int BS = 256;
 
@@ -337,9 +338,8 @@ static_assert(S_RR + 1 == S_BB, "slots");  // k_bicg_xr writes (rr, <rh,r>) into
 
 // ----------------------------------------------------------------- finalize
 // stage: 0 init, 1 alpha, 2 omega, 3 x/r update, 4 true residual, 5 restart
-__global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const double* __restrict__ partial,
-                           double rtol) {
-  rf_pdl_begin();
+__device__ __forceinline__ void finalize_body(int stage, int nblk, double* __restrict__ scal,
+                                              const double* __restrict__ partial, double rtol) {
   if (threadIdx.x >= 32) return;
   if (stage == 0) {
     const double bb = sum_partials(partial, S_BB, nblk);
@@ -348,6 +348,7 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
       scal[S_ALPHA] = 1.0; scal[S_OMEGA] = 1.0; scal[S_BETA] = 0.0;
       scal[S_CONV] = (bb == 0.0) ? 1.0 : 0.0; scal[S_BAD] = isfinite(bb) ? 0.0 : 1.0; scal[S_BREAK] = 0.0;
       scal[S_RTOL] = rtol;
+      scal[RF_SCAL_DONE] = 0.0;
     }
   } else if (stage == 1) {
     const double rhv = sum_partials(partial, S_RHV, nblk);
@@ -393,6 +394,12 @@ __global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const
       scal[S_CONV] = 0.0; scal[S_BREAK] = 0.0;
     }
   }
+}
+
+__global__ void k_finalize(int stage, int nblk, double* __restrict__ scal, const double* __restrict__ partial,
+                           double rtol) {
+  rf_pdl_begin();
+  finalize_body(stage, nblk, scal, partial, rtol);
 }
 
 // ----------------------------------------------------------------- launchers
@@ -510,6 +517,244 @@ __global__ void k_axpy_pairs(int64_t nv, double2* __restrict__ u, const double2*
 }
 void launch_axpy_pairs(int64_t nv, double2* u, const double2* du, void* s) {
   RF_LAUNCH(k_axpy_pairs, krylov_blocks(nv), BS, 0, s, nv, u, du);
+}
+
+// ----------------------------------------------------------------- batched iteration
+// The vector kernels and the outer operator of a BiCGSTAB iteration for the
+// systems of a KBatch, one system per blockIdx.y (the finalisation: one block
+// per system).  Each system runs the single-system kernel's loop over the same
+// grid-x extent, so its values and its block partials, hence its reduced
+// scalars, are bit for bit those of its own launches.  Finished systems
+// (RF_SCAL_DONE) return at once.
+__device__ __forceinline__ bool kdone(const SysKrylov& P) { return P.K.scal[RF_SCAL_DONE] != 0.0; }
+
+template <typename LV>
+__global__ void __launch_bounds__(BS) k_bicg_p_b(int64_t nv, const __grid_constant__ KBatch B) {
+  rf_pdl_begin();
+  const SysKrylov& P = B.s[blockIdx.y];
+  if (kdone(P)) return;
+  const double beta = P.K.scal[S_BETA], omega = P.K.scal[S_OMEGA];
+  const double2* __restrict__ r = P.K.r;
+  const double2* __restrict__ v = P.K.v;
+  double2* __restrict__ pp = P.K.p;
+  LV* __restrict__ plo = (LV*)P.K.p_lo;
+  for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
+    const double2 rv = r[q], vv = v[q], pv = pp[q];
+    const double p0 = rv.x + beta * (pv.x - omega * vv.x);
+    const double p1 = rv.y + beta * (pv.y - omega * vv.y);
+    pp[q] = make_double2(p0, p1);
+    plo[q] = to_lo<LV>(p0, p1);
+  }
+}
+
+template <typename LV>
+__global__ void __launch_bounds__(BS) k_bicg_s_b(int64_t nv, const __grid_constant__ KBatch B) {
+  rf_pdl_begin();
+  const SysKrylov& P = B.s[blockIdx.y];
+  if (kdone(P)) return;
+  const double alpha = P.K.scal[S_ALPHA];
+  const double2* __restrict__ r = P.K.r;
+  const double2* __restrict__ v = P.K.v;
+  double2* __restrict__ sv_out = P.K.s;
+  LV* __restrict__ slo = (LV*)P.K.s_lo;
+  for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
+    const double2 rv = r[q], vv = v[q];
+    const double s0 = rv.x - alpha * vv.x, s1 = rv.y - alpha * vv.y;
+    sv_out[q] = make_double2(s0, s1);
+    slo[q] = to_lo<LV>(s0, s1);
+  }
+}
+
+template <typename YV>
+__global__ void __launch_bounds__(BS) k_bicg_xr_b(int64_t nv, const __grid_constant__ KBatch B) {
+  rf_pdl_begin();
+  const SysKrylov& P = B.s[blockIdx.y];
+  if (kdone(P)) return;
+  const double alpha = P.K.scal[S_ALPHA], omega = P.K.scal[S_OMEGA];
+  const YV* __restrict__ y = (const YV*)P.K.y;
+  const YV* __restrict__ z = (const YV*)P.K.z;
+  const double2* __restrict__ s = P.K.s;
+  const double2* __restrict__ t = P.K.t;
+  const double2* __restrict__ rh = P.K.rh;
+  double2* __restrict__ x = P.K.x;
+  double2* __restrict__ r = P.K.r;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t q = blockIdx.x * (int64_t)BS + threadIdx.x; q < nv; q += (int64_t)gridDim.x * BS) {
+    const YV yv = y[q], zv = z[q];
+    const double2 sv = s[q], tv = t[q], hv = rh[q];
+    double2 xv = x[q];
+    xv.x += alpha * (double)yv.x + omega * (double)zv.x;
+    xv.y += alpha * (double)yv.y + omega * (double)zv.y;
+    x[q] = xv;
+    const double r0 = sv.x - omega * tv.x, r1 = sv.y - omega * tv.y;
+    r[q] = make_double2(r0, r1);
+    acc[0] += r0 * r0 + r1 * r1;
+    acc[1] += hv.x * r0 + hv.y * r1;
+  }
+  block_reduce_store<2>(acc, P.K.partial + S_RR * MAXB);
+}
+
+// v = A y with the fused <rh, v> (which = 0) or t = A z with <t, s>, <t, t> (which = 1)
+template <int NB>
+__global__ void __launch_bounds__(BS) k_bicg_op_b(Dims d, Nbr nb, const __grid_constant__ KBatch B, int which) {
+  rf_pdl_begin();
+  const SysKrylov& P = B.s[blockIdx.y];
+  if (kdone(P)) return;
+  const double2* md = (const double2*)P.mdiag;
+  const double2* __restrict__ x = which ? P.K.z64 : P.K.y64;
+  const double2* __restrict__ w = which ? P.K.s : P.K.rh;
+  double2* __restrict__ out = which ? P.K.t : P.K.v;
+  double acc[2] = {0.0, 0.0};
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
+    double y0, y1;
+    spmv64_row<double2, NB>(d, nb, P.J, md, P.shift, x, p, y0, y1);
+    out[p] = make_double2(y0, y1);
+    const double2 wv = w[p];
+    if (which) {
+      acc[0] += y0 * wv.x + y1 * wv.y;
+      acc[1] += y0 * y0 + y1 * y1;
+    } else {
+      acc[0] += wv.x * y0 + wv.y * y1;
+    }
+  }
+  if (which) block_reduce_store<2>(acc, P.K.partial + S_TS * MAXB);
+  else {
+    double a1[1] = {acc[0]};
+    block_reduce_store<1>(a1, P.K.partial + S_RHV * MAXB);
+  }
+}
+
+// The same for NS systems that share J (the LIMEX columns of one step): each
+// block of J is loaded once per vertex and applied to every system's operand.
+template <int NB, int NS>
+__global__ void __launch_bounds__(BS) k_bicg_op_shared(Dims d, Nbr nb, const __grid_constant__ KBatch B, int which) {
+  rf_pdl_begin();
+  const SysKrylov* G = B.s + blockIdx.y * NS;   // this group's systems (one shared J)
+  bool act[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) act[q] = !kdone(G[q]);
+  const double* __restrict__ J = G[0].J;
+  const double2* md = (const double2*)G[0].mdiag;
+  double acc[NS][2];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) { acc[q][0] = 0.0; acc[q][1] = 0.0; }
+  for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
+    const int par = (int)(p % d.nx) >= d.E;
+    double s0[NS], s1[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) { s0[q] = 0.0; s1[q] = 0.0; }
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const double2* qa = reinterpret_cast<const double2*>(J) + ((int64_t)b * d.nv + p) * 2;
+      const double2 a01 = __ldcs(qa), a23 = __ldcs(qa + 1);
+      const int off = par ? nb.off[1][b] : nb.off[0][b];
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        if (!act[q]) continue;
+        const double2 xv = (which ? G[q].K.z64 : G[q].K.y64)[p + off];
+        const double x0 = xv.x, x1 = xv.y;
+        s0[q] = fma(a01.x, x0, s0[q]);
+        s0[q] = fma(a01.y, x1, s0[q]);
+        s1[q] = fma(a23.x, x0, s1[q]);
+        s1[q] = fma(a23.y, x1, s1[q]);
+      }
+    }
+    const double2 m = md[p];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      if (!act[q]) continue;
+      const double xs = (which ? G[q].K.z64 : G[q].K.y64)[p].y;
+      const double y0 = G[q].shift * m.x * xs - s0[q];
+      const double y1 = G[q].shift * m.y * xs - s1[q];
+      (which ? G[q].K.t : G[q].K.v)[p] = make_double2(y0, y1);
+      const double2 wv = (which ? G[q].K.s : G[q].K.rh)[p];
+      if (which) {
+        acc[q][0] += y0 * wv.x + y1 * wv.y;
+        acc[q][1] += y0 * y0 + y1 * y1;
+      } else {
+        acc[q][0] += wv.x * y0 + wv.y * y1;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    // every thread of the block takes part in each reduction (a barrier inside)
+    if (which) {
+      double a2[2] = {acc[q][0], acc[q][1]};
+      block_reduce_store<2>(a2, G[q].K.partial + S_TS * MAXB);
+    } else {
+      double a1[1] = {acc[q][0]};
+      block_reduce_store<1>(a1, G[q].K.partial + S_RHV * MAXB);
+    }
+    __syncthreads();   // the shared staging of block_reduce_store is reused by the next system
+  }
+}
+
+__global__ void k_finalize_b(int stage, int nblk, const __grid_constant__ KBatch B) {
+  rf_pdl_begin();
+  const SysKrylov& P = B.s[blockIdx.x];
+  if (kdone(P)) return;
+  finalize_body(stage, nblk, P.K.scal, P.K.partial, 0.0);
+}
+
+__global__ void k_gather_scal(const __grid_constant__ KBatch B, double* __restrict__ out) {
+  const int q = blockIdx.x, t = threadIdx.x;
+  if (t < 16) out[16 * q + t] = B.s[q].K.scal[t];
+}
+
+static inline void fin_b(int stage, int nblk, const KBatch& B, void* s) {
+  RF_LAUNCH_PDL(k_finalize_b, B.n, 32, 0, s, stage, nblk, B);
+}
+
+void launch_bicg_p_b(int64_t nv, const KBatch& B, bool lo_is_f32, void* s) {
+  const dim3 g((unsigned)krylov_blocks(nv), (unsigned)B.n);
+  if (lo_is_f32) RF_LAUNCH_PDL(k_bicg_p_b<float2>, g, BS, 0, s, nv, B);
+  else RF_LAUNCH_PDL(k_bicg_p_b<double2>, g, BS, 0, s, nv, B);
+}
+
+void launch_bicg_s_b(int64_t nv, const KBatch& B, bool lo_is_f32, void* s) {
+  const dim3 g((unsigned)krylov_blocks(nv), (unsigned)B.n);
+  if (lo_is_f32) RF_LAUNCH_PDL(k_bicg_s_b<float2>, g, BS, 0, s, nv, B);
+  else RF_LAUNCH_PDL(k_bicg_s_b<double2>, g, BS, 0, s, nv, B);
+}
+
+void launch_bicg_xr_b(int64_t nv, const KBatch& B, bool yz_is_f32, void* s) {
+  const int gx = krylov_blocks(nv);
+  const dim3 g((unsigned)gx, (unsigned)B.n);
+  if (yz_is_f32) RF_LAUNCH_PDL(k_bicg_xr_b<float2>, g, BS, 0, s, nv, B);
+  else RF_LAUNCH_PDL(k_bicg_xr_b<double2>, g, BS, 0, s, nv, B);
+  fin_b(3, gx, B, s);
+}
+
+static void bicg_op_b(const Dims& d, const Nbr& nb, const KBatch& B, int share, int which, void* s) {
+  const int gx = krylov_blocks(d.nv);
+  if (share > 1) {
+    const dim3 gg((unsigned)gx, (unsigned)(B.n / share));
+#define RF_OPS(NBv, NSv) RF_LAUNCH_PDL((k_bicg_op_shared<NBv, NSv>), gg, BS, 0, s, d, nb, B, which)
+    if (d.nb == 27) {
+      switch (share) { case 1: RF_OPS(27, 1); break; case 2: RF_OPS(27, 2); break; case 3: RF_OPS(27, 3); break; default: RF_OPS(27, 4); }
+    } else {
+      switch (share) { case 1: RF_OPS(9, 1); break; case 2: RF_OPS(9, 2); break; case 3: RF_OPS(9, 3); break; default: RF_OPS(9, 4); }
+    }
+#undef RF_OPS
+  } else {
+    const dim3 g((unsigned)gx, (unsigned)B.n);
+    if (d.nb == 27) RF_LAUNCH_PDL(k_bicg_op_b<27>, g, BS, 0, s, d, nb, B, which);
+    else RF_LAUNCH_PDL(k_bicg_op_b<9>, g, BS, 0, s, d, nb, B, which);
+  }
+  fin_b(which ? 2 : 1, gx, B, s);
+}
+
+void launch_bicg_v_b(const Dims& d, const Nbr& nb, const KBatch& B, int share, void* s) {
+  bicg_op_b(d, nb, B, share, 0, s);
+}
+
+void launch_bicg_t_b(const Dims& d, const Nbr& nb, const KBatch& B, int share, void* s) {
+  bicg_op_b(d, nb, B, share, 1, s);
+}
+
+void launch_gather_scalars(const KBatch& B, double* out, void* s) {
+  RF_LAUNCH(k_gather_scal, B.n, 32, 0, s, B, out);
 }
 
 // ----------------------------------------------------------------- implicit Euler

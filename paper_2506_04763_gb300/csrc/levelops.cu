@@ -438,10 +438,10 @@ __global__ void __launch_bounds__(256) k_prolong(Dims df, Dims dc, const uint8_t
 // of the sums are those of restrict_point / prolong_point, so the results are
 // bitwise equal.  At 257^3 the transfers take 3.14 ms per solve against 4.14.
 template <typename T>
-__global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
-                                                         const uint8_t* __restrict__ dmc,
-                                                         const typename V2<T>::t* __restrict__ rf,
-                                                         typename V2<T>::t* __restrict__ bc) {
+__device__ __forceinline__ void restrict_planes_body(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
+                                                     const uint8_t* __restrict__ dmc,
+                                                     const typename V2<T>::t* __restrict__ rf,
+                                                     typename V2<T>::t* __restrict__ bc) {
   rf_pdl_begin();
   typedef typename V2<T>::t V;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -499,10 +499,18 @@ __global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
-                                                        const uint8_t* __restrict__ dmc,
-                                                        const typename V2<T>::t* __restrict__ xc,
-                                                        typename V2<T>::t* __restrict__ xf) {
+__global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                         const uint8_t* __restrict__ dmc,
+                                                         const typename V2<T>::t* __restrict__ rf,
+                                                         typename V2<T>::t* __restrict__ bc) {
+  restrict_planes_body<T>(df, dc, dmf, dmc, rf, bc);
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_planes_body(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
+                                                    const uint8_t* __restrict__ dmc,
+                                                    const typename V2<T>::t* __restrict__ xc,
+                                                    typename V2<T>::t* __restrict__ xf) {
   rf_pdl_begin();
   typedef typename V2<T>::t V;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -551,12 +559,20 @@ __global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const 
   xf[pf] = o;
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const uint8_t* __restrict__ dmf,
+                                                        const uint8_t* __restrict__ dmc,
+                                                        const typename V2<T>::t* __restrict__ xc,
+                                                        typename V2<T>::t* __restrict__ xf) {
+  prolong_planes_body<T>(df, dc, dmf, dmc, xc, xf);
+}
+
 // ----------------------------------------------------------------- coarsest solve
 // x = A^-1 b on the coarsest level: one warp per row of the explicit
 // inverse, lanes over its columns (coalesced), FP64 sums.
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
-                                                      const T* __restrict__ b, T* __restrict__ x) {
+__device__ __forceinline__ void coarse_solve_body(int N, const double* __restrict__ Ainv, const T* __restrict__ b,
+                                                  T* __restrict__ x) {
   rf_pdl_begin();
   extern __shared__ double sb[];
   for (int t = threadIdx.x; t < N; t += blockDim.x) sb[t] = (double)b[t];
@@ -570,6 +586,12 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __res
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[r] = (T)s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __restrict__ Ainv,
+                                                      const T* __restrict__ b, T* __restrict__ x) {
+  coarse_solve_body<T>(N, Ainv, b, x);
 }
 
 // ----------------------------------------------------------------- V-cycle tail
@@ -1104,6 +1126,247 @@ __global__ void k_cast_f32_f64(const float* __restrict__ in, double* __restrict_
     out[t] = (double)in[t];
 }
 
+// ----------------------------------------------------------------- batched
+// Several systems of one level shape per launch (see SysBatch): blockIdx.y
+// selects the system, whose operator pointers replace those of L; the point
+// functions are the single-system ones, so every value is computed exactly as
+// there.
+__device__ __forceinline__ bool sys_done(const SysLevel& P) {
+  return P.scal != nullptr && P.scal[RF_SCAL_DONE] != 0.0;
+}
+
+__device__ __forceinline__ LevelOp sys_op(const LevelOp& L, const SysLevel& P) {
+  LevelOp o = L;
+  o.A = P.A;
+  o.scale = P.scale;
+  o.Dinv = P.Dinv;
+  o.mdiag = P.mdiag;
+  o.shift = P.shift;
+  o.dmask = P.dmask;
+  return o;
+}
+
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_residual_b(const __grid_constant__ LevelOp L,
+                                                                   const __grid_constant__ SysBatch B) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  rf_pdl_begin();
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  residual_point<KIND, FINE, NB, CH>(sys_op(L, P), (const V*)P.in0, (const V*)P.in1, (V*)P.out, p);
+}
+
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_jacobi_b(const __grid_constant__ LevelOp L,
+                                                                 const __grid_constant__ SysBatch B, double omega,
+                                                                 int zero_x) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  rf_pdl_begin();
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  jacobi_point<KIND, FINE, NB, CH>(sys_op(L, P), (const V*)P.in0, (const V*)P.in1, (V*)P.out, omega, zero_x, p);
+}
+
+template <int KIND, bool FINE, int NB, int CH>
+__global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour_b(const __grid_constant__ LevelOp L,
+                                                                    const __grid_constant__ SysBatch B, int px,
+                                                                    int py, int pz, int cnt_x, int lines_y,
+                                                                    int64_t count, uint32_t skipmask) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  rf_pdl_begin();
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) return;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  gs_point<KIND, FINE, NB, CH>(sys_op(L, P), (const V*)P.in0, (V*)P.out, px, py, pz, cnt_x, lines_y, t, skipmask);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_restrict_planes_b(Dims df, Dims dc, const __grid_constant__ SysBatch B) {
+  const SysLevel& P = B.s[blockIdx.z];
+  // (the single-system kernel, with the system's masks and vectors)
+  if (sys_done(P)) {
+    rf_pdl_begin();
+    return;
+  }
+  restrict_planes_body<T>(df, dc, P.dmask, P.dmask_c, (const typename V2<T>::t*)P.in0, (typename V2<T>::t*)P.out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prolong_planes_b(Dims df, Dims dc, const __grid_constant__ SysBatch B) {
+  const SysLevel& P = B.s[blockIdx.z];
+  if (sys_done(P)) {
+    rf_pdl_begin();
+    return;
+  }
+  prolong_planes_body<T>(df, dc, P.dmask, P.dmask_c, (const typename V2<T>::t*)P.in0, (typename V2<T>::t*)P.out);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_solve_b(int N, const __grid_constant__ SysBatch B) {
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) {
+    rf_pdl_begin();
+    return;
+  }
+  coarse_solve_body<T>(N, (const double*)P.A, (const T*)P.in0, (T*)P.out);
+}
+
+__global__ void k_cast_f32_f64_b(int64_t n, const __grid_constant__ SysBatch B) {
+  rf_pdl_begin();
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) return;
+  const float* __restrict__ in = (const float*)P.in0;
+  double* __restrict__ out = (double*)P.out;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (double)in[t];
+}
+
+// Finest level of systems that share J (the LIMEX columns of one step): one
+// thread per vertex loads each stencil block once and applies it to the NS
+// systems' vectors, each with its own shift (and D^-1).  Per system the sums
+// run block by block in the order of stencil_sum with the same expressions,
+// so the values equal the single-system kernels' bit for bit.
+template <int KIND, int NB, int NS>
+__device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, int64_t p, int par, bool skip_centre,
+                                           uint32_t skipmask, const bool (&act)[NS],
+                                           typename Ty<KIND>::T (&s0)[NS], typename Ty<KIND>::T (&s1)[NS]) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  constexpr int C = NB == 27 ? 13 : 4;
+  float4 sc = make_float4(1.f, 1.f, 1.f, 1.f);
+  if (KIND == STORE_F16) sc = reinterpret_cast<const float4*>(G[0].scale)[p];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) { s0[q] = 0; s1[q] = 0; }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if (skip_centre && b == C) continue;
+    if ((skipmask >> b) & 1u) continue;
+    T a[4];
+    load_block<KIND>(G[0].A, L.d.nv, b, p, sc, a);
+    const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      if (!act[q]) continue;
+      const V xv = ((const V*)G[q].in1)[p + off];
+      s0[q] += a[0] * xv.x + a[1] * xv.y;
+      s1[q] += a[2] * xv.x + a[3] * xv.y;
+    }
+  }
+}
+
+template <int KIND, int NB, int NS>
+__global__ void __launch_bounds__(256) k_residual_shared(const __grid_constant__ LevelOp L,
+                                                         const __grid_constant__ SysBatch B) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  rf_pdl_begin();
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  const SysLevel* G = B.s + blockIdx.y * NS;   // this group's systems (one shared matrix)
+  bool act[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
+  const int par = (int)(p % L.d.nx) >= L.d.E;
+  T s0[NS], s1[NS];
+  shared_row<KIND, NB, NS>(L, G, p, par, false, L.nomask, act, s0, s1);
+  const double2 m = reinterpret_cast<const double2*>(G[0].mdiag)[p];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    if (!act[q]) continue;
+    const V* x = (const V*)G[q].in1;
+    const T xs = x[p].y, sh = (T)G[q].shift;
+    const T a0 = (T)(sh * (T)m.x) * xs - s0[q];
+    const T a1 = (T)(sh * (T)m.y) * xs - s1[q];
+    const V bv = ((const V*)G[q].in0)[p];
+    V o;
+    o.x = bv.x - a0;
+    o.y = bv.y - a1;
+    ((V*)G[q].out)[p] = o;
+  }
+}
+
+template <int KIND, int NB, int NS>
+__global__ void __launch_bounds__(256) k_jacobi_shared(const __grid_constant__ LevelOp L,
+                                                       const __grid_constant__ SysBatch B, double omega, int zero_x) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  rf_pdl_begin();
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= L.d.nv) return;
+  const SysLevel* G = B.s + blockIdx.y * NS;   // this group's systems (one shared matrix)
+  bool act[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
+  T s0[NS], s1[NS];
+  if (!zero_x) {
+    const int par = (int)(p % L.d.nx) >= L.d.E;
+    shared_row<KIND, NB, NS>(L, G, p, par, false, L.nomask, act, s0, s1);
+  }
+  const double2 m = reinterpret_cast<const double2*>(G[0].mdiag)[p];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    if (!act[q]) continue;
+    const V bv = ((const V*)G[q].in0)[p];
+    T r0 = bv.x, r1 = bv.y, x0 = 0, x1 = 0;
+    if (!zero_x) {
+      const V* x = (const V*)G[q].in1;
+      const T xs = x[p].y, sh = (T)G[q].shift;
+      const T a0 = (T)(sh * (T)m.x) * xs - s0[q];
+      const T a1 = (T)(sh * (T)m.y) * xs - s1[q];
+      r0 -= a0;
+      r1 -= a1;
+      x0 = x[p].x;
+      x1 = x[p].y;
+    }
+    T y0, y1;
+    dinv_apply<T>(reinterpret_cast<const T*>(G[q].Dinv), p, r0, r1, y0, y1);
+    V o;
+    o.x = x0 + (T)omega * y0;
+    o.y = x1 + (T)omega * y1;
+    ((V*)G[q].out)[p] = o;
+  }
+}
+
+template <int KIND, int NB, int NS>
+__global__ void __launch_bounds__(256) k_gs_colour_shared(const __grid_constant__ LevelOp L,
+                                                          const __grid_constant__ SysBatch B, int px, int py, int pz,
+                                                          int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  rf_pdl_begin();
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const SysLevel* G = B.s + blockIdx.y * NS;   // this group's systems (one shared matrix)
+  bool act[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
+  const int64_t line = t / cnt_x;
+  const int pos = (int)(t - line * cnt_x);
+  const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
+  const int j = 2 * jj + py, k = 2 * kk + pz;
+  const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
+  T s0[NS], s1[NS];
+  shared_row<KIND, NB, NS>(L, G, p, px, true, skipmask, act, s0, s1);
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    if (!act[q]) continue;
+    const V bv = ((const V*)G[q].in0)[p];
+    const T r0 = bv.x + s0[q];   // fine level: A_pq = -J_pq off the diagonal
+    const T r1 = bv.y + s1[q];
+    T y0, y1;
+    dinv_apply<T>(reinterpret_cast<const T*>(G[q].Dinv), p, r0, r1, y0, y1);
+    V o;
+    o.x = y0;
+    o.y = y1;
+    ((V*)G[q].out)[p] = o;
+  }
+}
+
 // ----------------------------------------------------------------- launchers
 template <int KIND, bool FINE>
 static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, void* s) {
@@ -1253,6 +1516,172 @@ void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, vo
     RF_LAUNCH_PDL(k_coarse_solve<float>, g, 256, smem, s, N, Ainv, (const float*)b, (float*)x);
 }
 
+
+// ----------------------------------------------------------------- batched launchers
+template <int KIND, bool FINE>
+static void residual_bt(const LevelOp& L, const SysBatch& B, void* s) {
+  const int bs = L.block > 0 ? L.block : 256;
+  const dim3 g((unsigned)((L.d.nv + bs - 1) / bs), (unsigned)B.n);
+  if (L.batched) {
+    if (L.d.nb == 27) RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B);
+    else RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B);
+  } else if (L.d.nb == 27) {
+    RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B);
+  } else {
+    RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 9, 0>), g, bs, 0, s, L, B);
+  }
+}
+
+template <int KIND, bool FINE>
+static void jacobi_bt(const LevelOp& L, const SysBatch& B, double omega, bool zero_x, void* s) {
+  const int bs = L.block > 0 ? L.block : 256;
+  const dim3 g((unsigned)((L.d.nv + bs - 1) / bs), (unsigned)B.n);
+  const int zx = zero_x ? 1 : 0;
+  if (L.batched) {
+    if (L.d.nb == 27) RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, omega, zx);
+    else RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, omega, zx);
+  } else if (L.d.nb == 27) {
+    RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, omega, zx);
+  } else {
+    RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 9, 0>), g, bs, 0, s, L, B, omega, zx);
+  }
+}
+
+// the colour loop of gs_t, with `launch(col, px, py, pz, cnt_x, lines_y, count, skip)` per colour
+template <typename F>
+static void for_colours(const Dims& d, bool forward, bool zero_start, F launch) {
+  const int ncol = 1 << d.dim;
+  for (int cc = 0; cc < ncol; ++cc) {
+    const int col = forward ? cc : ncol - 1 - cc;
+    const uint32_t skip = (zero_start && forward) ? zero_start_mask(d.dim, col) : 0u;
+    const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
+    const int cnt_x = px ? d.nx / 2 : (d.nx + 1) / 2;
+    const int lines_y = (d.ny - py + 1) / 2;
+    const int lines_z = d.dim == 3 ? (d.nz - pz + 1) / 2 : 1;
+    const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
+    if (count == 0) continue;
+    launch(px, py, pz, cnt_x, lines_y, count, skip);
+  }
+}
+
+template <int KIND, bool FINE>
+static void gs_bt(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
+  const int bs = L.block > 0 ? L.block : 256;
+  for_colours(L.d, forward, zero_start, [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count,
+                                            uint32_t skip) {
+    const dim3 g((unsigned)((count + bs - 1) / bs), (unsigned)B.n);
+    if (L.batched) {
+      if (L.d.nb == 27)
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+      else
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+    } else if (L.d.nb == 27) {
+      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+    } else {
+      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+    }
+  });
+}
+
+#define RF_KIND_FINE_SWITCH(L, CALL)                                                                  \
+  switch ((L).kind) {                                                                                  \
+    case STORE_F64: if ((L).fine) CALL(STORE_F64, true); else CALL(STORE_F64, false); break;         \
+    case STORE_F32: if ((L).fine) CALL(STORE_F32, true); else CALL(STORE_F32, false); break;         \
+    default: if ((L).fine) CALL(STORE_F16, true); else CALL(STORE_F16, false); break;                \
+  }
+
+void launch_residual_b(const LevelOp& L, const SysBatch& B, void* s) {
+#define RF_CALL(K, F) residual_bt<K, F>(L, B, s)
+  RF_KIND_FINE_SWITCH(L, RF_CALL)
+#undef RF_CALL
+}
+
+void launch_jacobi_b(const LevelOp& L, const SysBatch& B, double omega, bool zero_x, void* s) {
+#define RF_CALL(K, F) jacobi_bt<K, F>(L, B, omega, zero_x, s)
+  RF_KIND_FINE_SWITCH(L, RF_CALL)
+#undef RF_CALL
+}
+
+void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
+#define RF_CALL(K, F) gs_bt<K, F>(L, B, forward, zero_start, s)
+  RF_KIND_FINE_SWITCH(L, RF_CALL)
+#undef RF_CALL
+}
+
+void launch_restrict_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s) {
+  const dim3 g((unsigned)((C.d.nx * C.d.ny + 255) / 256), (unsigned)C.d.nz, (unsigned)B.n);
+  if (F.kind == STORE_F64) RF_LAUNCH_PDL(k_restrict_planes_b<double>, g, 256, 0, s, F.d, C.d, B);
+  else RF_LAUNCH_PDL(k_restrict_planes_b<float>, g, 256, 0, s, F.d, C.d, B);
+}
+
+void launch_prolong_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s) {
+  const dim3 g((unsigned)((F.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz, (unsigned)B.n);
+  if (F.kind == STORE_F64) RF_LAUNCH_PDL(k_prolong_planes_b<double>, g, 256, 0, s, F.d, C.d, B);
+  else RF_LAUNCH_PDL(k_prolong_planes_b<float>, g, 256, 0, s, F.d, C.d, B);
+}
+
+void launch_coarse_solve_b(const LevelOp& C, const SysBatch& B, void* s) {
+  const int N = (int)(2 * C.d.nv);
+  const dim3 g((unsigned)((N + 7) / 8), (unsigned)B.n);
+  const size_t smem = sizeof(double) * N;
+  if (C.kind == STORE_F64) RF_LAUNCH_PDL(k_coarse_solve_b<double>, g, 256, smem, s, N, B);
+  else RF_LAUNCH_PDL(k_coarse_solve_b<float>, g, 256, smem, s, N, B);
+}
+
+void launch_cast_f32_to_f64_b(int64_t n, const SysBatch& B, void* s) {
+  const dim3 g((unsigned)grid_for(n, 256), (unsigned)B.n);
+  RF_LAUNCH_PDL(k_cast_f32_f64_b, g, 256, 0, s, n, B);
+}
+
+template <int KIND, int NS>
+static void residual_sh(const LevelOp& L, const SysBatch& B, void* s) {
+  const dim3 g((unsigned)((L.d.nv + 255) / 256), (unsigned)(B.n / NS));
+  if (L.d.nb == 27) RF_LAUNCH_PDL((k_residual_shared<KIND, 27, NS>), g, 256, 0, s, L, B);
+  else RF_LAUNCH_PDL((k_residual_shared<KIND, 9, NS>), g, 256, 0, s, L, B);
+}
+template <int KIND, int NS>
+static void jacobi_sh(const LevelOp& L, const SysBatch& B, double omega, bool zero_x, void* s) {
+  const dim3 g((unsigned)((L.d.nv + 255) / 256), (unsigned)(B.n / NS));
+  if (L.d.nb == 27) RF_LAUNCH_PDL((k_jacobi_shared<KIND, 27, NS>), g, 256, 0, s, L, B, omega, zero_x ? 1 : 0);
+  else RF_LAUNCH_PDL((k_jacobi_shared<KIND, 9, NS>), g, 256, 0, s, L, B, omega, zero_x ? 1 : 0);
+}
+template <int KIND, int NS>
+static void gs_sh(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
+  for_colours(L.d, forward, zero_start, [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count,
+                                            uint32_t skip) {
+    const dim3 g((unsigned)((count + 255) / 256), (unsigned)(B.n / NS));
+    if (L.d.nb == 27)
+      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 27, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+    else
+      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 9, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+  });
+}
+
+#define RF_KIND_NS_SWITCH(L, NSV, CALL)                                                                    \
+  switch ((L).kind * 4 + (NSV) - 1) {                                                                      \
+    case 0: CALL(STORE_F64, 1); break; case 1: CALL(STORE_F64, 2); break;                                  \
+    case 2: CALL(STORE_F64, 3); break; case 3: CALL(STORE_F64, 4); break;                                  \
+    case 4: CALL(STORE_F32, 1); break; case 5: CALL(STORE_F32, 2); break;                                  \
+    case 6: CALL(STORE_F32, 3); break; case 7: CALL(STORE_F32, 4); break;                                  \
+    case 8: CALL(STORE_F16, 1); break; case 9: CALL(STORE_F16, 2); break;                                  \
+    case 10: CALL(STORE_F16, 3); break; default: CALL(STORE_F16, 4); break;                                \
+  }
+
+void launch_residual_shared(const LevelOp& L, const SysBatch& B, int share, void* s) {
+#define RF_CALL(K, N) residual_sh<K, N>(L, B, s)
+  RF_KIND_NS_SWITCH(L, share, RF_CALL)
+#undef RF_CALL
+}
+void launch_jacobi_shared(const LevelOp& L, const SysBatch& B, int share, double omega, bool zero_x, void* s) {
+#define RF_CALL(K, N) jacobi_sh<K, N>(L, B, omega, zero_x, s)
+  RF_KIND_NS_SWITCH(L, share, RF_CALL)
+#undef RF_CALL
+}
+void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s) {
+#define RF_CALL(K, N) gs_sh<K, N>(L, B, forward, zero_start, s)
+  RF_KIND_NS_SWITCH(L, share, RF_CALL)
+#undef RF_CALL
+}
 
 void launch_coarse_mask(const Dims& df, const uint8_t* dmf, const Dims& dc, uint8_t* dmc, void* s) {
   RF_LAUNCH(k_coarse_mask, (int)((dc.nv + 255) / 256), 256, 0, s, df, dmf, dc, dmc);

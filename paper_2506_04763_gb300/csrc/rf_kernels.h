@@ -161,6 +161,69 @@ void launch_ie_residual(int64_t nv, const double* F, const double* u, const doub
 
 void launch_axpby_pairs(int64_t nv, double* out, const double* a, const double2* d, double lam, void* s);
 
+// ---- batched execution: several systems of one level shape per launch ----
+// The systems of a batch (the active LIMEX columns of a step, the members of an
+// ensemble with equal grids) run in lock-step: every launch below serves all
+// of them, one system per blockIdx.y (or, for the finest level of systems that
+// share one Jacobian, all of them per thread, the matrix read once).  Each
+// system computes exactly what its own single-system launch would, in the same
+// order, so results are bitwise those of solving the systems one by one.  A
+// system whose Krylov scalar slot RF_SCAL_DONE is set has finished: its
+// blocks return at once and its data stay as they are.
+#define RF_MAXSYS 64
+constexpr int RF_SCAL_DONE = 15;
+struct SysLevel {                  // one system's operands of a batched level launch
+  const void* A;                   // blocks (coarse solve: the FP64 inverse)
+  const float* scale;              // FP16 row scales
+  const void* Dinv;
+  const double* mdiag;
+  const uint8_t* dmask;            // (transfers: the fine level's mask)
+  const uint8_t* dmask_c;          // (transfers: the coarse level's mask)
+  double shift;
+  const double* scal;              // the system's Krylov scalars
+  const void* in0;
+  const void* in1;
+  void* out;
+};
+struct SysBatch {
+  int n;
+  SysLevel s[RF_MAXSYS];
+};
+void launch_residual_b(const LevelOp& L, const SysBatch& B, void* s);
+void launch_jacobi_b(const LevelOp& L, const SysBatch& B, double omega, bool zero_x, void* s);
+void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s);
+void launch_restrict_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s);
+void launch_prolong_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s);
+void launch_coarse_solve_b(const LevelOp& C, const SysBatch& B, void* s);
+void launch_cast_f32_to_f64_b(int64_t n, const SysBatch& B, void* s);
+// finest level of systems that share J: consecutive groups of `share` (1..4)
+// systems of B (B.n a multiple of it) use one matrix, FP16 scales and mass
+// diagonal, those of the group's first system; a thread reads each block once
+// per vertex for all systems of its group (blockIdx.y = group)
+void launch_residual_shared(const LevelOp& L, const SysBatch& B, int share, void* s);
+void launch_jacobi_shared(const LevelOp& L, const SysBatch& B, int share, double omega, bool zero_x, void* s);
+void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s);
+
+struct SysKrylov {                 // one system of a batched BiCGSTAB iteration
+  KrylovVecs K;
+  const double* J;                 // FP64 Jacobian of the outer operator
+  const double* mdiag;
+  double shift;
+};
+struct KBatch {
+  int n;
+  SysKrylov s[RF_MAXSYS];
+};
+void launch_bicg_p_b(int64_t nv, const KBatch& B, bool lo_is_f32, void* s);
+void launch_bicg_s_b(int64_t nv, const KBatch& B, bool lo_is_f32, void* s);
+void launch_bicg_xr_b(int64_t nv, const KBatch& B, bool yz_is_f32, void* s);
+// outer operator with the fused dots; share > 1: consecutive groups of `share`
+// (<= 4) systems use one J (that of the group's first system), read once
+void launch_bicg_v_b(const Dims& d, const Nbr& nb, const KBatch& B, int share, void* s);
+void launch_bicg_t_b(const Dims& d, const Nbr& nb, const KBatch& B, int share, void* s);
+// copy scalar slots [0, 16) of every system into out[16 * system]
+void launch_gather_scalars(const KBatch& B, double* out, void* s);
+
 // ---- LIMEX (krylov.cu) ----
 void launch_extrapolate(int64_t n2, int kappa, double* T, void* s);
 void launch_error_norms(const Dims& d, const double* h, const double* Tkk, const double* Tkk1, double* out4,

@@ -147,64 +147,183 @@ def test_galerkin_levels_match_oracle(case):
     g.close()
 
 
+def _unit(prec):
+    return 2.0 ** -53 if prec == "fp64" else U32
+
+
 def _rel_bound(Ao, x, b, dim, n, prec):
-    """per-component bound: c u (|A||x| + |b|)."""
-    if prec == "fp64":
-        c, u = 64.0, 2.0 ** -53
-    else:
-        c, u = 64.0, U32
-    absx = np.abs(x)
-    ax = O.spmv(dim, n, np.abs(Ao), absx)
-    return c * u * (ax + np.abs(b)) + 1e-300
+    """Residual r = b - A x, per component: 64 u (|A||x| + |b|)."""
+    return 64.0 * _unit(prec) * (O.spmv(dim, n, np.abs(Ao), np.abs(x)) + np.abs(b)) + 1e-300
+
+
+def _centre(dim):
+    return 13 if dim == 3 else 4
+
+
+def _bmul(M, v):
+    """Per-vertex 2x2 blocks M [nv, 2, 2] times pairs v [2 nv]."""
+    return np.einsum("vab,vb->va", M, v.reshape(-1, 2)).ravel()
+
+
+def _diag_blocks(dim, A):
+    D = A[:, _centre(dim), :].reshape(-1, 2, 2)
+    Di = np.linalg.inv(D)
+    return np.abs(Di), np.einsum("vab,vbc,vcd->vad", np.abs(Di), np.abs(D), np.abs(Di))
+
+
+def _jacobi_bound(dim, n, A, b, x, xout, omega, prec, absA=None):
+    """x_out = x + omega D^-1 (b - A x), per component: the residual's bound
+    through |D^-1|, the rounding of D^-1 itself (|D^-1||D||D^-1| |r|, first
+    order), and the final update's rounding."""
+    u = _unit(prec)
+    aDi, K = _diag_blocks(dim, A)
+    absA = np.abs(A) if absA is None else absA
+    r = b - O.spmv(dim, n, A, x)
+    e_r = O.spmv(dim, n, absA, np.abs(x)) + np.abs(b)
+    return 64.0 * u * (omega * (_bmul(aDi, e_r) + _bmul(K, np.abs(r))) + np.abs(x) + np.abs(xout)) + 1e-300
+
+
+def _gs_bound(dim, n, A, b, x_in, x_out, prec, absA_off=None):
+    """Forward multicolour sweep, per component.  A vertex's error is its own
+    rounding (as in _jacobi_bound) plus |D^-1| times the errors of the
+    neighbours the sweep has already updated (earlier colours), accumulated
+    colour by colour in the smoother's order."""
+    from tests._helpers import colour
+    u = _unit(prec)
+    aDi, K = _diag_blocks(dim, A)
+    Aoff = A.copy()
+    Aoff[:, _centre(dim)] = 0.0
+    absAoff = np.abs(Aoff) if absA_off is None else absA_off
+    col = np.repeat(colour(dim, n), 2)
+    E = np.zeros_like(x_in)
+    xcur = x_in.copy()
+    for c in range(1 << dim):
+        sel = col == c
+        r = b - O.spmv(dim, n, Aoff, xcur)
+        own = 64.0 * u * (_bmul(aDi, O.spmv(dim, n, absAoff, np.abs(xcur)) + np.abs(b)) + _bmul(K, np.abs(r))
+                          + np.abs(x_out))
+        prop = _bmul(aDi, O.spmv(dim, n, absAoff, E))
+        E[sel] = (own + prop)[sel]
+        xcur[sel] = x_out[sel]
+    return E + 1e-300
+
+
+def _within(got, ref, bound):
+    err = np.abs(got - ref)
+    return np.all(err <= bound), (err / bound).max()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
 @pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "2d-17x13-stress"])
 def test_level_kernels_match_oracle(case, smoother, precision):
+    """Residual, one smoothing sweep and both transfers on every smoothed
+    level, each against a per-component rounding bound of its own arithmetic
+    (so an error confined to the small S_n rows cannot hide behind the p_w
+    rows)."""
     prob = CASES[case]()
     g, F, m, A, gm = _setup_both(prob, precision, smoother)
     rng = np.random.default_rng(5)
     rnd = np.float32 if precision == "fp32" else np.float64
+    u = _unit(precision)
     for level in range(gm.nlevels - 1):
         n = gm.level_dims(level)
         nv = int(np.prod(n))
         Ao = gm.level_matrix(level)
-        if precision == "fp32":
-            Ao32 = Ao.astype(np.float32).astype(np.float64)
-        else:
-            Ao32 = Ao
+        Ao32 = Ao.astype(np.float32).astype(np.float64) if precision == "fp32" else Ao
         b = rng.standard_normal(2 * nv).astype(rnd).astype(np.float64)
         x = rng.standard_normal(2 * nv).astype(rnd).astype(np.float64)
         # residual
         r = g.apply(rf.RF_OP_RESIDUAL, level, 1, b, x)[:2 * nv]
         r_o = O.residual(m.dim, n, Ao32, b, x)
-        assert np.all(np.abs(r - r_o) <= _rel_bound(Ao32, x, b, m.dim, n, precision)), level
-        # one smoothing sweep
+        ok, q = _within(r, r_o, _rel_bound(Ao32, x, b, m.dim, n, precision))
+        assert ok, ("residual", level, q)
+        # one smoothing sweep (the GPU's D^-1 is the rounded inverse of the
+        # FP64 diagonal block; the bound covers both sides' roundings of it)
         sm = g.apply(rf.RF_OP_SMOOTH, level, 1, b, x)[:2 * nv]
         if smoother == "jacobi":
             sm_o = O.jacobi(m.dim, n, Ao32, b, x, 0.8)
+            bound = _jacobi_bound(m.dim, n, Ao32, b, x, sm_o, 0.8, precision)
         else:
             sm_o = O.gs_sweep(m.dim, n, Ao32, b, x, True)
-        tol = 1e-9 if precision == "fp64" else 2e-4
-        assert np.abs(sm - sm_o).max() <= tol * np.abs(sm_o).max(), (level, np.abs(sm - sm_o).max() / np.abs(sm_o).max())
+            bound = _gs_bound(m.dim, n, Ao32, b, x, sm_o, precision)
+        ok, q = _within(sm, sm_o, bound)
+        assert ok, ("smoother", level, q)
         # transfers
         nc = gm.level_dims(level + 1)
         nvc = int(np.prod(nc))
-        dmf = np.zeros(nv, np.uint8)
-        dmc = np.zeros(nvc, np.uint8)
-        if level == 0:
-            dmf = prob["dir"]
-        else:
-            dmf = _mask_chain(prob, m, gm, level)
+        dmf = prob["dir"] if level == 0 else _mask_chain(prob, m, gm, level)
         dmc = _mask_chain(prob, m, gm, level + 1)
         rc = g.apply(rf.RF_OP_RESTRICT, level, 1, b)[:2 * nvc]
         rc_o = O.restrict(m.dim, n, dmf, nc, dmc, b)
-        assert np.abs(rc - rc_o).max() <= (1e-14 if precision == "fp64" else 1e-6) * np.abs(rc_o).max()
+        ok, q = _within(rc, rc_o, 64.0 * u * O.restrict(m.dim, n, dmf, nc, dmc, np.abs(b)) + 1e-300)
+        assert ok, ("restrict", level, q)
         xc = rng.standard_normal(2 * nvc).astype(rnd).astype(np.float64)
         pr = g.apply(rf.RF_OP_PROLONG, level, 1, xc, x)[:2 * nv]
         pr_o = O.prolong_add(m.dim, n, dmf, nc, dmc, xc, x)
-        assert np.abs(pr - pr_o).max() <= (1e-14 if precision == "fp64" else 1e-6) * np.abs(pr_o).max()
+        pbound = 64.0 * u * (np.abs(x) + O.prolong_add(m.dim, n, dmf, nc, dmc, np.abs(xc), np.zeros_like(x))) + 1e-300
+        ok, q = _within(pr, pr_o, pbound)
+        assert ok, ("prolong", level, q)
+    g.close()
+
+
+def _fp16_dequantised(J):
+    """The finest level's FP16 storage as the kernels define it: per vertex and
+    entry position q, scale = max over the stencil of |J_q| (as FP32; 1 when
+    below the smallest normal float), stored value = half(J_q / scale)
+    rounded to nearest, used as float(half) * scale in FP32."""
+    mx = np.abs(J).max(axis=1)                                   # [nv, 4]
+    sc = np.where(mx >= 1.17549435e-38, mx.astype(np.float32), np.float32(1.0)).astype(np.float32)
+    h = (J / sc[:, None, :].astype(np.float64)).astype(np.float16)
+    return (h.astype(np.float32) * sc[:, None, :]).astype(np.float64)
+
+
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-9x7x5-stress", "3d-lenses-33"])
+def test_fp16_storage_kernels_match_oracle(case):
+    """FP16 storage of the finest level (per-position FP32 row scales): the
+    residual, a block-Jacobi sweep and a forward 8-colour GS sweep against the
+    oracle applied to the same dequantised matrix, per component, to the FP32
+    accumulation bound.  The smoothers' D^-1 is that of the unquantised FP64
+    diagonal block, as in the kernels."""
+    prob = CASES[case]()
+    g, F = _assembled(prob)
+    shift = 1.0 / prob["H"]
+    L = _levels(prob)
+    m = O.Model(prob)
+    _, J_o, md_o = O.assemble(m, prob["u0"])
+    dim, n = m.dim, m.n
+    c = _centre(dim)
+    Jq = _fp16_dequantised(J_o)
+    Aq = O.make_A(Jq, md_o, shift)                 # quantised J, exact shift*M
+    Ax = O.make_A(J_o, md_o, shift)                # the FP64 operator (its diagonal feeds D^-1)
+    absA = np.abs(Jq)                              # |J| and |shift M| apart: the kernels add them in FP32
+    absA[:, c, 1] += shift * np.abs(md_o[:, 0])
+    absA[:, c, 3] += shift * np.abs(md_o[:, 1])
+    rng = np.random.default_rng(9)
+    nv = g.nv
+    b = rng.standard_normal(2 * nv).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal(2 * nv).astype(np.float32).astype(np.float64)
+    for smoother in ("jacobi", "gs8"):
+        g.gmg_setup([shift], rf.gmg_opts(L, smoother, precision="fp16"))
+        r = g.apply(rf.RF_OP_RESIDUAL, 0, 0, b, x)
+        r_o = O.residual(dim, n, Aq, b, x)
+        bound = 64.0 * U32 * (O.spmv(dim, n, absA, np.abs(x)) + np.abs(b)) + 1e-300
+        ok, q = _within(r, r_o, bound)
+        assert ok, ("residual", smoother, q)
+        sm = g.apply(rf.RF_OP_SMOOTH, 0, 0, b, x)
+        Amix = Aq.copy()
+        Amix[:, c] = Ax[:, c]                      # quantised off-diagonal, FP64 diagonal block
+        if smoother == "jacobi":
+            D = Ax[:, c, :].reshape(-1, 2, 2)
+            sm_o = x + 0.8 * _bmul(np.linalg.inv(D), r_o)
+            bound = _jacobi_bound(dim, n, Amix, b, x, sm_o, 0.8, "fp32", absA=absA)
+        else:
+            sm_o = O.gs_sweep(dim, n, Amix, b, x, True)
+            absoff = absA.copy()
+            absoff[:, c] = 0.0
+            bound = _gs_bound(dim, n, Amix, b, x, sm_o, "fp32", absA_off=absoff)
+        ok, q = _within(sm, sm_o, bound)
+        assert ok, ("smoother", smoother, q)
     g.close()
 
 
@@ -228,7 +347,8 @@ def test_vcycle_and_coarse_solve_match_oracle(case, smoother):
     b = np.random.default_rng(2).standard_normal(2 * g.nv)
     x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
     x_o = gm.vcycle(b)
-    assert np.abs(x - x_o).max() <= 1e-9 * np.abs(x_o).max()
+    for a in range(2):   # per component
+        assert np.abs(x[a::2] - x_o[a::2]).max() <= 1e-9 * np.abs(x_o[a::2]).max(), a
     L = gm.nlevels - 1
     nc = gm.level_dims(L)
     bc = np.random.default_rng(3).standard_normal(2 * int(np.prod(nc)))
@@ -236,6 +356,25 @@ def test_vcycle_and_coarse_solve_match_oracle(case, smoother):
     Ac = __import__("tests._helpers", fromlist=["x"]).stencil_to_dense(m.dim, nc, gm.level_matrix(L))
     xc_o = np.linalg.solve(Ac, bc)
     assert np.abs(xc - xc_o).max() <= 1e-10 * np.abs(xc_o).max()
+    g.close()
+
+
+@pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
+@pytest.mark.parametrize("case", ["2d-lens-33", "3d-17cube", "3d-lenses-33"])
+def test_fp32_vcycle_matches_fp32_emulation(case, smoother):
+    """The whole FP32 V-cycle against the oracle's FP32 emulation (the same
+    hierarchy with float storage and float sums): per component within 2e-6
+    of the largest value, and within the same bound of the FP64 V-cycle."""
+    prob = CASES[case]()
+    g, F, m, A, gm = _setup_both(prob, "fp32", smoother)
+    g32 = O.GMG32(gm)
+    b = np.random.default_rng(2).standard_normal(2 * g.nv).astype(np.float32).astype(np.float64)
+    x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
+    x32, x64 = g32.vcycle(b), gm.vcycle(b)
+    for a in range(2):
+        sc = np.abs(x64[a::2]).max()
+        assert np.abs(x[a::2] - x32[a::2]).max() <= 2e-6 * sc, (a, np.abs(x[a::2] - x32[a::2]).max() / sc)
+        assert np.abs(x[a::2] - x64[a::2]).max() <= 2e-6 * sc, (a, np.abs(x[a::2] - x64[a::2]).max() / sc)
     g.close()
 
 
@@ -251,7 +390,8 @@ def test_vcycle_cluster_tail_matches_oracle(smoother, precision, monkeypatch):
     x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
     x_o = gm.vcycle(b)
     tol = 1e-9 if precision == "fp64" else 1e-4
-    assert np.abs(x - x_o).max() <= tol * np.abs(x_o).max()
+    for a in range(2):   # per component
+        assert np.abs(x[a::2] - x_o[a::2]).max() <= tol * np.abs(x_o[a::2]).max(), a
     g.close()
 
 
@@ -412,14 +552,23 @@ def test_limex_step_matches_oracle(kappa):
     g.close()
 
 
-def test_batched_ensemble_equals_sequential_steps():
-    """rf_limex_step_batched runs uneven problems concurrently; every member's
-    result is bitwise the one of its own sequential rf_limex_step."""
+def _sequential_env(monkeypatch):
+    """The step with its columns one after another (no batched rounds)."""
+    monkeypatch.setenv("RF_LIMEX_BATCH", "0")
+    monkeypatch.setenv("RF_LIMEX_CONCURRENT", "0")
+
+
+def test_batched_ensemble_equals_sequential_steps(monkeypatch):
+    """rf_limex_step_batched groups the problems of equal shape and solves the
+    columns of all members of a group in shared batched rounds; every member's
+    result is bitwise the one of its own step with sequential columns."""
     probs = [I.random_problem(3, (17, 17, 17), 41), I.random_problem(3, (9, 9, 9), 42),
              I.random_problem(2, (33, 33), 43), I.random_problem(3, (33, 17, 9), 44),
-             I.random_problem(3, (17, 9, 9), 45)]
+             I.random_problem(3, (17, 9, 9), 45), I.random_problem(3, (17, 17, 17), 46),
+             I.random_problem(3, (9, 9, 9), 47), I.random_problem(3, (17, 17, 17), 49)]
     gm = [rf.gmg_opts(_levels(p), "jacobi", precision="fp32") for p in probs]
     seq = []
+    _sequential_env(monkeypatch)
     for p, o in zip(probs, gm):
         g = _grid(p)
         u = torch.tensor(p["u0"], device="cuda")
@@ -427,16 +576,23 @@ def test_batched_ensemble_equals_sequential_steps():
         torch.cuda.synchronize()
         seq.append((u.cpu().numpy(), info))
         g.close()
+    monkeypatch.delenv("RF_LIMEX_BATCH")
+    monkeypatch.delenv("RF_LIMEX_CONCURRENT")
     grids = [_grid(p) for p in probs]
     us = [torch.tensor(p["u0"], device="cuda") for p in probs]
-    st, infos = rf.limex_step_batched(grids, us, 5.0, kappa=3, tol=1e9, gmg=gm, rtol=1e-11, max_concurrent=3)
-    torch.cuda.synchronize()
-    assert st == max(i["status"] for _, i in seq)
-    assert sum(i["status"] == 0 for _, i in seq) >= 4
-    for (u_s, i_s), u_b, i_b in zip(seq, us, infos):
-        assert i_b["status"] == i_s["status"]
-        assert np.array_equal(u_s, u_b.cpu().numpy())
-        assert i_b["iterations"] == i_s["iterations"] and i_b["eps"] == i_s["eps"]
+    for rep in range(2):   # the second call re-captures after the new set-ups
+        for u, p in zip(us, probs):
+            u.copy_(torch.tensor(p["u0"], device="cuda"))
+        st, infos = rf.limex_step_batched(grids, us, 5.0, kappa=3, tol=1e9, gmg=gm, rtol=1e-11, max_concurrent=3)
+        torch.cuda.synchronize()
+        first_bad = next((i["status"] for _, i in seq if i["status"] != 0), 0)
+        assert st == first_bad
+        assert sum(i["status"] == 0 for _, i in seq) >= 6
+        for (u_s, i_s), u_b, i_b in zip(seq, us, infos):
+            assert i_b["status"] == i_s["status"]
+            assert np.array_equal(u_s, u_b.cpu().numpy())
+            assert i_b["iterations"] == i_s["iterations"] and i_b["eps"] == i_s["eps"]
+            assert i_b["solves"] == i_s["solves"]
     for g in grids:
         g.close()
 
@@ -474,15 +630,23 @@ def test_limex_rejects_and_keeps_state():
 
 
 @pytest.mark.parametrize("precision,smoother,outer", [("fp64", "jacobi", "fp64"), ("fp32", "gs8", "fp64"),
-                                                      ("fp32", "gs8", "df32")])
-def test_concurrent_limex_columns_equal_sequential(precision, smoother, outer, monkeypatch):
-    """The LIMEX columns run side by side on column grids (shared operators,
-    own vectors and streams); every column performs the same kernels in the
-    same order, so the step is bitwise the sequential one."""
+                                                      ("fp16", "gs8", "fp64"), ("fp32", "gs8", "df32"),
+                                                      ("fp32", "jacobi", "fp64")])
+def test_limex_column_schedules_are_bitwise_equal(precision, smoother, outer, monkeypatch):
+    """The LIMEX columns one after another, side by side on column grids (own
+    vectors and streams), and in batched rounds (every active column's solve
+    in the same launches, the shared J read once on the finest level) perform
+    the same operations per column: the steps are bitwise equal."""
     prob = I.random_problem(3, (17, 17, 9), 44)
+    modes = {"sequential": {"RF_LIMEX_BATCH": "0", "RF_LIMEX_CONCURRENT": "0"},
+             "concurrent": {"RF_LIMEX_BATCH": "0", "RF_LIMEX_CONCURRENT": "1"},
+             "batched": {"RF_LIMEX_BATCH": "1"}}
     out = {}
-    for conc in ("0", "1"):
-        monkeypatch.setenv("RF_LIMEX_CONCURRENT", conc)
+    for mode, env in modes.items():
+        for k in ("RF_LIMEX_BATCH", "RF_LIMEX_CONCURRENT"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
         g = _grid(prob)
         u = torch.tensor(prob["u0"], device="cuda")
         info = None
@@ -491,11 +655,12 @@ def test_concurrent_limex_columns_equal_sequential(precision, smoother, outer, m
                                 rtol=1e-11, max_it=300, outer=outer)
             assert info["status"] == 0, info
         torch.cuda.synchronize()
-        out[conc] = (u.cpu().numpy(), info)
+        out[mode] = (u.cpu().numpy(), info)
         g.close()
-    assert np.array_equal(out["0"][0], out["1"][0])
-    assert out["0"][1]["iterations"] == out["1"][1]["iterations"]
-    assert out["0"][1]["eps"] == out["1"][1]["eps"]
+    for mode in ("concurrent", "batched"):
+        assert np.array_equal(out["sequential"][0], out[mode][0]), mode
+        assert out["sequential"][1]["iterations"] == out[mode][1]["iterations"], mode
+        assert out["sequential"][1]["eps"] == out[mode][1]["eps"], mode
 
 
 @pytest.mark.parametrize("dim,nv", [(2, (2, 2)), (2, (3, 2)), (3, (2, 2, 2)), (3, (3, 2, 3))])
@@ -567,3 +732,29 @@ def test_plane_and_point_transfers_are_bitwise_equal(precision, monkeypatch):
     assert out["0"][1] == out["1"][1] and out["0"][1]["status"] == 0
     for a, b_ in zip(out["0"][0], out["1"][0]):
         assert np.array_equal(a, b_)
+
+
+def test_limex_run_matches_oracle_run():
+    """rf_limex_run against the oracle's rfo_limex_run (same policy: hold
+    after a rejection, H_max, landing on t_end) from a consistent state: the
+    same accept / reject sequence, the step sizes and the final state."""
+    prob = I.random_problem(2, (9, 9), 23)
+    m = O.Model(prob)
+    u0, inf = O.ie_step(m, prob["u0"], 1e-3, nlevels=2, atol=0.0, rtol=1e-11, lin_rtol=1e-14, max_newton=40)
+    assert inf["status"] == 0
+    kw = dict(t_end=3000.0, H_max=600.0, tol=1e-3, kappa=3)
+    u_o, info_o, hist_o = O.limex_run(m, u0, 50.0, nlevels=2, rtol=1e-12, **kw)
+    assert info_o["status"] == 0 and info_o["rejected"] >= 2
+    g = _grid(prob)
+    u = torch.tensor(u0, device="cuda")
+    t, hist = g.limex_run(u, 50.0, gmg=rf.gmg_opts(2, "jacobi", precision="fp64"), rtol=1e-12, max_it=300, **kw)
+    torch.cuda.synchronize()
+    assert g.last_run["status"] == 0
+    assert [h["accepted"] for h in hist] == [int(a) for a in hist_o[:, 2]]
+    np.testing.assert_allclose([h["H"] for h in hist], hist_o[:, 0], rtol=1e-7)
+    np.testing.assert_allclose([h["eps"] for h in hist], hist_o[:, 1], rtol=1e-5)
+    assert t == pytest.approx(info_o["t"], rel=1e-12)
+    us = u.cpu().numpy()
+    assert np.abs(us[0::2] - u_o[0::2]).max() <= 1e-8 * np.abs(u_o[0::2]).max()
+    assert np.abs(us[1::2] - u_o[1::2]).max() <= 1e-9
+    g.close()

@@ -1,15 +1,17 @@
 """The workloads end to end against the oracle: the 65^3 lognormal cube (one
-full FP64 LIMEX step) and members of the 64-realisation ensemble (one LIMEX
-step with FP32 multigrid inside FP64 BiCGSTAB, at 33^3 and 49^3).  The 97^3
-members and the 257^3 / 385^3 configurations are checked by sampled rows and
-invariants in test_gpu_fullsize.py and test_gpu_parity.py (the oracle would
-take minutes there).
+full FP64 LIMEX step) and one member of each size of the 64-realisation
+ensemble (one LIMEX step with FP32 multigrid inside FP64 BiCGSTAB, at 33^3,
+49^3, 65^3 and 97^3; the oracle runs with OpenMP on the host cores).  The
+257^3 / 385^3 configurations are checked in test_gpu_oracle_fullsize.py and by
+sampled rows and invariants in test_gpu_fullsize.py and test_gpu_parity.py.
 
 Both sides solve every stage to a true relative residual of 1e-12; the LIMEX
 results then agree to 1e-8 relative in p_w and 1e-9 absolute in S_n (the
 extrapolation weights amplify the solvers' differences by at most ~30), and
 the error estimates to 1e-5 relative.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -28,6 +30,7 @@ def _built():
     G.build()
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
+    O.set_threads(len(os.sched_getaffinity(0)))
 
 
 def _limex_parity(prob, precision, smoother, H=10.0):
@@ -56,8 +59,9 @@ def test_lognormal_cube_65_limex_step_matches_oracle():
     print("65^3 LIMEX step: GPU iterations", info["iterations"], "oracle", inf_o["iterations"])
 
 
-@pytest.mark.parametrize("seed,nvert", [(100, 33), (116, 49)])
+@pytest.mark.parametrize("seed,nvert", [(100, 33), (116, 49), (132, 65), (148, 97)])
 def test_ensemble_member_limex_step_matches_oracle(seed, nvert):
     """Ensemble members (seed order: 33^3 for seeds 100..115, 49^3 for
-    116..131): one LIMEX step with FP32 multigrid inside FP64 BiCGSTAB."""
+    116..131, 65^3 for 132..147, 97^3 for 148..163): one LIMEX step with FP32
+    multigrid inside FP64 BiCGSTAB."""
     _limex_parity(I.ensemble_member(seed, nvert), "fp32", "jacobi")

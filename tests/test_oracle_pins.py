@@ -803,3 +803,79 @@ def test_ie_line_search_converges_where_plain_newton_fails(oracle):
     R = F - dm.ravel() / H
     R[0::2][p["dir"].astype(bool)] = F[0::2][p["dir"].astype(bool)]
     assert np.linalg.norm(R) <= 1e-9 * inf["res0"] * 1.0000001
+
+
+# ---------------------------------------------------------------- adaptive LIMEX runs
+def test_limex_run_applies_the_step_control_policy(oracle):
+    """rfo_limex_run from a consistent state (tol 1e-3, H0 = 50 s, H_max =
+    600 s, t_end = 3000 s): accepted steps have eps <= tol and rejected ones
+    eps > tol; a rejected step is retried with a smaller H; the step after one
+    accepted right after a rejection is not larger (hold); H never exceeds
+    H_max; the last step lands on t_end.  Replaying the recorded steps with
+    rfo_limex_step gives the same state bit for bit, so the run is exactly a
+    composition of steps."""
+    p = I.random_problem(2, (9, 9), 23)
+    m = oracle.Model(p)
+    u0 = _consistent_start(oracle, m, p["u0"])
+    tol, H_max, t_end = 1e-3, 600.0, 3000.0
+    u, info, hist = oracle.limex_run(m, u0, 50.0, t_end=t_end, H_max=H_max, tol=tol, kappa=3, nlevels=2, rtol=1e-12)
+    assert info["status"] == 0 and info["steps"] == len(hist)
+    H, eps, acc = hist[:, 0], hist[:, 1], hist[:, 2].astype(bool)
+    assert info["rejected"] >= 2 and info["accepted"] == acc.sum() and info["rejected"] == (~acc).sum()
+    assert np.all(eps[acc] <= tol) and np.all(eps[~acc] > tol)
+    for k in range(len(hist) - 1):
+        if not acc[k]:
+            assert H[k + 1] < H[k]
+        if acc[k] and k > 0 and not acc[k - 1] and k + 1 < len(hist) - 1:
+            assert H[k + 1] <= H[k]
+    assert H.max() <= H_max and (H == H_max).any()
+    assert info["t"] == pytest.approx(t_end, rel=1e-12)
+    assert H[acc].sum() == pytest.approx(t_end, rel=1e-12)
+    # replay
+    v = u0.copy()
+    for k in range(len(hist)):
+        v2, inf = oracle.limex_step(m, v, H[k], kappa=3, tol=tol, nlevels=2, rtol=1e-12)
+        assert inf["accepted"] == acc[k] and inf["eps"] == eps[k]
+        v = v2
+    assert np.array_equal(v, u)
+
+
+# ---------------------------------------------------------------- FP32 emulation of the V-cycle
+@pytest.mark.parametrize("smoother", [0, 1])
+@pytest.mark.parametrize("case", ["2d-lens", "3d-random"])
+def test_fp32_vcycle_emulation_tracks_the_fp64_vcycle(oracle, case, smoother):
+    """The float V-cycle (float storage and sums) is the FP64 V-cycle up to
+    single-precision rounding: per component within 2e-6 of the largest
+    value (a dropped or misplaced term would move it by O(1)); as a
+    stationary iteration on the constant-coefficient Poisson stencil it
+    contracts like the FP64 cycle until the float floor."""
+    prob = I.lens_square_2d() if case == "2d-lens" else I.random_problem(3, (17, 17, 17), 5)
+    m = oracle.Model(prob)
+    F, J, md = oracle.assemble(m, prob["u0"])
+    A = oracle.make_A(J, md, 2.0 / prob["H"])
+    L = 4 if case == "2d-lens" else 3
+    gm = oracle.GMG(m.dim, m.n, A, prob["dir"], L, smoother=smoother)
+    g32 = oracle.GMG32(gm)
+    b = np.random.default_rng(2).standard_normal(2 * m.nv).astype(np.float32).astype(np.float64)
+    x64, x32 = gm.vcycle(b), g32.vcycle(b)
+    for a in range(2):
+        assert np.abs(x32[a::2] - x64[a::2]).max() <= 2e-6 * np.abs(x64[a::2]).max(), a
+
+
+def test_fp32_vcycle_emulation_converges_on_poisson(oracle):
+    dim, nv = 2, (33, 33)
+    p = _poisson_problem(dim, nv)
+    m = oracle.Model(p)
+    F, J, md = oracle.assemble(m, p["u0"])
+    A = oracle.make_A(J, md, 0.1)
+    gm = oracle.GMG(dim, m.n, A, p["dir"], 4, smoother=0)
+    g32 = oracle.GMG32(gm)
+    x = np.random.default_rng(3).standard_normal(2 * m.nv)
+    x[0::2][p["dir"].astype(bool)] = 0.0
+    rs = []
+    for _ in range(5):
+        r = -oracle.spmv(dim, m.n, A, x)
+        rs.append(np.linalg.norm(r))
+        x = x + g32.vcycle(r)
+    rates = [rs[k + 1] / rs[k] for k in range(1, 4)]
+    assert max(rates) <= 0.15, rates
