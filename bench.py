@@ -29,13 +29,19 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+
+class _Skip(Exception):
+    """A bench block switched off on the command line."""
+
+
 METRIC = "BiCGSTAB-GMG DoF/s to rel.res 1e-10, FP32-GMG vs FP64, % of HBM peak"
 RTOL = 1e-10
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per colour vertex of
-# a full fine-level FP32 GS colour launch, from one ncu capture of this
-# workload's recipe at 129^3 (traffic grows with the vertices processed); the
-# algorithmic count is 456 B.
-GS_TRAFFIC_PER_COLOUR_VERTEX = 560.0
+# a full fine-level FP32 GS colour launch, by vertices per axis of this
+# workload's recipe: ncu captures of the eight colour launches of the second
+# fine sweep in the solve's own launch sequence (caches not flushed, so a
+# launch finds in L2 what its predecessors left); the algorithmic count is 456 B.
+GS_TRAFFIC_PER_COLOUR_VERTEX = {257: 516.6}
 GS_ALGO_PER_COLOUR_VERTEX = 456.0
 # FP64 floating-point operations per vertex of one outer operator application
 # (k_bicg_v / k_bicg_t): 27 blocks x 4 FMA (216 flop), the shift*M diagonal
@@ -64,6 +70,7 @@ def args_():
                     help="extra solve variants to time: precision[+outer], comma separated ('none': no variants)")
     ap.add_argument("--sample-nvert", type=int, default=129, help="oracle sample size (vertices per axis)")
     ap.add_argument("--ensemble", type=int, default=1, help="also time the 64-realisation ensemble (1/0)")
+    ap.add_argument("--limex", type=int, default=1, help="also time one 65^3 LIMEX step and its schedules (1/0)")
     ap.add_argument("--infiltration-nvert", type=int, default=385,
                     help="also run adaptive LIMEX on the DNAPL-infiltration recipe at this size (0: skip)")
     ap.add_argument("--infiltration-steps", type=int, default=3,
@@ -344,12 +351,13 @@ def main():
     dv = prof[dom]
     achieved = dv["bytes"] / (dv["ms"] / 1e3) / 1e9
     traffic = None
-    if dom == "smooth_fine" and a.smoother == "gs8" and a.precision == "fp32":
+    if (dom == "smooth_fine" and a.smoother == "gs8" and a.precision == "fp32"
+            and a.nvert in GS_TRAFFIC_PER_COLOUR_VERTEX):
         colour_vertices = g.nv / 8.0
-        traffic = {"bytes_per_launch": GS_TRAFFIC_PER_COLOUR_VERTEX * colour_vertices,
+        traffic = {"bytes_per_launch": GS_TRAFFIC_PER_COLOUR_VERTEX[a.nvert] * colour_vertices,
                    "algorithmic_bytes_per_launch": GS_ALGO_PER_COLOUR_VERTEX * colour_vertices,
                    "launch": "one full-sweep colour (nv/8 vertices)",
-                   "source": "ncu capture at 129^3 scaled by vertices"}
+                   "source": "ncu capture of this size, colour launches in the solve's sequence"}
     # the FP64 pipe's roofline of the outer operator (FP64-pipe-bound: 108 FMA
     # per 864 B of J), against the FMA rate measured above
     sp = prof["spmv64"]
@@ -395,6 +403,8 @@ def main():
     # ---- one full LIMEX step (65^3 lognormal cube, kappa = 4, FP64 throughout)
     limex = None
     try:
+        if not a.limex:
+            raise _Skip()
         p2 = I.lognormal_cube_65()
         g2 = rf.Grid(p2)
         u_ref = torch.tensor(p2["u0"], device=dev)
@@ -436,6 +446,8 @@ def main():
                  "speedup_vs_sequential": round(sms / lms, 3),
                  "bitwise_equal_to_sequential": bool(np.array_equal(ub, us) and np.array_equal(ub, uc))}
         g2.close()
+    except _Skip:
+        pass
     except rf.RFError as e:
         limex = {"error": str(e)}
 

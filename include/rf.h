@@ -148,6 +148,29 @@ rf_status rf_assemble(rf_grid* g, const double* u, int want_jacobian, double* F_
 #define RF_SCHEME_DARCY_UPWIND 2
 rf_status rf_grid_set_scheme(rf_grid* g, int scheme);
 
+/* Per-medium relative permeabilities (Sec. 6, Case 2, Table "Parameters for
+ * Case-2": each of the two media has its own polynomial k_rw and k_rn).
+ * laws (host, 6 doubles per law, nlaws <= RF_MAX_KR_LAWS) holds rows
+ * {kind, a_w, n_w, a_n, b_n, c_n}:
+ *   RF_KR_BROOKS_COREY: the grid's Brooks-Corey laws (other entries unused);
+ *   RF_KR_POLY: k_rw = a_w S^n_w, k_rn = a_n (1 - b_n S)^2 (1 - c_n S^2)
+ *     while 1 - b_n S > 0 and 1 - c_n S^2 > 0, and k_rn = 0 from the first of
+ *     those roots on; S = S_e clamped to [0, 1], derivatives 0 outside
+ *     (0, 1); n_w a whole number 1..8, a_w, a_n >= 0.
+ * cell_law (host, one byte per cell in natural cell order) names each cell's
+ * law.  Every face of a cell uses that cell's law for the upwinded k_rw
+ * (Eq. krw_ip), the k_rw of the capillary term and k_rn of S hat (Eq.
+ * krn_ip).  Capillary pressure stays Brooks-Corey with the cell's p_d.
+ * nlaws = 0 returns to Brooks-Corey everywhere.  Both arrays are copied
+ * (synchronously on `stream`); the assembled Jacobian and the multigrid
+ * set-up are dropped.  RF_EINVAL for a bad count, kind or coefficient, a cell
+ * naming a missing law, or device pointers; RF_ENOMEM if the device copy
+ * cannot be allocated. */
+#define RF_MAX_KR_LAWS 4
+#define RF_KR_BROOKS_COREY 0
+#define RF_KR_POLY 1
+rf_status rf_grid_set_kr_laws(rf_grid* g, int nlaws, const double* laws, const uint8_t* cell_law, void* stream);
+
 /* Build the multigrid hierarchy for the stage matrices A_j = shift[j] M - J,
  * j < nshift <= 4 (shift = 1/h_j), from the last assembled J, M: Galerkin
  * coarse operators P^T A P with trilinear P (FP64), the preconditioner copies

@@ -55,7 +55,10 @@ class _Model(ctypes.Structure):
                 ("S_nr", ctypes.c_double), ("lam", ctypes.c_double),
                 ("K", ctypes.c_void_p), ("phi", ctypes.c_void_p), ("pd", ctypes.c_void_p),
                 ("dir", ctypes.c_void_p), ("pw_dir", ctypes.c_void_p), ("q_in", ctypes.c_void_p),
-                ("scheme", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("nlaws", ctypes.c_int), ("kr_laws", ctypes.c_void_p),
+                ("cell_law", ctypes.c_void_p)]
+
+KR_BROOKS_COREY, KR_POLY = 0, 1
 
 
 class _LimexOpts(ctypes.Structure):
@@ -81,6 +84,7 @@ def _declare(L):
         "rfo_get_threads": (_I, []),
         "rfo_brooks_corey": (None, [_P, _D, _P]),
         "rfo_shat": (None, [_P, _D, _D, _D, _P]),
+        "rfo_kr_law": (None, [_P, _I, _D, _P]),
         "rfo_pdmin": (None, [_P, _P]),
         "rfo_phiv": (None, [_P, _P]),
         "rfo_assemble": (None, [_P, _P, _P, _P, _P]),
@@ -154,6 +158,13 @@ class Model:
         for k in ("K", "phi", "pd", "dir", "pw_dir", "q_in"):
             setattr(s, k, _p(self._keep[k]))
         s.scheme = int(prob.get("scheme", 0))
+        laws = prob.get("kr_laws")
+        if laws is not None:
+            self._keep["kr_laws"] = _f64(np.asarray(laws, dtype=np.float64).reshape(-1, 6))
+            self._keep["cell_law"] = np.ascontiguousarray(prob["cell_law"], dtype=np.uint8)
+            s.nlaws = len(self._keep["kr_laws"])
+            s.kr_laws = _p(self._keep["kr_laws"])
+            s.cell_law = _p(self._keep["cell_law"])
         self.s = s
 
     @property
@@ -174,6 +185,13 @@ def get_threads():
 def brooks_corey(model, Se):
     out = np.zeros(6)
     lib().rfo_brooks_corey(model.ref, float(Se), _p(out))
+    return out
+
+
+def kr_law(model, cell, Se):
+    """(k_rw, dk_rw/dS_e, k_rn, dk_rn/dS_e) of the medium of `cell`."""
+    out = np.zeros(4)
+    lib().rfo_kr_law(model.ref, int(cell), float(Se), _p(out))
     return out
 
 

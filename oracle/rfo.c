@@ -120,6 +120,38 @@ void rfo_brooks_corey(const rfo_model* m, double Se, double out[6]) {
   leverett(lam, Se, &out[4], &out[5]);
 }
 
+/* Relative permeabilities of the medium of a cell.  The polynomial laws are
+ * those of Sec. 6, Table "Parameters for Case-2" (k_rw,1 = 1.831 S_e^4,
+ * k_rn,1 = 0.75 (1 - 1.25 S_e)^2 (1 - 1.652 S_e^2); k_rw,2 = 0.4687 S_e^2,
+ * k_rn,2 = 0.25 (1 - 1.25 S_e)^2) written with free coefficients.  Printed as
+ * they are, both k_rn turn negative (law 1) or rise again (law 2) past their
+ * first root below S_e = 1; k_rn is taken as 0 from that root on.          */
+void rfo_kr_law(const rfo_model* m, int cell, double Se, double out[4]) {
+  const double* L = (m->nlaws > 0 && m->cell_law) ? m->kr_laws + 6 * m->cell_law[cell] : NULL;
+  if (!L || L[0] == RFO_KR_BROOKS_COREY) {
+    double bc[6];
+    rfo_brooks_corey(m, Se, bc);
+    out[0] = bc[0]; out[1] = bc[1]; out[2] = bc[2]; out[3] = bc[3];
+    return;
+  }
+  const double aw = L[1], an = L[3], bn = L[4], cn = L[5];
+  const int nw = (int)L[2];
+  const double S = Se < 0.0 ? 0.0 : (Se > 1.0 ? 1.0 : Se);
+  const int inside = (Se > 0.0 && Se < 1.0);
+  double p = 1.0;                      /* S^(n_w - 1) */
+  for (int t = 1; t < nw; ++t) p = p * S;
+  out[0] = aw * (p * S);
+  out[1] = inside ? (aw * nw) * p : 0.0;
+  const double r = 1.0 - bn * S, q = 1.0 - cn * (S * S);
+  if (r > 0.0 && q > 0.0) {
+    out[2] = an * (r * r) * q;
+    out[3] = inside ? an * (-2.0 * bn * r * q - 2.0 * cn * S * (r * r)) : 0.0;
+  } else {
+    out[2] = 0.0;
+    out[3] = 0.0;
+  }
+}
+
 /* Eq. (hSw): the effective saturation seen by vertex i inside an element of
  * entry pressure p_d.  Case 1: p_d = p_dmin,i -> S_i.  Otherwise p_d J(S) =
  * p_dmin J(S_i) gives S = (p_d/p_dmin)^lambda S_i, capped at the residual-NAPL
@@ -263,16 +295,12 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
   double* pn = malloc(sizeof(double) * nv);
   double* pc = malloc(sizeof(double) * nv);
   double* dpc = malloc(sizeof(double) * nv);
-  double* krw = malloc(sizeof(double) * nv);
-  double* dkrw = malloc(sizeof(double) * nv);
   rfo_pdmin(m, pdmin);
 #pragma omp parallel for schedule(static)
   for (int v = 0; v < nv; ++v) {
     double bc[6];
     Se[v] = (1.0 - u[2 * v + 1] - m->S_wr) / den;
     rfo_brooks_corey(m, Se[v], bc);
-    krw[v] = bc[0];
-    dkrw[v] = -bc[1] / den;               /* d k_rw / d S_n */
     pc[v] = pdmin[v] * bc[4];
     dpc[v] = -(pdmin[v] * bc[5]) / den;   /* d p_c / d S_n */
     pn[v] = u[2 * v] + pc[v];
@@ -287,16 +315,21 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
         const int cell = ci + cx * (cj + cy * ck);
         const double Kc = m->K[cell], pdc = m->pd[cell];
         int vq[8], qoff[8][3];
-        double krn_h[8], dkrn_h[8];
+        double krn_h[8], dkrn_h[8], krw_c[8], dkrw_c[8];
         for (int q = 0; q < ncorner; ++q) {
           qoff[q][0] = q & 1; qoff[q][1] = (q >> 1) & 1; qoff[q][2] = (q >> 2) & 1;
           int vi = ci + qoff[q][0], vj = cj + qoff[q][1], vk = (dim == 3) ? ck + qoff[q][2] : 0;
           vq[q] = vi + nx * (vj + ny * vk);
-          double sh[2], bc[6];
+          double sh[2], kr[4];
           rfo_shat(m, Se[vq[q]], pdc, pdmin[vq[q]], sh);
-          rfo_brooks_corey(m, sh[0], bc);
-          krn_h[q] = bc[2];
-          dkrn_h[q] = bc[3] * sh[1] * (-1.0 / den);  /* d k_rn(S hat) / d S_n */
+          rfo_kr_law(m, cell, sh[0], kr);
+          krn_h[q] = kr[2];
+          dkrn_h[q] = kr[3] * sh[1] * (-1.0 / den);  /* d k_rn(S hat) / d S_n */
+          /* k_rw of the corner's S_w with this cell's law (Eq. krw_ip): the
+           * vertex value when one law holds everywhere */
+          rfo_kr_law(m, cell, Se[vq[q]], kr);
+          krw_c[q] = kr[0];
+          dkrw_c[q] = -kr[1] / den;                   /* d k_rw / d S_n */
         }
         for (int k = 0; k < dim; ++k) {
           int oth[2], no = 0;
@@ -344,9 +377,9 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
             const double Tpw = -KA * (gpw - m->rho_w * m->g[k]);
             const int uw = darcy ? ((Tpw >= 0.0) ? a : b) : ((Tw >= 0.0) ? a : b);
             const int un = (Tn >= 0.0) ? a : b;
-            double bcM[6];
-            rfo_brooks_corey(m, SeM, bcM);
-            const double lw_up = krw[vq[uw]] / m->mu_w;
+            double bcM[4];
+            rfo_kr_law(m, cell, SeM, bcM);
+            const double lw_up = krw_c[uw] / m->mu_w;
             const double lwM = bcM[0] / m->mu_w;
             const double ln_up = krn_h[un] / m->mu_n;
             const double Fw = darcy ? m->rho_w * (lw_up * Tpw) : m->rho_w * (lw_up * Tw - lwM * Tc);
@@ -354,7 +387,7 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
             F[2 * vq[a]] -= Fw; F[2 * vq[a] + 1] -= Fn;
             F[2 * vq[b]] += Fw; F[2 * vq[b] + 1] += Fn;
             if (!J) continue;
-            const double dlw_up = dkrw[vq[uw]] / m->mu_w;
+            const double dlw_up = dkrw_c[uw] / m->mu_w;
             const double dlwM_dSeM = bcM[1] / m->mu_w;
             const double dln_up = dkrn_h[un] / m->mu_n;
             for (int q = 0; q < ncorner; ++q) {
@@ -409,7 +442,7 @@ void rfo_assemble(const rfo_model* m, const double* u, double* F, double* J, dou
       J[((size_t)v * nb + centre(dim)) * 4 + 0] = -1.0;
     }
   }
-  free(phiv); free(pdmin); free(Se); free(pn); free(pc); free(dpc); free(krw); free(dkrw);
+  free(phiv); free(pdmin); free(Se); free(pn); free(pc); free(dpc);
 }
 
 /* ------------------------------------------------------------------------ */

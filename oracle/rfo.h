@@ -37,7 +37,18 @@ typedef struct {
   const double* pw_dir;      /* per vertex Dirichlet value (used where dir=1) */
   const double* q_in;        /* per vertex [2] mass source kg/s (may be NULL) */
   int scheme;                /* RFO_SCHEME_* bits; 0 = the discretisation of Sec. 3 */
+  /* Per-medium relative permeabilities (Sec. 6, Case 2 gives each of its two
+   * media its own polynomial k_rw, k_rn).  nlaws = 0 (and cell_law NULL):
+   * the Brooks-Corey laws everywhere.  Otherwise kr_laws[6m .. 6m+5] =
+   * {kind, a_w, n_w, a_n, b_n, c_n} for law m < nlaws and cell_law[c] < nlaws
+   * names the law of cell c; kind RFO_KR_BROOKS_COREY uses the Brooks-Corey
+   * laws, RFO_KR_POLY the polynomial laws of rfo_kr_law.  Capillary pressure
+   * stays Brooks-Corey with the cell's p_d. */
+  int nlaws;
+  const double* kr_laws;
+  const unsigned char* cell_law;
 } rfo_model;
+enum { RFO_KR_BROOKS_COREY = 0, RFO_KR_POLY = 1 };
 
 /* Discretisation variants (bits of rfo_model.scheme):
  *   RFO_SCHEME_SHAT_STORAGE: the storage term of sub-control volume b_i^j uses
@@ -59,6 +70,13 @@ void rfo_brooks_corey(const rfo_model* m, double Se, double out[6]);
 /* out = {krw, dkrw/dSe, krn, dkrn/dSe, J, dJ/dSe} */
 void rfo_shat(const rfo_model* m, double Se, double pd_cell, double pdmin, double out[2]);
 /* out = {S_e hat, d S_e hat / d S_e} */
+void rfo_kr_law(const rfo_model* m, int cell, double Se, double out[4]);
+/* relative permeabilities of cell's medium: out = {krw, dkrw/dSe, krn, dkrn/dSe}.
+ * RFO_KR_POLY (S = S_e clamped to [0, 1], derivatives 0 outside (0, 1)):
+ *   k_rw = a_w S^n_w (n_w a whole number, 1..8),
+ *   k_rn = a_n (1 - b_n S)^2 (1 - c_n S^2) while both 1 - b_n S and
+ *   1 - c_n S^2 are positive, and 0 from the first of their roots on (the
+ *   NAPL is immobile there). */
 
 /* ---- spatial discretisation ---- */
 void rfo_pdmin(const rfo_model* m, double* pdmin);   /* [nv] */

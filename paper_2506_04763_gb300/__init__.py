@@ -122,6 +122,7 @@ SIGNATURES = {
     "rf_grid_nv": (_I64, [_P]),
     "rf_assemble": (_I, [_P, _P, _I, _P, _P]),
     "rf_grid_set_scheme": (_I, [_P, _I]),
+    "rf_grid_set_kr_laws": (_I, [_P, _I, _P, _P, _P]),
     "rf_gmg_setup": (_I, [_P, _P, _I, _P, _P]),
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
@@ -185,6 +186,18 @@ def rf_assemble(grid, u_ptr, want_jacobian, F_ptr, stream):
 
 def rf_grid_set_scheme(grid, scheme):
     _check(lib().rf_grid_set_scheme(grid, int(scheme)))
+
+
+def rf_grid_set_kr_laws(grid, laws, cell_law, stream=None):
+    """laws: [nlaws, 6] rows {kind, a_w, n_w, a_n, b_n, c_n}; cell_law: one
+    law index per cell (natural cell order).  laws=None: Brooks-Corey
+    everywhere."""
+    if laws is None:
+        _check(lib().rf_grid_set_kr_laws(grid, 0, None, None, stream))
+        return
+    t = np.ascontiguousarray(np.asarray(laws, dtype=np.float64).reshape(-1, 6))
+    c = np.ascontiguousarray(cell_law, dtype=np.uint8)
+    _check(lib().rf_grid_set_kr_laws(grid, len(t), t.ctypes.data, c.ctypes.data, stream))
 
 
 def rf_gmg_setup(grid, shifts, opts, stream):
@@ -362,6 +375,8 @@ class Grid:
         self.handle = rf_grid_create(desc, fl, mat, bc, self._alloc, self.stream)
         if int(prob.get("scheme", 0)):
             self.set_scheme(prob["scheme"])
+        if prob.get("kr_laws") is not None:
+            self.set_kr_laws(prob["kr_laws"], prob["cell_law"])
 
     def close(self):
         if getattr(self, "handle", None):
@@ -382,6 +397,11 @@ class Grid:
     def set_scheme(self, scheme):
         """Discretisation variant bits (SCHEME_SHAT_STORAGE, SCHEME_DARCY_UPWIND)."""
         rf_grid_set_scheme(self.handle, scheme)
+
+    def set_kr_laws(self, laws, cell_law):
+        """Per-medium relative permeability laws (rows {kind, a_w, n_w, a_n,
+        b_n, c_n}) and each cell's law index; laws=None: Brooks-Corey."""
+        rf_grid_set_kr_laws(self.handle, laws, cell_law, self.stream)
 
     def gmg_setup(self, shifts, opts):
         rf_gmg_setup(self.handle, list(shifts), opts, self.stream)

@@ -104,6 +104,41 @@ __device__ __forceinline__ void krn_of(double lam, double Se, double& k, double&
   }
 }
 
+// Per-medium relative permeabilities (Sec. 6, Case 2: each medium has its own
+// polynomial k_rw, k_rn).  law < 0 or a row of kind 0: the Brooks-Corey laws
+// above.  Kind 1, row {1, a_w, n_w, a_n, b_n, c_n}: k_rw = a_w S^n_w, k_rn =
+// a_n (1 - b_n S)^2 (1 - c_n S^2) while both factors are positive and 0 from
+// the first of their roots on, S = S_e clamped to [0, 1], derivatives 0
+// outside (0, 1).
+__device__ __forceinline__ const double* law_row(const double* tab, int law) {
+  return (law < 0 || tab[6 * law] == 0.0) ? nullptr : tab + 6 * law;
+}
+
+__device__ __forceinline__ void krw_law(double lam, const double* L, double Se, double& k, double& dk) {
+  if (!L) { krw_of(lam, Se, k, dk); return; }
+  const double aw = L[1];
+  const int nw = (int)L[2];
+  const double S = fmin(fmax(Se, 0.0), 1.0);
+  double p = 1.0;                     // S^(n_w - 1)
+  for (int t = 1; t < nw; ++t) p = p * S;
+  k = aw * (p * S);
+  dk = (Se > 0.0 && Se < 1.0) ? (aw * nw) * p : 0.0;
+}
+
+__device__ __forceinline__ void krn_law(double lam, const double* L, double Se, double& k, double& dk) {
+  if (!L) { krn_of(lam, Se, k, dk); return; }
+  const double an = L[3], bn = L[4], cn = L[5];
+  const double S = fmin(fmax(Se, 0.0), 1.0);
+  const double r = 1.0 - bn * S, q = 1.0 - cn * (S * S);
+  if (r > 0.0 && q > 0.0) {
+    k = an * (r * r) * q;
+    dk = (Se > 0.0 && Se < 1.0) ? an * (-2.0 * bn * r * q - 2.0 * cn * S * (r * r)) : 0.0;
+  } else {
+    k = 0.0;
+    dk = 0.0;
+  }
+}
+
 // Eq. (hSw): S_e hat of vertex i inside an element of entry pressure pdc.
 __device__ __forceinline__ void shat_of(double lam, double Se, double pdc, double pdmin, double& s, double& ds) {
   if (pdc == pdmin) { s = Se; ds = 1.0; return; }
@@ -203,6 +238,8 @@ struct AsmIn {
   const uint8_t* dir;             // parity-split
   const double* pw_dir;           // parity-split
   const double2* q_in;            // parity-split (may be null)
+  const uint8_t* law;             // per cell k_r law (natural cell order), or null
+  const double* kr_tab;           // law table, 6 doubles per law
 };
 
 template <int DIM, bool WANT_J>
@@ -247,6 +284,7 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
     if (ci < 0 || ci >= cx || cj < 0 || cj >= cy || ck < 0 || ck >= cz) continue;
     const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
     const double Kc = in.K[cell], pdc = in.pd[cell];
+    const double* law = in.law ? law_row(in.kr_tab, in.law[cell]) : nullptr;
     int64_t vq[NC];
     double se[NC], pnq[NC], pcq[NC], dpcq[NC], pwq[NC];
 #pragma unroll
@@ -311,20 +349,28 @@ __global__ void __launch_bounds__(128) k_assemble(Dims d, Phys ph, AsmIn in, dou
       const bool wa = darcy ? Tpw >= 0.0 : Tw >= 0.0, na = Tn >= 0.0;
       const int64_t vw = wa ? vq[a] : vq[b];
       const int64_t vn = na ? vq[a] : vq[b];
-      const double lw_up = in.krw[vw];   // k_rw / mu_w
+      double lw_up, dlw_up;   // k_rw / mu_w of the upwind vertex (with this element's law) and its S_n-derivative
+      if (!law) {
+        lw_up = in.krw[vw];
+        dlw_up = in.dkrw[vw];
+      } else {
+        double k, dk;
+        krw_law(ph.lam, law, in.Se[vw], k, dk);
+        lw_up = k / ph.mu_w;
+        dlw_up = (-dk / ph.den) / ph.mu_w;
+      }
       double kM, dkM;
-      krw_of(ph.lam, SeM, kM, dkM);
+      krw_law(ph.lam, law, SeM, kM, dkM);
       const double lwM = kM / ph.mu_w;
       double sh, dsh, kn, dkn;
       shat_of(ph.lam, in.Se[vn], pdc, in.pdmin[vn], sh, dsh);
-      krn_of(ph.lam, sh, kn, dkn);
+      krn_law(ph.lam, law, sh, kn, dkn);
       const double ln_up = kn / ph.mu_n;
       const double Fw = darcy ? ph.rho_w * (lw_up * Tpw) : ph.rho_w * (lw_up * Tw - lwM * Tc);
       const double Fn = ph.rho_n * (ln_up * Tn);
       F0 += sgn * Fw;
       F1 += sgn * Fn;
       if (WANT_J) {
-        const double dlw_up = in.dkrw[vw];
         const double dlwM_dSeM = dkM / ph.mu_w;
         const double dln_up = dkn * dsh * neg_inv_den / ph.mu_n;
         const int qw = wa ? a : b, qn = na ? a : b;
@@ -418,6 +464,7 @@ __global__ void __launch_bounds__(128) k_assemble_cells(Dims d, Phys ph, AsmIn i
   const int ck = DIM == 3 ? 2 * (int)(line / nyp) + pz : 0;
   const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
   const double Kc = in.K[cell], pdc = in.pd[cell];
+  const double* law = in.law ? law_row(in.kr_tab, in.law[cell]) : nullptr;
   const double neg_inv_den = -1.0 / ph.den;
   const bool darcy = (ph.scheme & SCHEME_DARCY_UPWIND) != 0;
   double gtab[DIM][DIM];   // +-w / h_k by the number of 1/4 factors (see k_assemble)
@@ -497,13 +544,22 @@ __global__ void __launch_bounds__(128) k_assemble_cells(Dims d, Phys ph, AsmIn i
       const bool wa = darcy ? Tpw >= 0.0 : Tw >= 0.0, na = Tn >= 0.0;
       const int qw = wa ? a : b, qn = na ? a : b;
       const int64_t vw = wa ? vq[a] : vq[b], vn = na ? vq[a] : vq[b];   // selects, not indexing
-      const double lw_up = in.krw[vw];   // k_rw / mu_w
+      double lw_up, dlw_up;   // k_rw / mu_w of the upwind vertex (with this element's law) and its S_n-derivative
+      if (!law) {
+        lw_up = in.krw[vw];
+        dlw_up = in.dkrw[vw];
+      } else {
+        double k, dk;
+        krw_law(ph.lam, law, wa ? se[a] : se[b], k, dk);
+        lw_up = k / ph.mu_w;
+        dlw_up = (-dk / ph.den) / ph.mu_w;
+      }
       double kM, dkM;
-      krw_of(ph.lam, SeM, kM, dkM);
+      krw_law(ph.lam, law, SeM, kM, dkM);
       const double lwM = kM / ph.mu_w;
       double sh, dsh, kn, dkn;
       shat_of(ph.lam, na ? se[a] : se[b], pdc, in.pdmin[vn], sh, dsh);
-      krn_of(ph.lam, sh, kn, dkn);
+      krn_law(ph.lam, law, sh, kn, dkn);
       const double ln_up = kn / ph.mu_n;
       const double Fw = darcy ? ph.rho_w * (lw_up * Tpw) : ph.rho_w * (lw_up * Tw - lwM * Tc);
       const double Fn = ph.rho_n * (ln_up * Tn);
@@ -512,7 +568,6 @@ __global__ void __launch_bounds__(128) k_assemble_cells(Dims d, Phys ph, AsmIn i
       Fl[b][0] += Fw;
       Fl[b][1] += Fn;
       if (WANT_J) {
-        const double dlw_up = in.dkrw[vw];
         const double dlwM_dSeM = dkM / ph.mu_w;
         const double dln_up = dkn * dsh * neg_inv_den / ph.mu_n;
 #pragma unroll
@@ -687,6 +742,7 @@ cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays
   in.dkrw = a.dkrw; in.pdmin = a.pdmin; in.phiv = a.phiv; in.K = a.K; in.pd = a.pd; in.phi = a.phi;
   in.vol = a.vol; in.dir = a.dir;
   in.pw_dir = a.pw_dir; in.q_in = (const double2*)a.q_in;
+  in.law = a.law; in.kr_tab = a.kr_tab;
   static const bool per_vertex = getenv("RF_ASM_VERTEX") && atoi(getenv("RF_ASM_VERTEX")) != 0;
   if (!per_vertex) {
     launch_assemble_cells(d, ph, in, a, want_j, s);

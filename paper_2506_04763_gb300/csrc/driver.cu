@@ -132,6 +132,9 @@ struct rf_grid {
   double h[3], g[3];
   int64_t ncell = 0;
   double *Kcell = nullptr, *phi = nullptr, *pd = nullptr;
+  uint8_t* law = nullptr;       // per cell k_r law (rf_grid_set_kr_laws), null: Brooks-Corey everywhere
+  double* kr_tab = nullptr;     // [RF_MAX_KR_LAWS][6] law table
+  bool laws_on = false;
   double vol = 0.0;   // cell volume
   double* ie_old = nullptr;     // implicit Euler: u_old (parity-split pairs), allocated on first use
   double* ie_swold = nullptr;   // implicit Euler, S hat storage: water pore volume sums of u_old
@@ -580,6 +583,7 @@ static rf_status assemble_p(rf_grid* g, bool want_j, void* s) {
   a.pdmin = g->pdmin; a.phiv = g->phiv; a.K = g->Kcell; a.pd = g->pd; a.phi = g->phi; a.vol = g->vol;
   a.dir = g->dir; a.pw_dir = g->pw_dir;
   a.q_in = g->q_in; a.F = g->F_p; a.J = want_j ? g->J : nullptr; a.mdiag = want_j ? g->mdiag : nullptr;
+  a.law = g->laws_on ? g->law : nullptr; a.kr_tab = g->kr_tab;
   cudaError_t e = launch_assemble(g->d, g->pp, a, want_j, s);
   if (e != cudaSuccess) return fail(RF_ECUDA, "assembly launch: %s", cudaGetErrorString(e));
   if (want_j) { g->have_J = true; g->gmg_ready = false; g->jdf_valid = false; }
@@ -602,6 +606,40 @@ extern "C" rf_status rf_grid_set_scheme(rf_grid* g, int scheme) {
   if (scheme & ~(RF_SCHEME_SHAT_STORAGE | RF_SCHEME_DARCY_UPWIND)) return fail(RF_EINVAL, "unknown scheme bits 0x%x", scheme);
   if (g->pp.scheme != scheme) { g->have_J = false; g->gmg_ready = false; g->jdf_valid = false; }
   g->pp.scheme = scheme;
+  return RF_OK;
+}
+
+static_assert(RF_KR_BROOKS_COREY == 0 && RF_KR_POLY == 1, "law kinds of the C ABI and the kernels agree");
+extern "C" rf_status rf_grid_set_kr_laws(rf_grid* g, int nlaws, const double* laws, const uint8_t* cell_law,
+                                         void* stream) {
+  if (!g) return fail(RF_EINVAL, "grid is required");
+  if (nlaws < 0 || nlaws > RF_MAX_KR_LAWS) return fail(RF_EINVAL, "nlaws must be 0..%d", RF_MAX_KR_LAWS);
+  if (nlaws > 0) {
+    if (!laws || !cell_law) return fail(RF_EINVAL, "laws and cell_law are required");
+    if (is_device_ptr(laws) || is_device_ptr(cell_law)) return fail(RF_EINVAL, "laws and cell_law must be host memory");
+    for (int m = 0; m < nlaws; ++m) {
+      const double* L = laws + 6 * m;
+      if (L[0] == RF_KR_BROOKS_COREY) continue;
+      if (L[0] != RF_KR_POLY) return fail(RF_EINVAL, "law %d: unknown kind %g", m, L[0]);
+      bool ok = L[1] >= 0.0 && L[3] >= 0.0 && std::isfinite(L[1]) && std::isfinite(L[3]) && std::isfinite(L[4]) &&
+                std::isfinite(L[5]) && L[2] >= 1.0 && L[2] <= 8.0 && L[2] == (double)(int)L[2];
+      if (!ok) return fail(RF_EINVAL, "law %d: coefficients out of range (a_w, a_n >= 0, n_w whole in 1..8)", m);
+    }
+    for (int64_t c = 0; c < g->ncell; ++c)
+      if (cell_law[c] >= nlaws) return fail(RF_EINVAL, "cell %lld names law %d of %d", (long long)c, cell_law[c], nlaws);
+    if (!g->kr_tab) {
+      if (!g->law) g->law = (uint8_t*)dalloc(g, (size_t)g->ncell, stream, false);
+      if (g->law) g->kr_tab = (double*)dalloc(g, sizeof(double) * 6 * RF_MAX_KR_LAWS, stream, false);
+      if (!g->kr_tab) return fail(RF_ENOMEM, "device allocation of the k_r laws failed");
+    }
+    double tab[6 * RF_MAX_KR_LAWS] = {};
+    for (int t = 0; t < 6 * nlaws; ++t) tab[t] = laws[t];
+    CU(cudaMemcpyAsync(g->law, cell_law, (size_t)g->ncell, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CU(cudaMemcpyAsync(g->kr_tab, tab, sizeof(tab), cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    CU(cudaStreamSynchronize((cudaStream_t)stream));
+  }
+  g->laws_on = nlaws > 0;
+  g->have_J = false; g->gmg_ready = false; g->jdf_valid = false;
   return RF_OK;
 }
 
@@ -641,13 +679,12 @@ static std::map<std::string, TuneChoice> g_tune;
 static bool g_tune_loaded = false;
 
 static std::string tune_key(const Dims& d, int kind, int smoother, bool fine) {
-  static std::string dev;
-  if (dev.empty()) {
+  static const std::string dev = [] {   // initialised once, thread-safe (grids tune on worker threads)
     cudaDeviceProp p;
     int id = 0;
     cudaGetDevice(&id);
-    dev = (cudaGetDeviceProperties(&p, id) == cudaSuccess) ? p.name : "gpu";
-  }
+    return std::string((cudaGetDeviceProperties(&p, id) == cudaSuccess) ? p.name : "gpu");
+  }();
   char buf[256];
   snprintf(buf, sizeof buf, "%s|%dx%dx%d|k%d|s%d|f%d", dev.c_str(), d.nx, d.ny, d.nz, kind, smoother, fine ? 1 : 0);
   return buf;
@@ -1036,7 +1073,7 @@ static void smooth_post(rf_grid* g, int l, int sh, const void* b, void* x_final,
   } else {
     for (int k = 0; k < o.nu2; ++k) {
       ProfScope ps(g, s, cls, sweep_bytes(g, l, false), ncol);
-      launch_gs_sweep(op, b, x_final, false, false, s);
+      launch_gs_sweep(op, b, x_final, false, false, s, true);
     }
   }
 }
@@ -1460,8 +1497,8 @@ static void vcycle_batch(rf_grid* lead, const std::vector<BatchSys>& bs, int l, 
     }
     for (int it = 0; it < o.nu2; ++it) {
       ProfScope ps(lead, s, cls, batch_bytes(sweep_bytes(g0, l, false), mat, S, shl), ncol);
-      if (sh_l) launch_gs_sweep_shared(op, B, share, false, false, s);
-      else launch_gs_sweep_b(op, B, false, false, s);
+      if (sh_l) launch_gs_sweep_shared(op, B, share, false, false, s, true);
+      else launch_gs_sweep_b(op, B, false, false, s, true);
     }
   }
 }
@@ -1752,6 +1789,7 @@ static rf_status column_grid(rf_grid* g, int j, void* s, rf_grid** out) {
   for (int a = 0; a < 3; ++a) { c->h[a] = g->h[a]; c->g[a] = g->g[a]; }
   c->ncell = g->ncell;
   c->Kcell = g->Kcell; c->phi = g->phi; c->pd = g->pd; c->vol = g->vol;
+  c->law = g->law; c->kr_tab = g->kr_tab; c->laws_on = g->laws_on;
   c->dir = g->dir; c->pw_dir = g->pw_dir; c->q_in = g->q_in; c->pdmin = g->pdmin; c->phiv = g->phiv;
   c->J = g->J; c->mdiag = g->mdiag; c->have_J = g->have_J;
   c->Jdf = g->Jdf; c->jdf_valid = g->jdf_valid;

@@ -93,23 +93,60 @@ __device__ __forceinline__ double2 ld_keep(const double2* p) {
 }
 #endif
 
+// One stored 2x2 block as loaded (FP64: two double2; FP32: a float4; FP16:
+// four halves), and its entries in the arithmetic type (FP16: times the row's
+// per-entry FP32 scales).  Loading and unpacking are split so that a batch of
+// loads can be issued before any of them is unpacked.
+template <int KIND> struct RawBlock;
+template <> struct RawBlock<STORE_F64> { double2 u, w; };
+template <> struct RawBlock<STORE_F32> { float4 u; };
+template <> struct RawBlock<STORE_F16> { uint2 u; };
+
 template <int KIND>
-__device__ __forceinline__ void load_block(const void* A, int64_t nv, int b, int64_t p, const float4& sc,
-                                           typename Ty<KIND>::T (&a)[4]) {
+__device__ __forceinline__ void load_raw(const void* A, int64_t nv, int b, int64_t p, RawBlock<KIND>& r) {
   const int64_t o = (int64_t)b * nv + p;
-  if (KIND == STORE_F64) {
+  if constexpr (KIND == STORE_F64) {
     const double2* q = reinterpret_cast<const double2*>(A) + o * 2;
-    double2 u = ld_stream_d2(q), w = ld_stream_d2(q + 1);
-    a[0] = u.x; a[1] = u.y; a[2] = w.x; a[3] = w.y;
-  } else if (KIND == STORE_F32) {
-    float4 u = ld_stream_f4(reinterpret_cast<const float4*>(A) + o);
-    a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+    r.u = ld_stream_d2(q);
+    r.w = ld_stream_d2(q + 1);
+  } else if constexpr (KIND == STORE_F32) {
+    r.u = ld_stream_f4(reinterpret_cast<const float4*>(A) + o);
   } else {
-    uint2 u = ld_stream_u2(reinterpret_cast<const uint2*>(A) + o);
+    r.u = ld_stream_u2(reinterpret_cast<const uint2*>(A) + o);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void unpack_block(const RawBlock<KIND>& r, const float4& sc, typename Ty<KIND>::T (&a)[4]) {
+  if constexpr (KIND == STORE_F64) {
+    a[0] = r.u.x; a[1] = r.u.y; a[2] = r.w.x; a[3] = r.w.y;
+  } else if constexpr (KIND == STORE_F32) {
+    a[0] = r.u.x; a[1] = r.u.y; a[2] = r.u.z; a[3] = r.u.w;
+  } else {
+    uint2 u = r.u;
     __half2 h01 = *reinterpret_cast<__half2*>(&u.x), h23 = *reinterpret_cast<__half2*>(&u.y);
     float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
     a[0] = f01.x * sc.x; a[1] = f01.y * sc.y; a[2] = f23.x * sc.z; a[3] = f23.y * sc.w;
   }
+}
+
+template <int KIND>
+__device__ __forceinline__ void load_block(const void* A, int64_t nv, int b, int64_t p, const float4& sc,
+                                           typename Ty<KIND>::T (&a)[4]) {
+  RawBlock<KIND> r;
+  load_raw<KIND>(A, nv, b, p, r);
+  unpack_block<KIND>(r, sc, a);
+}
+
+// Row sum += (a_0 x_0 + a_1 x_1) for one block row: one explicit fused
+// multiply-add and an explicit add, so that every kernel applying a block
+// (per-block, batched, shared-matrix) rounds it identically, whatever the
+// compiler would otherwise contract.
+__device__ __forceinline__ float blk_acc(float s, float a0, float a1, float2 x) {
+  return __fadd_rn(s, __fmaf_rn(a0, x.x, __fmul_rn(a1, x.y)));
+}
+__device__ __forceinline__ double blk_acc(double s, double a0, double a1, double2 x) {
+  return __dadd_rn(s, __fma_rn(a0, x.x, __dmul_rn(a1, x.y)));
 }
 
 // sum over the stencil of blocks * x (centre optionally skipped)
@@ -131,18 +168,19 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
     load_block<KIND>(L.A, L.d.nv, b, p, sc, a);
     const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
     const typename V2<T>::t xv = x[p + off];
-    a0 += a[0] * xv.x + a[1] * xv.y;
-    a1 += a[2] * xv.x + a[3] * xv.y;
+    a0 = blk_acc(a0, a[0], a[1], xv);
+    a1 = blk_acc(a1, a[2], a[3], xv);
   }
   s0 = a0; s1 = a1;
 }
 
 // stencil_sum with the loads of CH blocks (and their x values) issued before
 // any is used: one memory round trip per CH blocks instead of one per block.
-// The block loads are the `volatile` streaming loads of load_block, which the
+// The block loads are the `volatile` streaming loads of load_raw, which the
 // compiler keeps in source order, so placing all CH of them ahead of the sums
 // is what batches them (ordinary loads get sunk back next to their uses).
-// Skipped blocks contribute exact zeros, so the sums equal stencil_sum's.
+// The same blocks are summed in the same order with the same blk_acc, so the
+// sums equal stencil_sum's bit for bit.
 // This is what the small levels need, where a thread's chain of round trips,
 // not bandwidth, sets the time.
 template <int KIND, int NB, int CH>
@@ -158,27 +196,29 @@ __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p,
   T a0 = 0, a1 = 0;
 #pragma unroll
   for (int b0 = 0; b0 < NB; b0 += CH) {
-    T a[CH][4];
+    RawBlock<KIND> raw[CH];
+    bool skip[CH];
     V xv[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       const int b = b0 + c;
       if (b >= NB) break;
-      const bool skip = (skip_centre && b == C) || ((skipmask >> b) & 1u);
-      if (!skip) {
-        load_block<KIND>(L.A, L.d.nv, b, p, sc, a[c]);
+      skip[c] = (skip_centre && b == C) || ((skipmask >> b) & 1u);
+      if (!skip[c]) {
+        load_raw<KIND>(L.A, L.d.nv, b, p, raw[c]);
         xv[c] = ld_keep(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]));
-      } else {
-        a[c][0] = a[c][1] = a[c][2] = a[c][3] = 0;
-        xv[c].x = 0;
-        xv[c].y = 0;
       }
     }
+    // unpacked only now: an FP16 block's scaling waits for its load, which
+    // would otherwise hold back the loads issued after it
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
       if (b0 + c >= NB) break;
-      a0 += a[c][0] * xv[c].x + a[c][1] * xv[c].y;
-      a1 += a[c][2] * xv[c].x + a[c][3] * xv[c].y;
+      if (skip[c]) continue;   // as in the per-block sum
+      T a[4];
+      unpack_block<KIND>(raw[c], sc, a);
+      a0 = blk_acc(a0, a[0], a[1], xv[c]);
+      a1 = blk_acc(a1, a[2], a[3], xv[c]);
     }
   }
   s0 = a0; s1 = a1;
@@ -312,9 +352,12 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
 template <int KIND, bool FINE, int NB, int CH>
 __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
                                                    typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py,
-                                                   int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+                                                   int pz, int cnt_x, int lines_y, int64_t count, uint32_t skipmask,
+                                                   int reverse) {
   rf_pdl_begin();
-  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // reverse: blocks take the colour's vertices from the end (see gs_zigzag)
+  const int64_t bx = reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+  int64_t t = bx * blockDim.x + threadIdx.x;
   if (t >= count) return;
   gs_point<KIND, FINE, NB, CH>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
 }
@@ -1175,12 +1218,13 @@ template <int KIND, bool FINE, int NB, int CH>
 __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour_b(const __grid_constant__ LevelOp L,
                                                                     const __grid_constant__ SysBatch B, int px,
                                                                     int py, int pz, int cnt_x, int lines_y,
-                                                                    int64_t count, uint32_t skipmask) {
+                                                                    int64_t count, uint32_t skipmask, int reverse) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
   rf_pdl_begin();
   const SysLevel& P = B.s[blockIdx.y];
   if (sys_done(P)) return;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t bx = reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+  const int64_t t = bx * blockDim.x + threadIdx.x;
   if (t >= count) return;
   gs_point<KIND, FINE, NB, CH>(sys_op(L, P), (const V*)P.in0, (V*)P.out, px, py, pz, cnt_x, lines_y, t, skipmask);
 }
@@ -1253,8 +1297,8 @@ __device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, 
     for (int q = 0; q < NS; ++q) {
       if (!act[q]) continue;
       const V xv = ((const V*)G[q].in1)[p + off];
-      s0[q] += a[0] * xv.x + a[1] * xv.y;
-      s1[q] += a[2] * xv.x + a[3] * xv.y;
+      s0[q] = blk_acc(s0[q], a[0], a[1], xv);
+      s1[q] = blk_acc(s1[q], a[2], a[3], xv);
     }
   }
 }
@@ -1335,11 +1379,13 @@ __global__ void __launch_bounds__(256) k_jacobi_shared(const __grid_constant__ L
 template <int KIND, int NB, int NS>
 __global__ void __launch_bounds__(256) k_gs_colour_shared(const __grid_constant__ LevelOp L,
                                                           const __grid_constant__ SysBatch B, int px, int py, int pz,
-                                                          int cnt_x, int lines_y, int64_t count, uint32_t skipmask) {
+                                                          int cnt_x, int lines_y, int64_t count, uint32_t skipmask,
+                                                          int reverse) {
   typedef typename Ty<KIND>::T T;
   typedef typename V2<T>::t V;
   rf_pdl_begin();
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t bx = reverse ? (int64_t)(gridDim.x - 1 - blockIdx.x) : (int64_t)blockIdx.x;
+  const int64_t t = bx * blockDim.x + threadIdx.x;
   if (t >= count) return;
   const SysLevel* G = B.s + blockIdx.y * NS;   // this group's systems (one shared matrix)
   bool act[NS];
@@ -1414,31 +1460,57 @@ static uint32_t zero_start_mask(int dim, int col) {
   return m;
 }
 
-template <int KIND, bool FINE>
-static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s) {
-  typedef typename V2<typename Ty<KIND>::T>::t V;
-  const int ncol = 1 << L.d.dim;
+// Consecutive colour launches of a sweep walk the grid in alternating
+// directions (blocks in order, then in reverse order): the vertices a launch
+// starts with are the neighbours of those the previous launch ended with, whose
+// x values are then still in L2.  The order within a colour changes nothing in
+// the results.  `flip` starts a sweep reversed (after a launch that ended at
+// the far end); RF_GS_ZIGZAG=0 keeps every launch in order.
+static bool gs_zigzag() {
+  const char* e = getenv("RF_GS_ZIGZAG");
+  return !(e && atoi(e) == 0);
+}
+
+// The colour launches of one sweep: launch(px, py, pz, cnt_x, lines_y, count,
+// skip, reverse) per colour, in sweep order.
+template <typename F>
+static void for_colours(const Dims& d, bool forward, bool zero_start, bool flip, F launch) {
+  const int ncol = 1 << d.dim;
+  const bool zigzag = gs_zigzag();
+  int nl = 0;
   for (int cc = 0; cc < ncol; ++cc) {
     const int col = forward ? cc : ncol - 1 - cc;
-    const uint32_t skip = (zero_start && forward) ? zero_start_mask(L.d.dim, col) : 0u;
+    const uint32_t skip = (zero_start && forward) ? zero_start_mask(d.dim, col) : 0u;
     const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
-    const int cnt_x = px ? L.d.nx / 2 : (L.d.nx + 1) / 2;
-    const int lines_y = (L.d.ny - py + 1) / 2;
-    const int lines_z = L.d.dim == 3 ? (L.d.nz - pz + 1) / 2 : 1;
+    const int cnt_x = px ? d.nx / 2 : (d.nx + 1) / 2;
+    const int lines_y = (d.ny - py + 1) / 2;
+    const int lines_z = d.dim == 3 ? (d.nz - pz + 1) / 2 : 1;
     const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
-    if (count == 0) continue;
-    const int bs = L.block > 0 ? L.block : 256;
+    if (count <= 0) continue;
+    const int rev = zigzag ? ((nl + (flip ? 1 : 0)) & 1) : 0;
+    ++nl;
+    launch(px, py, pz, cnt_x, lines_y, count, skip, rev);
+  }
+}
+
+template <int KIND, bool FINE>
+static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, bool flip, void* s) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  const int bs = L.block > 0 ? L.block : 256;
+  for_colours(L.d, forward, zero_start, flip,
+              [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
     const int g = (int)((count + bs - 1) / bs);
     if (L.batched) {
       if (L.d.nb == 27)
-        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
       else
-        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
-    } else if (L.d.nb == 27)
-      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
-    else
-      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip);
-  }
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
+    } else if (L.d.nb == 27) {
+      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
+    } else {
+      RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
+    }
+  });
 }
 
 void launch_residual(const LevelOp& L, const void* b, const void* x, void* r, void* s) {
@@ -1457,11 +1529,11 @@ void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout,
   }
 }
 
-void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s) {
+void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s, bool flip) {
   switch (L.kind) {
-    case STORE_F64: L.fine ? gs_t<STORE_F64, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F64, false>(L, b, x, forward, zero_start, s); break;
-    case STORE_F32: L.fine ? gs_t<STORE_F32, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F32, false>(L, b, x, forward, zero_start, s); break;
-    default: L.fine ? gs_t<STORE_F16, true>(L, b, x, forward, zero_start, s) : gs_t<STORE_F16, false>(L, b, x, forward, zero_start, s); break;
+    case STORE_F64: L.fine ? gs_t<STORE_F64, true>(L, b, x, forward, zero_start, flip, s) : gs_t<STORE_F64, false>(L, b, x, forward, zero_start, flip, s); break;
+    case STORE_F32: L.fine ? gs_t<STORE_F32, true>(L, b, x, forward, zero_start, flip, s) : gs_t<STORE_F32, false>(L, b, x, forward, zero_start, flip, s); break;
+    default: L.fine ? gs_t<STORE_F16, true>(L, b, x, forward, zero_start, flip, s) : gs_t<STORE_F16, false>(L, b, x, forward, zero_start, flip, s); break;
   }
 }
 
@@ -1547,38 +1619,21 @@ static void jacobi_bt(const LevelOp& L, const SysBatch& B, double omega, bool ze
   }
 }
 
-// the colour loop of gs_t, with `launch(col, px, py, pz, cnt_x, lines_y, count, skip)` per colour
-template <typename F>
-static void for_colours(const Dims& d, bool forward, bool zero_start, F launch) {
-  const int ncol = 1 << d.dim;
-  for (int cc = 0; cc < ncol; ++cc) {
-    const int col = forward ? cc : ncol - 1 - cc;
-    const uint32_t skip = (zero_start && forward) ? zero_start_mask(d.dim, col) : 0u;
-    const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
-    const int cnt_x = px ? d.nx / 2 : (d.nx + 1) / 2;
-    const int lines_y = (d.ny - py + 1) / 2;
-    const int lines_z = d.dim == 3 ? (d.nz - pz + 1) / 2 : 1;
-    const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
-    if (count == 0) continue;
-    launch(px, py, pz, cnt_x, lines_y, count, skip);
-  }
-}
-
 template <int KIND, bool FINE>
-static void gs_bt(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
+static void gs_bt(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, bool flip, void* s) {
   const int bs = L.block > 0 ? L.block : 256;
-  for_colours(L.d, forward, zero_start, [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count,
-                                            uint32_t skip) {
+  for_colours(L.d, forward, zero_start, flip,
+              [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
     const dim3 g((unsigned)((count + bs - 1) / bs), (unsigned)B.n);
     if (L.batched) {
       if (L.d.nb == 27)
-        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
       else
-        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else if (L.d.nb == 27) {
-      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else {
-      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     }
   });
 }
@@ -1602,8 +1657,8 @@ void launch_jacobi_b(const LevelOp& L, const SysBatch& B, double omega, bool zer
 #undef RF_CALL
 }
 
-void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
-#define RF_CALL(K, F) gs_bt<K, F>(L, B, forward, zero_start, s)
+void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s, bool flip) {
+#define RF_CALL(K, F) gs_bt<K, F>(L, B, forward, zero_start, flip, s)
   RF_KIND_FINE_SWITCH(L, RF_CALL)
 #undef RF_CALL
 }
@@ -1646,14 +1701,14 @@ static void jacobi_sh(const LevelOp& L, const SysBatch& B, double omega, bool ze
   else RF_LAUNCH_PDL((k_jacobi_shared<KIND, 9, NS>), g, 256, 0, s, L, B, omega, zero_x ? 1 : 0);
 }
 template <int KIND, int NS>
-static void gs_sh(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s) {
-  for_colours(L.d, forward, zero_start, [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count,
-                                            uint32_t skip) {
+static void gs_sh(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, bool flip, void* s) {
+  for_colours(L.d, forward, zero_start, flip,
+              [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
     const dim3 g((unsigned)((count + 255) / 256), (unsigned)(B.n / NS));
     if (L.d.nb == 27)
-      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 27, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 27, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     else
-      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 9, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip);
+      RF_LAUNCH_PDL((k_gs_colour_shared<KIND, 9, NS>), g, 256, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
   });
 }
 
@@ -1677,8 +1732,9 @@ void launch_jacobi_shared(const LevelOp& L, const SysBatch& B, int share, double
   RF_KIND_NS_SWITCH(L, share, RF_CALL)
 #undef RF_CALL
 }
-void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s) {
-#define RF_CALL(K, N) gs_sh<K, N>(L, B, forward, zero_start, s)
+void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s,
+                            bool flip) {
+#define RF_CALL(K, N) gs_sh<K, N>(L, B, forward, zero_start, flip, s)
   RF_KIND_NS_SWITCH(L, share, RF_CALL)
 #undef RF_CALL
 }

@@ -25,6 +25,8 @@ struct AsmArrays {
   const uint8_t* dir;              // [nv]
   const double* pw_dir;            // [nv]
   const double* q_in;              // [2nv] or null
+  const uint8_t* law;              // per cell: index of its k_r law, or null (Brooks-Corey everywhere)
+  const double* kr_tab;            // [RF_MAX_KR_LAWS][6] law table (with law)
   double* F;                       // [2nv]
   double* J;                       // [nb][nv][4] or null
   double* mdiag;                   // [2nv] or null
@@ -68,8 +70,11 @@ void launch_residual(const LevelOp& L, const void* b, const void* x, void* r, vo
 void launch_jacobi(const LevelOp& L, const void* b, const void* xin, void* xout, double omega, bool zero_x,
                    void* s);
 // zero_start: x holds no data yet (first forward sweep of a V-cycle); blocks that
-// reach colours not yet visited in this sweep are skipped and x need not be cleared
-void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s);
+// reach colours not yet visited in this sweep are skipped and x need not be cleared.
+// flip: the sweep's first colour launch walks the grid from its far end
+// (consecutive colour launches alternate their direction; see levelops.cu)
+void launch_gs_sweep(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, void* s,
+                     bool flip = false);
 void launch_restrict(const LevelOp& F, const LevelOp& C, const void* rf, void* bc, void* s);
 void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf, void* s);
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s);
@@ -191,7 +196,8 @@ struct SysBatch {
 };
 void launch_residual_b(const LevelOp& L, const SysBatch& B, void* s);
 void launch_jacobi_b(const LevelOp& L, const SysBatch& B, double omega, bool zero_x, void* s);
-void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s);
+void launch_gs_sweep_b(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, void* s,
+                       bool flip = false);
 void launch_restrict_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s);
 void launch_prolong_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s);
 void launch_coarse_solve_b(const LevelOp& C, const SysBatch& B, void* s);
@@ -202,7 +208,8 @@ void launch_cast_f32_to_f64_b(int64_t n, const SysBatch& B, void* s);
 // per vertex for all systems of its group (blockIdx.y = group)
 void launch_residual_shared(const LevelOp& L, const SysBatch& B, int share, void* s);
 void launch_jacobi_shared(const LevelOp& L, const SysBatch& B, int share, double omega, bool zero_x, void* s);
-void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s);
+void launch_gs_sweep_shared(const LevelOp& L, const SysBatch& B, int share, bool forward, bool zero_start, void* s,
+                            bool flip = false);
 
 struct SysKrylov {                 // one system of a batched BiCGSTAB iteration
   KrylovVecs K;

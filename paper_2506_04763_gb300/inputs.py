@@ -349,3 +349,63 @@ def case1_buckley_leverett(nx, ny=9):
         L += 1
     prob.update(name="case1-buckley-leverett-%d" % nx, nlevels=L, smoother="gs8")
     return prob
+
+
+# Case 2 (Sec. 6, Table case2): extended Buckley-Leverett through two media,
+# p_c = 0; each medium has its own polynomial relative permeabilities
+# (rows {kind, a_w, n_w, a_n, b_n, c_n}: k_rw = a_w S_e^n_w, k_rn = a_n (1 -
+# b_n S_e)^2 (1 - c_n S_e^2), kind 1 = polynomial).
+CASE2 = dict(L=300.0, W=75.0, x_if=150.0, K1=1e-13, K2=1e-14, phi=0.2, rho=1000.0, mu_w=1e-3, mu_n=5e-3,
+             p_in=2e5, q_out=2e-4, T=1500 * 86400.0,
+             laws=((1.0, 1.831, 4.0, 0.75, 1.25, 1.652), (1.0, 0.4687, 2.0, 0.25, 1.25, 0.0)))
+
+
+def case2_extended_buckley_leverett(nx, ny=9):
+    """Table case2's 300 m x 75 m strip with nx elements along x (nx even, so
+    that the media meet at a vertex line): medium 1 (x < 150 m) with K = 1e-13
+    m^2 and the first pair of laws, medium 2 with K = 1e-14 m^2 and the
+    second; Phi = 0.2, mu_w = 1e-3 and mu_n = 5e-3 Pa s, equal densities, no
+    gravity, S_wr = S_nr = 0, p_d = 0.  The inlet and outlet are set up as in
+    Case 1 (the inlet column water-filled with p_w = 2e5 Pa held, the outlet
+    column taking the NAPL outflow 2e-4 kg m^-2 s^-1 by face share); valid
+    while the water front is inside the strip (about 256 m at 1500 days)."""
+    if nx % 2:
+        raise ValueError("nx must be even")
+    c = CASE2
+    n = (nx + 1, ny, 1)
+    h = (c["L"] / nx, c["W"] / (ny - 1), 1.0)
+    nc = nx * (ny - 1)
+    nv = n[0] * n[1]
+    i = np.arange(nv) % n[0]
+    j = np.arange(nv) // n[0]
+    u = np.empty(2 * nv)
+    u[0::2] = c["p_in"]
+    u[1::2] = np.where(i == 0, 0.0, 1.0)
+    xc = (np.arange(nc) % nx + 0.5) * h[0]
+    law = (xc > c["x_if"]).astype(np.uint8)
+    share = np.where((j == 0) | (j == ny - 1), 0.5, 1.0) * h[1]
+    q = np.zeros(2 * nv)
+    q[1::2] = np.where(i == nx, -c["q_out"] * share, 0.0)
+    prob = dict(dim=2, n=n, h=h, g=(0.0, 0.0, 0.0), K=np.where(law == 0, c["K1"], c["K2"]),
+                phi=np.full(nc, c["phi"]), pd=np.zeros(nc), dir=(i == 0).astype(np.uint8),
+                pw_dir=np.where(i == 0, c["p_in"], 0.0), q_in=q, u0=u, rho_w=c["rho"], rho_n=c["rho"],
+                mu_w=c["mu_w"], mu_n=c["mu_n"], S_wr=0.0, S_nr=0.0, lam=2.0,
+                kr_laws=np.array(c["laws"]), cell_law=law)
+    L, m = 1, list(n[:2])
+    while all((t - 1) % 2 == 0 and t >= 3 for t in m):
+        m = [(t - 1) // 2 + 1 for t in m]
+        L += 1
+    prob.update(name="case2-extended-buckley-leverett-%d" % nx, nlevels=L, smoother="gs8")
+    return prob
+
+
+def mixed_kr_laws(prob, seed):
+    """A copy of `prob` whose cells draw (seeded) one of three relative
+    permeability laws: Brooks-Corey, and the two polynomial laws of Case 2."""
+    rng = np.random.default_rng(seed)
+    out = dict(prob)
+    out["kr_laws"] = np.array(((0.0, 0.0, 0.0, 0.0, 0.0, 0.0),) + CASE2["laws"])
+    out["cell_law"] = rng.integers(0, 3, np.asarray(prob["K"]).size).astype(np.uint8)
+    out["name"] = prob.get("name", "problem") + "-mixed-kr"
+    return out
+

@@ -120,3 +120,78 @@ def lp_error_1d(xv, sv, exact, p, samples=40):
         sh = sv[a] + (sv[a + 1] - sv[a]) * (xm - xv[a]) / h
         tot += (np.abs(sh - exact(xm)) ** p).sum() * h / samples
     return tot ** (1.0 / p)
+
+
+def poly_kr(S, law):
+    """The polynomial relative permeabilities of one medium, law = (kind,
+    a_w, n_w, a_n, b_n, c_n): k_rw = a_w S^n_w and k_rn = a_n (1 - b_n S)^2
+    (1 - c_n S^2) up to the first root of either factor, 0 beyond (S clamped
+    to [0, 1])."""
+    _, aw, nw, an, bn, cn = law
+    S = np.clip(S, 0.0, 1.0)
+    r, q = 1.0 - bn * S, 1.0 - cn * S * S
+    return aw * S ** nw, np.where((r > 0) & (q > 0), an * r * r * q, 0.0)
+
+
+def extended_buckley_leverett_sw(x, t, q, phi, mu_w, mu_n, law1, law2, x_if, ns=400001):
+    """Water saturation of the extended Buckley-Leverett problem (two media
+    meeting at x_if, no gravity, no capillarity, water injected at S_w = 1 and
+    total Darcy velocity q into S_w = 0), by characteristics.  Both fractional
+    flows f_m = lam_w / (lam_w + lam_n) increase with S, so information moves
+    downstream only:
+      medium 1: the textbook solution, Welge front S_f1, x = q t f1'(S) / phi;
+      at x_if the water flux is continuous, f2(S_2) = f1(S_1) (the saturation
+      jumps there), and the front arrives at t_a = x_if phi / (q f1'(S_f1));
+      medium 2: from (x_if, t_a) a centred wave, Welge front S_f2 of f2 and a
+      fan x = x_if + q (t - t_a) f2'(S) / phi up to S_2(t_a); behind it the
+      characteristics of the inflow, leaving x_if at tau with S_2(tau) (the
+      interface value of medium 1 at tau), x = x_if + q (t - tau) f2'(S_2) /
+      phi.  These neither cross nor leave gaps when f2' decreases above S_f2,
+      which is checked."""
+    S = np.linspace(0.0, 1.0, ns)
+
+    def frac(law):
+        kw, kn = poly_kr(S, law)
+        lw, ln = kw / mu_w, kn / mu_n
+        return lw / (lw + ln)
+
+    F1, F2 = frac(law1), frac(law2)
+    d1, d2 = np.gradient(F1, S), np.gradient(F2, S)
+    k1 = int(np.argmax(np.where(S > 0, F1 / np.where(S > 0, S, 1.0), 0.0)))
+    k2 = int(np.argmax(np.where(S > 0, F2 / np.where(S > 0, S, 1.0), 0.0)))
+    assert np.all(np.diff(d2[k2:]) <= 1e-9 * max(1.0, d2.max())), "f2' must decrease above the front"
+    x = np.asarray(x, dtype=float)
+    out = np.zeros_like(x)
+    # medium 1
+    xs1 = q * t * d1[k1:] / phi
+    a = x <= x_if
+    xa = x[a]
+    o = np.zeros_like(xa)
+    beh = xa <= xs1[0]
+    o[beh] = np.interp(xa[beh], xs1[::-1], S[k1:][::-1])
+    out[a] = o
+    ta = x_if * phi / (q * d1[k1])
+    if t <= ta:
+        return out
+    # medium 2: inflow characteristics (S_1 at the interface at time tau)
+    pos = d1[k1:] > 0
+    s1 = S[k1:][pos]
+    tau = x_if * phi / (q * d1[k1:][pos])
+    keep = tau <= t
+    s1, tau = s1[keep], tau[keep]
+    s2 = np.interp(np.interp(s1, S, F1), F2, S)
+    xb = x_if + q * (t - tau) * np.interp(s2, S, d2) / phi
+    s2a = np.interp(F1[k1], F2, S)
+    fan = (S >= S[k2]) & (S <= s2a)
+    xf = x_if + q * (t - ta) * d2[fan] / phi
+    X = np.concatenate((xf, xb))
+    SS = np.concatenate((S[fan], s2))
+    order = np.argsort(X, kind="stable")
+    X, SS = X[order], SS[order]
+    b = ~a
+    xb_ = x[b]
+    o = np.zeros_like(xb_)
+    inside = xb_ <= X[-1]
+    o[inside] = np.interp(xb_[inside], X, SS)
+    out[b] = o
+    return out

@@ -33,6 +33,9 @@ CASES = {
     # the full-size workload's recipe at 33^3: far-field S_n ~ 1e-13 gives k_rn
     # entries far below the FP32 normal range
     "3d-lenses-33": lambda: I.lognormal_lenses_box(33),
+    # each cell with one of Brooks-Corey and the two polynomial k_r laws of Case 2
+    "2d-17x13-stress-laws": lambda: I.mixed_kr_laws(I.random_problem(2, (17, 13), 3, stress=True), 21),
+    "3d-17x9x13-laws": lambda: I.mixed_kr_laws(I.random_problem(3, (17, 9, 13), 9), 22),
 }
 U32 = 2.0 ** -24
 
@@ -515,6 +518,24 @@ def test_invalid_arguments_are_rejected():
     g.gmg_setup([0.1], rf.gmg_opts(2))
     with pytest.raises(rf.RFError):
         g.solve(3, np.zeros(2 * g.nv), np.zeros(2 * g.nv))
+    nc = prob["K"].size
+    good = np.array([I.CASE2["laws"][0]])
+    for laws, cells in ((np.zeros((5, 6)), np.zeros(nc)),                  # more than RF_MAX_KR_LAWS
+                        (good, np.ones(nc)),                                # a cell names a missing law
+                        (np.array([[2.0, 1, 1, 1, 1, 1]]), np.zeros(nc)),   # unknown kind
+                        (np.array([[1.0, 1, 2.5, 1, 1, 1]]), np.zeros(nc)), # n_w not whole
+                        (np.array([[1.0, -1, 2, 1, 1, 1]]), np.zeros(nc))): # a_w < 0
+        with pytest.raises(rf.RFError) as e:
+            g.set_kr_laws(laws, cells)
+        assert e.value.status == rf.RF_EINVAL
+    dev_laws = torch.tensor(good.ravel(), device="cuda")
+    with pytest.raises(rf.RFError) as e:                                    # device pointers
+        rf._check(rf.lib().rf_grid_set_kr_laws(g.handle, 1, dev_laws.data_ptr(), np.zeros(nc, np.uint8).ctypes.data,
+                                               None))
+    assert e.value.status == rf.RF_EINVAL
+    g.set_kr_laws(good, np.zeros(nc))                                       # valid: drops J
+    with pytest.raises(rf.RFError):
+        g.gmg_setup([0.1], rf.gmg_opts(2))
     g.close()
 
 
@@ -758,3 +779,31 @@ def test_limex_run_matches_oracle_run():
     assert np.abs(us[0::2] - u_o[0::2]).max() <= 1e-8 * np.abs(u_o[0::2]).max()
     assert np.abs(us[1::2] - u_o[1::2]).max() <= 1e-9
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+def test_reversed_gs_colour_launches_are_bitwise_equal(precision, monkeypatch):
+    """Multicolour Gauss-Seidel sweeps whose colour launches alternate the
+    block order (the default; RF_GS_ZIGZAG=0 keeps every launch in order)
+    update each vertex from the same neighbour values: a solve and a batched
+    LIMEX step (the batched and shared-J smoother kernels) are bitwise equal."""
+    prob = I.random_problem(3, (17, 13, 25), 52)
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RF_GS_ZIGZAG", mode)
+        monkeypatch.setenv("RF_LIMEX_BATCH", "1")
+        g, F = _assembled(prob)
+        g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(3, "gs8", precision=precision))
+        b = torch.tensor(F, device="cuda")
+        x = torch.empty_like(b)
+        sinfo = g.solve(0, b, x, rtol=1e-11, max_it=300)
+        u = torch.tensor(prob["u0"], device="cuda")
+        linfo = g.limex_step(u, 5.0, kappa=3, tol=1e9, gmg=rf.gmg_opts(3, "gs8", precision=precision),
+                             rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert sinfo["status"] == 0 and linfo["status"] == 0, (mode, sinfo, linfo)
+        out[mode] = (x.cpu().numpy(), sinfo, u.cpu().numpy(), linfo["iterations"], linfo["eps"])
+        g.close()
+    a, b_ = out["0"], out["1"]
+    assert np.array_equal(a[0], b_[0]) and a[1] == b_[1]
+    assert np.array_equal(a[2], b_[2]) and a[3:] == b_[3:]

@@ -169,14 +169,17 @@ def test_p1_laplacian_stencil_closed_form(oracle, dim, nv, expect):
 
 
 # ---------------------------------------------------------------- P3 exact J
-@pytest.mark.parametrize("scheme", [0, 2])
+@pytest.mark.parametrize("scheme,laws", [(0, False), (2, False), (0, True)])
 @pytest.mark.parametrize("dim,nv,seed", [(2, (7, 6), 11), (3, (5, 4, 5), 12)])
-def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed, scheme):
+def test_p3_jacobian_equals_finite_differences(oracle, dim, nv, seed, scheme, laws):
     """J = F_u exactly (Sec. 4): central differences of the oracle's own F,
     entry by entry; columns where one-sided differences disagree (a kink or an
     upwind switch inside the step) are skipped.  scheme 2: Darcy-velocity
-    upwinding of the water flux."""
+    upwinding of the water flux; laws: each cell with one of Brooks-Corey and
+    the two polynomial laws of Case 2."""
     p = I.random_problem(dim, nv, seed)
+    if laws:
+        p = I.mixed_kr_laws(p, seed)
     p["scheme"] = scheme
     m = oracle.Model(p)
     u = p["u0"].copy()
@@ -879,3 +882,110 @@ def test_fp32_vcycle_emulation_converges_on_poisson(oracle):
         x = x + g32.vcycle(r)
     rates = [rs[k + 1] / rs[k] for k in range(1, 4)]
     assert max(rates) <= 0.15, rates
+
+
+# ---------------------------------------------------------------- Case 2 (extended Buckley-Leverett)
+def _case2_table():
+    rows, jump = {}, None
+    with open(os.path.join(GOLDEN, "case2_error2.txt")) as f:
+        for line in f:
+            t = line.split()
+            if t and t[0] in ("ie", "limex"):
+                rows[(t[0], int(t[1]))] = (int(t[2]), float(t[3]), float(t[4]))
+            elif t and t[0] == "interface_jump":
+                jump = (float(t[1]), float(t[2]))
+    return rows, jump
+
+
+def _case2_exact(x):
+    c = I.CASE2
+    return H.extended_buckley_leverett_sw(x, c["T"], c["q_out"] / c["rho"], c["phi"], c["mu_w"], c["mu_n"],
+                                          c["laws"][0], c["laws"][1], c["x_if"])
+
+
+def test_extended_buckley_leverett_solution():
+    """The reference solution used for Case 2: with the two media's laws as
+    printed (k_rn taken as 0 past its first root) the saturation jumps at the
+    interface from 0.52 to 0.48, the values the paper gives; with the same law
+    on both sides it is the textbook one-medium solution."""
+    c = I.CASE2
+    _, jump = _case2_table()
+    s = _case2_exact(np.array([c["x_if"] - 1e-9, c["x_if"] + 1e-9]))
+    assert s[0] == pytest.approx(jump[0], abs=5e-3) and s[1] == pytest.approx(jump[1], abs=5e-3)
+    bc = (1.0, 1.0, 4.0, 1.0, 1.0, 1.0)            # Brooks-Corey lambda = 2 written as a polynomial law
+    x = np.linspace(0.0, 300.0, 6001)
+    q, t = 3e-7, 1500 * 86400.0
+    one = H.extended_buckley_leverett_sw(x, t, q, 0.2, 1e-3, 1e-3, bc, bc, 150.0)
+    ref = H.buckley_leverett_sw(x, t, q, 0.2, 1e-3, 1e-3)[0]
+    assert np.abs(one - ref).sum() * (x[1] - x[0]) <= 0.05
+
+
+def test_case2_laws_reach_every_use_of_k_r(oracle):
+    """Per-cell laws in the assembly: a law table of Brooks-Corey rows gives
+    bitwise the assembly without one; polynomial rows equal to the
+    Brooks-Corey lambda = 2 laws (k_rw = S^4, k_rn = (1 - S)^2 (1 - S^2)) give
+    it up to rounding; and a cell's law changes F only in the rows of its own
+    corners (the upwinded k_rw, k_rw at the face and k_rn of S hat all come
+    from the face's cell)."""
+    p = I.random_problem(2, (9, 7), 11)
+    m0 = oracle.Model(p)
+    F0, J0, _ = oracle.assemble(m0, p["u0"])
+    nc = p["K"].size
+    for row, exact in (((0.0,) * 6, True), ((1.0, 1.0, 4.0, 1.0, 1.0, 1.0), False)):
+        q = dict(p, kr_laws=np.array([row]), cell_law=np.zeros(nc, np.uint8))
+        F1, J1, _ = oracle.assemble(oracle.Model(q), p["u0"])
+        if exact:
+            assert np.array_equal(F0, F1) and np.array_equal(J0, J1)
+        else:
+            assert np.abs(F1 - F0).max() <= 1e-13 * np.abs(F0).max()
+            assert np.abs(J1 - J0).max() <= 1e-13 * np.abs(J0).max()
+    law = np.zeros(nc, np.uint8)
+    cell = 3 + 8 * 2                                  # cell (3, 2) of the 8 x 6 cells
+    law[cell] = 1
+    q = dict(p, kr_laws=np.array([(0.0,) * 6, I.CASE2["laws"][0]]), cell_law=law)
+    F2 = oracle.assemble(oracle.Model(q), p["u0"], jacobian=False)[0]
+    changed = np.nonzero(np.abs(F2 - F0).reshape(-1, 2).max(axis=1))[0]
+    corners = {(3 + a) + 9 * (2 + b) for a in (0, 1) for b in (0, 1)}
+    assert len(changed) > 0 and set(changed.tolist()) <= corners
+
+
+def test_case2_polynomial_law_derivatives(oracle):
+    """dk_r/dS_e of the polynomial laws by central differences away from the
+    roots, k_rn = 0 from its first root on (law 1: 1.652 S^2 = 1, S = 0.7780;
+    law 2: 1.25 S = 1, S = 0.8), and both laws clamped outside [0, 1]."""
+    p = I.case2_extended_buckley_leverett(8)
+    m = oracle.Model(p)
+    for cell, root in ((0, 1.0 / np.sqrt(1.652)), (7, 0.8)):
+        for S in (0.1, 0.3, 0.55, 0.7, 0.95):
+            v = oracle.kr_law(m, cell, S)
+            d = 1e-6
+            fd = (oracle.kr_law(m, cell, S + d) - oracle.kr_law(m, cell, S - d)) / (2 * d)
+            assert v[1] == pytest.approx(fd[0], rel=1e-6, abs=1e-12)
+            if abs(S - root) > 1e-3:
+                assert v[3] == pytest.approx(fd[2], rel=1e-6, abs=1e-12)
+            assert (v[2] == 0.0) == (S >= root)
+        lo, hi = oracle.kr_law(m, cell, -0.2), oracle.kr_law(m, cell, 1.3)
+        assert np.array_equal(lo, oracle.kr_law(m, cell, 0.0) * [1, 0, 1, 0])
+        assert np.array_equal(hi, oracle.kr_law(m, cell, 1.0) * [1, 0, 1, 0])
+
+
+def test_case2_implicit_euler_errors_match_the_paper(oracle):
+    """The discretisation with per-medium laws against printed numbers:
+    implicit Euler on Case 2 with 64 elements and the paper's 65 steps gives
+    the L1 and L2 errors of Table error2 within 3%."""
+    c = I.CASE2
+    rows, _ = _case2_table()
+    nx = 64
+    steps, L1, L2 = rows[("ie", nx)]
+    p = I.case2_extended_buckley_leverett(nx)
+    m = oracle.Model(p)
+    u = p["u0"].copy()
+    for _ in range(steps):
+        u, inf = oracle.ie_step(m, u, c["T"] / steps, nlevels=p["nlevels"], atol=1e-9, rtol=1e-6, lin_rtol=1e-8,
+                                max_newton=30)
+        assert inf["status"] == 0, inf
+    sw = 1.0 - u[1::2].reshape(p["n"][1], p["n"][0])
+    assert np.abs(sw - sw[0]).max() <= 1e-9          # one-dimensional flow
+    xv = np.arange(nx + 1) * c["L"] / nx
+    assert H.lp_error_1d(xv, sw[0], _case2_exact, 1) == pytest.approx(L1, rel=0.03)
+    assert H.lp_error_1d(xv, sw[0], _case2_exact, 2) == pytest.approx(L2, rel=0.03)
