@@ -338,6 +338,19 @@ rf_status rf_fp64_fma_rate(void* stream, double* fma_per_s);
 
 /* Kernels launched by this library in this process so far. */
 int64_t rf_launch_count(void);
+
+/* Check of the bounded grid barrier that the cooperative V-cycle tail
+ * (environment RF_TAIL_NV) separates its phases with: one cooperative launch
+ * of every block that fits on the GPU at once passes `rounds` barriers.  With
+ * extra = 1 each barrier expects one block more than there are, so no barrier
+ * completes: every wait gives up after limit_s seconds and the call returns
+ * RF_ETIMEOUT with the context still usable.  blocks_out (host, may be NULL)
+ * receives the launch's block count.  RF_EINVAL unless 1 <= rounds <= 10^6,
+ * extra is 0 or 1 and 0 < limit_s <= 10; RF_ECUDA if the launch fails.
+ * Synchronous on `stream`.  The barrier: the last block to arrive resets the
+ * arrival count and publishes the next generation; the others poll the
+ * generation (with the global timer bounding the wait). */
+rf_status rf_barrier_check(int rounds, int extra, double limit_s, int* blocks_out, void* stream);
 const char* rf_status_string(rf_status s);
 const char* rf_last_error(void);
 

@@ -123,6 +123,7 @@ SIGNATURES = {
     "rf_assemble": (_I, [_P, _P, _I, _P, _P]),
     "rf_grid_set_scheme": (_I, [_P, _I]),
     "rf_grid_set_kr_laws": (_I, [_P, _I, _P, _P, _P]),
+    "rf_barrier_check": (_I, [_I, _I, _D, _P, _P]),
     "rf_gmg_setup": (_I, [_P, _P, _I, _P, _P]),
     "rf_solve": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "rf_limex_step": (_I, [_P, _P, _D, _P, _P, _P]),
@@ -279,6 +280,14 @@ def rf_profile_read(grid, cls):
     by = ctypes.c_double()
     _check(lib().rf_profile_read(grid, int(cls), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by)))
     return ms.value, n.value, by.value
+
+
+def rf_barrier_check(rounds, extra=0, limit_s=1.0, stream=None):
+    """Status of rf_barrier_check (not raised: RF_ETIMEOUT is the expected
+    answer for extra=1) and the launch's block count."""
+    nb = ctypes.c_int()
+    st = lib().rf_barrier_check(int(rounds), int(extra), float(limit_s), ctypes.byref(nb), _stream_handle(stream))
+    return int(st), nb.value
 
 
 def rf_fp64_fma_rate(stream=None):

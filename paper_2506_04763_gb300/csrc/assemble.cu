@@ -175,32 +175,32 @@ __global__ void k_vertex_setup(Dims d, const double* __restrict__ pd, const doub
 __global__ void k_perm_to_p(Dims d, const double2* __restrict__ nat, double2* __restrict__ out) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
-  int i = (int)(v % d.nx);
-  int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat[v];
 }
 
 __global__ void k_perm_from_p(Dims d, const double2* __restrict__ pl, double2* __restrict__ nat) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
-  int i = (int)(v % d.nx);
-  int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   nat[v] = pl[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))];
 }
 
 __global__ void k_perm_bytes_to_p(Dims d, const uint8_t* __restrict__ nat, uint8_t* __restrict__ out) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
-  int i = (int)(v % d.nx);
-  int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat ? nat[v] : 0;
 }
 
 __global__ void k_perm_scalar_to_p(Dims d, const double* __restrict__ nat, double* __restrict__ out) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
-  int i = (int)(v % d.nx);
-  int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   out[line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1))] = nat ? nat[v] : 0.0;
 }
 
@@ -458,10 +458,10 @@ __global__ void __launch_bounds__(128) k_assemble_cells(Dims d, Phys ph, AsmIn i
   const int cx = d.nx - 1, cy = d.ny - 1;
   const int px = colour & 1, py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
   const int nxp = (cx - px + 1) / 2, nyp = (cy - py + 1) / 2;
-  const int64_t line = t / nxp;
-  const int ci = 2 * (int)(t - line * nxp) + px;
-  const int cj = 2 * (int)(line % nyp) + py;
-  const int ck = DIM == 3 ? 2 * (int)(line / nyp) + pz : 0;
+  const uint32_t line = (uint32_t)t / (uint32_t)nxp, kl = line / (uint32_t)nyp;   // 32-bit: fewer than 2^31 cells
+  const int ci = 2 * (int)((uint32_t)t - line * (uint32_t)nxp) + px;
+  const int cj = 2 * (int)(line - kl * (uint32_t)nyp) + py;
+  const int ck = DIM == 3 ? 2 * (int)kl + pz : 0;
   const int64_t cell = ci + (int64_t)cx * (cj + (int64_t)cy * ck);
   const double Kc = in.K[cell], pdc = in.pd[cell];
   const double* law = in.law ? law_row(in.kr_tab, in.law[cell]) : nullptr;

@@ -109,11 +109,11 @@ struct Level {
 //   FP64 storage: equal on the two finest levels, batched 1.2-1.6x faster on
 //     the levels below.  (On the finest level of the 65^3 FP64 LIMEX step,
 //     batched Jacobi measured no faster either.)
-//   FP16 storage: batched loads are 1.8-2x slower on the two finest levels
-//     and equal below, so never.
+//   FP16 storage (the finest level only): loads batched two blocks at a
+//     time, 2.11 -> 2.01 ms per sweep + residual.
 static void default_shape(Level& Lv, int l, int kind) {
   Lv.block = 128;
-  Lv.batched = kind == STORE_F32 || (kind == STORE_F64 && l >= 2);
+  Lv.batched = kind == STORE_F32 || kind == STORE_F16 || (kind == STORE_F64 && l >= 2);
 }
 
 struct Alloc {
@@ -155,8 +155,10 @@ struct rf_grid {
   int nl = 0;
   Level L[RF_MAXL];
   double* Ainv[RF_MAXSHIFT] = {};
-  int tail_first = -1;      // first level run by the one-cluster V-cycle tail (-1: none)
-  int tail_cs = 0;          // its cluster size
+  int tail_first = -1;      // first level run by the one-launch V-cycle tail (-1: none)
+  int tail_cs = 0;          // its cluster size (cluster form)
+  int tail_blocks = 0;      // its blocks (cooperative form; 0: cluster form)
+  unsigned* tail_bar = nullptr;   // the cooperative tail's barrier words
   TailParams tail[RF_MAXSHIFT];
   // Krylov
   KrylovVecs K{};
@@ -400,6 +402,36 @@ static rf_status pairs_out(rf_grid* g, const Dims& d, const double* src_p, doubl
 
 // ------------------------------------------------------------------ ABI: grid
 extern "C" int64_t rf_launch_count(void) { return g_launches.load(); }
+
+extern "C" rf_status rf_barrier_check(int rounds, int extra, double limit_s, int* blocks_out, void* stream) {
+  if (rounds < 1 || rounds > 1000000 || extra < 0 || extra > 1 || !(limit_s > 0.0) || !(limit_s <= 10.0))
+    return fail(RF_EINVAL, "need 1 <= rounds <= 1e6, extra 0 or 1, 0 < limit_s <= 10");
+  // words: bar[2] and passed (unsigned), then the status flag (double, 8-aligned)
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, 32) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RF_ENOMEM, "barrier check: allocation failed");
+  }
+  unsigned* bar = (unsigned*)mem;
+  unsigned* passed = bar + 2;
+  double* status = (double*)((char*)mem + 16);
+  cudaStream_t s = (cudaStream_t)stream;
+  int blocks = 0;
+  cudaError_t e = cudaMemsetAsync(mem, 0, 32, s);
+  if (e == cudaSuccess) e = launch_barrier_check(bar, rounds, extra, status, (long long)(limit_s * 1e9), passed, &blocks, s);
+  unsigned h_passed = 0;
+  double h_status = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_passed, passed, sizeof h_passed, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_status, status, sizeof h_status, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(mem);
+  if (blocks_out) *blocks_out = blocks;
+  if (e != cudaSuccess) return fail(RF_ECUDA, "barrier check: %s", cudaGetErrorString(e));
+  if (h_status != 0.0) return fail(RF_ETIMEOUT, "barrier check: a wait gave up (%u passes)", h_passed);
+  if (h_passed != (unsigned)blocks * (unsigned)rounds)
+    return fail(RF_ECUDA, "barrier check: %u passes, expected %d", h_passed, blocks * rounds);
+  return RF_OK;
+}
 extern "C" const char* rf_last_error(void) { return t_err.c_str(); }
 extern "C" int64_t rf_grid_nv(const rf_grid* g) { return g ? g->d.nv : 0; }
 
@@ -555,6 +587,7 @@ extern "C" rf_status rf_grid_create(const rf_grid_desc* desc, const rf_fluids* f
   NEED(g->du = (double*)dalloc(g, sizeof(double) * 2 * nv, stream, false));
   NEED(g->K.partial = (double*)dalloc(g, sizeof(double) * 16 * 2048, stream, false));
   NEED(g->K.scal = (double*)dalloc(g, sizeof(double) * 32, stream, false));
+  CU(cudaMemsetAsync(g->K.scal, 0, sizeof(double) * 32, (cudaStream_t)stream));   // flags start clear
   NEED(g->norms = (double*)dalloc(g, sizeof(double) * 8, stream, false));
   if (cudaMallocHost((void**)&g->hscal, sizeof(double) * 32) != cudaSuccess) {
     cudaGetLastError();
@@ -961,22 +994,36 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     rf_status ts = autotune_levels(g, s);
     if (ts) { dfree_all(g, g->gbufs, s); return ts; }
   }
-  // Optionally the small levels (<= RF_TAIL_NV vertices) run as one cluster
-  // kernel.  Off by default: measured on GB300 it saves < 1% of a 257^3 solve
-  // (each of its ~100 barrier-separated phases is latency-bound) and costs ~40%
-  // of an FP64 LIMEX step at 65^3, where the tail's first level is too large
-  // for 16 SMs.
+  // Optionally the small levels (<= RF_TAIL_NV vertices) run as one launch:
+  // one thread-block cluster (RF_TAIL_MODE=cluster), or a cooperative launch
+  // of every co-resident block with bounded grid barriers (otherwise).  The
+  // cluster form, measured on GB300, saves < 1% of a 257^3 solve (each of its
+  // ~100 barrier-separated phases is latency-bound) and costs ~40% of an FP64
+  // LIMEX step at 65^3, where the tail's first level is too large for 16 SMs.
   g->tail_first = -1;
+  g->tail_blocks = 0;
+  g->tail_bar = nullptr;   // (a hierarchy buffer: freed with the previous set-up)
   {
     const char* env = getenv("RF_TAIL_NV");
+    const char* mode = getenv("RF_TAIL_MODE");
+    const bool cluster = mode && strcmp(mode, "cluster") == 0;
     const long long thr = env ? atoll(env) : 0;
     if (thr > 0)
       for (int l = 1; l < g->nl - 1; ++l)
         if (g->L[l].d.nv <= thr) { g->tail_first = l; break; }
-    if (g->tail_first > 0) {
+    if (g->tail_first > 0 && cluster) {
       g->tail_cs = tail_cluster_size(g->L[g->tail_first].kind, g->d.nb);
       cudaGetLastError();
       if (g->tail_cs == 0) g->tail_first = -1;
+    } else if (g->tail_first > 0) {
+      g->tail_blocks = coop_tail_blocks(g->L[g->tail_first].kind, g->d.nb);
+      g->tail_bar = g->tail_blocks > 0 ? (unsigned*)dalloc(g, 2 * sizeof(unsigned), s, true) : nullptr;
+      if (!g->tail_bar) {
+        g->tail_first = -1;
+        g->tail_blocks = 0;
+      } else {
+        CU(cudaMemsetAsync(g->tail_bar, 0, 2 * sizeof(unsigned), (cudaStream_t)s));
+      }
     }
     if (g->tail_first > 0)
       for (int j = 0; j < nshift; ++j) {
@@ -991,6 +1038,9 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
         fill_tail_masks(P, g->d.dim);
         P.Ainv = g->Ainv[j];
         P.N = (int)(2 * g->L[g->nl - 1].d.nv);
+        P.bar = g->tail_bar;
+        P.status = g->K.scal + RF_SCAL_TAIL;
+        P.limit_ns = 2000000000LL;   // 2 s: a phase takes microseconds
         for (int l = g->tail_first; l < g->nl; ++l) {
           P.L[l].op = level_op(g, l, j);
           P.L[l].x = g->L[l].x;
@@ -1091,7 +1141,8 @@ static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void
       by += nvq * (g->L[q].d.nb * blk_bytes(kq) + row_extra(kq) + 6 * T) + nvq * (6 * T + 2) + nvc * (4 * T + 2);
     }
     ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, by, 1);
-    launch_vcycle_tail(g->tail[sh], k, g->d.nb, g->tail_cs, s);
+    if (g->tail_blocks > 0) launch_vcycle_coop(g->tail[sh], k, g->d.nb, g->tail_blocks, s);
+    else launch_vcycle_tail(g->tail[sh], k, g->d.nb, g->tail_cs, s);
     return;
   }
   if (l == g->nl - 1) {
@@ -1127,7 +1178,8 @@ static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void
 enum { H_RHO = 0, H_RR = 5, H_BB = 6, H_CONV = 10, H_BAD = 11, H_TRUE = 12, H_BREAK = 13 };
 
 static rf_status read_scal(rf_grid* g, void* s) {
-  CU(cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, (cudaStream_t)s));
+  CU(cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * (RF_SCAL_TAIL + 1), cudaMemcpyDeviceToHost,
+                     (cudaStream_t)s));
   CU(cudaStreamSynchronize((cudaStream_t)s));
   return RF_OK;
 }
@@ -1191,7 +1243,7 @@ static rf_status run_iteration(rf_grid* g, int sh, cudaStream_t cs) {
   if (!G.exec || G.stale) {
     rf_status st = capture_graph(g, G, cs, "iteration", [&] {
       iteration_body(g, sh, cs);
-      cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * 16, cudaMemcpyDeviceToHost, cs);
+      cudaMemcpyAsync(g->hscal, g->K.scal, sizeof(double) * (RF_SCAL_TAIL + 1), cudaMemcpyDeviceToHost, cs);
     });
     if (st) return st;
   }
@@ -1258,6 +1310,14 @@ static rf_status solve_cs(rf_grid* g, int sh, const double2* b, double rtol, int
     const double bn = std::sqrt(bb);
     for (it = 1; it <= max_it; ++it) {
       if ((st = run_iteration(g, sh, s))) return st;
+      if (g->hscal[RF_SCAL_TAIL] != 0.0) {
+        // a barrier of the cooperative V-cycle tail gave up: its words are
+        // left mid-count, so reset them (and the flag) before any reuse
+        CU(cudaMemsetAsync(g->tail_bar, 0, 2 * sizeof(unsigned), s));
+        CU(cudaMemsetAsync(g->K.scal + RF_SCAL_TAIL, 0, sizeof(double), s));
+        CU(cudaStreamSynchronize(s));
+        return fail(RF_ETIMEOUT, "a grid barrier of the V-cycle tail timed out");
+      }
       if (g->hscal[H_BAD] != 0.0) { result = RF_ENONFINITE; break; }
       if (g->hscal[H_CONV] != 0.0 || g->hscal[H_BREAK] != 0.0) {
         {
@@ -1764,6 +1824,7 @@ static rf_status column_grid(rf_grid* g, int j, void* s, rf_grid** out) {
     for (auto p : kv) ok = ok && (*p = (double2*)dalloc(c, sizeof(double2) * nv, s, false));
     ok = ok && (c->K.partial = (double*)dalloc(c, sizeof(double) * 16 * 2048, s, false));
     ok = ok && (c->K.scal = (double*)dalloc(c, sizeof(double) * 32, s, false));
+    ok = ok && cudaMemsetAsync(c->K.scal, 0, sizeof(double) * 32, (cudaStream_t)s) == cudaSuccess;
     ok = ok && (c->norms = (double*)dalloc(c, sizeof(double) * 8, s, false));
     if (ok && cudaMallocHost((void**)&c->hscal, sizeof(double) * 32) != cudaSuccess) {
       cudaGetLastError();

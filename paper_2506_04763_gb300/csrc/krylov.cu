@@ -71,7 +71,7 @@ template <typename XV, int NB>
 __device__ __forceinline__ void spmv64_row(const Dims& d, const Nbr& nb, const double* __restrict__ J,
                                            const double2* __restrict__ md, double shift,
                                            const XV* __restrict__ x, int64_t p, double& y0, double& y1) {
-  const int par = (int)(p % d.nx) >= d.E;
+  const int par = (int)((uint32_t)p % (uint32_t)d.nx) >= d.E;   // nv < 2^31
   double s0 = 0.0, s1 = 0.0;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -111,7 +111,7 @@ template <int NB>
 __device__ __forceinline__ void spmvdf_row(const Dims& d, const Nbr& nb, const float4* __restrict__ Jdf,
                                            const double2* __restrict__ md, double shift,
                                            const float2* __restrict__ x, int64_t p, double& y0, double& y1) {
-  const int par = (int)(p % d.nx) >= d.E;
+  const int par = (int)((uint32_t)p % (uint32_t)d.nx) >= d.E;   // nv < 2^31
   float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(BS) k_bicg_op_shared(Dims d, Nbr nb, const __g
 #pragma unroll
   for (int q = 0; q < NS; ++q) { acc[q][0] = 0.0; acc[q][1] = 0.0; }
   for (int64_t p = blockIdx.x * (int64_t)BS + threadIdx.x; p < d.nv; p += (int64_t)gridDim.x * BS) {
-    const int par = (int)(p % d.nx) >= d.E;
+    const int par = (int)((uint32_t)p % (uint32_t)d.nx) >= d.E;   // nv < 2^31
     double s0[NS], s1[NS];
 #pragma unroll
     for (int q = 0; q < NS; ++q) { s0[q] = 0.0; s1[q] = 0.0; }

@@ -183,6 +183,12 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
 // sums equal stencil_sum's bit for bit.
 // This is what the small levels need, where a thread's chain of round trips,
 // not bandwidth, sets the time.
+// Stencil blocks whose loads a batched kernel issues per memory round trip.
+// FP16 blocks (8 B per thread and block) run best two at a time: on the
+// finest 257^3 level one sweep plus one residual took 2.01 ms with 2, 2.37 ms
+// with 4, 2.66 ms with 9, and 2.11 ms with one block per round trip.
+__host__ __device__ constexpr int chunk_of(int kind) { return kind == STORE_F16 ? 2 : 9; }
+
 template <int KIND, int NB, int CH>
 __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p, int par,
                                                     const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
@@ -265,7 +271,7 @@ __device__ __forceinline__ void residual_point(const LevelOp& L, const typename 
                                                const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                typename V2<typename Ty<KIND>::T>::t* __restrict__ r, int64_t p) {
   typedef typename Ty<KIND>::T T;
-  const int par = (int)(p % L.d.nx) >= L.d.E;
+  const int par = (int)((uint32_t)p % (uint32_t)L.d.nx) >= L.d.E;   // nv < 2^31
   const typename V2<T>::t bv = b[p];
   T s0, s1;
   apply_row<KIND, FINE, NB, CH>(L, p, par, x, s0, s1);
@@ -295,7 +301,7 @@ __device__ __forceinline__ void jacobi_point(const LevelOp& L, const typename V2
   const typename V2<T>::t bv = b[p];
   T r0 = bv.x, r1 = bv.y, x0 = 0, x1 = 0;
   if (!zero_x) {
-    const int par = (int)(p % L.d.nx) >= L.d.E;
+    const int par = (int)((uint32_t)p % (uint32_t)L.d.nx) >= L.d.E;   // nv < 2^31
     T s0, s1;
     apply_row<KIND, FINE, NB, CH>(L, p, par, xin, s0, s1);
     r0 -= s0;
@@ -330,9 +336,10 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
                                          typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int py, int pz,
                                          int cnt_x, int lines_y, int64_t t, uint32_t skipmask) {
   typedef typename Ty<KIND>::T T;
-  const int64_t line = t / cnt_x;
-  const int pos = (int)(t - line * cnt_x);
-  const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
+  // 32-bit index arithmetic: a colour has fewer than 2^31 vertices
+  const uint32_t tt = (uint32_t)t, line = tt / (uint32_t)cnt_x, kl = line / (uint32_t)lines_y;
+  const int pos = (int)(tt - line * (uint32_t)cnt_x);
+  const int jj = (int)(line - kl * (uint32_t)lines_y), kk = (int)kl;
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
   const typename V2<T>::t bv = b[p];
@@ -639,17 +646,67 @@ __global__ void __launch_bounds__(256) k_coarse_solve(int N, const double* __res
 
 // ----------------------------------------------------------------- V-cycle tail
 // Levels below a few 10^4 vertices cannot fill the GPU: launched one kernel per
-// GS colour, each costs a launch gap.  Here ONE thread-block cluster runs the
-// whole V-cycle from level `first` down to the coarsest and back up, phases
-// separated by hardware cluster barriers (every thread of the cluster reaches
-// every barrier: all loop bounds below are uniform across the cluster).
-template <int KIND, int NB>
-__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailParams P) {
+// GS colour, each costs a launch gap.  Here one launch runs the whole V-cycle
+// from level `first` down to the coarsest and back up, its phases separated by
+// barriers (every thread reaches every barrier: all loop bounds below are
+// uniform across the launch).  Two forms:
+//   k_vcycle_tail: ONE thread-block cluster, hardware cluster barriers;
+//   k_vcycle_coop: a cooperative launch of every co-resident block, grid
+//     barriers in global memory whose waits give up after P.limit_ns (the
+//     block then sets *P.status = 1 and leaves; the others see the flag in
+//     their own waits and leave too, so the kernel always ends).
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier of a cooperative launch: bar[0] counts this generation's
+// arrivals, bar[1] is the generation.  `gen` (held by thread 0) is the
+// generation this block last passed.  The last block to arrive resets the
+// count and then publishes gen + 1; the others wait for it, at most limit_ns.
+// Returns false when the wait gave up or another block already had.
+__device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned expected, unsigned& gen,
+                                                  double* status, long long limit_ns) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned want = gen + 1;
+    __threadfence();   // this block's phase results before its arrival
+    if (atomicAdd(&bar[0], 1u) == expected - 1) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicExch(&bar[1], want);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*(volatile unsigned*)&bar[1] != want) {
+        if (*(volatile double*)status != 0.0 || (long long)(global_ns() - t0) > limit_ns) {
+          *(volatile double*)status = 1.0;
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();   // the other blocks' results are read after the barrier
+    gen = want;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The V-cycle below level P.first; sync() separates phases and returns false
+// when the launch must end (coop: a barrier gave up).
+template <int KIND, int NB, typename Sync>
+__device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt, int64_t nthr, Sync&& sync) {
   typedef typename Ty<KIND>::T T;
   typedef typename V2<T>::t V;
-  cg::cluster_group cl = cg::this_cluster();
-  const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
-  const int64_t gt = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+  // batched stencil loads (a thread's round trips set a phase's time); FP64
+  // blocks three at a time, which keeps the whole V-cycle within the registers
+  constexpr int CH = KIND == STORE_F64 ? 3 : chunk_of(KIND);
   const int ncol = 1 << P.L[P.first].op.d.dim;
   V* curs[RF_MAXL];
   auto gs_sweep = [&](const LevelOp& op, const V* b, V* x, bool forward, bool zero_start) {
@@ -661,13 +718,14 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
       const int lines_z = op.d.dim == 3 ? (op.d.nz - pz + 1) / 2 : 1;
       const int64_t count = (int64_t)cnt_x * lines_y * lines_z;
       const uint32_t skip = (zero_start && forward) ? P.zmask[col] : 0u;
-      for (int64_t t = gt; t < count; t += nthr) gs_point<KIND, false, NB>(op, b, x, px, py, pz, cnt_x, lines_y, t, skip);
-      cl.sync();
+      for (int64_t t = gt; t < count; t += nthr) gs_point<KIND, false, NB, CH>(op, b, x, px, py, pz, cnt_x, lines_y, t, skip);
+      if (!sync()) return false;
     }
+    return true;
   };
   auto jacobi_sweep = [&](const LevelOp& op, const V* b, const V* xin, V* xout, bool zero_x) {
-    for (int64_t p = gt; p < op.d.nv; p += nthr) jacobi_point<KIND, false, NB>(op, b, xin, xout, P.omega, zero_x, p);
-    cl.sync();
+    for (int64_t p = gt; p < op.d.nv; p += nthr) jacobi_point<KIND, false, NB, CH>(op, b, xin, xout, P.omega, zero_x, p);
+    return sync();
   };
   for (int l = P.first; l < P.coarsest; ++l) {
     const TailLevel& Lv = P.L[l];
@@ -677,23 +735,24 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
     V* tmp = (V*)Lv.t;
     V* cur = x;
     if (P.smoother == 1) {
-      for (int sw = 0; sw < P.nu1; ++sw) gs_sweep(Lv.op, b, x, true, sw == 0);
+      for (int sw = 0; sw < P.nu1; ++sw)
+        if (!gs_sweep(Lv.op, b, x, true, sw == 0)) return;
     } else {
       V* first = ((P.nu1 + P.nu2) & 1) ? x : tmp;
-      jacobi_sweep(Lv.op, b, nullptr, first, true);
+      if (!jacobi_sweep(Lv.op, b, nullptr, first, true)) return;
       cur = first;
       for (int sw = 1; sw < P.nu1; ++sw) {
         V* dst = (cur == x) ? tmp : x;
-        jacobi_sweep(Lv.op, b, cur, dst, false);
+        if (!jacobi_sweep(Lv.op, b, cur, dst, false)) return;
         cur = dst;
       }
     }
     curs[l] = cur;
-    for (int64_t p = gt; p < Lv.op.d.nv; p += nthr) residual_point<KIND, false, NB>(Lv.op, b, cur, (V*)Lv.r, p);
-    cl.sync();
+    for (int64_t p = gt; p < Lv.op.d.nv; p += nthr) residual_point<KIND, false, NB, CH>(Lv.op, b, cur, (V*)Lv.r, p);
+    if (!sync()) return;
     for (int64_t p = gt; p < Lc.op.d.nv; p += nthr)
       restrict_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lv.r, (V*)Lc.b, p);
-    cl.sync();
+    if (!sync()) return;
   }
   {
     const T* bc = (const T*)P.L[P.coarsest].b;
@@ -704,7 +763,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
       for (int c = 0; c < P.N; ++c) s += row[c] * (double)bc[c];
       xc[r] = (T)s;
     }
-    cl.sync();
+    if (!sync()) return;
   }
   for (int l = P.coarsest - 1; l >= P.first; --l) {
     const TailLevel& Lv = P.L[l];
@@ -715,17 +774,106 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
     V* cur = curs[l];
     for (int64_t p = gt; p < Lv.op.d.nv; p += nthr)
       prolong_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lc.x, cur, p);
-    cl.sync();
+    if (!sync()) return;
     if (P.smoother == 1) {
-      for (int sw = 0; sw < P.nu2; ++sw) gs_sweep(Lv.op, b, x, false, false);
+      for (int sw = 0; sw < P.nu2; ++sw)
+        if (!gs_sweep(Lv.op, b, x, false, false)) return;
     } else {
       for (int sw = 0; sw < P.nu2; ++sw) {
         V* dst = (cur == x) ? tmp : x;
-        jacobi_sweep(Lv.op, b, cur, dst, false);
+        if (!jacobi_sweep(Lv.op, b, cur, dst, false)) return;
         cur = dst;
       }
     }
   }
+}
+
+template <int KIND, int NB>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_constant__ TailParams P) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
+  const int64_t gt = (int64_t)cl.block_rank() * blockDim.x + threadIdx.x;
+  vcycle_tail_body<KIND, NB>(P, gt, nthr, [&]() {
+    cl.sync();
+    return true;
+  });
+}
+
+template <int KIND, int NB>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_coop(const __grid_constant__ TailParams P) {
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = *(volatile unsigned*)&P.bar[1];   // cannot move before every block has read it
+  vcycle_tail_body<KIND, NB>(P, gt, nthr, [&]() { return grid_sync_bounded(P.bar, gridDim.x, gen, P.status, P.limit_ns); });
+}
+
+// `rounds` bounded grid barriers expecting `gridDim.x + extra` arrivals (a
+// check of the barrier: with extra > 0 every wait gives up after limit_ns).
+__global__ void __launch_bounds__(256) k_barrier_check(unsigned* bar, int rounds, int extra, double* status,
+                                                      long long limit_ns, unsigned* passed) {
+  unsigned gen = 0;
+  if (threadIdx.x == 0) gen = *(volatile unsigned*)&bar[1];
+  for (int r = 0; r < rounds; ++r) {
+    if (!grid_sync_bounded(bar, gridDim.x + (unsigned)extra, gen, status, limit_ns)) return;
+    if (threadIdx.x == 0) atomicAdd(passed, 1u);
+  }
+}
+
+template <typename K>
+static int coop_blocks(K kernel, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * num_sms();
+}
+
+template <typename K, typename... A>
+static cudaError_t coop_launch(K kernel, int blocks, int threads, void* s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = (cudaStream_t)s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+int coop_tail_blocks(int kind, int nb) {
+  if (nb == 27) {
+    if (kind == STORE_F64) return coop_blocks(k_vcycle_coop<STORE_F64, 27>, TAIL_THREADS);
+    if (kind == STORE_F32) return coop_blocks(k_vcycle_coop<STORE_F32, 27>, TAIL_THREADS);
+    return coop_blocks(k_vcycle_coop<STORE_F16, 27>, TAIL_THREADS);
+  }
+  if (kind == STORE_F64) return coop_blocks(k_vcycle_coop<STORE_F64, 9>, TAIL_THREADS);
+  if (kind == STORE_F32) return coop_blocks(k_vcycle_coop<STORE_F32, 9>, TAIL_THREADS);
+  return coop_blocks(k_vcycle_coop<STORE_F16, 9>, TAIL_THREADS);
+}
+
+cudaError_t launch_vcycle_coop(const TailParams& P, int kind, int nb, int blocks, void* s) {
+  if (nb == 27) {
+    if (kind == STORE_F64) return coop_launch(k_vcycle_coop<STORE_F64, 27>, blocks, TAIL_THREADS, s, P);
+    if (kind == STORE_F32) return coop_launch(k_vcycle_coop<STORE_F32, 27>, blocks, TAIL_THREADS, s, P);
+    return coop_launch(k_vcycle_coop<STORE_F16, 27>, blocks, TAIL_THREADS, s, P);
+  }
+  if (kind == STORE_F64) return coop_launch(k_vcycle_coop<STORE_F64, 9>, blocks, TAIL_THREADS, s, P);
+  if (kind == STORE_F32) return coop_launch(k_vcycle_coop<STORE_F32, 9>, blocks, TAIL_THREADS, s, P);
+  return coop_launch(k_vcycle_coop<STORE_F16, 9>, blocks, TAIL_THREADS, s, P);
+}
+
+cudaError_t launch_barrier_check(unsigned* bar, int rounds, int extra, double* status, long long limit_ns,
+                                 unsigned* passed, int* blocks_out, void* s) {
+  const int blocks = coop_blocks(k_barrier_check, 256);
+  if (blocks_out) *blocks_out = blocks;
+  if (blocks < 1) return cudaErrorInvalidConfiguration;
+  return coop_launch(k_barrier_check, blocks, 256, s, bar, rounds, extra, status, limit_ns, passed);
 }
 
 static uint32_t zero_start_mask(int dim, int col);
@@ -1115,8 +1263,8 @@ __global__ void k_export(Dims d, bool fine, const double* __restrict__ J, const 
                          const double2* __restrict__ md, double shift, double* __restrict__ out) {
   int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (v >= d.nv) return;
-  const int i = (int)(v % d.nx);
-  const int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   const int64_t p = line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1));
   const int C = d.dim == 3 ? 13 : 4;
   for (int b = 0; b < d.nb; ++b) {
@@ -1143,8 +1291,8 @@ __global__ void k_gather_rows(Dims d, const double* __restrict__ J, const double
   if (t >= count * d.nb) return;
   const int r = t / d.nb, b = t % d.nb;
   const int64_t v = verts[r];
-  const int i = (int)(v % d.nx);
-  const int64_t line = v / d.nx;
+  const uint32_t line = (uint32_t)v / (uint32_t)d.nx;   // nv < 2^31
+  const int i = (int)((uint32_t)v - line * (uint32_t)d.nx);
   const int64_t p = line * d.nx + ((i & 1) ? d.E + (i >> 1) : (i >> 1));
   const double* a = J + ((int64_t)b * d.nv + p) * 4;
   double* o = Jout + ((int64_t)r * d.nb + b) * 4;
@@ -1315,7 +1463,7 @@ __global__ void __launch_bounds__(256) k_residual_shared(const __grid_constant__
   bool act[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
-  const int par = (int)(p % L.d.nx) >= L.d.E;
+  const int par = (int)((uint32_t)p % (uint32_t)L.d.nx) >= L.d.E;   // nv < 2^31
   T s0[NS], s1[NS];
   shared_row<KIND, NB, NS>(L, G, p, par, false, L.nomask, act, s0, s1);
   const double2 m = reinterpret_cast<const double2*>(G[0].mdiag)[p];
@@ -1348,7 +1496,7 @@ __global__ void __launch_bounds__(256) k_jacobi_shared(const __grid_constant__ L
   for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
   T s0[NS], s1[NS];
   if (!zero_x) {
-    const int par = (int)(p % L.d.nx) >= L.d.E;
+    const int par = (int)((uint32_t)p % (uint32_t)L.d.nx) >= L.d.E;   // nv < 2^31
     shared_row<KIND, NB, NS>(L, G, p, par, false, L.nomask, act, s0, s1);
   }
   const double2 m = reinterpret_cast<const double2*>(G[0].mdiag)[p];
@@ -1391,9 +1539,10 @@ __global__ void __launch_bounds__(256) k_gs_colour_shared(const __grid_constant_
   bool act[NS];
 #pragma unroll
   for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
-  const int64_t line = t / cnt_x;
-  const int pos = (int)(t - line * cnt_x);
-  const int jj = (int)(line % lines_y), kk = (int)(line / lines_y);
+  // 32-bit index arithmetic: a colour has fewer than 2^31 vertices
+  const uint32_t tt = (uint32_t)t, line = tt / (uint32_t)cnt_x, kl = line / (uint32_t)lines_y;
+  const int pos = (int)(tt - line * (uint32_t)cnt_x);
+  const int jj = (int)(line - kl * (uint32_t)lines_y), kk = (int)kl;
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
   T s0[NS], s1[NS];
@@ -1421,9 +1570,9 @@ static void residual_t(const LevelOp& L, const void* b, const void* x, void* r, 
   const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.batched) {
     if (L.d.nb == 27)
-      RF_LAUNCH_PDL((k_residual<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+      RF_LAUNCH_PDL((k_residual<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
     else
-      RF_LAUNCH_PDL((k_residual<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
+      RF_LAUNCH_PDL((k_residual<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   } else if (L.d.nb == 27)
     RF_LAUNCH_PDL((k_residual<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)x, (V*)r);
   else
@@ -1438,9 +1587,9 @@ static void jacobi_t(const LevelOp& L, const void* b, const void* xin, void* xou
   const int g = (int)((L.d.nv + bs - 1) / bs);
   if (L.batched) {
     if (L.d.nb == 27)
-      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
     else
-      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
+      RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   } else if (L.d.nb == 27)
     RF_LAUNCH_PDL((k_jacobi<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (const V*)xin, (V*)xout, omega, (int)zero_x);
   else
@@ -1502,9 +1651,9 @@ static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool ze
     const int g = (int)((count + bs - 1) / bs);
     if (L.batched) {
       if (L.d.nb == 27)
-        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
       else
-        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, 9>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
+        RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else if (L.d.nb == 27) {
       RF_LAUNCH_PDL((k_gs_colour<KIND, FINE, 27, 0>), g, bs, 0, s, L, (const V*)b, (V*)x, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else {
@@ -1595,8 +1744,8 @@ static void residual_bt(const LevelOp& L, const SysBatch& B, void* s) {
   const int bs = L.block > 0 ? L.block : 256;
   const dim3 g((unsigned)((L.d.nv + bs - 1) / bs), (unsigned)B.n);
   if (L.batched) {
-    if (L.d.nb == 27) RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B);
-    else RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B);
+    if (L.d.nb == 27) RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, B);
+    else RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, B);
   } else if (L.d.nb == 27) {
     RF_LAUNCH_PDL((k_residual_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B);
   } else {
@@ -1610,8 +1759,8 @@ static void jacobi_bt(const LevelOp& L, const SysBatch& B, double omega, bool ze
   const dim3 g((unsigned)((L.d.nv + bs - 1) / bs), (unsigned)B.n);
   const int zx = zero_x ? 1 : 0;
   if (L.batched) {
-    if (L.d.nb == 27) RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, omega, zx);
-    else RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, omega, zx);
+    if (L.d.nb == 27) RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, B, omega, zx);
+    else RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, B, omega, zx);
   } else if (L.d.nb == 27) {
     RF_LAUNCH_PDL((k_jacobi_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, omega, zx);
   } else {
@@ -1627,9 +1776,9 @@ static void gs_bt(const LevelOp& L, const SysBatch& B, bool forward, bool zero_s
     const dim3 g((unsigned)((count + bs - 1) / bs), (unsigned)B.n);
     if (L.batched) {
       if (L.d.nb == 27)
-        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, chunk_of(KIND)>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
       else
-        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, 9>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
+        RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 9, chunk_of(KIND)>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else if (L.d.nb == 27) {
       RF_LAUNCH_PDL((k_gs_colour_b<KIND, FINE, 27, 0>), g, bs, 0, s, L, B, px, py, pz, cnt_x, lines_y, count, skip, rev);
     } else {

@@ -80,7 +80,7 @@ void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf
 void launch_coarse_solve(const LevelOp& C, const double* Ainv, const void* b, void* x, void* s);
 
 // The V-cycle below a size threshold, run by one thread-block cluster.
-#define TAIL_THREADS 512
+#define TAIL_THREADS 256
 struct TailLevel {
   LevelOp op;                 // coarse-level operator (blocks hold A)
   void *x, *b, *r, *t;        // level vectors (T2, padded)
@@ -92,11 +92,23 @@ struct TailParams {
   uint32_t zmask[8];          // first-sweep skip masks per colour
   const double* Ainv;         // coarsest inverse, N x N
   int N;
+  // cooperative form only: barrier words {count, generation}, the flag a
+  // barrier that gave up sets (a Krylov scalar slot), and the wait limit
+  unsigned* bar;
+  double* status;
+  long long limit_ns;
   TailLevel L[RF_MAXL];
 };
 int tail_cluster_size(int kind, int nb);
 void fill_tail_masks(TailParams& P, int dim);
 cudaError_t launch_vcycle_tail(const TailParams& P, int kind, int nb, int csize, void* s);
+// the same V-cycle as one cooperative launch of `blocks` blocks (coop_tail_blocks: all that fit at once)
+int coop_tail_blocks(int kind, int nb);
+cudaError_t launch_vcycle_coop(const TailParams& P, int kind, int nb, int blocks, void* s);
+// `rounds` bounded grid barriers over all co-resident blocks, each expecting `extra` more arrivals
+// than there are blocks; *passed counts the (block, round) passes, *status = 1 if a wait gave up
+cudaError_t launch_barrier_check(unsigned* bar, int rounds, int extra, double* status, long long limit_ns,
+                                 unsigned* passed, int* blocks_out, void* s);
 
 // set-up kernels (levelops.cu)
 void launch_galerkin_axis(int axis, const Dims& din, const uint8_t* dmf, const double* Jin, const double* Min,
@@ -177,6 +189,9 @@ void launch_axpby_pairs(int64_t nv, double* out, const double* a, const double2*
 // blocks return at once and its data stay as they are.
 #define RF_MAXSYS 64
 constexpr int RF_SCAL_DONE = 15;
+// set to 1 by a cooperative V-cycle tail whose barrier wait gave up (read by
+// the host with the iteration's scalars)
+constexpr int RF_SCAL_TAIL = 16;
 struct SysLevel {                  // one system's operands of a batched level launch
   const void* A;                   // blocks (coarse solve: the FP64 inverse)
   const float* scale;              // FP16 row scales

@@ -381,13 +381,17 @@ def test_fp32_vcycle_matches_fp32_emulation(case, smoother):
     g.close()
 
 
+@pytest.mark.parametrize("mode", ["cluster", "coop"])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_vcycle_cluster_tail_matches_oracle(smoother, precision, monkeypatch):
-    """The optional one-cluster execution of the small levels (RF_TAIL_NV)
-    computes the same V-cycle."""
+@pytest.mark.parametrize("case", ["3d-17cube", "3d-lenses-33"])
+def test_vcycle_tail_matches_oracle(case, precision, smoother, mode, monkeypatch):
+    """The optional one-launch execution of the small levels (RF_TAIL_NV):
+    one thread-block cluster, or a cooperative launch with bounded grid
+    barriers, computes the same V-cycle."""
     monkeypatch.setenv("RF_TAIL_NV", "100000")
-    prob = CASES["3d-17cube"]()
+    monkeypatch.setenv("RF_TAIL_MODE", mode)
+    prob = CASES[case]()
     g, F, m, A, gm = _setup_both(prob, precision, smoother)
     b = np.random.default_rng(2).standard_normal(2 * g.nv)
     x = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
@@ -396,6 +400,51 @@ def test_vcycle_cluster_tail_matches_oracle(smoother, precision, monkeypatch):
     for a in range(2):   # per component
         assert np.abs(x[a::2] - x_o[a::2]).max() <= tol * np.abs(x_o[a::2]).max(), a
     g.close()
+
+
+@pytest.mark.parametrize("precision,smoother", [("fp32", "gs8"), ("fp64", "jacobi")])
+def test_solve_with_cooperative_tail(precision, smoother, monkeypatch):
+    """Solves with the small levels in one cooperative launch (captured in the
+    iteration's CUDA graph, replayed every iteration) take the iterations of
+    the launch-per-phase V-cycle and agree with its solution to the solver
+    tolerance."""
+    prob = CASES["3d-lenses-33"]()
+    out = {}
+    for tail in ("0", "100000"):
+        monkeypatch.setenv("RF_TAIL_NV", tail)
+        g, F = _assembled(prob)
+        g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(_levels(prob), smoother, precision=precision))
+        b = torch.tensor(F, device="cuda")
+        x = torch.empty_like(b)
+        info = g.solve(0, b, x, rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, info
+        out[tail] = (x.cpu().numpy(), info)
+        g.close()
+    (x0, i0), (x1, i1) = out["0"], out["100000"]
+    assert abs(i0["iterations"] - i1["iterations"]) <= 1, (i0, i1)
+    assert np.abs(x1[0::2] - x0[0::2]).max() <= 1e-7 * np.abs(x0[0::2]).max()
+    assert np.abs(x1[1::2] - x0[1::2]).max() <= 1e-8
+
+
+def test_grid_barrier_completes_and_times_out():
+    """The bounded grid barrier of the cooperative tail (rf_barrier_check):
+    1000 rounds over every co-resident block complete; a barrier that expects
+    one block more than the launch has never completes, so every wait gives
+    up after its limit and the call returns RF_ETIMEOUT instead of hanging;
+    the context stays usable (the next check completes)."""
+    import time
+    st, blocks = rf.rf_barrier_check(1000, 0, 1.0)
+    assert st == rf.RF_OK and blocks >= 152, (st, blocks)
+    t0 = time.perf_counter()
+    st, _ = rf.rf_barrier_check(3, 1, 0.2)
+    dt = time.perf_counter() - t0
+    assert st == rf.RF_ETIMEOUT, st
+    assert 0.15 <= dt <= 5.0, dt
+    st, _ = rf.rf_barrier_check(10, 0, 1.0)
+    assert st == rf.RF_OK
+    for bad in ((0, 0, 1.0), (1, 2, 1.0), (1, 0, 0.0), (1, 0, 11.0)):
+        assert rf.rf_barrier_check(*bad)[0] == rf.RF_EINVAL
 
 
 # ------------------------------------------------------------------ solves
