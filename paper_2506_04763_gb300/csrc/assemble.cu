@@ -743,7 +743,8 @@ cudaError_t launch_assemble(const Dims& d, const PhysParams& pp, const AsmArrays
   in.vol = a.vol; in.dir = a.dir;
   in.pw_dir = a.pw_dir; in.q_in = (const double2*)a.q_in;
   in.law = a.law; in.kr_tab = a.kr_tab;
-  static const bool per_vertex = getenv("RF_ASM_VERTEX") && atoi(getenv("RF_ASM_VERTEX")) != 0;
+  const char* pv = getenv("RF_ASM_VERTEX");   // read per assembly (an alternative kept for comparison)
+  const bool per_vertex = pv && atoi(pv) != 0;
   if (!per_vertex) {
     launch_assemble_cells(d, ph, in, a, want_j, s);
     return cudaGetLastError();

@@ -89,6 +89,29 @@ def test_assembly_matches_oracle(case):
     g.close()
 
 
+@pytest.mark.parametrize("case", ["3d-9x7x5-stress", "2d-17x13-stress-laws", "3d-17x9x13-laws"])
+def test_vertex_and_element_assembly_agree(case, monkeypatch):
+    """The one-thread-per-vertex assembly (RF_ASM_VERTEX=1) evaluates every
+    face from both ends with the element kernel's face arithmetic, per-medium
+    laws included: F, J and M agree to the rounding of their different
+    summation orders."""
+    prob = CASES[case]()
+    out = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RF_ASM_VERTEX", mode)
+        g, F = _assembled(prob)
+        J, md = g.export_jacobian()
+        out.append((F, J, md))
+        g.close()
+    (F0, J0, m0), (F1, J1, m1) = out
+    for a in range(2):
+        rows = np.abs(J0[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2)) + 1e-300
+        err = np.abs(J1[:, :, 2 * a:2 * a + 2] - J0[:, :, 2 * a:2 * a + 2]).max(axis=(1, 2))
+        assert np.all(err <= 1e-13 * rows), (a, (err / rows).max())
+        assert np.abs(F1[a::2] - F0[a::2]).max() <= 1e-13 * np.abs(F0[a::2]).max()
+    np.testing.assert_allclose(m1, m0, rtol=1e-14, atol=0)
+
+
 def test_assembly_host_and_device_pointers_agree():
     prob = CASES["3d-9x7x5-stress"]()
     g = _grid(prob)
