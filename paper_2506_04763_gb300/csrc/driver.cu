@@ -109,11 +109,11 @@ struct Level {
 //   FP64 storage: equal on the two finest levels, batched 1.2-1.6x faster on
 //     the levels below.  (On the finest level of the 65^3 FP64 LIMEX step,
 //     batched Jacobi measured no faster either.)
-//   FP16 storage (the finest level only): loads batched two blocks at a
-//     time, 2.11 -> 2.01 ms per sweep + residual.
+//   FP16 storage (the finest level only, blocks stored in pairs): one pair
+//     per round trip, 1.80 ms per sweep + residual against 1.93 ms with two.
 static void default_shape(Level& Lv, int l, int kind) {
   Lv.block = 128;
-  Lv.batched = kind == STORE_F32 || kind == STORE_F16 || (kind == STORE_F64 && l >= 2);
+  Lv.batched = kind == STORE_F32 || (kind == STORE_F64 && l >= 2);
 }
 
 struct Alloc {
@@ -926,7 +926,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
         if (kind == STORE_F64) {
           Lv.A[0] = g->J;
         } else {
-          GNEED(Lv.A[0] = dalloc(g, se * 4 * d.nb * d.nv, s, true));
+          GNEED(Lv.A[0] = dalloc(g, se * 4 * stored_blocks(kind, d.nb) * d.nv, s, true));
           if (kind == STORE_F16) GNEED(Lv.scale[0] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
           launch_pack_level(d, true, g->J, nullptr, g->mdiag, 0.0, kind, Lv.A[0], Lv.scale[0], nullptr, s);
         }
@@ -936,7 +936,7 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
         }
       } else {
         for (int j = 0; j < nshift; ++j) {
-          GNEED(Lv.A[j] = dalloc(g, se * 4 * d.nb * d.nv, s, true));
+          GNEED(Lv.A[j] = dalloc(g, se * 4 * stored_blocks(lk, d.nb) * d.nv, s, true));
           if (lk == STORE_F16) GNEED(Lv.scale[j] = (float*)dalloc(g, sizeof(float) * 4 * d.nv, s, true));
           GNEED(Lv.Dinv[j] = dalloc(g, te * 4 * d.nv, s, true));
           launch_pack_level(d, false, Lv.Jc, Lv.Mc, nullptr, shifts[j], lk, Lv.A[j], Lv.scale[j], Lv.Dinv[j], s);

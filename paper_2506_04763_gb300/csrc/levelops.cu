@@ -57,6 +57,12 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2* p) {
   asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
 template <typename V>
 __device__ __forceinline__ V ld_keep(const V* p) { return *p; }
 #else
@@ -76,6 +82,12 @@ __device__ __forceinline__ uint2 ld_stream_u2(const uint2* p) {
   uint2 v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
                : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(l2_policy_first()));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p), "l"(l2_policy_first()));
   return v;
 }
 // Neighbour values of x: kept in L1 (neighbouring threads share them) and
@@ -149,6 +161,92 @@ __device__ __forceinline__ double blk_acc(double s, double a0, double a1, double
   return __dadd_rn(s, __fma_rn(a0, x.x, __dmul_rn(a1, x.y)));
 }
 
+// FP16 storage holds the blocks of a row in pairs, one 16-byte load per pair
+// (a warp reads 512 contiguous bytes per load, as with FP32 blocks): slot s
+// of row p is half s % 2 of uint4 number (s / 2) * nv + p.  The two blocks of
+// a pair have offsets of the same parity in every axis, so they reach
+// vertices of the same colour: the first sweep from zero, which skips the
+// blocks of colours not yet visited, skips whole pairs.  Slots (3D): the
+// pairs dx = -1, +1 for each (dy, dz); then the dx = 0 pairs (dy = -1, +1 at
+// dz = 0), (dz = -1, +1 at dy = 0), (dy = -1, +1 at dz = -1), (dy = -1, +1 at
+// dz = +1); then the centre and an empty slot.  2D: dx = -1, +1 for each dy,
+// then (dy = -1, +1 at dx = 0), then the centre and an empty slot.  A sweep
+// that skips the centre reads none of the last pair.
+__host__ __device__ constexpr int f16_block_of_slot(int nb, int s) {
+  if (nb == 27) {
+    if (s < 18) return ((s & 1) ? 2 : 0) + 3 * ((s >> 1) % 3) + 9 * ((s >> 1) / 3);
+    switch (s) {
+      case 18: return 10; case 19: return 16;   // (0, -1, 0), (0, +1, 0)
+      case 20: return 4;  case 21: return 22;   // (0, 0, -1), (0, 0, +1)
+      case 22: return 1;  case 23: return 7;    // (0, -1, -1), (0, +1, -1)
+      case 24: return 19; case 25: return 25;   // (0, -1, +1), (0, +1, +1)
+      case 26: return 13;                       // centre
+      default: return -1;
+    }
+  }
+  if (s < 6) return ((s & 1) ? 2 : 0) + 3 * (s >> 1);
+  return s == 6 ? 1 : s == 7 ? 7 : s == 8 ? 4 : -1;
+}
+__host__ __device__ constexpr int f16_slot_of_block(int nb, int b) {
+  int s = 0;
+  while (s < nb && f16_block_of_slot(nb, s) != b) ++s;
+  return s;
+}
+
+__device__ __forceinline__ void f16_half(const uint4& u, int h, const float4& sc, float (&a)[4]) {
+  RawBlock<STORE_F16> r;
+  r.u = h ? make_uint2(u.z, u.w) : make_uint2(u.x, u.y);
+  unpack_block<STORE_F16>(r, sc, a);
+}
+
+// The FP16 stencil sum, slot by slot: CP pairs (2 CP blocks) and their x values
+// loaded per memory round trip, then summed.  Per-block, batched and
+// shared-matrix FP16 kernels all sum in this slot order with blk_acc.
+template <int NB, int CP>
+__device__ __forceinline__ void stencil_sum_f16(const LevelOp& L, int64_t p, int par,
+                                                const float2* __restrict__ x, bool skip_centre, uint32_t skipmask,
+                                                float& s0, float& s1) {
+  constexpr int C = NB == 27 ? 13 : 4, NP = (NB + 1) / 2;
+  const float4 sc = reinterpret_cast<const float4*>(L.scale)[p];
+  const uint4* __restrict__ A = reinterpret_cast<const uint4*>(L.A);
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int q0 = 0; q0 < NP; q0 += CP) {
+    uint4 raw[CP];
+    float2 xv[CP][2];
+    bool use[CP][2];
+#pragma unroll
+    for (int c = 0; c < CP; ++c) {
+      const int q = q0 + c;
+      if (q >= NP) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int b = f16_block_of_slot(NB, 2 * q + h);
+        use[c][h] = b >= 0 && !(skip_centre && b == C) && !((skipmask >> (b >= 0 ? b : 0)) & 1u);
+      }
+      if (use[c][0] || use[c][1]) raw[c] = ld_stream_u4(A + (int64_t)q * L.d.nv + p);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int b = f16_block_of_slot(NB, 2 * q + h);
+        if (use[c][h]) xv[c][h] = ld_keep(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CP; ++c) {
+      if (q0 + c >= NP) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!use[c][h]) continue;
+        float a[4];
+        f16_half(raw[c], h, sc, a);
+        a0 = blk_acc(a0, a[0], a[1], xv[c][h]);
+        a1 = blk_acc(a1, a[2], a[3], xv[c][h]);
+      }
+    }
+  }
+  s0 = a0; s1 = a1;
+}
+
 // sum over the stencil of blocks * x (centre optionally skipped)
 template <int KIND, int NB>
 __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par,
@@ -183,10 +281,8 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
 // sums equal stencil_sum's bit for bit.
 // This is what the small levels need, where a thread's chain of round trips,
 // not bandwidth, sets the time.
-// Stencil blocks whose loads a batched kernel issues per memory round trip.
-// FP16 blocks (8 B per thread and block) run best two at a time: on the
-// finest 257^3 level one sweep plus one residual took 2.01 ms with 2, 2.37 ms
-// with 4, 2.66 ms with 9, and 2.11 ms with one block per round trip.
+// Stencil blocks (FP16: block pairs) whose loads a batched kernel issues per
+// memory round trip; an unbatched FP16 kernel loads one pair per round trip.
 __host__ __device__ constexpr int chunk_of(int kind) { return kind == STORE_F16 ? 2 : 9; }
 
 template <int KIND, int NB, int CH>
@@ -235,8 +331,12 @@ __device__ __forceinline__ void stencil_sum_any(const LevelOp& L, int64_t p, int
                                                 const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                 bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
                                                 typename Ty<KIND>::T& s1) {
-  if (CH > 0) stencil_sum_batched<KIND, NB, (CH > 0 ? CH : 1)>(L, p, par, x, skip_centre, skipmask, s0, s1);
-  else stencil_sum<KIND, NB>(L, p, par, x, skip_centre, skipmask, s0, s1);
+  if constexpr (KIND == STORE_F16)
+    stencil_sum_f16<NB, (CH > 0 ? CH : 1)>(L, p, par, x, skip_centre, skipmask, s0, s1);
+  else if constexpr (CH > 0)
+    stencil_sum_batched<KIND, NB, CH>(L, p, par, x, skip_centre, skipmask, s0, s1);
+  else
+    stencil_sum<KIND, NB>(L, p, par, x, skip_centre, skipmask, s0, s1);
 }
 
 // (A x)_p, with A = shift*M - J on the fine level (blocks hold J)
@@ -1079,8 +1179,13 @@ __global__ void k_pack(Dims d, bool fine, const double* __restrict__ J, const do
           const double* m = M + ((int64_t)b * d.nv + p) * 2;
           e[0] = -e[0]; e[1] = shift * m[0] - e[1]; e[2] = -e[2]; e[3] = shift * m[1] - e[3];
         }
-        __half* o = reinterpret_cast<__half*>(Aout) + ((int64_t)b * d.nv + p) * 4;
+        const int sl = f16_slot_of_block(nb, b);   // paired layout, see stencil_sum_f16
+        __half* o = reinterpret_cast<__half*>(Aout) + (((int64_t)(sl >> 1) * d.nv + p) * 2 + (sl & 1)) * 4;
         for (int q = 0; q < 4; ++q) o[q] = __double2half(e[q] / (double)sc[q]);
+      }
+      if (nb & 1) {   // the empty slot
+        __half* o = reinterpret_cast<__half*>(Aout) + (((int64_t)(nb >> 1) * d.nv + p) * 2 + 1) * 4;
+        for (int q = 0; q < 4; ++q) o[q] = __float2half(0.f);
       }
     }
   }
@@ -1434,6 +1539,37 @@ __device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, 
   if (KIND == STORE_F16) sc = reinterpret_cast<const float4*>(G[0].scale)[p];
 #pragma unroll
   for (int q = 0; q < NS; ++q) { s0[q] = 0; s1[q] = 0; }
+  if constexpr (KIND == STORE_F16) {
+    // pairs of slots, in the slot order of stencil_sum_f16
+    const uint4* __restrict__ A = reinterpret_cast<const uint4*>(G[0].A);
+#pragma unroll
+    for (int qp = 0; qp < (NB + 1) / 2; ++qp) {
+      bool use[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int b = f16_block_of_slot(NB, 2 * qp + h);
+        use[h] = b >= 0 && !(skip_centre && b == C) && !((skipmask >> (b >= 0 ? b : 0)) & 1u);
+      }
+      if (!use[0] && !use[1]) continue;
+      const uint4 raw = ld_stream_u4(A + (int64_t)qp * L.d.nv + p);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!use[h]) continue;
+        const int b = f16_block_of_slot(NB, 2 * qp + h);
+        float a[4];
+        f16_half(raw, h, sc, a);
+        const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+          if (!act[q]) continue;
+          const V xv = ((const V*)G[q].in1)[p + off];
+          s0[q] = blk_acc(s0[q], a[0], a[1], xv);
+          s1[q] = blk_acc(s1[q], a[2], a[3], xv);
+        }
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     if (skip_centre && b == C) continue;

@@ -46,6 +46,9 @@ void launch_storage_sw(const Dims& d, const PhysParams& pp, const double* u, con
 
 // ---- multigrid level operators (levelops.cu) ----
 enum StoreKind { STORE_F64 = 0, STORE_F32 = 1, STORE_F16 = 2 };
+// stencil blocks stored per row: FP16 rows are stored in block pairs (an odd
+// count gets an empty slot)
+inline int stored_blocks(int kind, int nb) { return kind == STORE_F16 ? (nb + 1) & ~1 : nb; }
 
 // One level's operator as seen by the smoothing / residual kernels.
 struct LevelOp {
