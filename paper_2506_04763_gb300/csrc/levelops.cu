@@ -656,57 +656,81 @@ __global__ void __launch_bounds__(256) k_restrict_planes(Dims df, Dims dc, const
   restrict_planes_body<T>(df, dc, dmf, dmc, rf, bc);
 }
 
+// Prolongation and correction x_f += P x_c, two fine vertices per thread:
+// thread (I, fj, fk) updates fine vertex 2I (even half of the parity-split
+// line) and 2I + 1 (odd half), whose coarse parents along x are I, and I and
+// I + 1.  Their (up to 8) parents are loaded once, before the first sum (one
+// memory round trip; a parent outside the coarse grid is read at coarse
+// vertex 0 and skipped).  Each fine value then sums its parents in the
+// (K, J, I) order of prolong_point with the same expressions, so the results
+// are the per-point kernel's bit for bit.  The pairing halves the gathered
+// loads and the index arithmetic per fine vertex (the one-vertex-per-thread
+// form issued ~330 instructions per vertex and was issue-bound).
 template <typename T>
-__device__ __forceinline__ void prolong_planes_body(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
-                                                    const uint8_t* __restrict__ dmc,
-                                                    const typename V2<T>::t* __restrict__ xc,
-                                                    typename V2<T>::t* __restrict__ xf) {
+__device__ __forceinline__ void prolong_pairs_body(const Dims& df, const Dims& dc, const uint8_t* __restrict__ dmf,
+                                                   const uint8_t* __restrict__ dmc,
+                                                   const typename V2<T>::t* __restrict__ xc,
+                                                   typename V2<T>::t* __restrict__ xf) {
   rf_pdl_begin();
   typedef typename V2<T>::t V;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= df.nx * df.ny) return;
-  const int fj = t / df.nx, pos = t - fj * df.nx, fk = blockIdx.y;
-  const int fi = pos < df.E ? 2 * pos : 2 * (pos - df.E) + 1;
-  const int64_t pf = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx + pos;
-  const bool mf = dmf[pf] != 0;
-  const int I0 = fi >> 1, J0 = fj >> 1, K0 = fk >> 1;
-  int xo[2];
-  int64_t lo[4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a) xo[a] = ((I0 + a) & 1) ? dc.E + ((I0 + a) >> 1) : ((I0 + a) >> 1);
-#pragma unroll
-  for (int c = 0; c < 2; ++c)
-#pragma unroll
-    for (int b = 0; b < 2; ++b) lo[2 * c + b] = ((int64_t)(J0 + b) + (int64_t)dc.ny * (K0 + c)) * dc.nx;
-  // as in the restriction, all loads go out before the first sum; a parent
-  // outside the coarse grid is read at coarse vertex 0 and skipped
-  const V xv = xf[pf];
+  if (t >= dc.nx * df.ny) return;
+  const int fj = t / dc.nx, I = t - fj * dc.nx, fk = blockIdx.y;
+  const int J0 = fj >> 1, K0 = fk >> 1;
+  const bool oy = (fj & 1) != 0, oz = df.dim == 3 && (fk & 1) != 0;
+  const bool odd = 2 * I + 1 < df.nx;   // fine vertex 2I + 1 exists
+  const int64_t fline = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx;
+  const int64_t pe = fline + I, po = fline + df.E + I;
+  const int xo[2] = {(I & 1) ? dc.E + (I >> 1) : (I >> 1), ((I + 1) & 1) ? dc.E + ((I + 1) >> 1) : ((I + 1) >> 1)};
   V c8[8];
   uint8_t m[8];
   bool in[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const int K = K0 + ((q >> 2) & 1), J = J0 + ((q >> 1) & 1), I = I0 + (q & 1);
-    in[q] = ((q & 1) == 0 || (fi & 1)) && (((q >> 1) & 1) == 0 || (fj & 1)) &&
-            (((q >> 2) & 1) == 0 || (fk & 1)) && K < dc.nz && J < dc.ny && I < dc.nx;
-    const int64_t pc = in[q] ? lo[q >> 1] + xo[q & 1] : 0;
+    const int ib = q & 1, jb = (q >> 1) & 1, kb = (q >> 2) & 1;
+    in[q] = (!jb || oy) && (!kb || oz) && (!ib || odd) && K0 + kb < dc.nz && J0 + jb < dc.ny && I + ib < dc.nx;
+    const int64_t pc = in[q] ? ((int64_t)(J0 + jb) + (int64_t)dc.ny * (K0 + kb)) * dc.nx + xo[ib] : 0;
     c8[q] = xc[pc];
     m[q] = dmc[pc];
   }
-  const T wz = (df.dim == 3 && (fk & 1)) ? (T)0.5 : (T)1;
-  const T wy = (fj & 1) ? (T)0.5 : (T)1;
-  const T w = ((fi & 1) ? (T)0.5 : (T)1) * wy * wz;
-  T s0 = 0, s1 = 0;
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    if (!in[q]) continue;
-    if (!(mf || m[q])) s0 += w * c8[q].x;
-    s1 += w * c8[q].y;
+  const V xe = xf[pe];
+  const bool me = dmf[pe] != 0;
+  V xo_v = xe;
+  bool mo = false;
+  if (odd) {
+    xo_v = xf[po];
+    mo = dmf[po] != 0;
   }
-  V o = xv;
-  o.x += s0;
-  o.y += s1;
-  xf[pf] = o;
+  const T wz = oz ? (T)0.5 : (T)1;
+  const T wy = oy ? (T)0.5 : (T)1;
+  {
+    const T w = (T)1 * wy * wz;   // fine x even
+    T s0 = 0, s1 = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      if (!in[q]) continue;
+      if (!(me || m[q])) s0 += w * c8[q].x;
+      s1 += w * c8[q].y;
+    }
+    V o = xe;
+    o.x += s0;
+    o.y += s1;
+    xf[pe] = o;
+  }
+  if (odd) {
+    const T w = (T)0.5 * wy * wz;   // fine x odd
+    T s0 = 0, s1 = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (!in[q]) continue;
+      if (!(mo || m[q])) s0 += w * c8[q].x;
+      s1 += w * c8[q].y;
+    }
+    V o = xo_v;
+    o.x += s0;
+    o.y += s1;
+    xf[po] = o;
+  }
 }
 
 template <typename T>
@@ -714,7 +738,7 @@ __global__ void __launch_bounds__(256) k_prolong_planes(Dims df, Dims dc, const 
                                                         const uint8_t* __restrict__ dmc,
                                                         const typename V2<T>::t* __restrict__ xc,
                                                         typename V2<T>::t* __restrict__ xf) {
-  prolong_planes_body<T>(df, dc, dmf, dmc, xc, xf);
+  prolong_pairs_body<T>(df, dc, dmf, dmc, xc, xf);
 }
 
 // ----------------------------------------------------------------- coarsest solve
@@ -1500,7 +1524,7 @@ __global__ void __launch_bounds__(256) k_prolong_planes_b(Dims df, Dims dc, cons
     rf_pdl_begin();
     return;
   }
-  prolong_planes_body<T>(df, dc, P.dmask, P.dmask_c, (const typename V2<T>::t*)P.in0, (typename V2<T>::t*)P.out);
+  prolong_pairs_body<T>(df, dc, P.dmask, P.dmask_c, (const typename V2<T>::t*)P.in0, (typename V2<T>::t*)P.out);
 }
 
 template <typename T>
@@ -1856,7 +1880,7 @@ void launch_prolong(const LevelOp& F, const LevelOp& C, const void* xc, void* xf
       RF_LAUNCH_PDL(k_prolong<float>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const float2*)xc, (float2*)xf);
     return;
   }
-  const dim3 g((unsigned)((F.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz);
+  const dim3 g((unsigned)((C.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz);   // two fine vertices per thread
   if (F.kind == STORE_F64)
     RF_LAUNCH_PDL(k_prolong_planes<double>, g, 256, 0, s, F.d, C.d, F.dmask, C.dmask, (const double2*)xc, (double2*)xf);
   else
@@ -1955,7 +1979,7 @@ void launch_restrict_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, vo
 }
 
 void launch_prolong_b(const LevelOp& F, const LevelOp& C, const SysBatch& B, void* s) {
-  const dim3 g((unsigned)((F.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz, (unsigned)B.n);
+  const dim3 g((unsigned)((C.d.nx * F.d.ny + 255) / 256), (unsigned)F.d.nz, (unsigned)B.n);
   if (F.kind == STORE_F64) RF_LAUNCH_PDL(k_prolong_planes_b<double>, g, 256, 0, s, F.d, C.d, B);
   else RF_LAUNCH_PDL(k_prolong_planes_b<float>, g, 256, 0, s, F.d, C.d, B);
 }
