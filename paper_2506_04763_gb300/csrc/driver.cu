@@ -1223,8 +1223,14 @@ static void iteration_body(rf_grid* g, int sh, void* s) {
     else launch_bicg_t(d, g->nb, g->J, g->mdiag, shift, K, lo32, s);
   }
   {
-    ProfScope ps(g, s, RF_PROF_VECTOR, nv * (4 * T + 16.0 * 6), 1);
-    launch_bicg_xr(d.nv, K, lo32, s);
+    // with an FP32 preconditioner the FP64 copies the operator read serve
+    // here too: the same values, and no FP32 -> FP64 conversions on the FP64
+    // pipe, which bounds this kernel (16 B more read per vertex)
+    const bool use64 = lo32 && !df;
+    KrylovVecs K2 = K;
+    if (use64) { K2.y = K.y64; K2.z = K.z64; }
+    ProfScope ps(g, s, RF_PROF_VECTOR, nv * ((use64 ? 32.0 : 4 * T) + 16.0 * 6), 1);
+    launch_bicg_xr(d.nv, K2, lo32 && !use64, s);
   }
 }
 
@@ -1622,8 +1628,12 @@ static void batch_body(rf_grid* lead, const std::vector<BatchSys>& bs, int share
     launch_bicg_t_b(d, g0->nb, KB, share, s);
   }
   {
-    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * (4 * T + 16.0 * 6), 1);
-    launch_bicg_xr_b(d.nv, KB, lo32, s);
+    // the FP64 copies of the preconditioned vectors, as in iteration_body
+    KBatch KB64 = KB;
+    if (lo32)
+      for (int q = 0; q < S; ++q) { KB64.s[q].K.y = bs[q].g->K.y64; KB64.s[q].K.z = bs[q].g->K.z64; }
+    ProfScope ps(lead, s, RF_PROF_VECTOR, S * nv * ((lo32 ? 32.0 : 4 * T) + 16.0 * 6), 1);
+    launch_bicg_xr_b(d.nv, KB64, false, s);
   }
   launch_gather_scalars(KB, lead->bscal, s);
   cudaMemcpyAsync(lead->bscal_h, lead->bscal, sizeof(double) * 16 * S, cudaMemcpyDeviceToHost, (cudaStream_t)s);
