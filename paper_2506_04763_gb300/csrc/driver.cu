@@ -994,20 +994,26 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
     rf_status ts = autotune_levels(g, s);
     if (ts) { dfree_all(g, g->gbufs, s); return ts; }
   }
-  // Optionally the small levels (<= RF_TAIL_NV vertices) run as one launch:
-  // one thread-block cluster (RF_TAIL_MODE=cluster), or a cooperative launch
-  // of every co-resident block with bounded grid barriers (otherwise).  The
-  // cluster form, measured on GB300, saves < 1% of a 257^3 solve (each of its
-  // ~100 barrier-separated phases is latency-bound) and costs ~40% of an FP64
-  // LIMEX step at 65^3, where the tail's first level is too large for 16 SMs.
+  // The small levels (<= RF_TAIL_NV vertices, default 6000: 17^3 and below)
+  // run as one launch: one thread-block cluster with hardware barriers, or
+  // with RF_TAIL_MODE=coop a cooperative launch of every co-resident block with
+  // bounded grid barriers; RF_TAIL_NV=0 launches every phase.  Both compute
+  // the launch-per-phase V-cycle bit for bit.  Measured on GB300 at 257^3:
+  // the cluster from 17^3 saves ~0.5 ms per solve (95.4 against 96.0 ms);
+  // from 33^3, or as a cooperative launch, the barrier-separated phases are
+  // no faster than the launches they replace, and a cluster whose first level
+  // is too large for 16 SMs (65^3) costs ~40% of an FP64 LIMEX step.
   g->tail_first = -1;
   g->tail_blocks = 0;
   g->tail_bar = nullptr;   // (a hierarchy buffer: freed with the previous set-up)
   {
     const char* env = getenv("RF_TAIL_NV");
     const char* mode = getenv("RF_TAIL_MODE");
-    const bool cluster = mode && strcmp(mode, "cluster") == 0;
-    const long long thr = env ? atoll(env) : 0;
+    const bool cluster = !(mode && strcmp(mode, "coop") == 0);
+    // the default applies to FP32 coarse levels: with FP64 storage the
+    // whole V-cycle in one kernel spills registers, and the 65^3 FP64 LIMEX
+    // step, its columns one after another, took 113.5 against 99.3 ms
+    const long long thr = env ? atoll(env) : (g->kind == STORE_F64 ? 0 : 6000);
     if (thr > 0)
       for (int l = 1; l < g->nl - 1; ++l)
         if (g->L[l].d.nv <= thr) { g->tail_first = l; break; }

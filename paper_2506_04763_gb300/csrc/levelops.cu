@@ -879,13 +879,20 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
     if (!sync()) return;
   }
   {
+    // x = A^-1 b on the coarsest level, one warp per row with lanes over the
+    // columns and the xor-shuffle sum of coarse_solve_body: the same values
+    // as the coarse-solve kernel, so the tail equals the V-cycle of
+    // one launch per phase bit for bit
     const T* bc = (const T*)P.L[P.coarsest].b;
     T* xc = (T*)P.L[P.coarsest].x;
-    for (int64_t r = gt; r < P.N; r += nthr) {
+    const int lane = (int)(gt & 31);
+    for (int64_t r = gt >> 5; r < P.N; r += nthr >> 5) {   // uniform per warp: nthr is a multiple of 32
       const double* row = P.Ainv + r * P.N;
       double s = 0.0;
-      for (int c = 0; c < P.N; ++c) s += row[c] * (double)bc[c];
-      xc[r] = (T)s;
+      for (int c = lane; c < P.N; c += 32) s += row[c] * (double)bc[c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) xc[r] = (T)s;
     }
     if (!sync()) return;
   }
