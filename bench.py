@@ -36,13 +36,14 @@ class _Skip(Exception):
 
 METRIC = "BiCGSTAB-GMG DoF/s to rel.res 1e-10, FP32-GMG vs FP64, % of HBM peak"
 RTOL = 1e-10
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per colour vertex of
-# a full fine-level FP32 GS colour launch, by vertices per axis of this
-# workload's recipe: ncu captures of the eight colour launches of the second
-# fine sweep in the solve's own launch sequence (caches not flushed, so a
-# launch finds in L2 what its predecessors left); the algorithmic count is 456 B.
-GS_TRAFFIC_PER_COLOUR_VERTEX = {257: 516.6}
-GS_ALGO_PER_COLOUR_VERTEX = 456.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per updated vertex
+# of a full fine-level FP32 GS launch, by launch form (one launch per colour
+# pair, the default, or per colour with RF_GS_PAIRS=0) and vertices per axis of
+# this workload's recipe: ncu captures of the launches of the second fine
+# sweep in the solve's own launch sequence (caches not flushed, so a launch
+# finds in L2 what its predecessors left); the algorithmic count is 456 B.
+GS_TRAFFIC_PER_VERTEX = {"pair": {}, "colour": {257: 516.6}}
+GS_ALGO_PER_VERTEX = 456.0
 # FP64 floating-point operations per vertex of one outer operator application
 # (k_bicg_v / k_bicg_t): 27 blocks x 4 FMA (216 flop), the shift*M diagonal
 # (4 flop) and the fused inner products (<rh, v>: 4 flop; <t, s>, <t, t>: 8
@@ -351,13 +352,15 @@ def main():
     dv = prof[dom]
     achieved = dv["bytes"] / (dv["ms"] / 1e3) / 1e9
     traffic = None
+    form = "colour" if os.environ.get("RF_GS_PAIRS", "1") == "0" else "pair"
     if (dom == "smooth_fine" and a.smoother == "gs8" and a.precision == "fp32"
-            and a.nvert in GS_TRAFFIC_PER_COLOUR_VERTEX):
-        colour_vertices = g.nv / 8.0
-        traffic = {"bytes_per_launch": GS_TRAFFIC_PER_COLOUR_VERTEX[a.nvert] * colour_vertices,
-                   "algorithmic_bytes_per_launch": GS_ALGO_PER_COLOUR_VERTEX * colour_vertices,
-                   "launch": "one full-sweep colour (nv/8 vertices)",
-                   "source": "ncu capture of this size, colour launches in the solve's sequence"}
+            and a.nvert in GS_TRAFFIC_PER_VERTEX[form]):
+        launch_vertices = g.nv / (8.0 if form == "colour" else 4.0)
+        traffic = {"bytes_per_launch": GS_TRAFFIC_PER_VERTEX[form][a.nvert] * launch_vertices,
+                   "algorithmic_bytes_per_launch": GS_ALGO_PER_VERTEX * launch_vertices,
+                   "launch": ("one full-sweep colour (nv/8 vertices)" if form == "colour"
+                              else "one full-sweep colour pair (nv/4 vertices)"),
+                   "source": "ncu capture of this size, launches in the solve's sequence"}
     # the FP64 pipe's roofline of the outer operator (FP64-pipe-bound: 108 FMA
     # per 864 B of J), against the FMA rate measured above
     sp = prof["spmv64"]

@@ -319,13 +319,13 @@ rf_status rf_profile_read(rf_grid* g, int cls, double* ms, int64_t* launches, do
  * operator, and allocates nothing: the LU factors, pivots and status live in
  * a static device array of RF_NOALLOC_MAX_N^2 * 8 bytes plus a little (about
  * 2 MiB), reserved on every GPU that loads the library until the process
- * exits.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and should therefore come before any stream
- * capture.  Calls share the array: calls that overlap on the GPU race and must
- * be serialised by the caller.  Returns RF_EINVAL for N outside
- * [1, RF_NOALLOC_MAX_N] or for pointers that are not device (or managed)
- * memory of the current device, RF_ENONFINITE for a singular matrix or one
- * with non-finite entries; synchronises `stream` before returning. */
+ * exits.  Calls share the array: calls that overlap on the GPU race and must
+ * be serialised by the caller.  Every call reads the status word back and
+ * synchronises `stream`, so no call can be captured into a CUDA graph: on a
+ * stream that is capturing it returns RF_EINVAL before enqueuing anything.
+ * Returns RF_EINVAL for N outside [1, RF_NOALLOC_MAX_N] or for pointers that
+ * are not device (or managed) memory of the current device, RF_ENONFINITE for
+ * a singular matrix or one with non-finite entries. */
 #define RF_NOALLOC_MAX_N 512
 rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ainv, void* stream);
 

@@ -105,6 +105,26 @@ __device__ __forceinline__ double2 ld_keep(const double2* p) {
 }
 #endif
 
+// Stencil blocks that reach the other x-parity run of the vertex's own x-line
+// (dx = -1, +1 with dy = dz = 0).  In a launch that sweeps a pair of colours
+// differing only in x parity (k_gs_pair) these are the only neighbours of the
+// second colour that the first one writes; the second colour reads them
+// coherently at L2 (SAME = true), never through the read-only path.
+template <int NB>
+__host__ __device__ constexpr bool same_line_block(int b) {
+  return NB == 27 ? (b == 12 || b == 14) : (b == 3 || b == 5);
+}
+template <bool SAME, int NB, typename V>
+__device__ __forceinline__ V ld_xn(const V* p, int b) {
+  if (SAME && same_line_block<NB>(b)) return __ldcg(p);
+  return ld_keep(p);
+}
+template <bool SAME, int NB, typename V>
+__device__ __forceinline__ V ld_xn_plain(const V* p, int b) {
+  if (SAME && same_line_block<NB>(b)) return __ldcg(p);
+  return *p;
+}
+
 // One stored 2x2 block as loaded (FP64: two double2; FP32: a float4; FP16:
 // four halves), and its entries in the arithmetic type (FP16: times the row's
 // per-entry FP32 scales).  Loading and unpacking are split so that a batch of
@@ -202,7 +222,7 @@ __device__ __forceinline__ void f16_half(const uint4& u, int h, const float4& sc
 // The FP16 stencil sum, slot by slot: CP pairs (2 CP blocks) and their x values
 // loaded per memory round trip, then summed.  Per-block, batched and
 // shared-matrix FP16 kernels all sum in this slot order with blk_acc.
-template <int NB, int CP>
+template <int NB, int CP, bool SAME = false>
 __device__ __forceinline__ void stencil_sum_f16(const LevelOp& L, int64_t p, int par,
                                                 const float2* __restrict__ x, bool skip_centre, uint32_t skipmask,
                                                 float& s0, float& s1) {
@@ -228,7 +248,7 @@ __device__ __forceinline__ void stencil_sum_f16(const LevelOp& L, int64_t p, int
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int b = f16_block_of_slot(NB, 2 * q + h);
-        if (use[c][h]) xv[c][h] = ld_keep(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]));
+        if (use[c][h]) xv[c][h] = ld_xn<SAME, NB>(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]), b);
       }
     }
 #pragma unroll
@@ -248,7 +268,7 @@ __device__ __forceinline__ void stencil_sum_f16(const LevelOp& L, int64_t p, int
 }
 
 // sum over the stencil of blocks * x (centre optionally skipped)
-template <int KIND, int NB>
+template <int KIND, int NB, bool SAME = false>
 __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par,
                                             const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                             bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
@@ -265,7 +285,7 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
     T a[4];
     load_block<KIND>(L.A, L.d.nv, b, p, sc, a);
     const int off = par ? L.nb.off[1][b] : L.nb.off[0][b];
-    const typename V2<T>::t xv = x[p + off];
+    const typename V2<T>::t xv = ld_xn_plain<SAME, NB>(x + p + off, b);
     a0 = blk_acc(a0, a[0], a[1], xv);
     a1 = blk_acc(a1, a[2], a[3], xv);
   }
@@ -285,7 +305,7 @@ __device__ __forceinline__ void stencil_sum(const LevelOp& L, int64_t p, int par
 // memory round trip; an unbatched FP16 kernel loads one pair per round trip.
 __host__ __device__ constexpr int chunk_of(int kind) { return kind == STORE_F16 ? 2 : 9; }
 
-template <int KIND, int NB, int CH>
+template <int KIND, int NB, int CH, bool SAME = false>
 __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p, int par,
                                                     const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                     bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
@@ -308,7 +328,7 @@ __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p,
       skip[c] = (skip_centre && b == C) || ((skipmask >> b) & 1u);
       if (!skip[c]) {
         load_raw<KIND>(L.A, L.d.nv, b, p, raw[c]);
-        xv[c] = ld_keep(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]));
+        xv[c] = ld_xn<SAME, NB>(x + p + (par ? L.nb.off[1][b] : L.nb.off[0][b]), b);
       }
     }
     // unpacked only now: an FP16 block's scaling waits for its load, which
@@ -326,17 +346,17 @@ __device__ __forceinline__ void stencil_sum_batched(const LevelOp& L, int64_t p,
   s0 = a0; s1 = a1;
 }
 
-template <int KIND, int NB, int CH>
+template <int KIND, int NB, int CH, bool SAME = false>
 __device__ __forceinline__ void stencil_sum_any(const LevelOp& L, int64_t p, int par,
                                                 const typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
                                                 bool skip_centre, uint32_t skipmask, typename Ty<KIND>::T& s0,
                                                 typename Ty<KIND>::T& s1) {
   if constexpr (KIND == STORE_F16)
-    stencil_sum_f16<NB, (CH > 0 ? CH : 1)>(L, p, par, x, skip_centre, skipmask, s0, s1);
+    stencil_sum_f16<NB, (CH > 0 ? CH : 1), SAME>(L, p, par, x, skip_centre, skipmask, s0, s1);
   else if constexpr (CH > 0)
-    stencil_sum_batched<KIND, NB, CH>(L, p, par, x, skip_centre, skipmask, s0, s1);
+    stencil_sum_batched<KIND, NB, CH, SAME>(L, p, par, x, skip_centre, skipmask, s0, s1);
   else
-    stencil_sum<KIND, NB>(L, p, par, x, skip_centre, skipmask, s0, s1);
+    stencil_sum<KIND, NB, SAME>(L, p, par, x, skip_centre, skipmask, s0, s1);
 }
 
 // (A x)_p, with A = shift*M - J on the fine level (blocks hold J)
@@ -429,7 +449,27 @@ __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_jacobi(LevelOp L, const 
 }
 
 // ----------------------------------------------------------------- multicolour GS
-// One colour (px,py,pz) of the sweep: x_p <- D_p^-1 (b_p - sum_{q != p} A_pq x_q).
+// One vertex p (x parity px) of a colour: x_p <- D_p^-1 (b_p - sum_{q != p} A_pq x_q).
+template <int KIND, bool FINE, int NB, int CH = 0, bool SAME = false>
+__device__ __forceinline__ void gs_vertex(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                          typename V2<typename Ty<KIND>::T>::t* __restrict__ x, int px, int64_t p,
+                                          uint32_t skipmask) {
+  typedef typename Ty<KIND>::T T;
+  const typename V2<T>::t bv = b[p];
+  T s0, s1;
+  stencil_sum_any<KIND, NB, CH, SAME>(L, p, px, x, true, skipmask, s0, s1);
+  // off-diagonal part of A: fine level A_pq = -J_pq (q != p), coarse A_pq
+  const T r0 = FINE ? bv.x + s0 : bv.x - s0;
+  const T r1 = FINE ? bv.y + s1 : bv.y - s1;
+  T y0, y1;
+  dinv_apply<T>(reinterpret_cast<const T*>(L.Dinv), p, r0, r1, y0, y1);
+  typename V2<T>::t o;
+  o.x = y0;
+  o.y = y1;
+  x[p] = o;
+}
+
+// One colour (px,py,pz) of the sweep.
 // Work item t of the colour: t enumerates the colour's x-runs line by line.
 template <int KIND, bool FINE, int NB, int CH = 0>
 __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
@@ -442,18 +482,7 @@ __device__ __forceinline__ void gs_point(const LevelOp& L, const typename V2<typ
   const int jj = (int)(line - kl * (uint32_t)lines_y), kk = (int)kl;
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
-  const typename V2<T>::t bv = b[p];
-  T s0, s1;
-  stencil_sum_any<KIND, NB, CH>(L, p, px, x, true, skipmask, s0, s1);
-  // off-diagonal part of A: fine level A_pq = -J_pq (q != p), coarse A_pq
-  const T r0 = FINE ? bv.x + s0 : bv.x - s0;
-  const T r1 = FINE ? bv.y + s1 : bv.y - s1;
-  T y0, y1;
-  dinv_apply<T>(reinterpret_cast<const T*>(L.Dinv), p, r0, r1, y0, y1);
-  typename V2<T>::t o;
-  o.x = y0;
-  o.y = y1;
-  x[p] = o;
+  gs_vertex<KIND, FINE, NB, CH>(L, b, x, px, p, skipmask);
 }
 
 template <int KIND, bool FINE, int NB, int CH>
@@ -467,6 +496,56 @@ __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour(LevelOp L, con
   int64_t t = bx * blockDim.x + threadIdx.x;
   if (t >= count) return;
   gs_point<KIND, FINE, NB, CH>(L, b, x, px, py, pz, cnt_x, lines_y, t, skipmask);
+}
+
+// Threads of a colour-pair block (k_gs_pair) at most.
+constexpr int GS_PAIR_MAX_THREADS = 320;
+
+// Vertex of item v of a pair block's run: line l0 + v / cnt of the pair's
+// lines (enumerated y first), position v % cnt in the run of parity px.
+__device__ __forceinline__ int64_t pair_vertex(const Dims& d, int l0, int v, int cnt, int px, int py, int pz,
+                                               int lines_y) {
+  const int li = v / cnt, pos = v - li * cnt;
+  const int line = l0 + li, kl = line / lines_y;
+  const int j = 2 * (line - kl * lines_y) + py, k = 2 * kl + pz;
+  return ((int64_t)j + (int64_t)d.ny * k) * d.nx + (px ? d.E : 0) + pos;
+}
+
+// Two consecutive colours of a sweep that differ only in x parity,
+// (first_px, py, pz) then (1 - first_px, py, pz), in one launch.  A vertex of
+// either colour reaches the other one only on its own x-line (dx = -1, +1 with
+// dy = dz = 0); all its other neighbours have colours that neither of the two
+// writes.  So a block that owns whole x-lines updates the first colour's run
+// of each of its lines, passes a block barrier, and then updates the second
+// colour's runs, reading the just-written neighbours at L2: every vertex sees
+// the values that the two separate colour launches give it, and the sums are
+// the same operations in the same order.  One launch instead of two, and the
+// other colours' x values are gathered once for both.  Block b owns lines
+// [b * lpb, b * lpb + lpb) of the pair (reversed block order: see gs_zigzag).
+template <int KIND, bool FINE, int NB, int CH, int FPX>
+__global__ void __launch_bounds__(GS_PAIR_MAX_THREADS) k_gs_pair(LevelOp L, const typename V2<typename Ty<KIND>::T>::t* __restrict__ b,
+                                                  typename V2<typename Ty<KIND>::T>::t* __restrict__ x,
+                                                  int py, int pz, int lines_y, int nlines, int lpb,
+                                                  uint32_t skip_first, uint32_t skip_second, int reverse) {
+  rf_pdl_begin();
+  const int bx = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int l0 = bx * lpb;
+  const int nl = min(lpb, nlines - l0);
+  // one vertex per thread and run: the launch gives every block at least
+  // lpb * (nx + 1) / 2 threads (a loop here would make the compiler hoist
+  // the stencil's address arithmetic and double the registers)
+  const int v = threadIdx.x;
+  {
+    const int cnt = FPX ? L.d.nx / 2 : (L.d.nx + 1) / 2;
+    if (v < nl * cnt)
+      gs_vertex<KIND, FINE, NB, CH, false>(L, b, x, FPX, pair_vertex(L.d, l0, v, cnt, FPX, py, pz, lines_y), skip_first);
+  }
+  __syncthreads();
+  {
+    const int cnt = FPX ? (L.d.nx + 1) / 2 : L.d.nx / 2;
+    if (v < nl * cnt)
+      gs_vertex<KIND, FINE, NB, CH, true>(L, b, x, 1 - FPX, pair_vertex(L.d, l0, v, cnt, 1 - FPX, py, pz, lines_y), skip_second);
+  }
 }
 
 // ----------------------------------------------------------------- transfers
@@ -1513,6 +1592,38 @@ __global__ void __launch_bounds__(CH > 0 ? 256 : 512) k_gs_colour_b(const __grid
   gs_point<KIND, FINE, NB, CH>(sys_op(L, P), (const V*)P.in0, (V*)P.out, px, py, pz, cnt_x, lines_y, t, skipmask);
 }
 
+// k_gs_pair for a batch of systems (blockIdx.y); a block of a converged
+// system returns as a whole, before the barrier.
+template <int KIND, bool FINE, int NB, int CH, int FPX>
+__global__ void __launch_bounds__(GS_PAIR_MAX_THREADS) k_gs_pair_b(const __grid_constant__ LevelOp L,
+                                                                    const __grid_constant__ SysBatch B, int py, int pz,
+                                                                    int lines_y, int nlines, int lpb,
+                                                                    uint32_t skip_first, uint32_t skip_second,
+                                                                    int reverse) {
+  typedef typename V2<typename Ty<KIND>::T>::t V;
+  rf_pdl_begin();
+  const SysLevel& P = B.s[blockIdx.y];
+  if (sys_done(P)) return;
+  const LevelOp Ls = sys_op(L, P);
+  const V* b = (const V*)P.in0;
+  V* x = (V*)P.out;
+  const int bx = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int l0 = bx * lpb;
+  const int nl = min(lpb, nlines - l0);
+  const int v = threadIdx.x;
+  {
+    const int cnt = FPX ? L.d.nx / 2 : (L.d.nx + 1) / 2;
+    if (v < nl * cnt)
+      gs_vertex<KIND, FINE, NB, CH, false>(Ls, b, x, FPX, pair_vertex(L.d, l0, v, cnt, FPX, py, pz, lines_y), skip_first);
+  }
+  __syncthreads();
+  {
+    const int cnt = FPX ? (L.d.nx + 1) / 2 : L.d.nx / 2;
+    if (v < nl * cnt)
+      gs_vertex<KIND, FINE, NB, CH, true>(Ls, b, x, 1 - FPX, pair_vertex(L.d, l0, v, cnt, 1 - FPX, py, pz, lines_y), skip_second);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_restrict_planes_b(Dims df, Dims dc, const __grid_constant__ SysBatch B) {
   const SysLevel& P = B.s[blockIdx.z];
@@ -1559,7 +1670,7 @@ __global__ void k_cast_f32_f64_b(int64_t n, const __grid_constant__ SysBatch B) 
 // systems' vectors, each with its own shift (and D^-1).  Per system the sums
 // run block by block in the order of stencil_sum with the same expressions,
 // so the values equal the single-system kernels' bit for bit.
-template <int KIND, int NB, int NS>
+template <int KIND, int NB, int NS, bool SAME = false>
 __device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, int64_t p, int par, bool skip_centre,
                                            uint32_t skipmask, const bool (&act)[NS],
                                            typename Ty<KIND>::T (&s0)[NS], typename Ty<KIND>::T (&s1)[NS]) {
@@ -1593,7 +1704,7 @@ __device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, 
 #pragma unroll
         for (int q = 0; q < NS; ++q) {
           if (!act[q]) continue;
-          const V xv = ((const V*)G[q].in1)[p + off];
+          const V xv = ld_xn_plain<SAME, NB>((const V*)G[q].in1 + p + off, b);
           s0[q] = blk_acc(s0[q], a[0], a[1], xv);
           s1[q] = blk_acc(s1[q], a[2], a[3], xv);
         }
@@ -1611,7 +1722,7 @@ __device__ __forceinline__ void shared_row(const LevelOp& L, const SysLevel* G, 
 #pragma unroll
     for (int q = 0; q < NS; ++q) {
       if (!act[q]) continue;
-      const V xv = ((const V*)G[q].in1)[p + off];
+      const V xv = ld_xn_plain<SAME, NB>((const V*)G[q].in1 + p + off, b);
       s0[q] = blk_acc(s0[q], a[0], a[1], xv);
       s1[q] = blk_acc(s1[q], a[2], a[3], xv);
     }
@@ -1691,6 +1802,30 @@ __global__ void __launch_bounds__(256) k_jacobi_shared(const __grid_constant__ L
   }
 }
 
+// One vertex p (x parity px) of a GS colour for a group of systems that share
+// the finest level's matrix.
+template <int KIND, int NB, int NS, bool SAME = false>
+__device__ __forceinline__ void gs_shared_vertex(const LevelOp& L, const SysLevel* G, int64_t p, int px,
+                                                 uint32_t skipmask, const bool (&act)[NS]) {
+  typedef typename Ty<KIND>::T T;
+  typedef typename V2<T>::t V;
+  T s0[NS], s1[NS];
+  shared_row<KIND, NB, NS, SAME>(L, G, p, px, true, skipmask, act, s0, s1);
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    if (!act[q]) continue;
+    const V bv = ((const V*)G[q].in0)[p];
+    const T r0 = bv.x + s0[q];   // fine level: A_pq = -J_pq off the diagonal
+    const T r1 = bv.y + s1[q];
+    T y0, y1;
+    dinv_apply<T>(reinterpret_cast<const T*>(G[q].Dinv), p, r0, r1, y0, y1);
+    V o;
+    o.x = y0;
+    o.y = y1;
+    ((V*)G[q].out)[p] = o;
+  }
+}
+
 template <int KIND, int NB, int NS>
 __global__ void __launch_bounds__(256) k_gs_colour_shared(const __grid_constant__ LevelOp L,
                                                           const __grid_constant__ SysBatch B, int px, int py, int pz,
@@ -1712,20 +1847,36 @@ __global__ void __launch_bounds__(256) k_gs_colour_shared(const __grid_constant_
   const int jj = (int)(line - kl * (uint32_t)lines_y), kk = (int)kl;
   const int j = 2 * jj + py, k = 2 * kk + pz;
   const int64_t p = ((int64_t)j + (int64_t)L.d.ny * k) * L.d.nx + (px ? L.d.E : 0) + pos;
-  T s0[NS], s1[NS];
-  shared_row<KIND, NB, NS>(L, G, p, px, true, skipmask, act, s0, s1);
+  gs_shared_vertex<KIND, NB, NS>(L, G, p, px, skipmask, act);
+}
+
+// k_gs_pair for groups of NS systems that share one matrix (blockIdx.y: group).
+template <int KIND, int NB, int NS, int FPX>
+__global__ void __launch_bounds__(GS_PAIR_MAX_THREADS) k_gs_pair_shared(const __grid_constant__ LevelOp L,
+                                                                         const __grid_constant__ SysBatch B, int py,
+                                                                         int pz, int lines_y, int nlines, int lpb,
+                                                                         uint32_t skip_first, uint32_t skip_second,
+                                                                         int reverse) {
+  rf_pdl_begin();
+  const SysLevel* G = B.s + blockIdx.y * NS;
+  bool act[NS];
 #pragma unroll
-  for (int q = 0; q < NS; ++q) {
-    if (!act[q]) continue;
-    const V bv = ((const V*)G[q].in0)[p];
-    const T r0 = bv.x + s0[q];   // fine level: A_pq = -J_pq off the diagonal
-    const T r1 = bv.y + s1[q];
-    T y0, y1;
-    dinv_apply<T>(reinterpret_cast<const T*>(G[q].Dinv), p, r0, r1, y0, y1);
-    V o;
-    o.x = y0;
-    o.y = y1;
-    ((V*)G[q].out)[p] = o;
+  for (int q = 0; q < NS; ++q) act[q] = !sys_done(G[q]);
+  const int bx = reverse ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+  const int l0 = bx * lpb;
+  const int nl = min(lpb, nlines - l0);
+  const int v = threadIdx.x;
+  {
+    const int cnt = FPX ? L.d.nx / 2 : (L.d.nx + 1) / 2;
+    if (v < nl * cnt)
+      gs_shared_vertex<KIND, NB, NS, false>(L, G, pair_vertex(L.d, l0, v, cnt, FPX, py, pz, lines_y), FPX, skip_first, act);
+  }
+  __syncthreads();
+  {
+    const int cnt = FPX ? (L.d.nx + 1) / 2 : L.d.nx / 2;
+    if (v < nl * cnt)
+      gs_shared_vertex<KIND, NB, NS, true>(L, G, pair_vertex(L.d, l0, v, cnt, 1 - FPX, py, pz, lines_y), 1 - FPX,
+                                           skip_second, act);
   }
 }
 
@@ -1809,9 +1960,90 @@ static void for_colours(const Dims& d, bool forward, bool zero_start, bool flip,
   }
 }
 
+// Colour pairs in one launch each (k_gs_pair) on FP32 and FP16 levels;
+// RF_GS_PAIRS=0 launches every colour on its own.  Both give bitwise the same
+// sweep.
+static bool gs_pairs() {
+  const char* e = getenv("RF_GS_PAIRS");
+  return !(e && atoi(e) == 0);
+}
+
+// Lines per block and threads of a pair launch: enough whole warps for the
+// longer run of all the block's lines at once (a thread updates one vertex
+// of each run), at most GS_PAIR_MAX_THREADS; of these shapes, the one with
+// the fewest idle threads over both runs.  Lines longer than
+// 2 GS_PAIR_MAX_THREADS - 1 vertices have no shape: their colours are
+// launched one by one.
+static bool pair_shape(int nx, int& lpb, int& threads) {
+  const int e = (nx + 1) / 2, o = nx / 2;
+  if (e > GS_PAIR_MAX_THREADS) return false;
+  lpb = 1;
+  threads = ((e + 31) / 32) * 32;
+  double best = -1.0;
+  for (int l = 1; l * e <= GS_PAIR_MAX_THREADS; ++l) {
+    const int t = ((l * e + 31) / 32) * 32;
+    const double eff = (double)l * (e + o) / (2.0 * t);
+    if (eff > best + 1e-9) {
+      best = eff;
+      lpb = l;
+      threads = t;
+    }
+  }
+  return true;
+}
+
+// The pair launches of one sweep: launch(first_px, py, pz, lines_y, nlines,
+// skip_first, skip_second, reverse) per pair, in sweep order.  Colour c =
+// px + 2 py + 4 pz, so the pairs are (0,1), (2,3), ... forward and (7,6),
+// (5,4), ... backward: the sweep's colour order is unchanged.
+template <typename F>
+static void for_colour_pairs(const Dims& d, bool forward, bool zero_start, bool flip, F launch) {
+  const int ncol = 1 << d.dim;
+  const bool zigzag = gs_zigzag();
+  int nl = 0;
+  for (int cc = 0; cc < ncol; cc += 2) {
+    const int c1 = forward ? cc : ncol - 1 - cc;
+    const int c2 = c1 ^ 1;
+    const uint32_t s1 = (zero_start && forward) ? zero_start_mask(d.dim, c1) : 0u;
+    const uint32_t s2 = (zero_start && forward) ? zero_start_mask(d.dim, c2) : 0u;
+    const int py = (c1 >> 1) & 1, pz = (c1 >> 2) & 1;
+    const int lines_y = (d.ny - py + 1) / 2;
+    const int lines_z = d.dim == 3 ? (d.nz - pz + 1) / 2 : 1;
+    const int nlines = lines_y * lines_z;
+    if (nlines <= 0 || d.nx <= 0) continue;
+    const int rev = zigzag ? ((nl + (flip ? 1 : 0)) & 1) : 0;
+    ++nl;
+    launch(c1 & 1, py, pz, lines_y, nlines, s1, s2, rev);
+  }
+}
+
 template <int KIND, bool FINE>
 static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, bool flip, void* s) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
+  // FP64 levels keep one launch per colour: the pair kernel's 129 registers
+  // at 288 threads leave one block per SM, and its sweeps measured 6% slower
+  int lpb = 1, threads = 32;
+  if (KIND != STORE_F64 && gs_pairs() && pair_shape(L.d.nx, lpb, threads)) {
+    for_colour_pairs(L.d, forward, zero_start, flip,
+                     [&](int fpx, int py, int pz, int lines_y, int nlines, uint32_t s1, uint32_t s2, int rev) {
+      const int g = (nlines + lpb - 1) / lpb;
+#define RF_PAIR(NBv, CHv, F)                                                                                     \
+  RF_LAUNCH_PDL((k_gs_pair<KIND, FINE, NBv, CHv, F>), g, threads, 0, s, L, (const V*)b, (V*)x, py, pz, lines_y, \
+                nlines, lpb, s1, s2, rev)
+#define RF_PAIR_PX(NBv, CHv) \
+  if (fpx) RF_PAIR(NBv, CHv, 1); else RF_PAIR(NBv, CHv, 0)
+      if (L.batched) {
+        if (L.d.nb == 27) { RF_PAIR_PX(27, chunk_of(KIND)); } else { RF_PAIR_PX(9, chunk_of(KIND)); }
+      } else if (L.d.nb == 27) {
+        RF_PAIR_PX(27, 0);
+      } else {
+        RF_PAIR_PX(9, 0);
+      }
+#undef RF_PAIR_PX
+#undef RF_PAIR
+    });
+    return;
+  }
   const int bs = L.block > 0 ? L.block : 256;
   for_colours(L.d, forward, zero_start, flip,
               [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
@@ -1937,6 +2169,27 @@ static void jacobi_bt(const LevelOp& L, const SysBatch& B, double omega, bool ze
 
 template <int KIND, bool FINE>
 static void gs_bt(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, bool flip, void* s) {
+  int lpb = 1, threads = 32;
+  if (KIND != STORE_F64 && gs_pairs() && pair_shape(L.d.nx, lpb, threads)) {   // as in gs_t
+    for_colour_pairs(L.d, forward, zero_start, flip,
+                     [&](int fpx, int py, int pz, int lines_y, int nlines, uint32_t s1, uint32_t s2, int rev) {
+      const dim3 g((unsigned)((nlines + lpb - 1) / lpb), (unsigned)B.n);
+#define RF_PAIR(NBv, CHv, F) \
+  RF_LAUNCH_PDL((k_gs_pair_b<KIND, FINE, NBv, CHv, F>), g, threads, 0, s, L, B, py, pz, lines_y, nlines, lpb, s1, s2, rev)
+#define RF_PAIR_PX(NBv, CHv) \
+  if (fpx) RF_PAIR(NBv, CHv, 1); else RF_PAIR(NBv, CHv, 0)
+      if (L.batched) {
+        if (L.d.nb == 27) { RF_PAIR_PX(27, chunk_of(KIND)); } else { RF_PAIR_PX(9, chunk_of(KIND)); }
+      } else if (L.d.nb == 27) {
+        RF_PAIR_PX(27, 0);
+      } else {
+        RF_PAIR_PX(9, 0);
+      }
+#undef RF_PAIR_PX
+#undef RF_PAIR
+    });
+    return;
+  }
   const int bs = L.block > 0 ? L.block : 256;
   for_colours(L.d, forward, zero_start, flip,
               [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
@@ -2018,6 +2271,22 @@ static void jacobi_sh(const LevelOp& L, const SysBatch& B, double omega, bool ze
 }
 template <int KIND, int NS>
 static void gs_sh(const LevelOp& L, const SysBatch& B, bool forward, bool zero_start, bool flip, void* s) {
+  int lpb = 1, threads = 32;
+  if (KIND != STORE_F64 && gs_pairs() && pair_shape(L.d.nx, lpb, threads)) {   // as in gs_t
+    for_colour_pairs(L.d, forward, zero_start, flip,
+                     [&](int fpx, int py, int pz, int lines_y, int nlines, uint32_t s1, uint32_t s2, int rev) {
+      const dim3 g((unsigned)((nlines + lpb - 1) / lpb), (unsigned)(B.n / NS));
+#define RF_PAIR(NBv, F) \
+  RF_LAUNCH_PDL((k_gs_pair_shared<KIND, NBv, NS, F>), g, threads, 0, s, L, B, py, pz, lines_y, nlines, lpb, s1, s2, rev)
+      if (L.d.nb == 27) {
+        if (fpx) RF_PAIR(27, 1); else RF_PAIR(27, 0);
+      } else {
+        if (fpx) RF_PAIR(9, 1); else RF_PAIR(9, 0);
+      }
+#undef RF_PAIR
+    });
+    return;
+  }
   for_colours(L.d, forward, zero_start, flip,
               [&](int px, int py, int pz, int cnt_x, int lines_y, int64_t count, uint32_t skip, int rev) {
     const dim3 g((unsigned)((count + 255) / 256), (unsigned)(B.n / NS));

@@ -78,13 +78,20 @@ bool on_this_device(const void* p) {
 
 extern "C" rf_status rf_dense_inverse_noalloc(int N, const double* A, double* Ainv, void* stream) {
   if (N < 1 || N > kMaxN) return RF_EINVAL;   // beyond the reserved scratch
-  if (!A || !Ainv || !on_this_device(A) || !on_this_device(Ainv)) return RF_EINVAL;
+  if (!A || !Ainv) return RF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return RF_EINVAL;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return RF_EINVAL;   // the read-back below cannot be captured
+  if (!on_this_device(A) || !on_this_device(Ainv)) return RF_EINVAL;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return RF_ECUDA;
   double* LU = static_cast<double*>(base);
   int* piv = reinterpret_cast<int*>(LU + kMat);
   int* status = piv + kMaxN;
-  cudaStream_t s = (cudaStream_t)stream;
   if (cudaMemcpyAsync(LU, A, sizeof(double) * (size_t)N * N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return RF_ECUDA;
   if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return RF_ECUDA;

@@ -883,3 +883,86 @@ def test_reversed_gs_colour_launches_are_bitwise_equal(precision, monkeypatch):
     a, b_ = out["0"], out["1"]
     assert np.array_equal(a[0], b_[0]) and a[1] == b_[1]
     assert np.array_equal(a[2], b_[2]) and a[3:] == b_[3:]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("shape,dim,tail", [((17, 13, 25), 3, "0"), ((33, 9, 17), 3, "default"),
+                                            ((9, 17, 5), 3, "0"), ((65, 33), 2, "0")])
+def test_colour_pair_launches_are_bitwise_equal(precision, shape, dim, tail, monkeypatch):
+    """Colours (0,py,pz) and (1,py,pz) reach each other only on their own
+    x-line, so the GS launches that sweep such a pair in one kernel (a block
+    barrier between the even- and the odd-x run of each line; the default)
+    update every vertex from the same neighbour values as one launch per
+    colour (RF_GS_PAIRS=0).  Whole solves (forward sweeps from zero, forward
+    and backward sweeps on every smoothed level) and one forward sweep of
+    each smoothed level are bitwise equal.  The shapes cover 2D and 3D,
+    several line lengths, and the small levels launched one by one
+    (RF_TAIL_NV=0) or in the one-launch tail."""
+    prob = I.random_problem(dim, shape if dim == 3 else shape + (1,), 61)
+    levels = _levels(prob)
+    assert levels >= 2
+    dims = [tuple(prob["n"][:dim])]
+    for _ in range(levels - 1):
+        dims.append(tuple((t - 1) // 2 + 1 for t in dims[-1]))
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RF_GS_PAIRS", mode)
+        if tail == "0":
+            monkeypatch.setenv("RF_TAIL_NV", "0")
+        else:
+            monkeypatch.delenv("RF_TAIL_NV", raising=False)
+        g, F = _assembled(prob)
+        g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(levels, "gs8", precision=precision))
+        b = torch.tensor(F, device="cuda")
+        x = torch.empty_like(b)
+        sinfo = g.solve(0, b, x, rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert sinfo["status"] == 0, (mode, sinfo)
+        rng = np.random.default_rng(7)
+        sweeps = []
+        for lev in range(levels - 1):
+            nv = int(np.prod(dims[lev]))
+            bl = rng.standard_normal(2 * nv)
+            xl = rng.standard_normal(2 * nv)
+            sweeps.append(g.apply(rf.RF_OP_SMOOTH, lev, 0, bl, xl)[:2 * nv])
+        out[mode] = (x.cpu().numpy(), sinfo["iterations"], sweeps)
+        g.close()
+    a, c = out["0"], out["1"]
+    assert a[1] == c[1] and np.array_equal(a[0], c[0])
+    for lev, (s0, s1) in enumerate(zip(a[2], c[2])):
+        assert np.array_equal(s0, s1), lev
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_colour_pair_launches_in_batched_paths_are_bitwise_equal(precision, monkeypatch):
+    """The colour-pair GS launches of the batched kernels: a LIMEX step whose
+    columns run in batched rounds on one shared Jacobian (the shared-matrix
+    kernels) and an ensemble step over grids of equal and unequal shapes (the
+    per-system batched kernels) are bitwise those of one launch per colour."""
+    one = I.random_problem(3, (17, 13, 25), 62)
+    probs = [I.random_problem(3, (17, 17, 17), 63), I.random_problem(3, (17, 17, 17), 64),
+             I.random_problem(3, (9, 9, 9), 65), I.random_problem(2, (33, 33), 66)]
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("RF_GS_PAIRS", mode)
+        monkeypatch.setenv("RF_LIMEX_BATCH", "1")
+        g = _grid(one)
+        u = torch.tensor(one["u0"], device="cuda")
+        info = g.limex_step(u, 5.0, kappa=3, tol=1e9, gmg=rf.gmg_opts(_levels(one), "gs8", precision=precision),
+                            rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, (mode, info)
+        res = [(u.cpu().numpy(), info["iterations"], info["eps"])]
+        g.close()
+        monkeypatch.delenv("RF_LIMEX_BATCH")
+        grids = [_grid(p) for p in probs]
+        us = [torch.tensor(p["u0"], device="cuda") for p in probs]
+        gm = [rf.gmg_opts(_levels(p), "gs8", precision=precision) for p in probs]
+        st, infos = rf.limex_step_batched(grids, us, 5.0, kappa=3, tol=1e9, gmg=gm, rtol=1e-11, max_concurrent=2)
+        torch.cuda.synchronize()
+        res += [(v.cpu().numpy(), i["iterations"], i["eps"], i["status"]) for v, i in zip(us, infos)]
+        for gg in grids:
+            gg.close()
+        out[mode] = res
+    for a, c in zip(out["0"], out["1"]):
+        assert np.array_equal(a[0], c[0]) and a[1:] == c[1:]

@@ -95,3 +95,26 @@ def test_dense_inverse_noalloc_at_the_size_limit_and_singular_input(rf):
     assert _call(rf, N, A_dev, Ainv) == rf.RF_OK
     torch.cuda.synchronize()
     assert np.abs(Ainv.cpu().numpy() - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_dense_inverse_noalloc_refuses_a_capturing_stream(rf):
+    """The call reads its status back and synchronises, so it cannot be part
+    of a CUDA graph: on a capturing stream it returns RF_EINVAL and enqueues
+    nothing, and the capture itself stays valid."""
+    N = 64
+    M = np.random.default_rng(13).standard_normal((N, N)) + 8.0 * np.eye(N)
+    A_dev = torch.tensor(M, device="cuda")
+    Ainv = torch.zeros_like(A_dev)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+        st = _call(rf, N, A_dev, Ainv)
+        Ainv.add_(1.0)                       # keeps the captured graph non-empty
+    assert st == rf.RF_EINVAL
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(Ainv, torch.ones_like(Ainv))
+    assert _call(rf, N, A_dev, Ainv) == rf.RF_OK      # outside a capture it works
+    torch.cuda.synchronize()
+    assert np.abs(Ainv.cpu().numpy() - np.linalg.inv(M)).max() <= 1e-11 * np.abs(np.linalg.inv(M)).max()
