@@ -42,7 +42,7 @@ RTOL = 1e-10
 # this workload's recipe: ncu captures of the launches of the second fine
 # sweep in the solve's own launch sequence (caches not flushed, so a launch
 # finds in L2 what its predecessors left); the algorithmic count is 456 B.
-GS_TRAFFIC_PER_VERTEX = {"pair": {}, "colour": {257: 516.6}}
+GS_TRAFFIC_PER_VERTEX = {"pair": {257: 496.2}, "colour": {257: 516.6}}
 GS_ALGO_PER_VERTEX = 456.0
 # FP64 floating-point operations per vertex of one outer operator application
 # (k_bicg_v / k_bicg_t): 27 blocks x 4 FMA (216 flop), the shift*M diagonal
