@@ -21,9 +21,12 @@
  *   Vectors: double, length 2*nv, u[2v] = p_w (Pa), u[2v+1] = S_n; residual
  *     F[2v] water mass balance, F[2v+1] NAPL mass balance (kg/s).
  *   Pointers: every array argument may be HOST or DEVICE memory (the library
- *     asks the CUDA driver which); host buffers are staged through device
- *     memory inside the call, device buffers are used in place.  All inputs
- *     stay owned by the caller and are only borrowed for the call.
+ *     asks the CUDA driver which); device buffers are used in place.  State
+ *     and solution vectors in page-locked host memory (cudaHostAlloc, or
+ *     cudaHostRegister with mapping) are read and written by the library's
+ *     kernels directly over the CPU-GPU interconnect; other host buffers
+ *     are staged through device memory inside the call.  All inputs stay
+ *     owned by the caller and are only borrowed for the call.
  *   Streams: every call is ordered on the given cudaStream_t (NULL = legacy
  *     default stream).  Calls that return numbers on the host (info structs,
  *     host outputs) synchronise that stream before returning.

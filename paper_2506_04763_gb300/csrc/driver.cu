@@ -375,10 +375,36 @@ static cudaError_t to_device(void* dst, const void* src, size_t bytes, void* str
                          (cudaStream_t)stream);
 }
 
+// The device's address of page-locked host memory (cudaHostAlloc, or
+// cudaHostRegister with mapping), or null for any other pointer.  Kernels
+// read and write such memory directly over the CPU-GPU interconnect.
+static void* mapped_host_ptr(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// Host vectors in page-locked memory are permuted by the kernels straight
+// from / into the host buffer (RF_HOST_DIRECT=0: staged through device
+// memory with cudaMemcpyAsync, as pageable memory always is).
+static bool host_direct() {
+  static const bool on = [] {
+    const char* e = getenv("RF_HOST_DIRECT");
+    return !(e && atoi(e) == 0);
+  }();
+  return on;
+}
+
 // natural-order pairs (host or device) -> parity-split device pairs
 static rf_status pairs_in(rf_grid* g, const Dims& d, const double* src, double* dst_p, void* s) {
   if (is_device_ptr(src)) {
     launch_perm_to_p(d, src, dst_p, s);
+  } else if (void* m = host_direct() ? mapped_host_ptr(src) : nullptr) {
+    launch_perm_to_p(d, (const double*)m, dst_p, s);
   } else {
     CU(cudaMemcpyAsync(g->nat_a, src, sizeof(double) * 2 * d.nv, cudaMemcpyHostToDevice, (cudaStream_t)s));
     launch_perm_to_p(d, g->nat_a, dst_p, s);
@@ -392,6 +418,10 @@ static rf_status pairs_out(rf_grid* g, const Dims& d, const double* src_p, doubl
   if (is_device_ptr(dst)) {
     launch_perm_from_p(d, src_p, dst, s);
     CU(cudaGetLastError());
+  } else if (void* m = host_direct() ? mapped_host_ptr(dst) : nullptr) {
+    launch_perm_from_p(d, src_p, (double*)m, s);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize((cudaStream_t)s));
   } else {
     launch_perm_from_p(d, src_p, g->nat_b, s);
     CU(cudaMemcpyAsync(dst, g->nat_b, sizeof(double) * 2 * d.nv, cudaMemcpyDeviceToHost, (cudaStream_t)s));

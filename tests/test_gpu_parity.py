@@ -966,3 +966,52 @@ def test_colour_pair_launches_in_batched_paths_are_bitwise_equal(precision, monk
         out[mode] = res
     for a, c in zip(out["0"], out["1"]):
         assert np.array_equal(a[0], c[0]) and a[1:] == c[1:]
+
+
+def test_host_buffers_pinned_pageable_and_device_agree():
+    """State and solution vectors may be device memory, page-locked host
+    memory (read and written by the permutation kernels over the CPU-GPU
+    interconnect) or pageable host memory (staged with copies): a solve and a
+    LIMEX step give bitwise the same results for all three."""
+    prob = I.random_problem(3, (17, 9, 13), 71)
+    g, F = _assembled(prob)
+    g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(_levels(prob), "gs8", precision="fp32"))
+    n = F.size
+    pinned_b = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pinned_x = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    pinned_b.copy_(torch.from_numpy(F))
+    xs = {}
+    b_pg, x_pg = F.copy(), np.full(n, np.nan)
+    info = g.solve(0, b_pg, x_pg, rtol=1e-11, max_it=300)
+    assert info["status"] == 0
+    xs["pageable"] = x_pg
+    pinned_x.fill_(float("nan"))
+    info = g.solve(0, pinned_b.numpy(), pinned_x.numpy(), rtol=1e-11, max_it=300)
+    assert info["status"] == 0
+    xs["pinned"] = pinned_x.numpy().copy()
+    b_d = torch.tensor(F, device="cuda")
+    x_d = torch.full_like(b_d, float("nan"))
+    info = g.solve(0, b_d, x_d, rtol=1e-11, max_it=300)
+    torch.cuda.synchronize()
+    assert info["status"] == 0
+    xs["device"] = x_d.cpu().numpy()
+    assert np.array_equal(xs["pageable"], xs["pinned"]) and np.array_equal(xs["pageable"], xs["device"])
+    g.close()
+    us = {}
+    for kind in ("pageable", "pinned", "device"):
+        g = _grid(prob)
+        if kind == "pageable":
+            u = prob["u0"].copy()
+        elif kind == "pinned":
+            u = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            u.copy_(torch.from_numpy(prob["u0"]))
+            u = u.numpy()
+        else:
+            u = torch.tensor(prob["u0"], device="cuda")
+        info = g.limex_step(u, 5.0, kappa=2, tol=1e9, gmg=rf.gmg_opts(_levels(prob), "gs8", precision="fp32"),
+                            rtol=1e-11, max_it=300)
+        torch.cuda.synchronize()
+        assert info["status"] == 0, (kind, info)
+        us[kind] = u.cpu().numpy() if kind == "device" else np.array(u, copy=True)
+        g.close()
+    assert np.array_equal(us["pageable"], us["pinned"]) and np.array_equal(us["pageable"], us["device"])
