@@ -2020,8 +2020,9 @@ static void for_colour_pairs(const Dims& d, bool forward, bool zero_start, bool 
 template <int KIND, bool FINE>
 static void gs_t(const LevelOp& L, const void* b, void* x, bool forward, bool zero_start, bool flip, void* s) {
   typedef typename V2<typename Ty<KIND>::T>::t V;
-  // FP64 levels keep one launch per colour: the pair kernel's 129 registers
-  // at 288 threads leave one block per SM, and its sweeps measured 6% slower
+  // FP64 levels keep one launch per colour: with pairs the all-FP64 solve
+  // measured 3% slower (its fine smoother 6%), and the batched FP64 pair
+  // kernel needs 129 registers, one 288-thread block per SM
   int lpb = 1, threads = 32;
   if (KIND != STORE_F64 && gs_pairs() && pair_shape(L.d.nx, lpb, threads)) {
     for_colour_pairs(L.d, forward, zero_start, flip,
