@@ -1084,6 +1084,13 @@ extern "C" rf_status rf_gmg_setup(rf_grid* g, const double* shifts, int nshift, 
           P.L[l].r = g->L[l].r;
           P.L[l].t = g->L[l].t;
         }
+        // the cluster form with the FP32 levels' matrices in shared memory
+        // (GS smoother; RF_TAIL_SMEM=0 keeps them in global memory): when
+        // every CTA's rows fit
+        const char* sm_env = getenv("RF_TAIL_SMEM");
+        if (g->tail_blocks == 0 && g->L[g->tail_first].kind == STORE_F32 && o->smoother == RF_SMOOTH_GS8 &&
+            !(sm_env && atoi(sm_env) == 0))
+          tail_sm_plan(P, g->d.nb, g->tail_cs);
       }
   }
   CU(cudaStreamSynchronize((cudaStream_t)s));
@@ -1178,6 +1185,7 @@ static void vcycle_level(rf_grid* g, int l, int sh, const void* b, void* x, void
     }
     ProfScope ps(g, s, RF_PROF_COARSE_LEVELS, by, 1);
     if (g->tail_blocks > 0) launch_vcycle_coop(g->tail[sh], k, g->d.nb, g->tail_blocks, s);
+    else if (g->tail[sh].sm_bytes > 0) launch_vcycle_tail_sm(g->tail[sh], g->d.nb, s);
     else launch_vcycle_tail(g->tail[sh], k, g->d.nb, g->tail_cs, s);
     return;
   }

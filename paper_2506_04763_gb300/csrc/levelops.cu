@@ -901,10 +901,44 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned* bar, unsigned expect
   return s_ok != 0;
 }
 
+// Shared-memory rows of the tail (k_vcycle_tail_sm, FP32 levels).  A row's
+// stencil sum takes its blocks from shared memory (sA: block b of local row
+// lr at sA[b * rows + lr]) and gathers all its x values first, then sums the
+// blocks in stencil order with blk_acc: the values of stencil_sum_batched.
+// x is read with ordinary (coherent) loads: other CTAs of the cluster wrote it
+// in earlier phases.
+template <int NB>
+__device__ __forceinline__ void sm_row_sum(const LevelOp& L, const float4* __restrict__ sA, int rows, int lr,
+                                           int64_t p, int par, const float2* x, bool skip_centre,
+                                           uint32_t skipmask, float& s0, float& s1) {
+  constexpr int C = NB == 27 ? 13 : 4;
+  float2 xv[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (!((skip_centre && b == C) || ((skipmask >> b) & 1u))) xv[b] = x[p + (par ? L.nb.off[1][b] : L.nb.off[0][b])];
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    if ((skip_centre && b == C) || ((skipmask >> b) & 1u)) continue;
+    const float4 a = sA[b * rows + lr];
+    a0 = blk_acc(a0, a.x, a.y, xv[b]);
+    a1 = blk_acc(a1, a.z, a.w, xv[b]);
+  }
+  s0 = a0;
+  s1 = a1;
+}
+
+// The line owned as item i by CTA `rank` of a cluster of cs CTAs.
+__device__ __forceinline__ int sm_line(int rank, int cs, int i) { return rank + cs * i; }
+
 // The V-cycle below level P.first; sync() separates phases and returns false
-// when the launch must end (coop: a barrier gave up).
-template <int KIND, int NB, typename Sync>
-__device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt, int64_t nthr, Sync&& sync) {
+// when the launch must end (coop: a barrier gave up).  SM: the shared-memory
+// form (FP32 levels, GS smoother; sm holds this CTA's rows, rank is its rank
+// in the cluster), whose GS and residual phases update the vertices of the
+// CTA's own x-lines.
+template <int KIND, int NB, bool SM = false, typename Sync>
+__device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt, int64_t nthr, Sync&& sync,
+                                                 const float4* sm = nullptr, int rank = 0) {
   typedef typename Ty<KIND>::T T;
   typedef typename V2<T>::t V;
   // batched stencil loads (a thread's round trips set a phase's time); FP64
@@ -912,6 +946,38 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
   constexpr int CH = KIND == STORE_F64 ? 3 : chunk_of(KIND);
   const int ncol = 1 << P.L[P.first].op.d.dim;
   V* curs[RF_MAXL];
+  auto gs_sweep_sm = [&](int l, const LevelOp& op, const V* b, V* x, bool forward, bool zero_start) {
+    const int nx = op.d.nx, ny = op.d.ny, nlines = op.d.ny * (op.d.dim == 3 ? op.d.nz : 1);
+    const int rows = P.sm_rows[l];
+    const float4* sA = sm + P.sm_base[l];
+    const float* sD = reinterpret_cast<const float*>(sA + NB * rows);
+    for (int cc = 0; cc < ncol; ++cc) {
+      const int col = forward ? cc : ncol - 1 - cc;
+      const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
+      const int cnt = px ? nx / 2 : (nx + 1) / 2;
+      const uint32_t skip = (zero_start && forward) ? P.zmask[col] : 0u;
+      const int items = P.sm_lines[l] * cnt;
+      for (int t = threadIdx.x; t < items; t += blockDim.x) {
+        const int i = t / cnt, pos = t - i * cnt;
+        const int Ln = sm_line(rank, P.sm_cs, i);
+        if (Ln >= nlines) continue;
+        const int k = Ln / ny, j = Ln - k * ny;
+        if ((j & 1) != py || (k & 1) != pz) continue;
+        const int u = (px ? op.d.E : 0) + pos;
+        const int64_t p = (int64_t)Ln * nx + u;
+        const int lr = i * nx + u;
+        const float2 bv = ((const float2*)b)[p];
+        float s0, s1;
+        sm_row_sum<NB>(op, sA, rows, lr, p, px, (const float2*)x, true, skip, s0, s1);
+        const float r0 = bv.x - s0, r1 = bv.y - s1;   // coarse level: A_pq as stored
+        float y0, y1;
+        dinv_apply<float>(sD, lr, r0, r1, y0, y1);
+        ((float2*)x)[p] = make_float2(y0, y1);
+      }
+      if (!sync()) return false;
+    }
+    return true;
+  };
   auto gs_sweep = [&](const LevelOp& op, const V* b, V* x, bool forward, bool zero_start) {
     for (int cc = 0; cc < ncol; ++cc) {
       const int col = forward ? cc : ncol - 1 - cc;
@@ -938,8 +1004,13 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
     V* tmp = (V*)Lv.t;
     V* cur = x;
     if (P.smoother == 1) {
-      for (int sw = 0; sw < P.nu1; ++sw)
-        if (!gs_sweep(Lv.op, b, x, true, sw == 0)) return;
+      for (int sw = 0; sw < P.nu1; ++sw) {
+        if constexpr (SM) {
+          if (!gs_sweep_sm(l, Lv.op, b, x, true, sw == 0)) return;
+        } else {
+          if (!gs_sweep(Lv.op, b, x, true, sw == 0)) return;
+        }
+      }
     } else {
       V* first = ((P.nu1 + P.nu2) & 1) ? x : tmp;
       if (!jacobi_sweep(Lv.op, b, nullptr, first, true)) return;
@@ -951,7 +1022,23 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
       }
     }
     curs[l] = cur;
-    for (int64_t p = gt; p < Lv.op.d.nv; p += nthr) residual_point<KIND, false, NB, CH>(Lv.op, b, cur, (V*)Lv.r, p);
+    if constexpr (SM) {
+      const int nx = Lv.op.d.nx, nlines = Lv.op.d.ny * (Lv.op.d.dim == 3 ? Lv.op.d.nz : 1);
+      const int rows = P.sm_rows[l];
+      const float4* sA = sm + P.sm_base[l];
+      for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int i = t / nx, u = t - i * nx;
+        const int Ln = sm_line(rank, P.sm_cs, i);
+        if (Ln >= nlines) continue;
+        const int64_t p = (int64_t)Ln * nx + u;
+        const float2 bv = ((const float2*)b)[p];
+        float s0, s1;
+        sm_row_sum<NB>(Lv.op, sA, rows, t, p, u >= Lv.op.d.E, (const float2*)cur, false, 0u, s0, s1);
+        ((float2*)Lv.r)[p] = make_float2(bv.x - s0, bv.y - s1);
+      }
+    } else {
+      for (int64_t p = gt; p < Lv.op.d.nv; p += nthr) residual_point<KIND, false, NB, CH>(Lv.op, b, cur, (V*)Lv.r, p);
+    }
     if (!sync()) return;
     for (int64_t p = gt; p < Lc.op.d.nv; p += nthr)
       restrict_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lv.r, (V*)Lc.b, p);
@@ -986,8 +1073,13 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
       prolong_point<T>(Lv.op.d, Lc.op.d, Lv.op.dmask, Lc.op.dmask, (const V*)Lc.x, cur, p);
     if (!sync()) return;
     if (P.smoother == 1) {
-      for (int sw = 0; sw < P.nu2; ++sw)
-        if (!gs_sweep(Lv.op, b, x, false, false)) return;
+      for (int sw = 0; sw < P.nu2; ++sw) {
+        if constexpr (SM) {
+          if (!gs_sweep_sm(l, Lv.op, b, x, false, false)) return;
+        } else {
+          if (!gs_sweep(Lv.op, b, x, false, false)) return;
+        }
+      }
     } else {
       for (int sw = 0; sw < P.nu2; ++sw) {
         V* dst = (cur == x) ? tmp : x;
@@ -1007,6 +1099,51 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail(const __grid_const
     cl.sync();
     return true;
   });
+}
+
+// The tail with the levels' matrices in shared memory: each CTA of the
+// cluster first copies the stencil blocks and D^-1 of its own x-lines
+// (cp.async, 16 bytes per copy; the matrices are not written during the
+// launch), then runs the V-cycle.  Its GS colour phases read no matrix data
+// from L2 or HBM, only the x values around each vertex.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <int NB>
+__global__ void __launch_bounds__(TAIL_THREADS) k_vcycle_tail_sm(const __grid_constant__ TailParams P) {
+  extern __shared__ float4 tail_sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  for (int l = P.first; l < P.coarsest; ++l) {
+    const LevelOp& op = P.L[l].op;
+    const int nx = op.d.nx, nlines = op.d.ny * (op.d.dim == 3 ? op.d.nz : 1);
+    const int rows = P.sm_rows[l], items = (NB + 1) * rows;
+    float4* dst = tail_sm + P.sm_base[l];
+    const float4* A = reinterpret_cast<const float4*>(op.A);
+    const float4* D = reinterpret_cast<const float4*>(op.Dinv);
+    for (int t = threadIdx.x; t < items; t += blockDim.x) {
+      const int b = t / rows, lr = t - b * rows;
+      const int i = lr / nx, u = lr - i * nx;
+      const int Ln = sm_line(rank, P.sm_cs, i);
+      if (Ln >= nlines) continue;
+      const int64_t p = (int64_t)Ln * nx + u;
+      cp_async16(dst + t, b < NB ? A + (int64_t)b * op.d.nv + p : D + p);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int64_t nthr = (int64_t)cl.num_blocks() * blockDim.x;
+  const int64_t gt = (int64_t)rank * blockDim.x + threadIdx.x;
+  vcycle_tail_body<STORE_F32, NB, true>(
+      P, gt, nthr,
+      [&]() {
+        cl.sync();
+        return true;
+      },
+      tail_sm, rank);
 }
 
 template <int KIND, int NB>
@@ -1136,6 +1273,68 @@ int tail_cluster_size(int kind, int nb) {
 
 void fill_tail_masks(TailParams& P, int dim) {
   for (int c = 0; c < 8; ++c) P.zmask[c] = c < (1 << dim) ? zero_start_mask(dim, c) : 0u;
+}
+
+template <int NB>
+static cudaLaunchConfig_t tail_sm_config(int csize, int bytes, void* s, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = tail_config<STORE_F32, NB>(csize, s, attr);
+  cfg.dynamicSmemBytes = (size_t)bytes;
+  return cfg;
+}
+
+template <int NB>
+static bool tail_sm_fits(int csize, int bytes) {
+  if (cudaFuncSetAttribute(k_vcycle_tail_sm<NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_vcycle_tail_sm<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = tail_sm_config<NB>(csize, bytes, nullptr, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_vcycle_tail_sm<NB>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+bool tail_sm_plan(TailParams& P, int nb, int csize) {
+  P.sm_bytes = 0;
+  P.sm_cs = 0;
+  if (csize <= 0) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  long long base = 0;
+  for (int l = P.first; l < P.coarsest; ++l) {
+    const Dims& d = P.L[l].op.d;
+    const int nlines = d.ny * (d.dim == 3 ? d.nz : 1);
+    P.sm_lines[l] = (nlines + csize - 1) / csize;
+    P.sm_rows[l] = P.sm_lines[l] * d.nx;
+    P.sm_base[l] = (int)base;
+    base += (long long)(nb + 1) * P.sm_rows[l];
+  }
+  const long long bytes = 16 * base;
+  if (bytes <= 0 || bytes > optin) return false;
+  if (!(nb == 27 ? tail_sm_fits<27>(csize, (int)bytes) : tail_sm_fits<9>(csize, (int)bytes))) return false;
+  P.sm_bytes = (int)bytes;
+  P.sm_cs = csize;
+  return true;
+}
+
+cudaError_t launch_vcycle_tail_sm(const TailParams& P, int nb, void* s) {
+  cudaLaunchAttribute attr[1];
+  count_launch();
+  if (nb == 27) {
+    cudaLaunchConfig_t cfg = tail_sm_config<27>(P.sm_cs, P.sm_bytes, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_vcycle_tail_sm<27>, P);
+  }
+  cudaLaunchConfig_t cfg = tail_sm_config<9>(P.sm_cs, P.sm_bytes, s, attr);
+  return cudaLaunchKernelEx(&cfg, k_vcycle_tail_sm<9>, P);
 }
 
 cudaError_t launch_vcycle_tail(const TailParams& P, int kind, int nb, int csize, void* s) {

@@ -100,11 +100,22 @@ struct TailParams {
   unsigned* bar;
   double* status;
   long long limit_ns;
+  // shared-memory form (k_vcycle_tail_sm, sm_bytes > 0): CTA r of the
+  // cluster's sm_cs keeps the stencil blocks and D^-1 of its x-lines
+  // L = r + sm_cs * i (i < sm_lines[l]) of every level below the coarsest,
+  // level l's blocks from float4 sm_base[l] on, block b of local row lr at
+  // sm_base[l] + b * sm_rows[l] + lr, D^-1 after the last block
+  int sm_bytes, sm_cs;
+  int sm_lines[RF_MAXL], sm_rows[RF_MAXL], sm_base[RF_MAXL];
   TailLevel L[RF_MAXL];
 };
 int tail_cluster_size(int kind, int nb);
 void fill_tail_masks(TailParams& P, int dim);
 cudaError_t launch_vcycle_tail(const TailParams& P, int kind, int nb, int csize, void* s);
+// the shared-memory form (FP32 levels, GS smoother): fills P.sm_* for cluster
+// size csize and returns true if it fits and can be co-scheduled
+bool tail_sm_plan(TailParams& P, int nb, int csize);
+cudaError_t launch_vcycle_tail_sm(const TailParams& P, int nb, void* s);
 // the same V-cycle as one cooperative launch of `blocks` blocks (coop_tail_blocks: all that fit at once)
 int coop_tail_blocks(int kind, int nb);
 cudaError_t launch_vcycle_coop(const TailParams& P, int kind, int nb, int blocks, void* s);

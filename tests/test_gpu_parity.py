@@ -404,21 +404,30 @@ def test_fp32_vcycle_matches_fp32_emulation(case, smoother):
     g.close()
 
 
-@pytest.mark.parametrize("mode", ["cluster", "coop"])
+def _tail_env(monkeypatch, mode):
+    """RF_TAIL_MODE / RF_TAIL_SMEM of a tail form: the cluster with the FP32
+    GS levels' matrices in shared memory (the default), the cluster reading
+    them from global memory, or the cooperative launch."""
+    monkeypatch.setenv("RF_TAIL_MODE", "coop" if mode == "coop" else "cluster")
+    monkeypatch.setenv("RF_TAIL_SMEM", "0" if mode == "cluster-global" else "1")
+
+
+@pytest.mark.parametrize("mode", ["cluster", "cluster-global", "coop"])
 @pytest.mark.parametrize("smoother", ["jacobi", "gs8"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", ["3d-17cube", "3d-lenses-33"])
+@pytest.mark.parametrize("case", ["3d-17cube", "3d-lenses-33", "2d-lens-33"])
 def test_vcycle_tail_matches_oracle(case, precision, smoother, mode, monkeypatch):
     """The one-launch execution of the small levels (RF_TAIL_NV; one
-    thread-block cluster, or a cooperative launch with bounded grid
-    barriers) computes the V-cycle of one launch per phase bit for bit (the
-    same device code per vertex, the coarsest solve summed in the coarse
-    kernel's order), and so the oracle's V-cycle."""
+    thread-block cluster, with the FP32 GS levels' matrices in its shared
+    memory or not, or a cooperative launch with bounded grid barriers)
+    computes the V-cycle of one launch per phase bit for bit (the same
+    arithmetic per vertex in the same order, the coarsest solve summed in
+    the coarse kernel's order), and so the oracle's V-cycle."""
     prob = CASES[case]()
     out = {}
     for tail in ("0", "100000"):
         monkeypatch.setenv("RF_TAIL_NV", tail)
-        monkeypatch.setenv("RF_TAIL_MODE", mode)
+        _tail_env(monkeypatch, mode)
         g, F, m, A, gm = _setup_both(prob, precision, smoother)
         b = np.random.default_rng(2).standard_normal(2 * g.nv)
         out[tail] = g.apply(rf.RF_OP_VCYCLE, 0, 1, b)
@@ -430,15 +439,15 @@ def test_vcycle_tail_matches_oracle(case, precision, smoother, mode, monkeypatch
         assert np.abs(x[a::2] - x_o[a::2]).max() <= tol * np.abs(x_o[a::2]).max(), a
 
 
-@pytest.mark.parametrize("mode", ["cluster", "coop"])
-@pytest.mark.parametrize("precision,smoother", [("fp32", "gs8"), ("fp64", "jacobi")])
+@pytest.mark.parametrize("mode", ["cluster", "cluster-global", "coop"])
+@pytest.mark.parametrize("precision,smoother", [("fp32", "gs8"), ("fp64", "jacobi"), ("fp16", "gs8")])
 def test_solve_with_one_launch_tail(precision, smoother, mode, monkeypatch):
     """Solves with the small levels in one launch, captured in the
     iteration's CUDA graph and replayed every iteration, are bitwise those of
     the launch-per-phase V-cycle."""
     prob = CASES["3d-lenses-33"]()
     out = {}
-    monkeypatch.setenv("RF_TAIL_MODE", mode)
+    _tail_env(monkeypatch, mode)
     for tail in ("0", "100000"):
         monkeypatch.setenv("RF_TAIL_NV", tail)
         g, F = _assembled(prob)
