@@ -951,28 +951,37 @@ __device__ __forceinline__ void vcycle_tail_body(const TailParams& P, int64_t gt
     const int rows = P.sm_rows[l];
     const float4* sA = sm + P.sm_base[l];
     const float* sD = reinterpret_cast<const float*>(sA + NB * rows);
-    for (int cc = 0; cc < ncol; ++cc) {
-      const int col = forward ? cc : ncol - 1 - cc;
-      const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
-      const int cnt = px ? nx / 2 : (nx + 1) / 2;
-      const uint32_t skip = (zero_start && forward) ? P.zmask[col] : 0u;
-      const int items = P.sm_lines[l] * cnt;
-      for (int t = threadIdx.x; t < items; t += blockDim.x) {
-        const int i = t / cnt, pos = t - i * cnt;
-        const int Ln = sm_line(rank, P.sm_cs, i);
-        if (Ln >= nlines) continue;
-        const int k = Ln / ny, j = Ln - k * ny;
-        if ((j & 1) != py || (k & 1) != pz) continue;
-        const int u = (px ? op.d.E : 0) + pos;
-        const int64_t p = (int64_t)Ln * nx + u;
-        const int lr = i * nx + u;
-        const float2 bv = ((const float2*)b)[p];
-        float s0, s1;
-        sm_row_sum<NB>(op, sA, rows, lr, p, px, (const float2*)x, true, skip, s0, s1);
-        const float r0 = bv.x - s0, r1 = bv.y - s1;   // coarse level: A_pq as stored
-        float y0, y1;
-        dinv_apply<float>(sD, lr, r0, r1, y0, y1);
-        ((float2*)x)[p] = make_float2(y0, y1);
+    // colour pairs (c, c ^ 1), as in k_gs_pair: the CTA owns whole x-lines,
+    // so the pair's second colour waits only for a block barrier and reads
+    // its same-line neighbours after it (plain loads); one cluster barrier
+    // per pair
+    for (int cc = 0; cc < ncol; cc += 2) {
+      const int c1 = forward ? cc : ncol - 1 - cc;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int col = h ? (c1 ^ 1) : c1;
+        const int px = col & 1, py = (col >> 1) & 1, pz = (col >> 2) & 1;
+        const int cnt = px ? nx / 2 : (nx + 1) / 2;
+        const uint32_t skip = (zero_start && forward) ? P.zmask[col] : 0u;
+        const int items = P.sm_lines[l] * cnt;
+        for (int t = threadIdx.x; t < items; t += blockDim.x) {
+          const int i = t / cnt, pos = t - i * cnt;
+          const int Ln = sm_line(rank, P.sm_cs, i);
+          if (Ln >= nlines) continue;
+          const int k = Ln / ny, j = Ln - k * ny;
+          if ((j & 1) != py || (k & 1) != pz) continue;
+          const int u = (px ? op.d.E : 0) + pos;
+          const int64_t p = (int64_t)Ln * nx + u;
+          const int lr = i * nx + u;
+          const float2 bv = ((const float2*)b)[p];
+          float s0, s1;
+          sm_row_sum<NB>(op, sA, rows, lr, p, px, (const float2*)x, true, skip, s0, s1);
+          const float r0 = bv.x - s0, r1 = bv.y - s1;   // coarse level: A_pq as stored
+          float y0, y1;
+          dinv_apply<float>(sD, lr, r0, r1, y0, y1);
+          ((float2*)x)[p] = make_float2(y0, y1);
+        }
+        if (h == 0) __syncthreads();
       }
       if (!sync()) return false;
     }
