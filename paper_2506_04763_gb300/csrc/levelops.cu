@@ -1291,10 +1291,13 @@ static cudaLaunchConfig_t tail_sm_config(int csize, int bytes, void* s, cudaLaun
   return cfg;
 }
 
+// The kernel's dynamic shared-memory cap is set to the device's opt-in
+// maximum, not to this plan's size: grids of different sizes share the
+// kernel, and each launch passes its own size.
 template <int NB>
-static bool tail_sm_fits(int csize, int bytes) {
+static bool tail_sm_fits(int csize, int bytes, int optin) {
   if (cudaFuncSetAttribute(k_vcycle_tail_sm<NB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
-      cudaFuncSetAttribute(k_vcycle_tail_sm<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+      cudaFuncSetAttribute(k_vcycle_tail_sm<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -1329,7 +1332,7 @@ bool tail_sm_plan(TailParams& P, int nb, int csize) {
   }
   const long long bytes = 16 * base;
   if (bytes <= 0 || bytes > optin) return false;
-  if (!(nb == 27 ? tail_sm_fits<27>(csize, (int)bytes) : tail_sm_fits<9>(csize, (int)bytes))) return false;
+  if (!(nb == 27 ? tail_sm_fits<27>(csize, (int)bytes, optin) : tail_sm_fits<9>(csize, (int)bytes, optin))) return false;
   P.sm_bytes = (int)bytes;
   P.sm_cs = csize;
   return true;

@@ -1024,3 +1024,30 @@ def test_host_buffers_pinned_pageable_and_device_agree():
         us[kind] = u.cpu().numpy() if kind == "device" else np.array(u, copy=True)
         g.close()
     assert np.array_equal(us["pageable"], us["pinned"]) and np.array_equal(us["pageable"], us["device"])
+
+
+def test_shared_memory_tails_of_grids_of_different_sizes():
+    """Grids whose one-launch tails keep different amounts of matrix data in
+    shared memory share the tail kernel: a solve on the larger grid after the
+    smaller grid's set-up (and the other way round) succeeds and repeats its
+    first result bit for bit."""
+    big = CASES["3d-lenses-33"]()        # tail from 17^3: ~169 KB per CTA
+    small = CASES["3d-17cube"]()         # tail from 9^3: ~24 KB per CTA
+    grids, res = {}, {}
+    for name, prob in (("big", big), ("small", small)):
+        g, F = _assembled(prob)
+        g.gmg_setup([1.0 / prob["H"]], rf.gmg_opts(_levels(prob), "gs8", precision="fp32"))
+        grids[name] = (g, torch.tensor(F, device="cuda"))
+    for rep in range(2):
+        for name in ("big", "small"):
+            g, b = grids[name]
+            x = torch.empty_like(b)
+            info = g.solve(0, b, x, rtol=1e-11, max_it=300)
+            torch.cuda.synchronize()
+            assert info["status"] == 0, (name, info)
+            if rep == 0:
+                res[name] = (x.cpu().numpy(), info["iterations"])
+            else:
+                assert np.array_equal(res[name][0], x.cpu().numpy()) and res[name][1] == info["iterations"]
+    for g, _ in grids.values():
+        g.close()
