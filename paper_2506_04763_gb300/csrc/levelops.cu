@@ -677,7 +677,8 @@ __device__ __forceinline__ void restrict_planes_body(const Dims& df, const Dims&
   if (t >= dc.nx * dc.ny) return;
   const int J = t / dc.nx, pos = t - J * dc.nx, K = blockIdx.y;
   const int I = pos < dc.E ? 2 * pos : 2 * (pos - dc.E) + 1;
-  const int64_t pc = ((int64_t)J + (int64_t)dc.ny * K) * dc.nx + pos;
+  // 32-bit vertex indices: a grid has at most 2^31 vertices (rf_grid_create)
+  const int pc = (J + dc.ny * K) * dc.nx + pos;
   const bool mc = dmc[pc] != 0;
   int xo[3];
   bool xin[3];
@@ -687,7 +688,7 @@ __device__ __forceinline__ void restrict_planes_body(const Dims& df, const Dims&
     xin[a] = fi >= 0 && fi < df.nx;
     xo[a] = (fi & 1) ? df.E + (fi >> 1) : (fi >> 1);
   }
-  int64_t lo[9];
+  int lo[9];
   bool lin[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c)
@@ -695,12 +696,12 @@ __device__ __forceinline__ void restrict_planes_body(const Dims& df, const Dims&
     for (int b = 0; b < 3; ++b) {
       const int fj = 2 * J + b - 1, fk = df.dim == 3 ? 2 * K + c - 1 : 0;
       lin[3 * c + b] = (df.dim == 3 || c == 1) && fj >= 0 && fj < df.ny && fk >= 0 && fk < df.nz;
-      lo[3 * c + b] = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx;
+      lo[3 * c + b] = lin[3 * c + b] ? (fj + df.ny * fk) * df.nx : 0;   // (no overflow outside the grid)
     }
   // every load is issued, without a branch, before the first sum: a value
   // outside the grid is read at the vertex's own fine position (always
   // inside) and then skipped, so the 27 loads are one memory round trip
-  const int64_t pf0 = lo[4] + xo[1];
+  const int pf0 = lo[4] + xo[1];
   V r[27];
   uint8_t m[27];
   bool in[27];
@@ -708,7 +709,7 @@ __device__ __forceinline__ void restrict_planes_body(const Dims& df, const Dims&
   for (int q = 0; q < 27; ++q) {
     const int a = q % 3, bc3 = q / 3;   // bc3 = 3 * (dz + 1) + (dy + 1)
     in[q] = lin[bc3] && xin[a];
-    const int64_t pf = in[q] ? lo[bc3] + xo[a] : pf0;
+    const int pf = in[q] ? lo[bc3] + xo[a] : pf0;
     r[q] = rf[pf];
     m[q] = dmf[pf];
   }
@@ -758,8 +759,9 @@ __device__ __forceinline__ void prolong_pairs_body(const Dims& df, const Dims& d
   const int J0 = fj >> 1, K0 = fk >> 1;
   const bool oy = (fj & 1) != 0, oz = df.dim == 3 && (fk & 1) != 0;
   const bool odd = 2 * I + 1 < df.nx;   // fine vertex 2I + 1 exists
-  const int64_t fline = ((int64_t)fj + (int64_t)df.ny * fk) * df.nx;
-  const int64_t pe = fline + I, po = fline + df.E + I;
+  // 32-bit vertex indices: a grid has at most 2^31 vertices (rf_grid_create)
+  const int fline = (fj + df.ny * fk) * df.nx;
+  const int pe = fline + I, po = fline + df.E + I;
   const int xo[2] = {(I & 1) ? dc.E + (I >> 1) : (I >> 1), ((I + 1) & 1) ? dc.E + ((I + 1) >> 1) : ((I + 1) >> 1)};
   V c8[8];
   uint8_t m[8];
@@ -768,7 +770,7 @@ __device__ __forceinline__ void prolong_pairs_body(const Dims& df, const Dims& d
   for (int q = 0; q < 8; ++q) {
     const int ib = q & 1, jb = (q >> 1) & 1, kb = (q >> 2) & 1;
     in[q] = (!jb || oy) && (!kb || oz) && (!ib || odd) && K0 + kb < dc.nz && J0 + jb < dc.ny && I + ib < dc.nx;
-    const int64_t pc = in[q] ? ((int64_t)(J0 + jb) + (int64_t)dc.ny * (K0 + kb)) * dc.nx + xo[ib] : 0;
+    const int pc = in[q] ? ((J0 + jb) + dc.ny * (K0 + kb)) * dc.nx + xo[ib] : 0;
     c8[q] = xc[pc];
     m[q] = dmc[pc];
   }
