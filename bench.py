@@ -50,10 +50,11 @@ GS_ALGO_PER_VERTEX = 456.0
 # flop), averaged over the two applications of an iteration.
 SPMV64_FLOP_PER_VERTEX = 216.0 + 4.0 + 6.0
 # FP64 instructions (DADD + DMUL + DFMA) per vertex of one K1 assembly with the
-# Jacobian, from one ncu capture of this recipe at 129^3 (231 per cycle over
-# 18.6 ms per assembly); K1 is FP64-issue-bound, so its roofline is that
-# instruction rate against the FMA issue rate rf_fp64_fma_rate measures.
-K1_FP64_INST_PER_VERTEX = 4150.0
+# Jacobian, counted by ncu (smsp__sass_thread_inst_executed_op_d{add,mul,fma})
+# over the 8 colour launches of one assembly of this recipe at 129^3; K1 is
+# FP64-issue-bound, so its roofline is that instruction rate against the FMA
+# issue rate rf_fp64_fma_rate measures.
+K1_FP64_INST_PER_VERTEX = 4154.0
 
 
 def args_():
